@@ -1,0 +1,430 @@
+#!/usr/bin/env python3
+"""THC-oo-K exchange-build benchmark (arXiv 2304.05505, Algorithm 2's K build).
+
+One step is one exchange build (S1 collocation, S2 point-space density, S3
+k-convolution, S4 back-projection, S5 energy) on the benzene-shaped cell:
+4 x 4 x 4 k, N_P = 1200 interpolation points, n = 60 occupied orbitals,
+N = 432 basis functions, with X and V already resident on the GPU.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is mixed-precision builds/s summed
+over ranks (each rank runs its own independent build: weak scaling, no
+collective on the data path).  The FP64 GPU build, per-stage times, the
+error against the FP64 CPU oracle, the end-to-end host-buffer number and the
+oracle's own CPU rate are reported beside it.  --impl reference times the
+FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "THC-oo-K exchange builds/s, mixed vs FP64 on one GB300 at <=1e-6 Ha; % roofline"
+WORKLOAD = ("benzene-shaped orthorhombic cell 13.9x17.8x12.9 bohr, 48 centres, N=432, n_occ=60, "
+            "4x4x4 k (N_k=64), N_ISDF=1200, 40^3 grid (config C2)")
+CONFIG = "C2"
+SAMPLE_FRACTION = 8      # the CPU oracle sample is 1/8 of a build
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-samples", type=int, default=4)
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error and CPU baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+
+def dist_setup(gpus: int):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(self.dev)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+
+def peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return dict(hbm_gbs=float(p["hbm_gbs"]), bf16_tflops=float(p["bf16_tflops"]),
+                    bf16_tflops_sustained=float(p.get("bf16_tflops_sustained", p["bf16_tflops"])),
+                    sm_max_mhz=float(p.get("sm_max_mhz", 2070.0)), source="measured")
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, sm_max_mhz=2070.0,
+                source="fallback")
+
+
+def stage_work(d: dict) -> dict:
+    """Algorithmic work of each stage of one build (complex MAC = 8 flops;
+    bytes are the arrays a stage must read and write once, complex64)."""
+    nk = d["n1"] * d["n2"] * d["n3"]
+    N, n, P = d["nbas"], d["nocc"], d["nisdf"]
+    c64 = 8
+    return {
+        "S1_collocate": dict(flops=8.0 * nk * P * n * N, bytes=c64 * nk * (N * P + P * n) + 16 * nk * N * n),
+        "S2_density": dict(flops=8.0 * nk * P * P * n, bytes=c64 * nk * (P * n + P * P)),
+        "S3_kconv": dict(flops=None, bytes=3.0 * c64 * nk * P * P),
+        "S4a_apply_M": dict(flops=8.0 * nk * P * P * n, bytes=c64 * nk * (P * P + 2 * P * n)),
+        "S4b_backproject": dict(flops=8.0 * nk * N * n * P, bytes=c64 * nk * (N * P + P * n) + 16 * nk * N * n),
+        "S5_energy": dict(flops=8.0 * nk * P * n, bytes=2.0 * c64 * nk * P * n),
+    }
+
+
+def kernel_roofline(stage: str, ms: float, work: dict, pk: dict, clocks: dict) -> dict:
+    w = work[stage]
+    traffic = measured_traffic(stage)
+    if w["flops"] is None or stage == "S5_energy":
+        achieved = w["bytes"] / (ms * 1e-3) / 1e9
+        peak = pk["hbm_gbs"]
+        return {"kernel": stage, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": pk["source"],
+                "algorithmic_bytes": w["bytes"], "ms": ms}
+    # CUDA-core FP32 GEMM: bound by the FP32 pipe.  Peak = 152 SMs x 128 lanes
+    # x 2 flop x the maximum SM clock (2070 MHz): 80.6 TFLOP/s.
+    peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    achieved = w["flops"] / (ms * 1e-3) / 1e12
+    return {"kernel": stage, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+            "algorithmic_flops": w["flops"], "ms": ms}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2304_05505_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(stage: str):
+    """DRAM bytes per launch from the committed ncu capture, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        t = json.load(open(path))
+    except Exception:
+        return None
+    if t.get("source_hash") != source_hash():
+        return None
+    v = t.get("per_launch_bytes", {}).get(stage)
+    return float(v) if v is not None else None
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_step(p, part: int):
+    """1/SAMPLE_FRACTION of one oracle build: steps 1, 2, 4 on a slice of the
+    k-points and step 3 (FFT route) on a slice of the P rows."""
+    from oracle import thc_oracle as O
+    nk = p.X.shape[0]
+    f = SAMPLE_FRACTION
+    ks = slice(part * nk // f, (part + 1) * nk // f)
+    Psi = O.collocate(p.X[ks], p.C[ks])
+    D = O.density(Psi)
+    P = p.V.shape[1]
+    rows = slice(part * P // f, (part + 1) * P // f)
+    Dfull = np.zeros((nk, P // f if P % f == 0 else rows.stop - rows.start, P), dtype=np.complex128)
+    Dfull[ks] = D[:, rows, :]
+    M = O.kconv_fft(Dfull, p.V[:, rows, :], p.cell.mesh)
+    Y = O.apply_M(np.ascontiguousarray(M[ks]), Psi)
+    O.backproject(np.ascontiguousarray(p.X[ks][:, :, rows]), Y)
+    return Y
+
+
+def cpu_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(int(i.get("num_threads", 1)) for i in info)
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def time_oracle(p, steps: int, warmup: int) -> dict:
+    for i in range(warmup):
+        oracle_sample_step(p, i % SAMPLE_FRACTION)
+    t = []
+    for i in range(steps):
+        t0 = time.perf_counter()
+        oracle_sample_step(p, i % SAMPLE_FRACTION)
+        t.append(time.perf_counter() - t0)
+    step_s = sum(t) / len(t)
+    return {"value": 1.0 / (step_s * SAMPLE_FRACTION), "unit": "builds/s", "cores": cpu_threads(),
+            "kind": "oracle", "step_s": step_s,
+            "sample": f"each step = 1/{SAMPLE_FRACTION} of one FP64 oracle build (steps 1, 2, 4 on "
+                      f"{{N_k/{SAMPLE_FRACTION}}} k-points, FFT-route step 3 on N_P/{SAMPLE_FRACTION} rows); "
+                      f"builds/s = 1 / ({SAMPLE_FRACTION} x mean step time); {steps} steps"}
+
+
+import numpy as np  # noqa: E402  (after sys.path set-up)
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_2304_05505_gb300 import cells
+    p = cells.make_problem(CONFIG)
+    steps = args.steps
+    warm = args.warmup
+    cb = time_oracle(p, steps, warm)
+    line = {"metric": METRIC, "value": cb["value"], "unit": "builds/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": cb["step_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (oracle/thc_oracle.py)"},
+            "impl": "reference",
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cb["value"], "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2304_05505_gb300 import cells, thc
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    if not os.path.exists(thc.LIB_PATH):
+        raise RuntimeError("libthc.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    thc.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p = cells.make_problem(CONFIG)
+    d = p.dims
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+
+    # --- mixed build, device-resident inputs -----------------------------
+    eb = thc.ExchangeBuild(d, "mixed", device=dev, stream=stream)
+    eb.set_collocation(p.X)
+    eb.set_kernel(p.V)
+    C = torch.from_numpy(p.C).to(dev)
+    KC = torch.empty(eb.kc_shape, dtype=torch.complex128, device=dev)
+    ex = torch.empty(2, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        eb.build(C, KC, ex)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = Clocks(dev.index)
+    clk.start()
+    time.sleep(0.3)
+    thc.thc_profile_begin(eb.ctx, args.steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0.record(stream)
+    for _ in range(args.steps):
+        eb.build(C, KC, ex)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    ms_total = max_over_ranks(world, e0.elapsed_time(e1))
+    stage_ms, nprof = thc.thc_profile_end(eb.ctx)
+    launches = thc.thc_launches_per_build(eb.ctx) * args.steps
+    KC_mixed = KC.cpu().numpy()
+    ex_mixed = ex.cpu().numpy().copy()
+    ms_per = ms_total / args.steps
+    value = world * args.steps / (ms_total * 1e-3)
+
+    # --- end to end through the host-buffer call ---------------------------
+    Ch = torch.from_numpy(p.C).pin_memory()
+    KCh = torch.empty(eb.kc_shape, dtype=torch.complex128).pin_memory()
+    exh = torch.empty(2, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        thc.thc_build_host(eb.ctx, Ch, KCh, exh)
+    ne2e = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(ne2e):
+        thc.thc_build_host(eb.ctx, Ch, KCh, exh)
+    t_e2e = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": world * ne2e / t_e2e, "unit": "builds/s",
+           "h2d_bytes_per_step": int(Ch.numel() * 16), "d2h_bytes_per_step": int(KCh.numel() * 16 + 16),
+           "steps": ne2e, "api": "thc_build_host (pinned host C in, KC and E_x out)"}
+    eb.close()
+    del eb
+    torch.cuda.empty_cache()
+
+    # --- FP64 GPU build -----------------------------------------------------
+    e64 = thc.ExchangeBuild(d, "fp64", device=dev, stream=stream)
+    e64.set_collocation(p.X)
+    e64.set_kernel(p.V)
+    e64.build(C, KC, ex)
+    torch.cuda.synchronize()
+    thc.thc_profile_begin(e64.ctx, args.fp64_steps)
+    e0.record(stream)
+    for _ in range(args.fp64_steps):
+        e64.build(C, KC, ex)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = max_over_ranks(world, e0.elapsed_time(e1)) / args.fp64_steps
+    st64, _ = thc.thc_profile_end(e64.ctx)
+    KC_64 = KC.cpu().numpy()
+    ex_64 = ex.cpu().numpy().copy()
+    e64.close()
+
+    if rank != 0:
+        return
+    pk = peaks()
+    work = stage_work(d)
+    names = thc.STAGES
+    stages = {nm: ms for nm, ms in zip(names, stage_ms)}
+    dominant = max(stages, key=stages.get)
+    roof = kernel_roofline(dominant, stages[dominant], work, pk, clocks)
+    per_stage = {nm: kernel_roofline(nm, stages[nm], work, pk, clocks) for nm in names}
+
+    line = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 operands, compensated sums, FP64 E_x)",
+                       "l2": "inputs larger than L2 (prepared kernel 737 MB, X 265 MB complex64)",
+                       "parallelism": f"{world} independent builds (one per GPU)"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "stages_ms": stages, "stage_roofline": {k: {"frac": v["frac"], "bound": v["bound"],
+                                                        "achieved": v["achieved"], "unit": v["unit"]}
+                                                    for k, v in per_stage.items()},
+            "fp64_gpu": {"value": world / (ms64 * 1e-3), "unit": "builds/s", "ms_per_step": ms64,
+                         "stages_ms": {nm: ms for nm, ms in zip(names, st64)}},
+            "Ex_mixed": float(ex_mixed[0]), "Ex_fp64_gpu": float(ex_64[0])}
+    if not args.no_oracle:
+        from oracle import thc_oracle as O
+        t0 = time.perf_counter()
+        ref = O.build(p.X, p.C, p.V, p.cell.mesh, route="fft")
+        t_full = time.perf_counter() - t0
+        line["accuracy_vs_oracle"] = {
+            "mixed": {"max_abs_dKC": float(np.abs(KC_mixed - ref["KC"]).max()),
+                      "abs_dEx": abs(float(ex_mixed[0]) - ref["Ex"])},
+            "fp64_gpu": {"max_abs_dKC": float(np.abs(KC_64 - ref["KC"]).max()),
+                         "abs_dEx": abs(float(ex_64[0]) - ref["Ex"])},
+            "Ex_oracle": ref["Ex"], "oracle_full_build_s": t_full}
+        cb = time_oracle(p, args.cpu_samples, 1)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,140 @@
+/*
+ * thc.h -- C ABI of the GB300 THC-oo-K exact-exchange build.
+ *
+ * One build is the per-SCF-iteration exchange step of THC-oo-K
+ * (Rettig, Lee, Head-Gordon, arXiv 2304.05505, Algorithm 2, the lines that
+ * form X^k_PQ by FFT convolution and K_ij):
+ *
+ *   S1  Psi^k[P,i] = sum_mu X^k[mu,P] C^k[mu,i]        orbitals at the points
+ *                                                      (u^k_i(r_P) of Eq. thcoccrik)
+ *   S2  D^k[P,Q]   = sum_i Psi^k[P,i] conj(Psi^k[Q,i]) point-space density
+ *   S3  M^k[P,Q]   = sum_k' D^k'[P,Q] V^(k'-k)[P,Q]     k-convolution (Sec. 2.2:
+ *                                                      done as DFT over the mesh,
+ *                                                      Hadamard product, inverse DFT)
+ *   S4  (KC)^k     = conj(X^k) (M^k Psi^k)             K^k C^k, K^k = conj(X) M X^T
+ *   S5  E_x        = -(1/N_k) sum_k sum_{P,i} conj(Psi^k[P,i]) (M^k Psi^k)[P,i]
+ *                                                      (Eq. thcoccrik, closed shell,
+ *                                                      per cell)
+ *
+ * Conventions.
+ *  - Complex numbers are interleaved (re, im) doubles, i.e. C99 double _Complex
+ *    / numpy complex128.  Arrays are dense and row-major with k slowest.
+ *  - k and q share one index on the Gamma-centred n1 x n2 x n3 mesh:
+ *    k = (a1 * n2 + a2) * n3 + a3 for k = sum_a (a_a / n_a) b_a.
+ *    q = k' - k (Sec. 2.2) is wrapped onto the mesh.
+ *  - X^k[mu,P] is the Bloch basis at the points with its Bloch phase,
+ *    normalised per cell (no 1/sqrt(N_k)).  V^q[P,Q] is the ISDF Coulomb
+ *    kernel M^q_PQ of Sec. 2.2 times exp(-i q.(r_P - r_Q)) and carries the
+ *    1/N_k of the k sum.  The library only needs V^q Hermitian in (P,Q).
+ *  - Pointers named *_host are host memory; every other pointer is device
+ *    memory on the context's device.  Device pointers must be 16-byte aligned.
+ *  - The caller owns every buffer it passes.  The library owns its context,
+ *    its copies of X and of the prepared kernel, and its workspace; it never
+ *    keeps a caller pointer past the call.
+ *  - Device work is queued on the context's stream.  thc_build returns as
+ *    soon as its work is queued; thc_build_host returns when the results
+ *    are in host memory.
+ *  - No call throws.  Every call returns a thc_status.  On THC_ERR_CUDA the
+ *    CUDA error string is kept and thc_last_error() returns it.
+ *  - Calls on one context are not thread-safe.  Contexts are independent.
+ */
+#ifndef THC_H
+#define THC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  THC_OK = 0,
+  THC_ERR_ARG = 1,         /* bad dimension, null or misaligned pointer, bad enum */
+  THC_ERR_OOM = 2,         /* device allocation failed; nothing leaked */
+  THC_ERR_CUDA = 3,        /* a CUDA call failed; see thc_last_error() */
+  THC_ERR_NONFINITE = 4,   /* a NaN or Inf in an input checked by the call */
+  THC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  THC_ERR_STATE = 6,       /* call order: build before set_collocation/set_kernel */
+  THC_ERR_UNSUPPORTED = 7  /* valid request this build of the library cannot run */
+} thc_status;
+
+typedef enum {
+  THC_FP64 = 0,            /* every step in FP64 on CUDA cores */
+  THC_MIXED = 1            /* S1, S4 with FP32-precision operands and compensated
+                              accumulation; S2, S3 in FP32; E_x summed in FP64 */
+} thc_precision;
+
+typedef struct {
+  int n1, n2, n3;          /* k mesh, each >= 1 and <= 8 */
+  int nbas;                /* N, basis functions, >= 1 */
+  int nocc;                /* n, occupied orbitals, >= 1 */
+  int nisdf;               /* N_P, interpolation points, >= 1 */
+} thc_dims;
+
+typedef struct thc_ctx thc_ctx;
+
+/* Create a context on the current CUDA device.  `stream` is a cudaStream_t
+ * (NULL = legacy default stream).  Allocates the context's device memory
+ * (thc_memory_bytes tells how much) up front.  *ctx is NULL on failure. */
+thc_status thc_create(thc_ctx** ctx, const thc_dims* dims, int precision, void* stream);
+
+/* Device bytes the context holds (X copy, prepared kernel, workspace). */
+thc_status thc_memory_bytes(const thc_dims* dims, int precision, size_t* bytes);
+
+/* X: device, [N_k][nbas][nisdf] complex128.  Copied (and converted for
+ * THC_MIXED) into the context; checked for NaN/Inf (THC_ERR_NONFINITE).
+ * Synchronises the context's stream. */
+thc_status thc_set_collocation(thc_ctx* ctx, const double* X);
+
+/* V: device, [N_k][nisdf][nisdf] complex128, V[q] for q on the mesh index.
+ * Prepares the DFT of V over the mesh, Vcheck[a] = (1/N_k) sum_q V[q] w^{+a.q}
+ * (w = exp(2 pi i / n) per axis), in FP64, and keeps it (complex64 for
+ * THC_MIXED).  Checked for NaN/Inf.  Synchronises the context's stream. */
+thc_status thc_set_kernel(thc_ctx* ctx, const double* V);
+
+/* One build.  C: device [N_k][nbas][nocc] complex128 (read only).
+ * KC: device [N_k][nbas][nocc] complex128 (written; must not alias C).
+ * ex: device, 2 doubles: ex[0] = E_x (Hartree per cell), ex[1] = the
+ * imaginary part of the S5 sum (a residual, zero for Hermitian V).
+ * Asynchronous on the context's stream. */
+thc_status thc_build(thc_ctx* ctx, const double* C, double* KC, double* ex);
+
+/* The same build from and to host memory: copies C_host in, runs the build,
+ * copies KC and E_x out, and waits for the stream.  Host buffers should be
+ * pinned for full copy bandwidth (pageable memory works, more slowly).
+ * ex_host: 2 doubles as in thc_build. */
+thc_status thc_build_host(thc_ctx* ctx, const double* C_host, double* KC_host, double* ex_host);
+
+/* Intermediates of the last build, copied to device buffers the caller owns
+ * (for tests).  which: 0 = Psi [N_k][nisdf][nocc], 1 = D [N_k][nisdf][nisdf],
+ * 2 = M [N_k][nisdf][nisdf], 3 = Y = M Psi [N_k][nisdf][nocc].  Written as
+ * complex128 whatever the precision.  Synchronises the stream. */
+thc_status thc_get_intermediate(thc_ctx* ctx, int which, double* out);
+
+/* Per-stage device time of the last build in milliseconds (CUDA events on
+ * the context's stream; 0 until a build ran).  stage_ms[0..5] = S1, S2, S3,
+ * S4a, S4b, S5.  Synchronises the stream. */
+thc_status thc_stage_times(thc_ctx* ctx, float stage_ms[6]);
+
+/* Stage timing over many builds.  After thc_profile_begin(ctx, max_builds)
+ * each thc_build records CUDA events around its stages on the context's
+ * stream into a slot of its own, for up to max_builds builds (1..4096).
+ * thc_profile_end waits for those events, writes the mean device time per
+ * build of each stage in milliseconds (mean_ms[0..5] = S1, S2, S3, S4a, S4b,
+ * S5) and the number of builds recorded, and stops recording. */
+thc_status thc_profile_begin(thc_ctx* ctx, int max_builds);
+thc_status thc_profile_end(thc_ctx* ctx, float mean_ms[6], int* nbuilds);
+
+/* Number of kernel launches one thc_build makes. */
+thc_status thc_launches_per_build(const thc_ctx* ctx, int* launches);
+
+thc_status thc_destroy(thc_ctx* ctx);
+
+const char* thc_status_string(thc_status s);
+const char* thc_last_error(const thc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* THC_H */

@@ -402,26 +402,55 @@ def promolecular_density(cell: Cell, points: np.ndarray, beta: float = 1.0) -> n
     return rho
 
 
-def sample_points(cell: Cell, npoints: int | None = None, seed: int | None = None) -> np.ndarray:
-    """Interpolation points drawn without replacement from the quadrature grid
-    with probability proportional to a promolecular density plus a floor.
+def _inclusion_probabilities(p: np.ndarray, n: int) -> np.ndarray:
+    """pi_i = min(1, c p_i) with sum_i pi_i = n (c by bisection)."""
+    lo, hi = 0.0, float(n) / p.min()
+    for _ in range(200):
+        c = 0.5 * (lo + hi)
+        s = np.minimum(1.0, c * p).sum()
+        if s < n:
+            lo = c
+        else:
+            hi = c
+    return np.minimum(1.0, hi * p)
+
+
+def sample_points(cell: Cell, npoints: int | None = None, seed: int | None = None):
+    """Interpolation points drawn from the quadrature grid with inclusion
+    probabilities proportional to a promolecular density plus a floor.
 
     A stand-in for the paper's point selection (CVT k-means or QRCP) on cells
-    too large for a CPU pivoted Cholesky.  Returns grid indices (C order over
-    the full grid) sorted ascending."""
+    too large for a CPU pivoted Cholesky.  Returns (full-grid indices sorted
+    ascending, quadrature weight of each point).  The weight is the grid
+    volume element divided by the point's inclusion probability (the
+    Horvitz-Thompson weight), so the weights sum to about Omega."""
     npoints = cell.nisdf if npoints is None else npoints
     rng = np.random.default_rng((cell.seed if seed is None else seed) + 17)
     s = cell.quad_stride
     pts = grid_points(cell, s)
+    ngq = pts.shape[0]
     rho = promolecular_density(cell, pts)
     p = rho + 0.05 * rho.mean()
     p /= p.sum()
-    sel = rng.choice(pts.shape[0], size=npoints, replace=False, p=p)
-    # map strided index back to the full grid index
+    pi = _inclusion_probabilities(p, npoints)
+    # systematic sampling in a random order gives exactly npoints with
+    # inclusion probabilities pi
+    order = rng.permutation(ngq)
+    cum = np.cumsum(pi[order])
+    u = rng.uniform(0.0, 1.0)
+    hits = np.searchsorted(cum, u + np.arange(npoints), side="right")
+    sel = order[np.clip(hits, 0, ngq - 1)]
+    sel = np.unique(sel)
+    if sel.size < npoints:                      # rounding at the ends
+        rest = np.setdiff1d(np.argsort(-pi), sel, assume_unique=False)[: npoints - sel.size]
+        sel = np.union1d(sel, rest)
+    sel = sel[:npoints]
     q = tuple(g // s for g in cell.grid)
     i, j, k = np.unravel_index(sel, q)
     full = np.ravel_multi_index((i * s, j * s, k * s), cell.grid)
-    return np.sort(full)
+    order = np.argsort(full)
+    weight = (cell.volume / ngq) / pi[sel]
+    return full[order], weight[order]
 
 
 def points_from_indices(cell: Cell, idx: np.ndarray) -> np.ndarray:
@@ -446,16 +475,21 @@ def _coset_vectors(cell: Cell, qfrac: np.ndarray, kmax: float) -> np.ndarray:
     return K[keep]
 
 
-def model_kernel(cell: Cell, points: np.ndarray, smear: float = MODEL_SMEAR) -> np.ndarray:
-    """V^q[P, Q] = Omega/(N_k N_P^2) sum_K 4 pi/|K|^2 exp(-|K|^2/(2a)) exp(-i K.(r_P - r_Q)).
+def model_kernel(cell: Cell, points: np.ndarray, weights: np.ndarray | None = None,
+                 smear: float = MODEL_SMEAR) -> np.ndarray:
+    """V^q[P, Q] = w_P w_Q / (N_k Omega) sum_K 4 pi/|K|^2 exp(-|K|^2/(2a)) exp(-i K.(r_P - r_Q)).
 
+    The interpolation vector of point P is w_P times a unit Gaussian of
+    exponent a centred at r_P (w_P = Omega / N_P when no weights are given).
     K runs over the coset q + G inside a sphere, K = 0 excluded.  Shape
     (Nk, N_P, N_P) c128, q on the same mesh index as k."""
     kf = kmesh_frac(cell.mesh)
     mk = minus_k_index(cell.mesh)
     nk, npnt = kf.shape[0], points.shape[0]
     kmax = math.sqrt(2 * smear * MODEL_LOG_CUT)
-    pref = cell.volume / (nk * npnt * npnt)
+    if weights is None:
+        weights = np.full(npnt, cell.volume / npnt)
+    pref = 1.0 / (nk * cell.volume)
     V = np.zeros((nk, npnt, npnt), dtype=np.complex128)
     done = np.zeros(nk, dtype=bool)
     for q in range(nk):
@@ -464,7 +498,7 @@ def model_kernel(cell: Cell, points: np.ndarray, smear: float = MODEL_SMEAR) -> 
         K = _coset_vectors(cell, kf[q], kmax)
         K2 = np.einsum("gi,gi->g", K, K)
         w = pref * 4 * np.pi / K2 * np.exp(-K2 / (2 * smear))
-        A = np.exp(-1j * (points @ K.T)) * np.sqrt(w)[None, :]
+        A = np.exp(-1j * (points @ K.T)) * np.sqrt(w)[None, :] * weights[:, None]
         Vq = A @ A.conj().T
         Vq = 0.5 * (Vq + Vq.conj().T)
         if mk[q] == q:
@@ -486,6 +520,7 @@ class Problem:
     cell: Cell
     points: np.ndarray        # (N_P, 3) cartesian
     point_index: np.ndarray   # (N_P,) full-grid indices
+    weights: np.ndarray       # (N_P,) quadrature weight of each point
     X: np.ndarray             # (Nk, N, N_P) c128
     C: np.ndarray             # (Nk, N, n) c128
     V: np.ndarray             # (Nk, N_P, N_P) c128
@@ -510,21 +545,21 @@ def make_problem(name: str = "C0", seed: int | None = None, cache: bool = True, 
     if cdir:
         tag = "_".join([name, str(seed)] + [f"{k}{v}" for k, v in sorted(over.items())])
         tag = tag.replace(" ", "").replace("(", "").replace(")", "").replace(",", "x")
-        path = os.path.join(cdir, f"problem_v1_{tag}.npz")
+        path = os.path.join(cdir, f"problem_v2_{tag}.npz")
     cell = make_cell(name, seed, **over)
     if path and os.path.exists(path):
         z = np.load(path)
-        prob = Problem(cell, z["points"], z["point_index"], z["X"], z["C"], z["V"])
+        prob = Problem(cell, z["points"], z["point_index"], z["weights"], z["X"], z["C"], z["V"])
     else:
-        idx = sample_points(cell)
+        idx, wts = sample_points(cell)
         pts = points_from_indices(cell, idx)
         X = bloch_collocation(cell, pts, kmesh_frac(cell.mesh))
         C = occupied_coefficients(cell)
-        V = model_kernel(cell, pts)
-        prob = Problem(cell, pts, idx, X, C, V)
+        V = model_kernel(cell, pts, wts)
+        prob = Problem(cell, pts, idx, wts, X, C, V)
         if path:
             os.makedirs(cdir, exist_ok=True)
-            np.savez(path, points=pts, point_index=idx, X=X, C=C, V=V)
+            np.savez(path, points=pts, point_index=idx, weights=wts, X=X, C=C, V=V)
     if cache:
         _MEMO[key] = prob
     return prob

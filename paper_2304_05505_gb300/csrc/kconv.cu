@@ -1,0 +1,255 @@
+// The k-mesh convolution of the build, step S3 (Sec. 2.2: the sum over q of
+// M^q against the occupied products is a convolution in k space, done by FFT
+// in O(N_k log N_k)):
+//
+//   M^k[P,Q] = sum_{k'} D^{k'}[P,Q] V^{k'-k}[P,Q]
+//            = sum_a w^{+a.k} ( sum_{k'} w^{-a.k'} D^{k'}[P,Q] ) Vh^a[P,Q]
+//   Vh^a[P,Q] = (1/N_k) sum_q w^{+a.q} V^q[P,Q]           (prepare_kernel)
+//
+// with w = exp(2 pi i / n) per mesh axis.  Every (P,Q) element is independent:
+// one thread owns one element, keeps its N_k values in shared memory (column
+// layout [k][thread], conflict-free), runs the separable 3-D DFT axis by axis
+// with radix-2/3/4 butterflies or a direct DFT for other lengths, multiplies by
+// Vh and transforms back.  Loads and stores of D, Vh and M are coalesced
+// across the threads of a block (consecutive elements).  The stage is bound by
+// HBM: 3 N_k complex values move per element against ~6 N_k L flops.
+//
+// FP32 form: a 2- or 4-point DFT has twiddles 1, -1, +-i and is exact up to the
+// additions; the only irrational twiddles (sqrt(3)/2 for lengths 3 and 6, the
+// table for lengths 5, 7, 8) are applied as an FP32 hi + lo pair so that the
+// forward and inverse transforms do not pick up a systematic scale error.
+#include "thc_internal.cuh"
+
+#include <math.h>
+
+namespace {
+
+constexpr int MAXL = 8;
+
+struct Twiddles {
+  int n[3];
+  double c[3][MAXL], s[3][MAXL];      // cos, sin of 2 pi r / n_ax
+  float ch[3][MAXL], cl[3][MAXL];     // FP32 hi/lo split of c
+  float sh[3][MAXL], sl[3][MAXL];
+};
+
+template <typename R> struct Tw;
+template <> struct Tw<double> {
+  __device__ static double2 mul(double2 v, const Twiddles& t, int ax, int r, int sign) {
+    double c = t.c[ax][r], s = sign * t.s[ax][r];
+    return make_double2(v.x * c - v.y * s, v.x * s + v.y * c);
+  }
+  __device__ static double2 mul_s3(double2 d, int sign) {
+    // i * sign * sqrt(3)/2 * d
+    const double h = 0.86602540378443864676;
+    return make_double2(-sign * h * d.y, sign * h * d.x);
+  }
+};
+template <> struct Tw<float> {
+  __device__ static float2 mul(float2 v, const Twiddles& t, int ax, int r, int sign) {
+    float ch = t.ch[ax][r], cl = t.cl[ax][r];
+    float sh = sign * t.sh[ax][r], sl = sign * t.sl[ax][r];
+    float re = fmaf(v.x, ch, -v.y * sh) + (v.x * cl - v.y * sl);
+    float im = fmaf(v.x, sh, v.y * ch) + (v.x * sl + v.y * cl);
+    return make_float2(re, im);
+  }
+  __device__ static float2 mul_s3(float2 d, int sign) {
+    const float hh = 0.866025388240814208984375f;       // float(sqrt(3)/2)
+    const float hl = 1.5543625e-8f;                     // sqrt(3)/2 - hh
+    float re = -(d.y * hh + d.y * hl);
+    float im = d.x * hh + d.x * hl;
+    return make_float2(sign * re, sign * im);
+  }
+};
+
+template <typename R, int L>
+__device__ __forceinline__ void line_dft(typename cplx<R>::type* x, int step, const Twiddles& tw,
+                                         int ax, int sign) {
+  typedef typename cplx<R>::type CT;
+  CT v[L];
+#pragma unroll
+  for (int j = 0; j < L; j++) v[j] = x[j * step];
+  if constexpr (L == 2) {
+    x[0] = cadd(v[0], v[1]);
+    x[step] = csub(v[0], v[1]);
+  } else if constexpr (L == 3) {
+    CT t = cadd(v[1], v[2]);
+    CT d = csub(v[1], v[2]);
+    CT m = CT{v[0].x - (R)0.5 * t.x, v[0].y - (R)0.5 * t.y};
+    CT s = Tw<R>::mul_s3(d, sign);
+    x[0] = cadd(v[0], t);
+    x[step] = cadd(m, s);
+    x[2 * step] = csub(m, s);
+  } else if constexpr (L == 4) {
+    CT a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+    CT b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
+    CT ib1 = CT{-sign * b1.y, sign * b1.x};   // i * sign * b1
+    x[0] = cadd(a0, b0);
+    x[2 * step] = csub(a0, b0);
+    x[step] = cadd(a1, ib1);
+    x[3 * step] = csub(a1, ib1);
+  } else {
+#pragma unroll
+    for (int m = 0; m < L; m++) {
+      CT acc = v[0];
+#pragma unroll
+      for (int j = 1; j < L; j++) acc = cadd(acc, Tw<R>::mul(v[j], tw, ax, (j * m) % L, sign));
+      x[m * step] = acc;
+    }
+  }
+}
+
+template <typename R>
+__device__ void dft_axis(typename cplx<R>::type* x, int T, const Twiddles& tw, int ax, int sign) {
+  const int n1 = tw.n[0], n2 = tw.n[1], n3 = tw.n[2];
+  const int L = tw.n[ax];
+  if (L == 1) return;
+  int nout, sout, nin, sin_, step;
+  if (ax == 0) { nout = n2; sout = n3; nin = n3; sin_ = 1; step = n2 * n3; }
+  else if (ax == 1) { nout = n1; sout = n2 * n3; nin = n3; sin_ = 1; step = n3; }
+  else { nout = n1; sout = n2 * n3; nin = n2; sin_ = n3; step = 1; }
+  for (int o = 0; o < nout; o++)
+    for (int i = 0; i < nin; i++) {
+      typename cplx<R>::type* base = x + (long)(o * sout + i * sin_) * T;
+      const int st = step * T;
+      switch (L) {
+        case 2: line_dft<R, 2>(base, st, tw, ax, sign); break;
+        case 3: line_dft<R, 3>(base, st, tw, ax, sign); break;
+        case 4: line_dft<R, 4>(base, st, tw, ax, sign); break;
+        case 5: line_dft<R, 5>(base, st, tw, ax, sign); break;
+        case 6: line_dft<R, 6>(base, st, tw, ax, sign); break;
+        case 7: line_dft<R, 7>(base, st, tw, ax, sign); break;
+        default: line_dft<R, 8>(base, st, tw, ax, sign); break;
+      }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void dft3(typename cplx<R>::type* x, int T, const Twiddles& tw, int sign) {
+  dft_axis<R>(x, T, tw, 0, sign);
+  dft_axis<R>(x, T, tw, 1, sign);
+  dft_axis<R>(x, T, tw, 2, sign);
+}
+
+// M = IDFT(DFT(D) o Vh), one element per thread.
+template <typename R>
+__global__ void kconv_kernel(const typename cplx<R>::type* __restrict__ D,
+                             const typename cplx<R>::type* __restrict__ Vh,
+                             typename cplx<R>::type* __restrict__ M, long npq, Twiddles tw) {
+  typedef typename cplx<R>::type CT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CT* buf = reinterpret_cast<CT*>(smem_raw);
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int nk = tw.n[0] * tw.n[1] * tw.n[2];
+  const long e = (long)blockIdx.x * T + tid;
+  const bool ok = e < npq;
+  CT* x = buf + tid;
+  for (int k = 0; k < nk; k++) x[(long)k * T] = ok ? D[(long)k * npq + e] : CT{(R)0, (R)0};
+  dft3<R>(x, T, tw, -1);
+  for (int a = 0; a < nk; a++) {
+    CT v = ok ? Vh[(long)a * npq + e] : CT{(R)0, (R)0};
+    x[(long)a * T] = cmul(x[(long)a * T], v);
+  }
+  dft3<R>(x, T, tw, +1);
+  if (ok)
+    for (int k = 0; k < nk; k++) M[(long)k * npq + e] = x[(long)k * T];
+}
+
+// Vh[a] = (1/N_k) sum_q w^{+a.q} V[q], FP64; stored FP64 and/or FP32.
+__global__ void prepare_kernel(const double2* __restrict__ V, double2* __restrict__ Vh64,
+                               float2* __restrict__ Vh32, long npq, Twiddles tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* buf = reinterpret_cast<double2*>(smem_raw);
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int nk = tw.n[0] * tw.n[1] * tw.n[2];
+  const long e = (long)blockIdx.x * T + tid;
+  const bool ok = e < npq;
+  double2* x = buf + tid;
+  for (int k = 0; k < nk; k++) x[(long)k * T] = ok ? V[(long)k * npq + e] : make_double2(0, 0);
+  dft3<double>(x, T, tw, +1);
+  if (!ok) return;
+  const double sc = 1.0 / nk;
+  for (int a = 0; a < nk; a++) {
+    double2 v = x[(long)a * T];
+    v.x *= sc;
+    v.y *= sc;
+    if (Vh64) Vh64[(long)a * npq + e] = v;
+    if (Vh32) Vh32[(long)a * npq + e] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+Twiddles make_twiddles(int n1, int n2, int n3) {
+  Twiddles t;
+  t.n[0] = n1; t.n[1] = n2; t.n[2] = n3;
+  for (int ax = 0; ax < 3; ax++)
+    for (int r = 0; r < MAXL; r++) {
+      int L = t.n[ax];
+      double c = 1.0, s = 0.0;
+      if (r < L && L > 0) {
+        // exact values at multiples of pi/2
+        if ((4 * r) % L == 0) {
+          int q = (4 * r) / L;   // quarter turns
+          c = (q == 0) ? 1.0 : (q == 2) ? -1.0 : 0.0;
+          s = (q == 1) ? 1.0 : (q == 3) ? -1.0 : 0.0;
+        } else {
+          c = cos(2.0 * M_PI * r / L);
+          s = sin(2.0 * M_PI * r / L);
+        }
+      }
+      t.c[ax][r] = c;
+      t.s[ax][r] = s;
+      t.ch[ax][r] = (float)c;
+      t.cl[ax][r] = (float)(c - (double)t.ch[ax][r]);
+      t.sh[ax][r] = (float)s;
+      t.sl[ax][r] = (float)(s - (double)t.sh[ax][r]);
+    }
+  return t;
+}
+
+int pick_threads(int nk, size_t elem) {
+  const size_t budget = 100 * 1024;
+  int T = 256;
+  while (T > 32 && (size_t)T * nk * elem > budget) T /= 2;
+  return T;
+}
+
+template <typename R>
+cudaError_t kconv_launch(const typename cplx<R>::type* D, const typename cplx<R>::type* Vh,
+                         typename cplx<R>::type* M, long npq, int n1, int n2, int n3,
+                         cudaStream_t s) {
+  const int nk = n1 * n2 * n3;
+  const size_t el = sizeof(typename cplx<R>::type);
+  const int T = pick_threads(nk, el);
+  const size_t sm = (size_t)T * nk * el;
+  cudaError_t e = cudaFuncSetAttribute(kconv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  const long blocks = (npq + T - 1) / T;
+  kconv_kernel<R><<<(unsigned)blocks, T, sm, s>>>(D, Vh, M, npq, make_twiddles(n1, n2, n3));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t kconv_z(const double2* D, const double2* Vh, double2* M, long npq, int n1, int n2,
+                    int n3, cudaStream_t s) {
+  return kconv_launch<double>(D, Vh, M, npq, n1, n2, n3, s);
+}
+
+cudaError_t kconv_c(const float2* D, const float2* Vh, float2* M, long npq, int n1, int n2,
+                    int n3, cudaStream_t s) {
+  return kconv_launch<float>(D, Vh, M, npq, n1, n2, n3, s);
+}
+
+cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long npq, int n1,
+                             int n2, int n3, cudaStream_t s) {
+  const int nk = n1 * n2 * n3;
+  const int T = pick_threads(nk, sizeof(double2));
+  const size_t sm = (size_t)T * nk * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(prepare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  const long blocks = (npq + T - 1) / T;
+  prepare_kernel<<<(unsigned)blocks, T, sm, s>>>(V, Vh64, Vh32, npq, make_twiddles(n1, n2, n3));
+  return cudaGetLastError();
+}

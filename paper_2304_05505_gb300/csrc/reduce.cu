@@ -1,0 +1,137 @@
+// Step S5, the exchange energy (Eq. thcoccrik):
+//   E_x = -(1/N_k) sum_k sum_{P,i} conj(Psi^k[P,i]) Y^k[P,i],  Y = M Psi,
+// plus element-wise conversions and the finite-value check of the inputs.
+//
+// The sum is deterministic: a fixed grid of blocks writes one FP64 partial per
+// block, and a single block adds the partials in a fixed order.  In the mixed
+// form each product is formed in FP32 and a thread's products are summed in a
+// float-float (two-sum) pair, which is carried into FP64 before any sum across
+// threads; every sum across threads and blocks is FP64.
+#include "thc_internal.cuh"
+
+namespace {
+
+constexpr int RT = 256;
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += sh[i];
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(RT) ex_partial_z(const double2* __restrict__ Psi,
+                                                    const double2* __restrict__ Y, long n,
+                                                    double* __restrict__ partial) {
+  __shared__ double sh[RT / 32];
+  double re = 0.0, im = 0.0;
+  for (long i = (long)blockIdx.x * RT + threadIdx.x; i < n; i += (long)gridDim.x * RT) {
+    double2 p = Psi[i], y = Y[i];
+    re += p.x * y.x + p.y * y.y;
+    im += p.x * y.y - p.y * y.x;
+  }
+  re = block_sum(re, sh);
+  im = block_sum(im, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = re;
+    partial[2 * blockIdx.x + 1] = im;
+  }
+}
+
+__global__ void __launch_bounds__(RT) ex_partial_c(const float2* __restrict__ Psi,
+                                                    const float2* __restrict__ Y, long n,
+                                                    double* __restrict__ partial) {
+  __shared__ double sh[RT / 32];
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  for (long i = (long)blockIdx.x * RT + threadIdx.x; i < n; i += (long)gridDim.x * RT) {
+    float2 p = Psi[i], y = Y[i];
+    float re = fmaf(p.x, y.x, p.y * y.y);
+    float im = fmaf(p.x, y.y, -p.y * y.x);
+    float s, e;
+    two_sum(rh, re, s, e); rh = s; rl += e;
+    two_sum(ih, im, s, e); ih = s; il += e;
+  }
+  double re = block_sum((double)rh + (double)rl, sh);
+  double im = block_sum((double)ih + (double)il, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = re;
+    partial[2 * blockIdx.x + 1] = im;
+  }
+}
+
+__global__ void ex_final(const double* __restrict__ partial, int np, int nk, double* ex) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double re = 0.0, im = 0.0;
+  for (int i = 0; i < np; i++) {
+    re += partial[2 * i];
+    im += partial[2 * i + 1];
+  }
+  ex[0] = -re / nk;
+  ex[1] = -im / nk;
+}
+
+__global__ void z2c_kernel(const double2* __restrict__ in, float2* __restrict__ out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+__global__ void c2z_kernel(const float2* __restrict__ in, double2* __restrict__ out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+
+__global__ void finite_kernel(const double2* __restrict__ in, long n, int* flag) {
+  int bad = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    bad |= !(isfinite(in[i].x) && isfinite(in[i].y));
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+unsigned grid_for(long n, int t) {
+  long b = (n + t - 1) / t;
+  if (b > 152L * 16) b = 152L * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t ex_reduce_z(const double2* Psi, const double2* Y, long n, int nk, double* partial,
+                        int npartial, double* ex, cudaStream_t s) {
+  ex_partial_z<<<npartial, RT, 0, s>>>(Psi, Y, n, partial);
+  ex_final<<<1, 32, 0, s>>>(partial, npartial, nk, ex);
+  return cudaGetLastError();
+}
+
+cudaError_t ex_reduce_c(const float2* Psi, const float2* Y, long n, int nk, double* partial,
+                        int npartial, double* ex, cudaStream_t s) {
+  ex_partial_c<<<npartial, RT, 0, s>>>(Psi, Y, n, partial);
+  ex_final<<<1, 32, 0, s>>>(partial, npartial, nk, ex);
+  return cudaGetLastError();
+}
+
+cudaError_t convert_z2c(const double2* in, float2* out, long n, cudaStream_t s) {
+  z2c_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t convert_c2z(const float2* in, double2* out, long n, cudaStream_t s) {
+  c2z_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t check_finite_z(const double2* in, long n, int* flag, cudaStream_t s) {
+  finite_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, n, flag);
+  return cudaGetLastError();
+}

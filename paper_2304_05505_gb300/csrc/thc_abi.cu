@@ -1,0 +1,382 @@
+// C ABI of the THC-oo-K exchange build (declared in include/thc.h).
+//
+// Owns the context: the copy of the collocation X, the prepared kernel
+// Vh = DFT_q(V)/N_k, and the workspace for Psi, D, M and Y.  thc_build queues
+// the five steps of the build on the context's stream:
+//   S1  Psi = X^T C            gemm   (A = X transposed, B = C)
+//   S2  D   = Psi Psi^H        gemm   (B = Psi conjugate-transposed)
+//   S3  M   = IDFT(DFT(D) o Vh) kconv
+//   S4a Y   = M Psi            gemm
+//   S4b KC  = conj(X) Y        gemm   (A = X conjugated)
+//   S5  E_x = -(1/N_k) <Psi, Y> ex_reduce
+#include "thc_internal.cuh"
+
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+namespace {
+
+thread_local std::string g_create_error;
+
+#define CKC(ctx, call)                                                       \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      (ctx)->last_error = std::string(#call) + ": " + cudaGetErrorString(e_); \
+      return THC_ERR_CUDA;                                                   \
+    }                                                                        \
+  } while (0)
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+struct Sizes {
+  long nk, x, v, psi, kc;
+  size_t el;  // bytes of a workspace complex element
+};
+
+Sizes sizes_of(const thc_dims* d, int precision) {
+  Sizes s;
+  s.nk = (long)d->n1 * d->n2 * d->n3;
+  s.x = s.nk * d->nbas * d->nisdf;
+  s.v = s.nk * d->nisdf * d->nisdf;
+  s.psi = s.nk * d->nisdf * d->nocc;
+  s.kc = s.nk * d->nbas * d->nocc;
+  s.el = precision == THC_FP64 ? sizeof(double2) : sizeof(float2);
+  return s;
+}
+
+constexpr int kPartials = 1216;  // 152 SMs x 8 blocks
+
+thc_status check_dims(const thc_dims* d, int precision) {
+  if (!d) return THC_ERR_ARG;
+  if (d->n1 < 1 || d->n2 < 1 || d->n3 < 1 || d->n1 > 8 || d->n2 > 8 || d->n3 > 8) return THC_ERR_ARG;
+  if (d->nbas < 1 || d->nocc < 1 || d->nisdf < 1) return THC_ERR_ARG;
+  if (d->nocc > d->nbas) return THC_ERR_ARG;
+  if (precision != THC_FP64 && precision != THC_MIXED) return THC_ERR_ARG;
+  // element counts must fit the kernels' index arithmetic
+  const double v = (double)d->n1 * d->n2 * d->n3 * d->nisdf * (double)d->nisdf;
+  if (v > 4.0e10) return THC_ERR_UNSUPPORTED;
+  if ((double)d->nisdf * d->nisdf > 2.0e9) return THC_ERR_UNSUPPORTED;
+  return THC_OK;
+}
+
+size_t memory_bytes(const thc_dims* d, int precision) {
+  Sizes s = sizes_of(d, precision);
+  size_t b = 0;
+  b += s.x * s.el;               // X copy
+  b += s.v * s.el;               // prepared kernel
+  b += 2 * s.psi * s.el;         // Psi, Y
+  b += 2 * s.v * s.el;           // D, M
+  b += 2 * s.kc * sizeof(double2) + 2 * sizeof(double);  // host-build staging
+  b += 2 * kPartials * sizeof(double) + 64;
+  return b;
+}
+
+void free_all(thc_ctx* c) {
+  void* ptrs[] = {c->X64, c->Vh64, c->X32, c->Vh32, c->Psi, c->D, c->M, c->Y,
+                  c->Cdev, c->KCdev, c->exdev, c->partial, c->flag};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (int i = 0; i < 7; i++)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  for (cudaEvent_t e : c->prof) cudaEventDestroy(e);
+  c->prof.clear();
+}
+
+constexpr int kStages = 6;
+
+}  // namespace
+
+extern "C" {
+
+const char* thc_status_string(thc_status s) {
+  switch (s) {
+    case THC_OK: return "ok";
+    case THC_ERR_ARG: return "invalid argument";
+    case THC_ERR_OOM: return "device out of memory";
+    case THC_ERR_CUDA: return "CUDA error";
+    case THC_ERR_NONFINITE: return "non-finite input";
+    case THC_ERR_TIMEOUT: return "device wait timed out";
+    case THC_ERR_STATE: return "call out of order";
+    case THC_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+const char* thc_last_error(const thc_ctx* ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->last_error.c_str();
+}
+
+thc_status thc_memory_bytes(const thc_dims* dims, int precision, size_t* bytes) {
+  thc_status st = check_dims(dims, precision);
+  if (st != THC_OK) return st;
+  if (!bytes) return THC_ERR_ARG;
+  *bytes = memory_bytes(dims, precision);
+  return THC_OK;
+}
+
+thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* stream) {
+  if (!out) return THC_ERR_ARG;
+  *out = nullptr;
+  thc_status st = check_dims(d, precision);
+  if (st != THC_OK) return st;
+  thc_ctx* c = new (std::nothrow) thc_ctx();
+  if (!c) return THC_ERR_OOM;
+  c->n1 = d->n1; c->n2 = d->n2; c->n3 = d->n3;
+  c->nk = d->n1 * d->n2 * d->n3;
+  c->nbas = d->nbas; c->nocc = d->nocc; c->nisdf = d->nisdf;
+  c->precision = precision;
+  c->stream = (cudaStream_t)stream;
+  c->n_partial = kPartials;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    delete c;
+    return THC_ERR_CUDA;
+  }
+  Sizes s = sizes_of(d, precision);
+  struct Want { void** p; size_t bytes; };
+  const bool f64 = precision == THC_FP64;
+  Want want[] = {
+      {f64 ? (void**)&c->X64 : (void**)&c->X32, s.x * s.el},
+      {f64 ? (void**)&c->Vh64 : (void**)&c->Vh32, s.v * s.el},
+      {&c->Psi, s.psi * s.el},
+      {&c->Y, s.psi * s.el},
+      {&c->D, s.v * s.el},
+      {&c->M, s.v * s.el},
+      {(void**)&c->Cdev, s.kc * sizeof(double2)},
+      {(void**)&c->KCdev, s.kc * sizeof(double2)},
+      {(void**)&c->exdev, 2 * sizeof(double)},
+      {(void**)&c->partial, 2 * kPartials * sizeof(double)},
+      {(void**)&c->flag, 64},
+  };
+  for (auto& w : want) {
+    e = cudaMalloc(w.p, w.bytes);
+    if (e != cudaSuccess) {
+      *w.p = nullptr;
+      cudaGetLastError();  // clear the sticky-free allocation error
+      g_create_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      free_all(c);
+      delete c;
+      return e == cudaErrorMemoryAllocation ? THC_ERR_OOM : THC_ERR_CUDA;
+    }
+  }
+  for (int i = 0; i < 7; i++) {
+    e = cudaEventCreate(&c->ev[i]);
+    if (e != cudaSuccess) {
+      g_create_error = std::string("cudaEventCreate: ") + cudaGetErrorString(e);
+      free_all(c);
+      delete c;
+      return THC_ERR_CUDA;
+    }
+  }
+  *out = c;
+  return THC_OK;
+}
+
+thc_status thc_destroy(thc_ctx* c) {
+  if (!c) return THC_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+  return THC_OK;
+}
+
+static thc_status finite_check(thc_ctx* c, const double2* p, long n) {
+  CKC(c, cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+  CKC(c, check_finite_z(p, n, c->flag, c->stream));
+  int h = 0;
+  CKC(c, cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return h ? THC_ERR_NONFINITE : THC_OK;
+}
+
+thc_status thc_set_collocation(thc_ctx* c, const double* X) {
+  if (!c || !X || !aligned16(X)) return THC_ERR_ARG;
+  const long n = (long)c->nk * c->nbas * c->nisdf;
+  const double2* x = (const double2*)X;
+  thc_status st = finite_check(c, x, n);
+  if (st != THC_OK) return st;
+  if (c->precision == THC_FP64)
+    CKC(c, cudaMemcpyAsync(c->X64, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  else
+    CKC(c, convert_z2c(x, c->X32, n, c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  c->have_x = true;
+  return THC_OK;
+}
+
+thc_status thc_set_kernel(thc_ctx* c, const double* V) {
+  if (!c || !V || !aligned16(V)) return THC_ERR_ARG;
+  const long npq = (long)c->nisdf * c->nisdf;
+  const double2* v = (const double2*)V;
+  thc_status st = finite_check(c, v, npq * c->nk);
+  if (st != THC_OK) return st;
+  CKC(c, prepare_kernel_z(v, c->Vh64, c->Vh32, npq, c->n1, c->n2, c->n3, c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  c->have_v = true;
+  return THC_OK;
+}
+
+// Event marking the start of stage i (i = 6: end of the build).
+static cudaEvent_t stage_event(thc_ctx* c, int i) {
+  if (c->prof_max > 0 && c->prof_n < c->prof_max) return c->prof[(size_t)c->prof_n * 7 + i];
+  return c->ev[i];
+}
+
+static thc_status build_fp64(thc_ctx* c, const double2* C, double2* KC, double* ex) {
+  const int nk = c->nk, N = c->nbas, n = c->nocc, P = c->nisdf;
+  const long PP = (long)P * P;
+  double2* Psi = (double2*)c->Psi;
+  double2* D = (double2*)c->D;
+  double2* M = (double2*)c->M;
+  double2* Y = (double2*)c->Y;
+  cudaStream_t s = c->stream;
+  CKC(c, cudaEventRecord(stage_event(c, 0), s));
+  CKC(c, gemm_z(A_KM, B_KN, P, n, N, c->X64, P, (long)N * P, C, n, (long)N * n, Psi, n,
+                (long)P * n, nk, s));
+  CKC(c, cudaEventRecord(stage_event(c, 1), s));
+  CKC(c, gemm_z(A_MK, B_NK_CONJ, P, P, n, Psi, n, (long)P * n, Psi, n, (long)P * n, D, P, PP,
+                nk, s));
+  CKC(c, cudaEventRecord(stage_event(c, 2), s));
+  CKC(c, kconv_z(D, c->Vh64, M, PP, c->n1, c->n2, c->n3, s));
+  CKC(c, cudaEventRecord(stage_event(c, 3), s));
+  CKC(c, gemm_z(A_MK, B_KN, P, n, P, M, P, PP, Psi, n, (long)P * n, Y, n, (long)P * n, nk, s));
+  CKC(c, cudaEventRecord(stage_event(c, 4), s));
+  CKC(c, gemm_z(A_MK_CONJ, B_KN, N, n, P, c->X64, P, (long)N * P, Y, n, (long)P * n, KC, n,
+                (long)N * n, nk, s));
+  CKC(c, cudaEventRecord(stage_event(c, 5), s));
+  CKC(c, ex_reduce_z(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
+  CKC(c, cudaEventRecord(stage_event(c, 6), s));
+  return THC_OK;
+}
+
+static thc_status build_mixed(thc_ctx* c, const double2* C, double2* KC, double* ex) {
+  const int nk = c->nk, N = c->nbas, n = c->nocc, P = c->nisdf;
+  const long PP = (long)P * P;
+  float2* Psi = (float2*)c->Psi;
+  float2* D = (float2*)c->D;
+  float2* M = (float2*)c->M;
+  float2* Y = (float2*)c->Y;
+  cudaStream_t s = c->stream;
+  CKC(c, cudaEventRecord(stage_event(c, 0), s));
+  CKC(c, (gemm_c_comp<float2, double2, float2>(A_KM, B_KN, P, n, N, c->X32, P, (long)N * P, C, n,
+                                               (long)N * n, Psi, n, (long)P * n, nk, s)));
+  CKC(c, cudaEventRecord(stage_event(c, 1), s));
+  CKC(c, gemm_c_plain(A_MK, B_NK_CONJ, P, P, n, Psi, n, (long)P * n, Psi, n, (long)P * n, D, P,
+                      PP, nk, s));
+  CKC(c, cudaEventRecord(stage_event(c, 2), s));
+  CKC(c, kconv_c(D, c->Vh32, M, PP, c->n1, c->n2, c->n3, s));
+  CKC(c, cudaEventRecord(stage_event(c, 3), s));
+  CKC(c, (gemm_c_comp<float2, float2, float2>(A_MK, B_KN, P, n, P, M, P, PP, Psi, n, (long)P * n,
+                                              Y, n, (long)P * n, nk, s)));
+  CKC(c, cudaEventRecord(stage_event(c, 4), s));
+  CKC(c, (gemm_c_comp<float2, float2, double2>(A_MK_CONJ, B_KN, N, n, P, c->X32, P, (long)N * P,
+                                               Y, n, (long)P * n, KC, n, (long)N * n, nk, s)));
+  CKC(c, cudaEventRecord(stage_event(c, 5), s));
+  CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
+  CKC(c, cudaEventRecord(stage_event(c, 6), s));
+  return THC_OK;
+}
+
+thc_status thc_build(thc_ctx* c, const double* C, double* KC, double* ex) {
+  if (!c || !C || !KC || !ex) return THC_ERR_ARG;
+  if (!aligned16(C) || !aligned16(KC) || ((uintptr_t)ex & 7u)) return THC_ERR_ARG;
+  const size_t kcb = (size_t)c->nk * c->nbas * c->nocc * sizeof(double2);
+  const char* a = (const char*)C;
+  const char* b = (const char*)KC;
+  if (a < b + kcb && b < a + kcb) return THC_ERR_ARG;  // KC aliases C
+  if (!c->have_x || !c->have_v) return THC_ERR_STATE;
+  thc_status st = c->precision == THC_FP64
+                      ? build_fp64(c, (const double2*)C, (double2*)KC, ex)
+                      : build_mixed(c, (const double2*)C, (double2*)KC, ex);
+  if (st == THC_OK) {
+    c->built = true;
+    if (c->prof_max > 0 && c->prof_n < c->prof_max) {
+      c->prof_n++;
+    }
+  }
+  return st;
+}
+
+thc_status thc_build_host(thc_ctx* c, const double* C_host, double* KC_host, double* ex_host) {
+  if (!c || !C_host || !KC_host || !ex_host) return THC_ERR_ARG;
+  if (!c->have_x || !c->have_v) return THC_ERR_STATE;
+  const size_t kcb = (size_t)c->nk * c->nbas * c->nocc * sizeof(double2);
+  CKC(c, cudaMemcpyAsync(c->Cdev, C_host, kcb, cudaMemcpyHostToDevice, c->stream));
+  thc_status st = thc_build(c, (const double*)c->Cdev, (double*)c->KCdev, c->exdev);
+  if (st != THC_OK) return st;
+  CKC(c, cudaMemcpyAsync(KC_host, c->KCdev, kcb, cudaMemcpyDeviceToHost, c->stream));
+  CKC(c, cudaMemcpyAsync(ex_host, c->exdev, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return THC_OK;
+}
+
+thc_status thc_get_intermediate(thc_ctx* c, int which, double* out) {
+  if (!c || !out || !aligned16(out) || which < 0 || which > 3) return THC_ERR_ARG;
+  if (!c->built) return THC_ERR_STATE;
+  const long n = (which == 0 || which == 3) ? (long)c->nk * c->nisdf * c->nocc
+                                            : (long)c->nk * c->nisdf * c->nisdf;
+  void* src = which == 0 ? c->Psi : which == 1 ? c->D : which == 2 ? c->M : c->Y;
+  if (c->precision == THC_FP64)
+    CKC(c, cudaMemcpyAsync(out, src, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  else
+    CKC(c, convert_c2z((const float2*)src, (double2*)out, n, c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return THC_OK;
+}
+
+thc_status thc_stage_times(thc_ctx* c, float ms[6]) {
+  if (!c || !ms) return THC_ERR_ARG;
+  for (int i = 0; i < kStages; i++) ms[i] = 0.f;
+  if (!c->built) return THC_OK;
+  if (c->prof_max > 0) return THC_ERR_STATE;  // events are going to the profile slots
+  CKC(c, cudaEventSynchronize(c->ev[6]));
+  for (int i = 0; i < kStages; i++) CKC(c, cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]));
+  return THC_OK;
+}
+
+thc_status thc_profile_begin(thc_ctx* c, int max_builds) {
+  if (!c || max_builds < 1 || max_builds > 4096) return THC_ERR_ARG;
+  for (cudaEvent_t e : c->prof) cudaEventDestroy(e);
+  c->prof.assign((size_t)max_builds * 7, nullptr);
+  for (auto& e : c->prof) CKC(c, cudaEventCreate(&e));
+  c->prof_max = max_builds;
+  c->prof_n = 0;
+  return THC_OK;
+}
+
+thc_status thc_profile_end(thc_ctx* c, float mean_ms[6], int* nbuilds) {
+  if (!c || !mean_ms || !nbuilds) return THC_ERR_ARG;
+  if (c->prof_max <= 0) return THC_ERR_STATE;
+  for (int i = 0; i < kStages; i++) mean_ms[i] = 0.f;
+  const int nb = c->prof_n;
+  for (int b = 0; b < nb; b++) {
+    cudaEvent_t* e = &c->prof[(size_t)b * 7];
+    CKC(c, cudaEventSynchronize(e[6]));
+    for (int i = 0; i < kStages; i++) {
+      float t = 0.f;
+      CKC(c, cudaEventElapsedTime(&t, e[i], e[i + 1]));
+      mean_ms[i] += t;
+    }
+  }
+  if (nb > 0)
+    for (int i = 0; i < kStages; i++) mean_ms[i] /= nb;
+  *nbuilds = nb;
+  for (cudaEvent_t e : c->prof) cudaEventDestroy(e);
+  c->prof.clear();
+  c->prof_max = 0;
+  c->prof_n = 0;
+  return THC_OK;
+}
+
+thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
+  if (!c || !launches) return THC_ERR_ARG;
+  *launches = 7;  // S1, S2, S3, S4a, S4b, E_x partial, E_x final
+  return THC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// Internal declarations shared by the CUDA translation units of libthc.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/thc.h"
+
+// ---------------------------------------------------------------------------
+// complex helpers (interleaved re, im)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) {
+  return make_double2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return make_float2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+template <typename T> struct cplx;
+template <> struct cplx<double> { typedef double2 type; };
+template <> struct cplx<float> { typedef float2 type; };
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct thc_ctx {
+  int n1, n2, n3, nk, nbas, nocc, nisdf;
+  int precision;
+  int device;
+  cudaStream_t stream;
+  bool have_x, have_v, built;
+  // FP64 state
+  double2* X64;     // [nk][nbas][nisdf]
+  double2* Vh64;    // [nk][nisdf][nisdf] prepared kernel (FP64 mode)
+  // mixed state
+  float2* X32;      // [nk][nbas][nisdf]
+  float2* Vh32;     // [nk][nisdf][nisdf]
+  // workspace (element type follows the precision)
+  void* Psi;        // [nk][nisdf][nocc]
+  void* D;          // [nk][nisdf][nisdf]
+  void* M;          // [nk][nisdf][nisdf]
+  void* Y;          // [nk][nisdf][nocc]
+  double2* Cdev;    // [nk][nbas][nocc] staging for thc_build_host
+  double2* KCdev;   // [nk][nbas][nocc] staging for thc_build_host
+  double* exdev;    // 2 doubles staging for thc_build_host
+  double* partial;  // reduction scratch
+  int* flag;        // device flag word (finite checks)
+  int n_partial;
+  cudaEvent_t ev[7];               // stage boundaries of the last build
+  std::vector<cudaEvent_t> prof;   // 7 per profiled build
+  int prof_max, prof_n;            // slots, builds recorded
+  std::string last_error;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (each queues kernels on `s`; returns cudaGetLastError())
+// ---------------------------------------------------------------------------
+
+// GEMM operand layouts.  A(m, k) and B(k, n) for C(m, n) = sum_k A B.
+enum GemmA { A_MK = 0, A_KM = 1, A_MK_CONJ = 2 };   // A[m*lda+k], A[k*lda+m], conj(A[m*lda+k])
+enum GemmB { B_KN = 0, B_NK_CONJ = 1 };             // B[k*ldb+n], conj(B[n*ldb+k])
+
+// FP64 complex batched GEMM on CUDA cores.
+cudaError_t gemm_z(int la, int lb, int M, int N, int K, const double2* A, int lda, long sA,
+                   const double2* B, int ldb, long sB, double2* C, int ldc, long sC, int batch,
+                   cudaStream_t s);
+
+// Mixed complex batched GEMM on CUDA cores: operands rounded to FP32, products
+// in FP32, sums of 16 products in FP32 then added into a float-float (two-sum)
+// accumulator.  TA/TB are float2 or double2 in memory, TC float2 or double2.
+template <typename TA, typename TB, typename TC>
+cudaError_t gemm_c_comp(int la, int lb, int M, int N, int K, const TA* A, int lda, long sA,
+                        const TB* B, int ldb, long sB, TC* C, int ldc, long sC, int batch,
+                        cudaStream_t s);
+
+// Plain FP32 complex batched GEMM (S2).
+cudaError_t gemm_c_plain(int la, int lb, int M, int N, int K, const float2* A, int lda, long sA,
+                         const float2* B, int ldb, long sB, float2* C, int ldc, long sC,
+                         int batch, cudaStream_t s);
+
+// k-mesh convolution M = IDFT(DFT(D) o Vh) per (P,Q) element; npq = elements per k.
+cudaError_t kconv_z(const double2* D, const double2* Vh, double2* M, long npq, int n1, int n2,
+                    int n3, cudaStream_t s);
+cudaError_t kconv_c(const float2* D, const float2* Vh, float2* M, long npq, int n1, int n2,
+                    int n3, cudaStream_t s);
+// Vh[a] = (1/N_k) sum_q V[q] w^{+a.q} in FP64; writes FP64 or FP32 output.
+cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long npq, int n1,
+                             int n2, int n3, cudaStream_t s);
+
+// E_x = -(1/nk) sum conj(Psi) Y, FP64 accumulation, deterministic two-pass.
+cudaError_t ex_reduce_z(const double2* Psi, const double2* Y, long n, int nk, double* partial,
+                        int npartial, double* ex, cudaStream_t s);
+cudaError_t ex_reduce_c(const float2* Psi, const float2* Y, long n, int nk, double* partial,
+                        int npartial, double* ex, cudaStream_t s);
+
+// conversions and checks
+cudaError_t convert_z2c(const double2* in, float2* out, long n, cudaStream_t s);
+cudaError_t convert_c2z(const float2* in, double2* out, long n, cudaStream_t s);
+cudaError_t check_finite_z(const double2* in, long n, int* flag, cudaStream_t s);

@@ -1,0 +1,264 @@
+"""Python binding of libthc (include/thc.h): argument marshalling only.
+
+Every step of the build runs in the library's CUDA kernels.  The functions
+here carry the C names; they take torch tensors (complex128, contiguous, on
+the context's device) or numpy arrays (for the host-buffer build) and pass
+their pointers.  There is no fallback: if the library or a GPU is missing,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libthc.so")
+
+THC_FP64 = 0
+THC_MIXED = 1
+PRECISIONS = {"fp64": THC_FP64, "mixed": THC_MIXED}
+
+STATUS = {0: "THC_OK", 1: "THC_ERR_ARG", 2: "THC_ERR_OOM", 3: "THC_ERR_CUDA",
+          4: "THC_ERR_NONFINITE", 5: "THC_ERR_TIMEOUT", 6: "THC_ERR_STATE",
+          7: "THC_ERR_UNSUPPORTED"}
+
+EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_kernel",
+           "thc_build", "thc_build_host", "thc_get_intermediate", "thc_stage_times",
+           "thc_launches_per_build", "thc_destroy", "thc_status_string", "thc_last_error",
+           "thc_profile_begin", "thc_profile_end"]
+
+
+class ThcDims(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("n3", ctypes.c_int),
+                ("nbas", ctypes.c_int), ("nocc", ctypes.c_int), ("nisdf", ctypes.c_int)]
+
+
+class ThcError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}" + (f" ({detail})" if detail else ""))
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libthc.so (built by build_lib.build()).  Raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libthc.so not built at {p}; run paper_2304_05505_gb300.build_lib.build()")
+    lib = ctypes.CDLL(p)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p
+    lib.thc_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ThcDims), ip, vp]
+    lib.thc_memory_bytes.argtypes = [ctypes.POINTER(ThcDims), ip, ctypes.POINTER(ctypes.c_size_t)]
+    lib.thc_set_collocation.argtypes = [vp, dp]
+    lib.thc_set_kernel.argtypes = [vp, dp]
+    lib.thc_build.argtypes = [vp, dp, dp, dp]
+    lib.thc_build_host.argtypes = [vp, dp, dp, dp]
+    lib.thc_get_intermediate.argtypes = [vp, ip, dp]
+    lib.thc_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.thc_launches_per_build.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.thc_profile_begin.argtypes = [vp, ip]
+    lib.thc_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]
+    lib.thc_destroy.argtypes = [vp]
+    lib.thc_status_string.argtypes = [ip]
+    lib.thc_status_string.restype = ctypes.c_char_p
+    lib.thc_last_error.argtypes = [vp]
+    lib.thc_last_error.restype = ctypes.c_char_p
+    for f in EXPORTS:
+        if f not in ("thc_status_string", "thc_last_error"):
+            getattr(lib, f).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(code: int, where: str, ctx=None):
+    if code != 0:
+        detail = ""
+        try:
+            detail = load().thc_last_error(ctx).decode()
+        except Exception:
+            pass
+        raise ThcError(code, where, detail)
+
+
+def _dims(d: dict) -> ThcDims:
+    return ThcDims(int(d["n1"]), int(d["n2"]), int(d["n3"]), int(d["nbas"]), int(d["nocc"]),
+                   int(d["nisdf"]))
+
+
+def _dev_ptr(t, shape=None, name="tensor") -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if t.dtype != torch.complex128:
+        raise TypeError(f"{name}: expected complex128, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------------------
+# C calls, same names
+# ---------------------------------------------------------------------------
+
+def thc_memory_bytes(dims: dict, precision: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check(load().thc_memory_bytes(ctypes.byref(_dims(dims)), int(precision), ctypes.byref(b)),
+           "thc_memory_bytes")
+    return int(b.value)
+
+
+def thc_create(dims: dict, precision: int, stream: int | None = None) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    h = ctypes.c_void_p(0)
+    _check(load().thc_create(ctypes.byref(h), ctypes.byref(_dims(dims)), int(precision),
+                             ctypes.c_void_p(stream)), "thc_create")
+    return h
+
+
+def thc_set_collocation(ctx, X) -> None:
+    _check(load().thc_set_collocation(ctx, _dev_ptr(X, name="X")), "thc_set_collocation", ctx)
+
+
+def thc_set_kernel(ctx, V) -> None:
+    _check(load().thc_set_kernel(ctx, _dev_ptr(V, name="V")), "thc_set_kernel", ctx)
+
+
+def thc_build(ctx, C, KC, ex) -> None:
+    import torch
+    if not (isinstance(ex, torch.Tensor) and ex.is_cuda and ex.dtype == torch.float64 and ex.numel() >= 2):
+        raise TypeError("ex: expected a CUDA float64 tensor with 2 elements")
+    _check(load().thc_build(ctx, _dev_ptr(C, name="C"), _dev_ptr(KC, name="KC"), ex.data_ptr()),
+           "thc_build", ctx)
+
+
+def _host_ptr(a, dtype, name) -> int:
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != dtype or not a.is_contiguous():
+            raise TypeError(f"{name}: expected a contiguous host tensor of {dtype}")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name}: must be contiguous")
+        return a.ctypes.data
+    raise TypeError(f"{name}: expected a host tensor or numpy array")
+
+
+def thc_build_host(ctx, C_host, KC_host, ex_host) -> None:
+    import torch
+    _check(load().thc_build_host(ctx, _host_ptr(C_host, torch.complex128, "C_host"),
+                                 _host_ptr(KC_host, torch.complex128, "KC_host"),
+                                 _host_ptr(ex_host, torch.float64, "ex_host")),
+           "thc_build_host", ctx)
+
+
+def thc_get_intermediate(ctx, which: int, out) -> None:
+    _check(load().thc_get_intermediate(ctx, int(which), _dev_ptr(out, name="out")),
+           "thc_get_intermediate", ctx)
+
+
+STAGES = ["S1_collocate", "S2_density", "S3_kconv", "S4a_apply_M", "S4b_backproject", "S5_energy"]
+
+
+def thc_profile_begin(ctx, max_builds: int) -> None:
+    _check(load().thc_profile_begin(ctx, int(max_builds)), "thc_profile_begin", ctx)
+
+
+def thc_profile_end(ctx) -> tuple:
+    arr = (ctypes.c_float * 6)()
+    n = ctypes.c_int(0)
+    _check(load().thc_profile_end(ctx, arr, ctypes.byref(n)), "thc_profile_end", ctx)
+    return [float(x) for x in arr], int(n.value)
+
+
+def thc_stage_times(ctx) -> list:
+    arr = (ctypes.c_float * 6)()
+    _check(load().thc_stage_times(ctx, arr), "thc_stage_times", ctx)
+    return [float(x) for x in arr]
+
+
+def thc_launches_per_build(ctx) -> int:
+    n = ctypes.c_int(0)
+    _check(load().thc_launches_per_build(ctx, ctypes.byref(n)), "thc_launches_per_build", ctx)
+    return int(n.value)
+
+
+def thc_destroy(ctx) -> None:
+    _check(load().thc_destroy(ctx), "thc_destroy")
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+
+class ExchangeBuild:
+    """One context: set X and V once, then call build(C) every SCF iteration."""
+
+    def __init__(self, dims: dict, precision="mixed", device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.dims = dict(dims)
+        self.precision = PRECISIONS.get(precision, precision)
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            self.stream = stream or torch.cuda.current_stream(self.device)
+            self.ctx = thc_create(self.dims, self.precision, self.stream.cuda_stream)
+        d = self.dims
+        self.nk = d["n1"] * d["n2"] * d["n3"]
+        self.kc_shape = (self.nk, d["nbas"], d["nocc"])
+
+    def set_collocation(self, X):
+        thc_set_collocation(self.ctx, self._to_dev(X))
+
+    def set_kernel(self, V):
+        thc_set_kernel(self.ctx, self._to_dev(V))
+
+    def _to_dev(self, a):
+        t = self.torch
+        if isinstance(a, np.ndarray):
+            a = t.from_numpy(np.ascontiguousarray(a, dtype=np.complex128))
+        return a.to(self.device, non_blocking=False).contiguous()
+
+    def build(self, C, KC=None, ex=None):
+        t = self.torch
+        C = self._to_dev(C)
+        if KC is None:
+            KC = t.empty(self.kc_shape, dtype=t.complex128, device=self.device)
+        if ex is None:
+            ex = t.empty(2, dtype=t.float64, device=self.device)
+        thc_build(self.ctx, C, KC, ex)
+        return KC, ex
+
+    def intermediate(self, which: int):
+        t = self.torch
+        d = self.dims
+        shape = (self.nk, d["nisdf"], d["nocc"]) if which in (0, 3) else (self.nk, d["nisdf"], d["nisdf"])
+        out = t.empty(shape, dtype=t.complex128, device=self.device)
+        thc_get_intermediate(self.ctx, which, out)
+        return out
+
+    def stage_times(self):
+        return thc_stage_times(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            thc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,82 @@
+"""The C-ABI library loads and exports what include/thc.h declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2304_05505_gb300 import build_lib, thc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(thc.LIB_PATH):
+        build_lib.build()
+    return thc.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "thc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(thc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for f in ["thc_create", "thc_set_collocation", "thc_set_kernel", "thc_build", "thc_destroy"]:
+        assert f in names
+
+
+def test_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_binding_covers_header():
+    assert set(declared_functions()) <= set(thc.EXPORTS)
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        s = lib.thc_status_string(code)
+        assert s and s != b"unknown status"
+    assert lib.thc_status_string(99) == b"unknown status"
+
+
+def test_memory_bytes_arithmetic():
+    d = dict(n1=4, n2=4, n3=4, nbas=432, nocc=60, nisdf=1200)
+    nk, N, n, P = 64, 432, 60, 1200
+    got = thc.thc_memory_bytes(d, thc.THC_MIXED)
+    expect = 8 * (nk * N * P + nk * P * P + 2 * nk * P * n + 2 * nk * P * P) \
+        + 2 * 16 * nk * N * n + 16 + 2 * 1216 * 8 + 64
+    assert got == expect
+    got64 = thc.thc_memory_bytes(d, thc.THC_FP64)
+    assert got64 > got
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n1=0, n2=1, n3=1, nbas=4, nocc=2, nisdf=4),
+    dict(n1=9, n2=1, n3=1, nbas=4, nocc=2, nisdf=4),
+    dict(n1=1, n2=1, n3=1, nbas=4, nocc=0, nisdf=4),
+    dict(n1=1, n2=1, n3=1, nbas=4, nocc=5, nisdf=4),
+    dict(n1=1, n2=1, n3=1, nbas=4, nocc=2, nisdf=0),
+])
+def test_bad_dims_rejected(bad):
+    with pytest.raises(thc.ThcError) as e:
+        thc.thc_memory_bytes(bad, thc.THC_FP64)
+    assert e.value.code == 1
+
+
+def test_bad_precision_rejected():
+    with pytest.raises(thc.ThcError) as e:
+        thc.thc_memory_bytes(dict(n1=1, n2=1, n3=1, nbas=4, nocc=2, nisdf=4), 7)
+    assert e.value.code == 1
+
+
+def test_null_context_calls(lib):
+    assert lib.thc_build(None, None, None, None) == 1
+    assert lib.thc_destroy(None) == 1
+    assert lib.thc_set_kernel(None, None) == 1

@@ -1,0 +1,218 @@
+"""GPU build vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (written here, used by every case):
+* FP64 build: max|dKC| <= 1e-10 and |dE_x| <= 1e-9 Ha per cell (absolute).
+* Mixed build on the 4x4x4, N_P = 1200 benzene-shaped cell: max|dKC| <= 1e-7
+  and |dE_x| <= 1e-6 Ha per cell (absolute).
+* Mixed build elsewhere (random and small cells, whose scales differ): a few
+  FP32 unit roundoffs of the output scale, max|dKC| <= 1e-6 max|KC| and
+  |dE_x| <= 1e-6 |E_x|.  The mixed path rounds each operand to FP32
+  (2^-24 = 6e-8 relative) and forms FP32 products; the compensated sums add
+  nothing at this level, so the error is a small multiple of 6e-8 of the
+  largest terms, and 1e-6 leaves room for the cancellation in X^T C.
+"""
+import numpy as np
+import pytest
+
+from oracle import thc_oracle as O
+from paper_2304_05505_gb300 import cells
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(kc=1e-10, ex=1e-9)}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(cuda_required):
+    import torch
+    from paper_2304_05505_gb300 import build_lib, thc
+    import os
+    if not os.path.exists(thc.LIB_PATH):
+        build_lib.build()
+    thc.load()
+    return torch
+
+
+def gpu_build(torch, X, C, V, mesh, precision, keep=False):
+    from paper_2304_05505_gb300 import thc
+    nk, nb, npt = X.shape
+    dims = dict(n1=mesh[0], n2=mesh[1], n3=mesh[2], nbas=nb, nocc=C.shape[2], nisdf=npt)
+    eb = thc.ExchangeBuild(dims, precision)
+    try:
+        eb.set_collocation(X)
+        eb.set_kernel(V)
+        KC, ex = eb.build(C)
+        torch.cuda.synchronize()
+        out = dict(KC=KC.cpu().numpy(), Ex=float(ex[0]), Ex_imag=float(ex[1]))
+        if keep:
+            for i, nm in enumerate(["Psi", "D", "M", "Y"]):
+                out[nm] = eb.intermediate(i).cpu().numpy()
+        return out
+    finally:
+        eb.close()
+
+
+def assert_close(ref, got, precision, target=False):
+    dkc = float(np.abs(got["KC"] - ref["KC"]).max())
+    dex = abs(got["Ex"] - ref["Ex"])
+    if precision == "fp64":
+        assert dkc <= 1e-10, dkc
+        assert dex <= 1e-9, dex
+    elif target:
+        assert dkc <= 1e-7, dkc
+        assert dex <= 1e-6, dex
+    else:
+        scale = float(np.abs(ref["KC"]).max())
+        assert dkc <= 1e-6 * scale, (dkc, scale)
+        assert dex <= 1e-6 * abs(ref["Ex"]) + 1e-12, (dex, ref["Ex"])
+    return dkc, dex
+
+
+RANDOM_CASES = [
+    ((2, 2, 2), 70, 9, 150),     # several 64-wide tiles with ragged tails
+    ((3, 2, 4), 33, 5, 67),      # non-cubic mesh, odd sizes
+    ((3, 3, 3), 40, 7, 130),
+    ((1, 1, 1), 1, 1, 1),        # degenerate: one of everything
+    ((5, 1, 1), 3, 1, 2),        # 5-point DFT (direct form), n = 1
+    ((2, 3, 1), 17, 17, 16),     # n = N
+    ((4, 4, 4), 20, 3, 65),
+    ((6, 1, 2), 10, 2, 33),      # 6-point DFT
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("mesh,nbas,nocc,nisdf", RANDOM_CASES)
+def test_random_parity(torch_cuda, precision, mesh, nbas, nocc, nisdf):
+    r = cells.random_problem(mesh, nbas=nbas, nocc=nocc, nisdf=nisdf, seed=nbas + nisdf)
+    ref = O.build(r["X"], r["C"], r["V"], mesh, route="direct")
+    got = gpu_build(torch_cuda, r["X"], r["C"], r["V"], mesh, precision)
+    assert_close(ref, got, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("mesh", [(2, 2, 2), (3, 3, 3)])
+def test_toy_cell_parity(torch_cuda, precision, mesh):
+    p = cells.make_problem("C0", mesh=mesh)
+    ref = O.build(p.X, p.C, p.V, p.cell.mesh, route="direct")
+    got = gpu_build(torch_cuda, p.X, p.C, p.V, p.cell.mesh, precision)
+    assert_close(ref, got, precision)
+    assert got["Ex"] < 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_intermediates(torch_cuda, precision):
+    r = cells.random_problem((3, 2, 2), nbas=21, nocc=4, nisdf=70, seed=9)
+    ref = O.build(r["X"], r["C"], r["V"], r["mesh"], keep=True)
+    got = gpu_build(torch_cuda, r["X"], r["C"], r["V"], r["mesh"], precision, keep=True)
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    for nm in ["Psi", "D", "M", "Y"]:
+        err = np.abs(got[nm] - ref[nm]).max() / np.abs(ref[nm]).max()
+        assert err < tol, (nm, err)
+
+
+@pytest.fixture(scope="module")
+def c1(torch_cuda):
+    p = cells.make_problem("C1")
+    ref = O.build(p.X, p.C, p.V, p.cell.mesh, route="direct")
+    return p, ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_benzene_3x3x3_parity(torch_cuda, c1, precision):
+    """Benzene-shaped cell, 3x3x3 k, N_P = 600, n = 60, N = 432: full size."""
+    p, ref = c1
+    got = gpu_build(torch_cuda, p.X, p.C, p.V, p.cell.mesh, precision)
+    assert_close(ref, got, precision)
+
+
+@pytest.fixture(scope="module")
+def c2(torch_cuda):
+    p = cells.make_problem("C2")
+    ref = O.build(p.X, p.C, p.V, p.cell.mesh, route="fft")
+    return p, ref
+
+
+def test_benzene_4x4x4_mixed_target(torch_cuda, c2):
+    """The target configuration: 4x4x4 k, N_P = 1200, mixed precision,
+    every output compared; the launch configuration the bench times."""
+    p, ref = c2
+    got = gpu_build(torch_cuda, p.X, p.C, p.V, p.cell.mesh, "mixed")
+    dkc, dex = assert_close(ref, got, "mixed", target=True)
+    print(f"mixed 4x4x4: max|dKC| = {dkc:.3e}, |dE_x| = {dex:.3e}, E_x = {ref['Ex']:.9f}")
+
+
+def test_benzene_4x4x4_fp64(torch_cuda, c2):
+    p, ref = c2
+    got = gpu_build(torch_cuda, p.X, p.C, p.V, p.cell.mesh, "fp64")
+    assert_close(ref, got, "fp64")
+
+
+def test_time_reversal_on_gpu(torch_cuda, c2):
+    """KC^{-k} = conj(KC^k) holds on the device output at full size."""
+    p, _ = c2
+    got = gpu_build(torch_cuda, p.X, p.C, p.V, p.cell.mesh, "mixed")
+    mk = cells.minus_k_index(p.cell.mesh)
+    assert np.abs(got["KC"][mk] - got["KC"].conj()).max() < 1e-7
+
+
+def test_build_host_matches_build(torch_cuda):
+    from paper_2304_05505_gb300 import thc
+    torch = torch_cuda
+    r = cells.random_problem((2, 2, 1), nbas=12, nocc=3, nisdf=40, seed=4)
+    dims = dict(n1=2, n2=2, n3=1, nbas=12, nocc=3, nisdf=40)
+    for prec in ("fp64", "mixed"):
+        eb = thc.ExchangeBuild(dims, prec)
+        eb.set_collocation(r["X"])
+        eb.set_kernel(r["V"])
+        KC, ex = eb.build(r["C"])
+        Ch = torch.from_numpy(r["C"]).pin_memory()
+        KCh = torch.empty(eb.kc_shape, dtype=torch.complex128).pin_memory()
+        exh = torch.empty(2, dtype=torch.float64).pin_memory()
+        thc.thc_build_host(eb.ctx, Ch, KCh, exh)
+        assert torch.equal(KC.cpu(), KCh)
+        assert torch.equal(ex.cpu(), exh)
+        eb.close()
+
+
+def test_error_paths(torch_cuda):
+    from paper_2304_05505_gb300 import thc
+    torch = torch_cuda
+    r = cells.random_problem((2, 1, 1), nbas=6, nocc=2, nisdf=10, seed=2)
+    dims = dict(n1=2, n2=1, n3=1, nbas=6, nocc=2, nisdf=10)
+    eb = thc.ExchangeBuild(dims, "mixed")
+    C = torch.from_numpy(r["C"]).cuda()
+    KC = torch.empty_like(C)
+    ex = torch.empty(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(thc.ThcError) as e:       # build before set_*
+        thc.thc_build(eb.ctx, C, KC, ex)
+    assert e.value.code == 6
+    Xbad = r["X"].copy()
+    Xbad[1, 2, 3] = np.nan
+    with pytest.raises(thc.ThcError) as e:
+        eb.set_collocation(Xbad)
+    assert e.value.code == 4
+    eb.set_collocation(r["X"])
+    eb.set_kernel(r["V"])
+    with pytest.raises(thc.ThcError) as e:       # KC aliases C
+        thc.thc_build(eb.ctx, C, C, ex)
+    assert e.value.code == 1
+    thc.thc_build(eb.ctx, C, KC, ex)
+    torch.cuda.synchronize()
+    eb.close()
+
+
+def test_profile_stage_times(torch_cuda):
+    from paper_2304_05505_gb300 import thc
+    r = cells.random_problem((2, 2, 2), nbas=30, nocc=5, nisdf=100, seed=3)
+    dims = dict(n1=2, n2=2, n3=2, nbas=30, nocc=5, nisdf=100)
+    eb = thc.ExchangeBuild(dims, "mixed")
+    eb.set_collocation(r["X"])
+    eb.set_kernel(r["V"])
+    thc.thc_profile_begin(eb.ctx, 4)
+    for _ in range(6):
+        eb.build(r["C"])
+    ms, n = thc.thc_profile_end(eb.ctx)
+    assert n == 4 and all(t > 0 for t in ms)
+    last = thc.thc_stage_times(eb.ctx)
+    assert all(t > 0 for t in last)
+    eb.close()
