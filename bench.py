@@ -166,7 +166,7 @@ def stage_work(d: dict) -> dict:
     }
 
 
-def kernel_roofline(stage: str, ms: float, work: dict, pk: dict, clocks: dict) -> dict:
+def kernel_roofline(stage: str, ms: float, work: dict, pk: dict, clocks: dict, tensor: bool = True) -> dict:
     w = work[stage]
     traffic = measured_traffic(stage)
     if w["flops"] is None or stage == "S5_energy":
@@ -175,6 +175,17 @@ def kernel_roofline(stage: str, ms: float, work: dict, pk: dict, clocks: dict) -
         return {"kernel": stage, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": pk["source"],
                 "algorithmic_bytes": w["bytes"], "ms": ms}
+    if tensor:
+        # tcgen05 bf16 GEMM on three-plane split operands: six bf16 products per
+        # real product.  Achieved counts the algorithmic complex flops (8 per
+        # complex multiply-add); the issued bf16 flops are 6x that.
+        peak = pk["bf16_tflops_sustained"]
+        achieved = w["flops"] / (ms * 1e-3) / 1e12
+        return {"kernel": stage, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{pk['source']} bf16 sustained (cuBLAS)",
+                "algorithmic_flops": w["flops"], "issued_bf16_flops": 6 * w["flops"],
+                "issued_frac": 6 * achieved / peak, "ms": ms}
     # CUDA-core FP32 GEMM: bound by the FP32 pipe.  Peak = 152 SMs x 128 lanes
     # x 2 flop x the maximum SM clock (2070 MHz): 80.6 TFLOP/s.
     peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
@@ -328,6 +339,7 @@ def run_ours(args, world, rank, local):
     clocks = clk.stop()
     ms_total = max_over_ranks(world, e0.elapsed_time(e1))
     stage_ms, nprof = thc.thc_profile_end(eb.ctx)
+    eb.sync()   # raises if a device-side wait gave up during the timed builds
     launches = thc.thc_launches_per_build(eb.ctx) * args.steps
     KC_mixed = KC.cpu().numpy()
     ex_mixed = ex.cpu().numpy().copy()
@@ -352,6 +364,28 @@ def run_ours(args, world, rank, local):
            "steps": ne2e, "api": "thc_build_host (pinned host C in, KC and E_x out)"}
     eb.close()
     del eb
+    torch.cuda.empty_cache()
+
+    # --- the same precision on CUDA cores (comparison) -----------------------
+    es = thc.ExchangeBuild(d, "mixed_simt", device=dev, stream=stream)
+    es.set_collocation(p.X)
+    es.set_kernel(p.V)
+    for _ in range(2):
+        es.build(C, KC, ex)
+    torch.cuda.synchronize()
+    nsimt = max(3, min(args.steps, 10))
+    thc.thc_profile_begin(es.ctx, nsimt)
+    e0.record(stream)
+    for _ in range(nsimt):
+        es.build(C, KC, ex)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_simt = max_over_ranks(world, e0.elapsed_time(e1)) / nsimt
+    st_simt, _ = thc.thc_profile_end(es.ctx)
+    KC_simt = KC.cpu().numpy()
+    ex_simt = ex.cpu().numpy().copy()
+    es.close()
+    del es
     torch.cuda.empty_cache()
 
     # --- FP64 GPU build -----------------------------------------------------
@@ -382,10 +416,13 @@ def run_ours(args, world, rank, local):
     roof = kernel_roofline(dominant, stages[dominant], work, pk, clocks)
     per_stage = {nm: kernel_roofline(nm, stages[nm], work, pk, clocks) for nm in names}
 
+
     line = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 operands, compensated sums, FP64 E_x)",
+            "config": {"workload": WORKLOAD,
+                       "precision": "mixed: tcgen05 bf16 GEMMs on 3-plane split operands (24-bit), FP32 "
+                                    "accumulation with float-float drain, FP32 k-convolution, FP64 E_x sum",
                        "l2": "inputs larger than L2 (prepared kernel 737 MB, X 265 MB complex64)",
                        "parallelism": f"{world} independent builds (one per GPU)"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
@@ -394,6 +431,8 @@ def run_ours(args, world, rank, local):
                                                     for k, v in per_stage.items()},
             "fp64_gpu": {"value": world / (ms64 * 1e-3), "unit": "builds/s", "ms_per_step": ms64,
                          "stages_ms": {nm: ms for nm, ms in zip(names, st64)}},
+            "mixed_cuda_cores": {"value": world / (ms_simt * 1e-3), "unit": "builds/s", "ms_per_step": ms_simt,
+                                 "stages_ms": {nm: ms for nm, ms in zip(names, st_simt)}},
             "Ex_mixed": float(ex_mixed[0]), "Ex_fp64_gpu": float(ex_64[0])}
     if not args.no_oracle:
         from oracle import thc_oracle as O
@@ -405,6 +444,8 @@ def run_ours(args, world, rank, local):
                       "abs_dEx": abs(float(ex_mixed[0]) - ref["Ex"])},
             "fp64_gpu": {"max_abs_dKC": float(np.abs(KC_64 - ref["KC"]).max()),
                          "abs_dEx": abs(float(ex_64[0]) - ref["Ex"])},
+            "mixed_cuda_cores": {"max_abs_dKC": float(np.abs(KC_simt - ref["KC"]).max()),
+                                 "abs_dEx": abs(float(ex_simt[0]) - ref["Ex"])},
             "Ex_oracle": ref["Ex"], "oracle_full_build_s": t_full}
         cb = time_oracle(p, args.cpu_samples, 1)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

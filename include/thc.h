@@ -60,8 +60,12 @@ typedef enum {
 
 typedef enum {
   THC_FP64 = 0,            /* every step in FP64 on CUDA cores */
-  THC_MIXED = 1            /* S1, S4 with FP32-precision operands and compensated
-                              accumulation; S2, S3 in FP32; E_x summed in FP64 */
+  THC_MIXED = 1,           /* S1, S2, S4a, S4b on tensor cores (tcgen05) with each
+                              operand split into three bf16 planes (24 significant
+                              bits) and FP32 accumulation, the leading term drained
+                              into float-float sums; S3 in FP32; E_x summed in FP64 */
+  THC_MIXED_SIMT = 2       /* the same precision on CUDA cores: FP32 operands,
+                              float-float compensated sums in S1, S4a, S4b */
 } thc_precision;
 
 typedef struct {
@@ -124,6 +128,11 @@ thc_status thc_stage_times(thc_ctx* ctx, float stage_ms[6]);
  * S5) and the number of builds recorded, and stops recording. */
 thc_status thc_profile_begin(thc_ctx* ctx, int max_builds);
 thc_status thc_profile_end(thc_ctx* ctx, float mean_ms[6], int* nbuilds);
+
+/* Wait for the context's stream.  Returns THC_ERR_TIMEOUT if a device-side
+ * wait of a tensor-core kernel gave up since the last thc_sync (its outputs
+ * are then invalid; the context stays usable), else THC_OK. */
+thc_status thc_sync(thc_ctx* ctx);
 
 /* Number of kernel launches one thc_build makes. */
 thc_status thc_launches_per_build(const thc_ctx* ctx, int* launches);

@@ -70,15 +70,21 @@ __global__ void __launch_bounds__(RT) ex_partial_c(const float2* __restrict__ Ps
   }
 }
 
-__global__ void ex_final(const double* __restrict__ partial, int np, int nk, double* ex) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One block; thread t adds partials t, t + RT, ... and the block tree adds
+// the thread sums: a fixed order, so the result is reproducible.
+__global__ void __launch_bounds__(RT) ex_final(const double* __restrict__ partial, int np, int nk, double* ex) {
+  __shared__ double sh[RT / 32];
   double re = 0.0, im = 0.0;
-  for (int i = 0; i < np; i++) {
+  for (int i = threadIdx.x; i < np; i += RT) {
     re += partial[2 * i];
     im += partial[2 * i + 1];
   }
-  ex[0] = -re / nk;
-  ex[1] = -im / nk;
+  re = block_sum(re, sh);
+  im = block_sum(im, sh);
+  if (threadIdx.x == 0) {
+    ex[0] = -re / nk;
+    ex[1] = -im / nk;
+  }
 }
 
 __global__ void z2c_kernel(const double2* __restrict__ in, float2* __restrict__ out, long n) {
@@ -110,14 +116,14 @@ unsigned grid_for(long n, int t) {
 cudaError_t ex_reduce_z(const double2* Psi, const double2* Y, long n, int nk, double* partial,
                         int npartial, double* ex, cudaStream_t s) {
   ex_partial_z<<<npartial, RT, 0, s>>>(Psi, Y, n, partial);
-  ex_final<<<1, 32, 0, s>>>(partial, npartial, nk, ex);
+  ex_final<<<1, RT, 0, s>>>(partial, npartial, nk, ex);
   return cudaGetLastError();
 }
 
 cudaError_t ex_reduce_c(const float2* Psi, const float2* Y, long n, int nk, double* partial,
                         int npartial, double* ex, cudaStream_t s) {
   ex_partial_c<<<npartial, RT, 0, s>>>(Psi, Y, n, partial);
-  ex_final<<<1, 32, 0, s>>>(partial, npartial, nk, ex);
+  ex_final<<<1, RT, 0, s>>>(partial, npartial, nk, ex);
   return cudaGetLastError();
 }
 

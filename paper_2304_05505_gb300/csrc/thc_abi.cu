@@ -34,7 +34,12 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 struct Sizes {
   long nk, x, v, psi, kc;
   size_t el;  // bytes of a workspace complex element
+  // tensor-core planes (elements of one plane)
+  int ldXT, ldM, ldPs;
+  long plXn, plXT, plM, plPs, plBc, plBd, plBp;
 };
+
+int pad8(int x) { return (x + 7) & ~7; }
 
 Sizes sizes_of(const thc_dims* d, int precision) {
   Sizes s;
@@ -44,6 +49,16 @@ Sizes sizes_of(const thc_dims* d, int precision) {
   s.psi = s.nk * d->nisdf * d->nocc;
   s.kc = s.nk * d->nbas * d->nocc;
   s.el = precision == THC_FP64 ? sizeof(double2) : sizeof(float2);
+  s.ldXT = pad8(2 * d->nbas);
+  s.ldM = pad8(2 * d->nisdf);
+  s.ldPs = pad8(2 * d->nocc);
+  s.plXn = s.nk * d->nbas * s.ldM;
+  s.plXT = s.nk * d->nisdf * s.ldXT;
+  s.plM = s.nk * d->nisdf * (long)s.ldM;
+  s.plPs = s.nk * d->nisdf * s.ldPs;
+  s.plBc = s.nk * 2 * d->nocc * s.ldXT;
+  s.plBd = s.nk * 2L * d->nisdf * s.ldPs;
+  s.plBp = s.nk * 2 * d->nocc * (long)s.ldM;
   return s;
 }
 
@@ -54,7 +69,7 @@ thc_status check_dims(const thc_dims* d, int precision) {
   if (d->n1 < 1 || d->n2 < 1 || d->n3 < 1 || d->n1 > 8 || d->n2 > 8 || d->n3 > 8) return THC_ERR_ARG;
   if (d->nbas < 1 || d->nocc < 1 || d->nisdf < 1) return THC_ERR_ARG;
   if (d->nocc > d->nbas) return THC_ERR_ARG;
-  if (precision != THC_FP64 && precision != THC_MIXED) return THC_ERR_ARG;
+  if (precision != THC_FP64 && precision != THC_MIXED && precision != THC_MIXED_SIMT) return THC_ERR_ARG;
   // element counts must fit the kernels' index arithmetic
   const double v = (double)d->n1 * d->n2 * d->n3 * d->nisdf * (double)d->nisdf;
   if (v > 4.0e10) return THC_ERR_UNSUPPORTED;
@@ -65,18 +80,24 @@ thc_status check_dims(const thc_dims* d, int precision) {
 size_t memory_bytes(const thc_dims* d, int precision) {
   Sizes s = sizes_of(d, precision);
   size_t b = 0;
-  b += s.x * s.el;               // X copy
   b += s.v * s.el;               // prepared kernel
   b += 2 * s.psi * s.el;         // Psi, Y
-  b += 2 * s.v * s.el;           // D, M
+  b += s.v * s.el;               // D
+  if (precision == THC_MIXED) {
+    b += 3 * 2 * (s.plXn + s.plXT + s.plM + s.plPs + s.plBc + s.plBd + s.plBp);
+  } else {
+    b += s.x * s.el;             // X copy
+    b += s.v * s.el;             // M
+  }
   b += 2 * s.kc * sizeof(double2) + 2 * sizeof(double);  // host-build staging
-  b += 2 * kPartials * sizeof(double) + 64;
+  b += 2 * kPartials * sizeof(double) + 64 + 64;
   return b;
 }
 
 void free_all(thc_ctx* c) {
   void* ptrs[] = {c->X64, c->Vh64, c->X32, c->Vh32, c->Psi, c->D, c->M, c->Y,
-                  c->Cdev, c->KCdev, c->exdev, c->partial, c->flag};
+                  c->Cdev, c->KCdev, c->exdev, c->partial, c->flag, c->Xn_pl, c->XT_pl,
+                  c->M_pl, c->PsiA_pl, c->Bc_pl, c->Bd_pl, c->Bp_pl, c->tc_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 7; i++)
@@ -139,30 +160,75 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
   }
   Sizes s = sizes_of(d, precision);
   struct Want { void** p; size_t bytes; };
-  const bool f64 = precision == THC_FP64;
-  Want want[] = {
-      {f64 ? (void**)&c->X64 : (void**)&c->X32, s.x * s.el},
-      {f64 ? (void**)&c->Vh64 : (void**)&c->Vh32, s.v * s.el},
-      {&c->Psi, s.psi * s.el},
-      {&c->Y, s.psi * s.el},
-      {&c->D, s.v * s.el},
-      {&c->M, s.v * s.el},
-      {(void**)&c->Cdev, s.kc * sizeof(double2)},
-      {(void**)&c->KCdev, s.kc * sizeof(double2)},
-      {(void**)&c->exdev, 2 * sizeof(double)},
-      {(void**)&c->partial, 2 * kPartials * sizeof(double)},
-      {(void**)&c->flag, 64},
-  };
-  for (auto& w : want) {
+  Want want[24];
+  int nw = 0;
+  auto W = [&](void** p, size_t bytes) { want[nw++] = Want{p, bytes}; };
+  if (precision == THC_FP64) {
+    W((void**)&c->X64, s.x * s.el);
+    W((void**)&c->Vh64, s.v * s.el);
+    W(&c->M, s.v * s.el);
+  } else if (precision == THC_MIXED_SIMT) {
+    W((void**)&c->X32, s.x * s.el);
+    W((void**)&c->Vh32, s.v * s.el);
+    W(&c->M, s.v * s.el);
+  } else {
+    W((void**)&c->Vh32, s.v * s.el);
+    W((void**)&c->Xn_pl, 3 * 2 * s.plXn);
+    W((void**)&c->XT_pl, 3 * 2 * s.plXT);
+    W((void**)&c->M_pl, 3 * 2 * s.plM);
+    W((void**)&c->PsiA_pl, 3 * 2 * s.plPs);
+    W((void**)&c->Bc_pl, 3 * 2 * s.plBc);
+    W((void**)&c->Bd_pl, 3 * 2 * s.plBd);
+    W((void**)&c->Bp_pl, 3 * 2 * s.plBp);
+    W((void**)&c->tc_err, 64);
+  }
+  W(&c->Psi, s.psi * s.el);
+  W(&c->Y, s.psi * s.el);
+  W(&c->D, s.v * s.el);
+  W((void**)&c->Cdev, s.kc * sizeof(double2));
+  W((void**)&c->KCdev, s.kc * sizeof(double2));
+  W((void**)&c->exdev, 2 * sizeof(double));
+  W((void**)&c->partial, 2 * kPartials * sizeof(double));
+  W((void**)&c->flag, 64);
+  for (int i = 0; i < nw; i++) {
+    Want& w = want[i];
     e = cudaMalloc(w.p, w.bytes);
+    if (e == cudaSuccess) e = cudaMemset(*w.p, 0, w.bytes);   // plane padding stays zero
     if (e != cudaSuccess) {
+      if (*w.p) cudaFree(*w.p);
       *w.p = nullptr;
-      cudaGetLastError();  // clear the sticky-free allocation error
+      cudaGetLastError();
       g_create_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
       free_all(c);
       delete c;
       return e == cudaErrorMemoryAllocation ? THC_ERR_OOM : THC_ERR_CUDA;
     }
+  }
+  if (precision == THC_MIXED) {
+    c->ldXT = s.ldXT; c->ldM = s.ldM; c->ldPs = s.ldPs;
+    c->plXn = s.plXn; c->plXT = s.plXT; c->plM = s.plM; c->plPs = s.plPs;
+    c->plBc = s.plBc; c->plBd = s.plBd; c->plBp = s.plBp;
+    const int nk = (int)s.nk, N = d->nbas, n = d->nocc, P = d->nisdf;
+    struct MapReq { TcOperand* op; uint16_t* base; long pl; int rows, cols, ld; };
+    MapReq reqs[] = {
+        {&c->opXT, c->XT_pl, s.plXT, P, 2 * N, s.ldXT},
+        {&c->opPs, c->PsiA_pl, s.plPs, P, 2 * n, s.ldPs},
+        {&c->opM, c->M_pl, s.plM, P, 2 * P, s.ldM},
+        {&c->opXn, c->Xn_pl, s.plXn, N, 2 * P, s.ldM},
+        {&c->opBc, c->Bc_pl, s.plBc, 2 * n, 2 * N, s.ldXT},
+        {&c->opBd, c->Bd_pl, s.plBd, 2 * P, 2 * n, s.ldPs},
+        {&c->opBp, c->Bp_pl, s.plBp, 2 * n, 2 * P, s.ldM},
+    };
+    for (auto& r : reqs)
+      for (int p = 0; p < 3; p++) {
+        e = make_plane_map(r.op->map[p], r.base + p * r.pl, nk, r.rows, r.cols, r.ld);
+        if (e != cudaSuccess) {
+          g_create_error = std::string("cuTensorMapEncodeTiled: ") + cudaGetErrorString(e);
+          free_all(c);
+          delete c;
+          return e == cudaErrorNotSupported ? THC_ERR_UNSUPPORTED : THC_ERR_CUDA;
+        }
+      }
   }
   for (int i = 0; i < 7; i++) {
     e = cudaEventCreate(&c->ev[i]);
@@ -200,10 +266,17 @@ thc_status thc_set_collocation(thc_ctx* c, const double* X) {
   const double2* x = (const double2*)X;
   thc_status st = finite_check(c, x, n);
   if (st != THC_OK) return st;
-  if (c->precision == THC_FP64)
+  if (c->precision == THC_FP64) {
     CKC(c, cudaMemcpyAsync(c->X64, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-  else
+  } else if (c->precision == THC_MIXED_SIMT) {
     CKC(c, convert_z2c(x, c->X32, n, c->stream));
+  } else {
+    const long sb = (long)c->nbas * c->nisdf;
+    CKC(c, split_rows_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->Xn_pl, c->Xn_pl + c->plXn,
+                        c->Xn_pl + 2 * c->plXn, c->ldM, c->stream));
+    CKC(c, split_cols_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->XT_pl, c->XT_pl + c->plXT,
+                        c->XT_pl + 2 * c->plXT, c->ldXT, c->stream));
+  }
   CKC(c, cudaStreamSynchronize(c->stream));
   c->have_x = true;
   return THC_OK;
@@ -282,6 +355,44 @@ static thc_status build_mixed(thc_ctx* c, const double2* C, double2* KC, double*
   return THC_OK;
 }
 
+static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex) {
+  const int nk = c->nk, N = c->nbas, n = c->nocc, P = c->nisdf;
+  const long PP = (long)P * P, Pn = (long)P * n;
+  float2* Psi = (float2*)c->Psi;
+  float2* D = (float2*)c->D;
+  float2* Y = (float2*)c->Y;
+  uint16_t* Bc[3] = {c->Bc_pl, c->Bc_pl + c->plBc, c->Bc_pl + 2 * c->plBc};
+  uint16_t* Bd[3] = {c->Bd_pl, c->Bd_pl + c->plBd, c->Bd_pl + 2 * c->plBd};
+  uint16_t* Bp[3] = {c->Bp_pl, c->Bp_pl + c->plBp, c->Bp_pl + 2 * c->plBp};
+  uint16_t* Pa[3] = {c->PsiA_pl, c->PsiA_pl + c->plPs, c->PsiA_pl + 2 * c->plPs};
+  uint16_t* Mp[3] = {c->M_pl, c->M_pl + c->plM, c->M_pl + 2 * c->plM};
+  cudaStream_t s = c->stream;
+  CKC(c, cudaEventRecord(stage_event(c, 0), s));
+  // S1  Psi = X^T C
+  CKC(c, embed_b(C, true, (long)N * n, n, 1, false, false, nk, N, n, Bc[0], Bc[1], Bc[2], c->ldXT, s));
+  CKC(c, tc_gemm(c->opXT, c->opBc, P, 2 * n, 2 * N, nk, Psi, false, 2 * n, 2 * Pn, c->tc_err, s));
+  CKC(c, cudaEventRecord(stage_event(c, 1), s));
+  // S2  D = Psi Psi^H
+  CKC(c, split_rows_c(Psi, Pn, n, nk, P, n, Pa[0], Pa[1], Pa[2], c->ldPs, s));
+  CKC(c, embed_b(Psi, false, Pn, 1, n, true, false, nk, n, P, Bd[0], Bd[1], Bd[2], c->ldPs, s));
+  CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, D, false, 2 * P, 2 * PP, c->tc_err, s));
+  CKC(c, cudaEventRecord(stage_event(c, 2), s));
+  // S3  M = IDFT(DFT(D) o Vh), written as bf16 planes
+  CKC(c, kconv_c_planes(D, c->Vh32, Mp[0], Mp[1], Mp[2], PP, P, c->ldM, c->n1, c->n2, c->n3, s));
+  CKC(c, cudaEventRecord(stage_event(c, 3), s));
+  // S4a Y = M Psi
+  CKC(c, embed_b(Psi, false, Pn, n, 1, false, false, nk, P, n, Bp[0], Bp[1], Bp[2], c->ldM, s));
+  CKC(c, tc_gemm(c->opM, c->opBp, P, 2 * n, 2 * P, nk, Y, false, 2 * n, 2 * Pn, c->tc_err, s));
+  CKC(c, cudaEventRecord(stage_event(c, 4), s));
+  // S4b KC = conj(X) Y
+  CKC(c, embed_b(Y, false, Pn, n, 1, false, true, nk, P, n, Bp[0], Bp[1], Bp[2], c->ldM, s));
+  CKC(c, tc_gemm(c->opXn, c->opBp, N, 2 * n, 2 * P, nk, KC, true, 2 * n, 2L * N * n, c->tc_err, s));
+  CKC(c, cudaEventRecord(stage_event(c, 5), s));
+  CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
+  CKC(c, cudaEventRecord(stage_event(c, 6), s));
+  return THC_OK;
+}
+
 thc_status thc_build(thc_ctx* c, const double* C, double* KC, double* ex) {
   if (!c || !C || !KC || !ex) return THC_ERR_ARG;
   if (!aligned16(C) || !aligned16(KC) || ((uintptr_t)ex & 7u)) return THC_ERR_ARG;
@@ -290,9 +401,10 @@ thc_status thc_build(thc_ctx* c, const double* C, double* KC, double* ex) {
   const char* b = (const char*)KC;
   if (a < b + kcb && b < a + kcb) return THC_ERR_ARG;  // KC aliases C
   if (!c->have_x || !c->have_v) return THC_ERR_STATE;
-  thc_status st = c->precision == THC_FP64
-                      ? build_fp64(c, (const double2*)C, (double2*)KC, ex)
-                      : build_mixed(c, (const double2*)C, (double2*)KC, ex);
+  thc_status st;
+  if (c->precision == THC_FP64) st = build_fp64(c, (const double2*)C, (double2*)KC, ex);
+  else if (c->precision == THC_MIXED_SIMT) st = build_mixed(c, (const double2*)C, (double2*)KC, ex);
+  else st = build_tc(c, (const double2*)C, (double2*)KC, ex);
   if (st == THC_OK) {
     c->built = true;
     if (c->prof_max > 0 && c->prof_n < c->prof_max) {
@@ -311,7 +423,20 @@ thc_status thc_build_host(thc_ctx* c, const double* C_host, double* KC_host, dou
   if (st != THC_OK) return st;
   CKC(c, cudaMemcpyAsync(KC_host, c->KCdev, kcb, cudaMemcpyDeviceToHost, c->stream));
   CKC(c, cudaMemcpyAsync(ex_host, c->exdev, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return thc_sync(c);
+}
+
+thc_status thc_sync(thc_ctx* c) {
+  if (!c) return THC_ERR_ARG;
   CKC(c, cudaStreamSynchronize(c->stream));
+  if (!c->tc_err) return THC_OK;
+  int h = 0;
+  CKC(c, cudaMemcpy(&h, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    CKC(c, cudaMemset(c->tc_err, 0, sizeof(int)));
+    c->last_error = "device wait timed out, code " + std::to_string(h);
+    return THC_ERR_TIMEOUT;
+  }
   return THC_OK;
 }
 
@@ -321,7 +446,10 @@ thc_status thc_get_intermediate(thc_ctx* c, int which, double* out) {
   const long n = (which == 0 || which == 3) ? (long)c->nk * c->nisdf * c->nocc
                                             : (long)c->nk * c->nisdf * c->nisdf;
   void* src = which == 0 ? c->Psi : which == 1 ? c->D : which == 2 ? c->M : c->Y;
-  if (c->precision == THC_FP64)
+  if (c->precision == THC_MIXED && which == 2)
+    CKC(c, combine_planes(c->M_pl, c->M_pl + c->plM, c->M_pl + 2 * c->plM, c->nk, c->nisdf, c->nisdf,
+                          c->ldM, (double2*)out, c->stream));
+  else if (c->precision == THC_FP64)
     CKC(c, cudaMemcpyAsync(out, src, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
   else
     CKC(c, convert_c2z((const float2*)src, (double2*)out, n, c->stream));
@@ -375,7 +503,10 @@ thc_status thc_profile_end(thc_ctx* c, float mean_ms[6], int* nbuilds) {
 
 thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   if (!c || !launches) return THC_ERR_ARG;
-  *launches = 7;  // S1, S2, S3, S4a, S4b, E_x partial, E_x final
+  // FP64 and CUDA-core forms: S1, S2, S3, S4a, S4b, E_x partial, E_x final.
+  // Tensor-core form adds the operand preparation: 2 (S1) + 3 (S2) + 1 (S3)
+  // + 2 (S4a) + 2 (S4b) + 2 (E_x).
+  *launches = c->precision == THC_MIXED ? 12 : 7;
   return THC_OK;
 }
 

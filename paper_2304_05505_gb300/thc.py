@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(PKG, "libthc.so")
 
 THC_FP64 = 0
 THC_MIXED = 1
-PRECISIONS = {"fp64": THC_FP64, "mixed": THC_MIXED}
+THC_MIXED_SIMT = 2
+PRECISIONS = {"fp64": THC_FP64, "mixed": THC_MIXED, "mixed_simt": THC_MIXED_SIMT}
 
 STATUS = {0: "THC_OK", 1: "THC_ERR_ARG", 2: "THC_ERR_OOM", 3: "THC_ERR_CUDA",
           4: "THC_ERR_NONFINITE", 5: "THC_ERR_TIMEOUT", 6: "THC_ERR_STATE",
@@ -27,7 +28,7 @@ STATUS = {0: "THC_OK", 1: "THC_ERR_ARG", 2: "THC_ERR_OOM", 3: "THC_ERR_CUDA",
 EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_kernel",
            "thc_build", "thc_build_host", "thc_get_intermediate", "thc_stage_times",
            "thc_launches_per_build", "thc_destroy", "thc_status_string", "thc_last_error",
-           "thc_profile_begin", "thc_profile_end"]
+           "thc_profile_begin", "thc_profile_end", "thc_sync"]
 
 
 class ThcDims(ctypes.Structure):
@@ -66,6 +67,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_profile_begin.argtypes = [vp, ip]
     lib.thc_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]
     lib.thc_destroy.argtypes = [vp]
+    lib.thc_sync.argtypes = [vp]
     lib.thc_status_string.argtypes = [ip]
     lib.thc_status_string.restype = ctypes.c_char_p
     lib.thc_last_error.argtypes = [vp]
@@ -195,6 +197,10 @@ def thc_launches_per_build(ctx) -> int:
     return int(n.value)
 
 
+def thc_sync(ctx) -> None:
+    _check(load().thc_sync(ctx), "thc_sync", ctx)
+
+
 def thc_destroy(ctx) -> None:
     _check(load().thc_destroy(ctx), "thc_destroy")
 
@@ -240,6 +246,9 @@ class ExchangeBuild:
             ex = t.empty(2, dtype=t.float64, device=self.device)
         thc_build(self.ctx, C, KC, ex)
         return KC, ex
+
+    def sync(self):
+        thc_sync(self.ctx)
 
     def intermediate(self, which: int):
         t = self.torch

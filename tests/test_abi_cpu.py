@@ -47,14 +47,21 @@ def test_status_strings(lib):
 
 
 def test_memory_bytes_arithmetic():
+    """Device bytes a context holds, counted from the array shapes."""
     d = dict(n1=4, n2=4, n3=4, nbas=432, nocc=60, nisdf=1200)
     nk, N, n, P = 64, 432, 60, 1200
-    got = thc.thc_memory_bytes(d, thc.THC_MIXED)
-    expect = 8 * (nk * N * P + nk * P * P + 2 * nk * P * n + 2 * nk * P * P) \
-        + 2 * 16 * nk * N * n + 16 + 2 * 1216 * 8 + 64
-    assert got == expect
-    got64 = thc.thc_memory_bytes(d, thc.THC_FP64)
-    assert got64 > got
+    common = 2 * 16 * nk * N * n + 16 + 2 * 1216 * 8 + 64 + 64
+    simt = 8 * (nk * N * P + nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + common
+    assert thc.thc_memory_bytes(d, thc.THC_MIXED_SIMT) == simt
+    fp64 = 16 * (nk * N * P + nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + common
+    assert thc.thc_memory_bytes(d, thc.THC_FP64) == fp64
+
+    def pad8(x):
+        return (x + 7) // 8 * 8
+    planes = nk * (N * pad8(2 * P) + P * pad8(2 * N) + P * pad8(2 * P) + P * pad8(2 * n)
+                   + 2 * n * pad8(2 * N) + 2 * P * pad8(2 * n) + 2 * n * pad8(2 * P))
+    tc = 8 * (nk * P * P + 2 * nk * P * n + nk * P * P) + 3 * 2 * planes + common
+    assert thc.thc_memory_bytes(d, thc.THC_MIXED) == tc
 
 
 @pytest.mark.parametrize("bad", [

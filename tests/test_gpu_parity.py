@@ -42,7 +42,7 @@ def gpu_build(torch, X, C, V, mesh, precision, keep=False):
         eb.set_collocation(X)
         eb.set_kernel(V)
         KC, ex = eb.build(C)
-        torch.cuda.synchronize()
+        eb.sync()      # raises on a device-side wait that gave up
         out = dict(KC=KC.cpu().numpy(), Ex=float(ex[0]), Ex_imag=float(ex[1]))
         if keep:
             for i, nm in enumerate(["Psi", "D", "M", "Y"]):
@@ -80,7 +80,10 @@ RANDOM_CASES = [
 ]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+PRECISIONS = ["fp64", "mixed", "mixed_simt"]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("mesh,nbas,nocc,nisdf", RANDOM_CASES)
 def test_random_parity(torch_cuda, precision, mesh, nbas, nocc, nisdf):
     r = cells.random_problem(mesh, nbas=nbas, nocc=nocc, nisdf=nisdf, seed=nbas + nisdf)
@@ -89,7 +92,7 @@ def test_random_parity(torch_cuda, precision, mesh, nbas, nocc, nisdf):
     assert_close(ref, got, precision)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("mesh", [(2, 2, 2), (3, 3, 3)])
 def test_toy_cell_parity(torch_cuda, precision, mesh):
     p = cells.make_problem("C0", mesh=mesh)
@@ -99,7 +102,7 @@ def test_toy_cell_parity(torch_cuda, precision, mesh):
     assert got["Ex"] < 0
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_intermediates(torch_cuda, precision):
     r = cells.random_problem((3, 2, 2), nbas=21, nocc=4, nisdf=70, seed=9)
     ref = O.build(r["X"], r["C"], r["V"], r["mesh"], keep=True)
@@ -117,7 +120,7 @@ def c1(torch_cuda):
     return p, ref
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_benzene_3x3x3_parity(torch_cuda, c1, precision):
     """Benzene-shaped cell, 3x3x3 k, N_P = 600, n = 60, N = 432: full size."""
     p, ref = c1
@@ -132,13 +135,14 @@ def c2(torch_cuda):
     return p, ref
 
 
-def test_benzene_4x4x4_mixed_target(torch_cuda, c2):
+@pytest.mark.parametrize("precision", ["mixed", "mixed_simt"])
+def test_benzene_4x4x4_mixed_target(torch_cuda, c2, precision):
     """The target configuration: 4x4x4 k, N_P = 1200, mixed precision,
     every output compared; the launch configuration the bench times."""
     p, ref = c2
-    got = gpu_build(torch_cuda, p.X, p.C, p.V, p.cell.mesh, "mixed")
+    got = gpu_build(torch_cuda, p.X, p.C, p.V, p.cell.mesh, precision)
     dkc, dex = assert_close(ref, got, "mixed", target=True)
-    print(f"mixed 4x4x4: max|dKC| = {dkc:.3e}, |dE_x| = {dex:.3e}, E_x = {ref['Ex']:.9f}")
+    print(f"{precision} 4x4x4: max|dKC| = {dkc:.3e}, |dE_x| = {dex:.3e}, E_x = {ref['Ex']:.9f}")
 
 
 def test_benzene_4x4x4_fp64(torch_cuda, c2):
@@ -160,7 +164,7 @@ def test_build_host_matches_build(torch_cuda):
     torch = torch_cuda
     r = cells.random_problem((2, 2, 1), nbas=12, nocc=3, nisdf=40, seed=4)
     dims = dict(n1=2, n2=2, n3=1, nbas=12, nocc=3, nisdf=40)
-    for prec in ("fp64", "mixed"):
+    for prec in PRECISIONS:
         eb = thc.ExchangeBuild(dims, prec)
         eb.set_collocation(r["X"])
         eb.set_kernel(r["V"])
