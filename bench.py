@@ -421,8 +421,8 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD,
-                       "precision": "mixed: tcgen05 bf16 GEMMs on 3-plane split operands (24-bit), FP32 "
-                                    "accumulation with float-float drain, FP32 k-convolution, FP64 E_x sum",
+                       "precision": "mixed: S1/S2/S4b tcgen05 bf16 GEMMs on 4-slice fixed-point operands "
+                                    "(exact leading sums), S3 FP32, S4a FP32 compensated, E_x FP64 sum",
                        "l2": "inputs larger than L2 (prepared kernel 737 MB, X 265 MB complex64)",
                        "parallelism": f"{world} independent builds (one per GPU)"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,

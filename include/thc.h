@@ -60,10 +60,11 @@ typedef enum {
 
 typedef enum {
   THC_FP64 = 0,            /* every step in FP64 on CUDA cores */
-  THC_MIXED = 1,           /* S1, S2, S4a, S4b on tensor cores (tcgen05) with each
-                              operand split into three bf16 planes (24 significant
-                              bits) and FP32 accumulation, the leading term drained
-                              into float-float sums; S3 in FP32; E_x summed in FP64 */
+  THC_MIXED = 1,           /* S1, S2, S4b on tensor cores (tcgen05): each operand
+                              row scaled by a power of two and cut into four 8-bit
+                              fixed-point slices held in bf16, the leading products
+                              summed exactly; S3 in FP32; S4a on CUDA cores with
+                              compensated FP32 sums; E_x summed in FP64 */
   THC_MIXED_SIMT = 2       /* the same precision on CUDA cores: FP32 operands,
                               float-float compensated sums in S1, S4a, S4b */
 } thc_precision;

@@ -22,8 +22,6 @@
 
 #include <math.h>
 
-#include <cuda_bf16.h>
-
 namespace {
 
 constexpr int MAXL = 8;
@@ -157,44 +155,6 @@ __global__ void kconv_kernel(const typename cplx<R>::type* __restrict__ D,
     for (int k = 0; k < nk; k++) M[(long)k * npq + e] = x[(long)k * T];
 }
 
-// As kconv_kernel<float>, but M is written as three bf16 planes (the split
-// operand of the tensor-core S4a GEMM): plane[p][k][row][2 col + d] with
-// row = e / ncols, col = e % ncols.
-__global__ void kconv_planes_kernel(const float2* __restrict__ D, const float2* __restrict__ Vh,
-                                    uint16_t* __restrict__ p0, uint16_t* __restrict__ p1,
-                                    uint16_t* __restrict__ p2, long npq, int ncols, int ldp, Twiddles tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* buf = reinterpret_cast<float2*>(smem_raw);
-  const int T = blockDim.x, tid = threadIdx.x;
-  const int nk = tw.n[0] * tw.n[1] * tw.n[2];
-  const long e = (long)blockIdx.x * T + tid;
-  const bool ok = e < npq;
-  float2* x = buf + tid;
-  for (int k = 0; k < nk; k++) x[(long)k * T] = ok ? D[(long)k * npq + e] : make_float2(0.f, 0.f);
-  dft3<float>(x, T, tw, -1);
-  for (int a = 0; a < nk; a++) {
-    float2 v = ok ? Vh[(long)a * npq + e] : make_float2(0.f, 0.f);
-    x[(long)a * T] = cmul(x[(long)a * T], v);
-  }
-  dft3<float>(x, T, tw, +1);
-  if (!ok) return;
-  const long nrows = npq / ncols;
-  const long row = e / ncols, col = e % ncols;
-  for (int k = 0; k < nk; k++) {
-    const float2 v = x[(long)k * T];
-    const long off = ((long)k * nrows + row) * ldp + 2 * col;
-    __nv_bfloat16 r0 = __float2bfloat16_rn(v.x), i0 = __float2bfloat16_rn(v.y);
-    float rr = v.x - __bfloat162float(r0), ri = v.y - __bfloat162float(i0);
-    __nv_bfloat16 r1 = __float2bfloat16_rn(rr), i1 = __float2bfloat16_rn(ri);
-    rr -= __bfloat162float(r1);
-    ri -= __bfloat162float(i1);
-    __nv_bfloat16 r2 = __float2bfloat16_rn(rr), i2 = __float2bfloat16_rn(ri);
-    *reinterpret_cast<uint32_t*>(p0 + off) = (uint32_t)__bfloat16_as_ushort(r0) | ((uint32_t)__bfloat16_as_ushort(i0) << 16);
-    *reinterpret_cast<uint32_t*>(p1 + off) = (uint32_t)__bfloat16_as_ushort(r1) | ((uint32_t)__bfloat16_as_ushort(i1) << 16);
-    *reinterpret_cast<uint32_t*>(p2 + off) = (uint32_t)__bfloat16_as_ushort(r2) | ((uint32_t)__bfloat16_as_ushort(i2) << 16);
-  }
-}
-
 // Vh[a] = (1/N_k) sum_q w^{+a.q} V[q], FP64; stored FP64 and/or FP32.
 __global__ void prepare_kernel(const double2* __restrict__ V, double2* __restrict__ Vh64,
                                float2* __restrict__ Vh32, long npq, Twiddles tw) {
@@ -294,16 +254,3 @@ cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long
   return cudaGetLastError();
 }
 
-cudaError_t kconv_c_planes(const float2* D, const float2* Vh, uint16_t* p0, uint16_t* p1, uint16_t* p2,
-                           long npq, int ncols, int ldp, int n1, int n2, int n3, cudaStream_t s) {
-  const int nk = n1 * n2 * n3;
-  const int T = pick_threads(nk, sizeof(float2));
-  const size_t sm = (size_t)T * nk * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(kconv_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
-  if (e != cudaSuccess) return e;
-  const long blocks = (npq + T - 1) / T;
-  kconv_planes_kernel<<<(unsigned)blocks, T, sm, s>>>(D, Vh, p0, p1, p2, npq, ncols, ldp,
-                                                      make_twiddles(n1, n2, n3));
-  return cudaGetLastError();
-}

@@ -4,41 +4,56 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-// Three bf16 planes of one GEMM operand, each a TMA tensor map over
-// [batch][rows][ld] (64-element K boxes, 128 rows, 128B swizzle).
+// Four bf16 fixed-point slices of one GEMM operand, each a TMA tensor map
+// over [batch][rows][ld] (32-element K boxes, 128 rows, 64B swizzle).
 struct TcOperand {
-  alignas(64) unsigned char map[3][128];
+  alignas(64) unsigned char map[4][128];
 };
 
 // Encode the map of one bf16 plane: `rows` x `cols` valid elements per batch,
 // leading dimension `ld` elements (ld * 2 bytes must be a multiple of 16).
 cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows, int cols, int ld);
 
-// out[b][m][n] (n < Nr real columns, interleaved complex) = A'[b] B'[b]^T with
-// A' = A planes (M rows, Kr real K) and B' = B planes (Nr rows, Kr real K).
-// FP32 output, or FP64 output when out_f64.  `err` receives a nonzero code if a
-// device wait gave up.
-cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch, void* out,
-                    bool out_f64, long ldo, long sbo, int* err, cudaStream_t s);
+// out[b][m][n] (n < Nr real columns, interleaved complex) = A'[b] B'[b]^T for
+// sliced operands: A' has M rows with exponents eA[b * seA + m], B' has Nr rows
+// whose pair (2j, 2j + 1) shares the exponent eB[b * seB + j]; Kr real K.
+// FP32 output, or FP64 output when out_f64.  `err` receives a nonzero code if
+// a device wait gave up.
+cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
+                    const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
+                    long sbo, int* err, cudaStream_t s);
 
-// Split a complex matrix into three bf16 planes: planes[p][b][r][2c + d] of
-// src[b][r][c] (rows x cols, leading dimension lds complex); ldp = plane ld.
-cudaError_t split_rows_z(const double2* src, long sbs, int lds, int batch, int rows, int cols,
-                         uint16_t* p0, uint16_t* p1, uint16_t* p2,
-                         int ldp, cudaStream_t s);
-cudaError_t split_rows_c(const float2* src, long sbs, int lds, int batch, int rows, int cols,
-                         uint16_t* p0, uint16_t* p1, uint16_t* p2,
-                         int ldp, cudaStream_t s);
-// Transposed split: planes[p][b][c][2r + d] of src[b][r][c].
-cudaError_t split_cols_z(const double2* src, long sbs, int lds, int batch, int rows, int cols,
-                         uint16_t* p0, uint16_t* p1, uint16_t* p2,
-                         int ldp, cudaStream_t s);
+// Row exponents of src[b][r][0..cols) (contiguous rows): e[b * rows + r], the
+// smallest e with max_c max(|re|, |im|) < 2^e (0 for a zero row).
+cudaError_t row_exponents_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
+                            cudaStream_t s);
+cudaError_t row_exponents_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
+                            cudaStream_t s);
+// Column exponents: e[b * cols + c] over r of src[b][r][c].
+cudaError_t col_exponents_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
+                            cudaStream_t s);
+cudaError_t col_exponents_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
+                            cudaStream_t s);
+
+// Fixed-point slices of src[b][r][c] into planes[p][b][r][2c + d] (plane p at
+// planes + p * plane elements, leading dimension ldp) with row exponents e[b][r].
+cudaError_t slice_rows_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
+                         uint16_t* planes, long plane, int ldp, cudaStream_t s);
+cudaError_t slice_rows_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
+                         uint16_t* planes, long plane, int ldp, cudaStream_t s);
+// Transposed: planes[p][b][c][2r + d] of src[b][r][c] with column exponents e[b][c].
+cudaError_t slice_cols_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
+                         uint16_t* planes, long plane, int ldp, cudaStream_t s);
 
 // Embedded B operand planes of a complex B(k, j) (K x J per batch):
-//   planes[p][b][2j + c][2k + d] = split_p(E_cd(B(k, j)))
-// with E = [[Br, -Bi], [Bi, Br]] (conj_a = 0) or [[Br, Bi], [Bi, -Br]]
-// (conj_a = 1).  B(k, j) = src[b * sbs + k * ldk + j * ldj], conjugated if
-// conj_src.  The source is complex128 (src_f64) or complex64.
-cudaError_t embed_b(const void* src, bool src_f64, long sbs, long ldk, long ldj, bool conj_src,
-                    bool conj_a, int batch, int K, int J, uint16_t* p0,
-                    uint16_t* p1, uint16_t* p2, int ldp, cudaStream_t s);
+//   planes[p][b][2j + c][2k + d] = slice_p(E_cd(B(k, j)))  with row exponent e[b][j]
+// E = [[Br, -Bi], [Bi, Br]] (conj_a = 0) or [[Br, Bi], [Bi, -Br]] (conj_a = 1).
+// B(k, j) = src[b * sbs + k * ldk + j * ldj], conjugated if conj_src; the
+// source is complex128 (src_f64) or complex64.
+cudaError_t embed_b(const void* src, bool src_f64, long sbs, long ldk, long ldj, bool conj_src, bool conj_a,
+                    int batch, int K, int J, const int* e, uint16_t* planes, long plane, int ldp,
+                    cudaStream_t s);
+
+// out[b][r][c] = 2^(e[b][r] - 7) (P0 + P1 + P2 + P3) at [b][r][2c + d], for tests.
+cudaError_t combine_planes(const uint16_t* planes, long plane, const int* e, int batch, int rows, int cols,
+                           int ldp, double2* out, cudaStream_t s);

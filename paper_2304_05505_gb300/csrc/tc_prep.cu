@@ -1,7 +1,14 @@
-// Operand preparation of the tensor-core GEMMs: splitting complex matrices
-// into three bf16 planes (x = x0 + x1 + x2, each the bf16 rounding of what
-// the previous planes left) and building the real embedding of the thin B
-// operand.  See tc_gemm.cu for the layout the planes feed.
+// Operand preparation of the tensor-core GEMMs (tc_gemm.cu): fixed-point
+// slicing of complex matrices into four bf16 planes, and the real embedding
+// of the thin B operand.
+//
+// A row r with exponent e_r (max |re|, |im| over the row < 2^e_r) is written
+// as x = 2^(e_r - 7) (P0 + P1 + P2 + P3) with P_s = 2^(-8 s) S_s and S_s the
+// integers
+//   y0 = 2^(7 - e_r) x,  S0 = rint(y0),  y_{s+1} = 2^8 (y_s - S_s),  S_{s+1} = rint(y_{s+1})
+// each in [-128, 128].  Every step is exact in the working precision (FP64 for
+// the static collocation X, FP32 for per-build operands), so the planes carry
+// the first 32 bits of x relative to its row scale.
 #include "thc_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -9,53 +16,78 @@
 
 namespace {
 
-__device__ __forceinline__ void split3(float x, uint16_t& a, uint16_t& b, uint16_t& c) {
-  __nv_bfloat16 h0 = __float2bfloat16_rn(x);
-  float r = x - __bfloat162float(h0);
-  __nv_bfloat16 h1 = __float2bfloat16_rn(r);
-  r -= __bfloat162float(h1);
-  __nv_bfloat16 h2 = __float2bfloat16_rn(r);
-  a = __bfloat16_as_ushort(h0);
-  b = __bfloat16_as_ushort(h1);
-  c = __bfloat16_as_ushort(h2);
+__device__ __forceinline__ void slice4(double x, int e, uint16_t* s) {
+  double y = ldexp(x, 7 - e);
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    const double sp = rint(y);
+    s[p] = __bfloat16_as_ushort(__float2bfloat16_rn(ldexpf((float)sp, -8 * p)));   // exact, |sp| <= 128
+    y = (y - sp) * 256.0;
+  }
 }
 
-// From FP64: the residuals are formed in FP64 so the planes carry the first
-// 24 significant bits of the double, not of its FP32 rounding.
-__device__ __forceinline__ void split3(double x, uint16_t& a, uint16_t& b, uint16_t& c) {
-  __nv_bfloat16 h0 = __double2bfloat16(x);
-  double r = x - (double)__bfloat162float(h0);
-  __nv_bfloat16 h1 = __double2bfloat16(r);
-  r -= (double)__bfloat162float(h1);
-  __nv_bfloat16 h2 = __double2bfloat16(r);
-  a = __bfloat16_as_ushort(h0);
-  b = __bfloat16_as_ushort(h1);
-  c = __bfloat16_as_ushort(h2);
+__device__ __forceinline__ void slice4(float x, int e, uint16_t* s) {
+  float y = ldexpf(x, 7 - e);
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    const float sp = rintf(y);
+    s[p] = __bfloat16_as_ushort(__float2bfloat16_rn(ldexpf(sp, -8 * p)));
+    y = (y - sp) * 256.0f;
+  }
 }
 
-__device__ __forceinline__ void store_pair(uint16_t* p0, uint16_t* p1, uint16_t* p2, long off, float re,
-                                           float im) {
-  uint16_t a0, a1, a2, b0, b1, b2;
-  split3(re, a0, a1, a2);
-  split3(im, b0, b1, b2);
-  *reinterpret_cast<uint32_t*>(p0 + off) = (uint32_t)a0 | ((uint32_t)b0 << 16);
-  *reinterpret_cast<uint32_t*>(p1 + off) = (uint32_t)a1 | ((uint32_t)b1 << 16);
-  *reinterpret_cast<uint32_t*>(p2 + off) = (uint32_t)a2 | ((uint32_t)b2 << 16);
+__device__ __forceinline__ int row_exponent(double m) {
+  if (!(m > 0.0)) return 0;
+  int e;
+  frexp(m, &e);
+  return e;   // m < 2^e
 }
 
-__device__ __forceinline__ void store_pair(uint16_t* p0, uint16_t* p1, uint16_t* p2, long off, double re,
-                                           double im) {
-  uint16_t a0, a1, a2, b0, b1, b2;
-  split3(re, a0, a1, a2);
-  split3(im, b0, b1, b2);
-  *reinterpret_cast<uint32_t*>(p0 + off) = (uint32_t)a0 | ((uint32_t)b0 << 16);
-  *reinterpret_cast<uint32_t*>(p1 + off) = (uint32_t)a1 | ((uint32_t)b1 << 16);
-  *reinterpret_cast<uint32_t*>(p2 + off) = (uint32_t)a2 | ((uint32_t)b2 << 16);
+__device__ __forceinline__ void store4(uint16_t* base, long plane, long off, const uint16_t* re,
+                                       const uint16_t* im) {
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+    *reinterpret_cast<uint32_t*>(base + p * plane + off) = (uint32_t)re[p] | ((uint32_t)im[p] << 16);
 }
 
 template <typename CT>
-__global__ void split_rows_kernel(const CT* __restrict__ src, long sbs, int lds, int batch, int rows,
-                                  int cols, uint16_t* p0, uint16_t* p1, uint16_t* p2, int ldp) {
+__device__ __forceinline__ double cmax(CT v) {
+  return fmax(fabs((double)v.x), fabs((double)v.y));
+}
+
+// Exponent of each contiguous row: e[b * rows + r] over src[b][r][0..cols).
+// One warp per row.
+template <typename CT>
+__global__ void rowexp_kernel(const CT* __restrict__ src, long sbs, int lds, int batch, int rows, int cols,
+                              int* __restrict__ e) {
+  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (long)batch * rows) return;
+  const int b = (int)(w / rows), r = (int)(w % rows);
+  const CT* p = src + (long)b * sbs + (long)r * lds;
+  double m = 0.0;
+  for (int c = lane; c < cols; c += 32) m = fmax(m, cmax(p[c]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) e[w] = row_exponent(m);
+}
+
+// Exponent of each column: e[b * cols + c] = max over r of src[b][r][c].
+template <typename CT>
+__global__ void colexp_kernel(const CT* __restrict__ src, long sbs, int lds, int batch, int rows, int cols,
+                              int* __restrict__ e) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)batch * cols) return;
+  const int b = (int)(i / cols), c = (int)(i % cols);
+  const CT* p = src + (long)b * sbs + c;
+  double m = 0.0;
+  for (int r = 0; r < rows; r++) m = fmax(m, cmax(p[(long)r * lds]));
+  e[i] = row_exponent(m);
+}
+
+// planes[p][b][r][2c + d] of src[b][r][c] with row exponents e[b][r].
+template <typename CT, typename R>
+__global__ void slice_rows_kernel(const CT* __restrict__ src, long sbs, int lds, int batch, int rows, int cols,
+                                  const int* __restrict__ e, uint16_t* planes, long plane, int ldp) {
   const long total = (long)batch * rows * cols;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int c = (int)(i % cols);
@@ -63,13 +95,18 @@ __global__ void split_rows_kernel(const CT* __restrict__ src, long sbs, int lds,
     const int r = (int)(br % rows);
     const int b = (int)(br / rows);
     const CT v = src[(long)b * sbs + (long)r * lds + c];
-    store_pair(p0, p1, p2, ((long)b * rows + r) * ldp + 2L * c, v.x, v.y);
+    const int ex = e[br];
+    uint16_t sr[4], si[4];
+    slice4((R)v.x, ex, sr);
+    slice4((R)v.y, ex, si);
+    store4(planes, plane, br * ldp + 2L * c, sr, si);
   }
 }
 
-// planes[b][c][2r + d] of src[b][r][c]; 32 x 32 tiles through shared memory.
-__global__ void split_cols_kernel(const double2* __restrict__ src, long sbs, int lds, int rows, int cols,
-                                  uint16_t* p0, uint16_t* p1, uint16_t* p2, int ldp) {
+// planes[p][b][c][2r + d] of src[b][r][c] (the transpose), column exponents
+// e[b][c]; 32 x 32 tiles through shared memory.
+__global__ void slice_cols_kernel(const double2* __restrict__ src, long sbs, int lds, int rows, int cols,
+                                  const int* __restrict__ e, uint16_t* planes, long plane, int ldp) {
   __shared__ double2 t[32][33];
   const int b = blockIdx.z;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -82,15 +119,23 @@ __global__ void split_cols_kernel(const double2* __restrict__ src, long sbs, int
     const int c = c0 + y, r = r0 + threadIdx.x;
     if (c < cols && r < rows) {
       const double2 v = t[threadIdx.x][y];
-      store_pair(p0, p1, p2, ((long)b * cols + c) * ldp + 2L * r, v.x, v.y);
+      const int ex = e[(long)b * cols + c];
+      uint16_t sr[4], si[4];
+      slice4(v.x, ex, sr);
+      slice4(v.y, ex, si);
+      store4(planes, plane, ((long)b * cols + c) * ldp + 2L * r, sr, si);
     }
   }
 }
 
-template <typename CT>
+// Embedded B planes of B(k, j) = src[b*sbs + k*ldk + j*ldj] (conjugated if
+// conj_src), row exponents e[b][j]:
+//   planes[p][b][2j + c][2k + d] = slice_p(E_cd(B(k, j)))
+// E = [[Br, -Bi], [Bi, Br]] (conj_a = 0) or [[Br, Bi], [Bi, -Br]] (conj_a = 1).
+template <typename CT, typename R>
 __global__ void embed_kernel(const CT* __restrict__ src, long sbs, long ldk, long ldj, bool conj_src,
-                             bool conj_a, int batch, int K, int J, uint16_t* p0, uint16_t* p1, uint16_t* p2,
-                             int ldp) {
+                             bool conj_a, int batch, int K, int J, const int* __restrict__ e, uint16_t* planes,
+                             long plane, int ldp) {
   const long total = (long)batch * J * K;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int k = (int)(i % K);
@@ -98,34 +143,22 @@ __global__ void embed_kernel(const CT* __restrict__ src, long sbs, long ldk, lon
     const int j = (int)(bj % J);
     const int b = (int)(bj / J);
     const CT v = src[(long)b * sbs + (long)k * ldk + (long)j * ldj];
-    const float br = (float)v.x;
-    const float bi = conj_src ? -(float)v.y : (float)v.y;
+    const R br = (R)v.x;
+    const R bi = conj_src ? -(R)v.y : (R)v.y;
+    const int ex = e[bj];
     const long row0 = ((long)b * 2 * J + 2L * j) * ldp + 2L * k;
-    const long row1 = row0 + ldp;
+    uint16_t s_br[4], s_bi[4], s_nbr[4], s_nbi[4];
+    slice4(br, ex, s_br);
+    slice4(bi, ex, s_bi);
+    slice4(-br, ex, s_nbr);
+    slice4(-bi, ex, s_nbi);
     if (!conj_a) {
-      store_pair(p0, p1, p2, row0, br, -bi);
-      store_pair(p0, p1, p2, row1, bi, br);
+      store4(planes, plane, row0, s_br, s_nbi);
+      store4(planes, plane, row0 + ldp, s_bi, s_br);
     } else {
-      store_pair(p0, p1, p2, row0, br, bi);
-      store_pair(p0, p1, p2, row1, bi, -br);
+      store4(planes, plane, row0, s_br, s_bi);
+      store4(planes, plane, row0 + ldp, s_bi, s_nbr);
     }
-  }
-}
-
-__global__ void combine_kernel(const uint16_t* p0, const uint16_t* p1, const uint16_t* p2, int batch, int rows,
-                               int cols, int ldp, double2* out) {
-  const long total = (long)batch * rows * cols;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % cols);
-    const long br = i / cols;
-    const long off = br * ldp + 2L * c;
-    double re = 0.0, im = 0.0;
-    const uint16_t* ps[3] = {p0, p1, p2};
-    for (int p = 0; p < 3; p++) {
-      re += (double)__bfloat162float(__ushort_as_bfloat16(ps[p][off]));
-      im += (double)__bfloat162float(__ushort_as_bfloat16(ps[p][off + 1]));
-    }
-    out[i] = make_double2(re, im);
   }
 }
 
@@ -137,41 +170,86 @@ unsigned grid1(long n) {
 
 }  // namespace
 
-cudaError_t split_rows_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, uint16_t* p0,
-                         uint16_t* p1, uint16_t* p2, int ldp, cudaStream_t s) {
-  split_rows_kernel<double2><<<grid1((long)batch * rows * cols), 256, 0, s>>>(src, sbs, lds, batch, rows, cols,
-                                                                              p0, p1, p2, ldp);
+cudaError_t row_exponents_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
+                            cudaStream_t s) {
+  const long warps = (long)batch * rows;
+  rowexp_kernel<double2><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(src, sbs, lds, batch, rows, cols, e);
   return cudaGetLastError();
 }
 
-cudaError_t split_rows_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, uint16_t* p0,
-                         uint16_t* p1, uint16_t* p2, int ldp, cudaStream_t s) {
-  split_rows_kernel<float2><<<grid1((long)batch * rows * cols), 256, 0, s>>>(src, sbs, lds, batch, rows, cols,
-                                                                             p0, p1, p2, ldp);
+cudaError_t row_exponents_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
+                            cudaStream_t s) {
+  const long warps = (long)batch * rows;
+  rowexp_kernel<float2><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(src, sbs, lds, batch, rows, cols, e);
   return cudaGetLastError();
 }
 
-cudaError_t split_cols_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, uint16_t* p0,
-                         uint16_t* p1, uint16_t* p2, int ldp, cudaStream_t s) {
+cudaError_t col_exponents_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
+                            cudaStream_t s) {
+  const long n = (long)batch * cols;
+  colexp_kernel<double2><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(src, sbs, lds, batch, rows, cols, e);
+  return cudaGetLastError();
+}
+
+cudaError_t col_exponents_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
+                            cudaStream_t s) {
+  const long n = (long)batch * cols;
+  colexp_kernel<float2><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(src, sbs, lds, batch, rows, cols, e);
+  return cudaGetLastError();
+}
+
+cudaError_t slice_rows_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
+                         uint16_t* planes, long plane, int ldp, cudaStream_t s) {
+  slice_rows_kernel<double2, double><<<grid1((long)batch * rows * cols), 256, 0, s>>>(
+      src, sbs, lds, batch, rows, cols, e, planes, plane, ldp);
+  return cudaGetLastError();
+}
+
+cudaError_t slice_rows_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
+                         uint16_t* planes, long plane, int ldp, cudaStream_t s) {
+  slice_rows_kernel<float2, float><<<grid1((long)batch * rows * cols), 256, 0, s>>>(
+      src, sbs, lds, batch, rows, cols, e, planes, plane, ldp);
+  return cudaGetLastError();
+}
+
+cudaError_t slice_cols_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
+                         uint16_t* planes, long plane, int ldp, cudaStream_t s) {
   dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch);
-  split_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(src, sbs, lds, rows, cols, p0, p1, p2, ldp);
+  slice_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(src, sbs, lds, rows, cols, e, planes, plane, ldp);
   return cudaGetLastError();
 }
 
 cudaError_t embed_b(const void* src, bool src_f64, long sbs, long ldk, long ldj, bool conj_src, bool conj_a,
-                    int batch, int K, int J, uint16_t* p0, uint16_t* p1, uint16_t* p2, int ldp, cudaStream_t s) {
+                    int batch, int K, int J, const int* e, uint16_t* planes, long plane, int ldp,
+                    cudaStream_t s) {
   const long n = (long)batch * J * K;
   if (src_f64)
-    embed_kernel<double2><<<grid1(n), 256, 0, s>>>((const double2*)src, sbs, ldk, ldj, conj_src, conj_a, batch,
-                                                   K, J, p0, p1, p2, ldp);
+    embed_kernel<double2, double><<<grid1(n), 256, 0, s>>>((const double2*)src, sbs, ldk, ldj, conj_src, conj_a, batch,
+                                                   K, J, e, planes, plane, ldp);
   else
-    embed_kernel<float2><<<grid1(n), 256, 0, s>>>((const float2*)src, sbs, ldk, ldj, conj_src, conj_a, batch, K,
-                                                  J, p0, p1, p2, ldp);
+    embed_kernel<float2, float><<<grid1(n), 256, 0, s>>>((const float2*)src, sbs, ldk, ldj, conj_src, conj_a, batch, K,
+                                                  J, e, planes, plane, ldp);
   return cudaGetLastError();
 }
 
-cudaError_t combine_planes(const uint16_t* p0, const uint16_t* p1, const uint16_t* p2, int batch, int rows,
-                           int cols, int ldp, double2* out, cudaStream_t s) {
-  combine_kernel<<<grid1((long)batch * rows * cols), 256, 0, s>>>(p0, p1, p2, batch, rows, cols, ldp, out);
+__global__ void combine_kernel(const uint16_t* planes, long plane, const int* e, int batch, int rows, int cols,
+                               int ldp, double2* out) {
+  const long total = (long)batch * rows * cols;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % cols);
+    const long br = i / cols;
+    const long off = br * ldp + 2L * c;
+    double re = 0.0, im = 0.0;
+    for (int p = 0; p < 4; p++) {
+      re += (double)__bfloat162float(__ushort_as_bfloat16(planes[p * plane + off]));
+      im += (double)__bfloat162float(__ushort_as_bfloat16(planes[p * plane + off + 1]));
+    }
+    out[i] = make_double2(ldexp(re, e[br] - 7), ldexp(im, e[br] - 7));
+  }
+}
+
+cudaError_t combine_planes(const uint16_t* planes, long plane, const int* e, int batch, int rows, int cols,
+                           int ldp, double2* out, cudaStream_t s) {
+  combine_kernel<<<grid1((long)batch * rows * cols), 256, 0, s>>>(planes, plane, e, batch, rows, cols, ldp, out);
   return cudaGetLastError();
 }

@@ -36,7 +36,8 @@ struct Sizes {
   size_t el;  // bytes of a workspace complex element
   // tensor-core planes (elements of one plane)
   int ldXT, ldM, ldPs;
-  long plXn, plXT, plM, plPs, plBc, plBd, plBp;
+  long plXn, plXT, plPs, plBc, plBd, plBy;
+  long nexp;  // exponents: eXn + eXT + ePsi + eC + eY
 };
 
 int pad8(int x) { return (x + 7) & ~7; }
@@ -54,11 +55,11 @@ Sizes sizes_of(const thc_dims* d, int precision) {
   s.ldPs = pad8(2 * d->nocc);
   s.plXn = s.nk * d->nbas * s.ldM;
   s.plXT = s.nk * d->nisdf * s.ldXT;
-  s.plM = s.nk * d->nisdf * (long)s.ldM;
   s.plPs = s.nk * d->nisdf * s.ldPs;
   s.plBc = s.nk * 2 * d->nocc * s.ldXT;
   s.plBd = s.nk * 2L * d->nisdf * s.ldPs;
-  s.plBp = s.nk * 2 * d->nocc * (long)s.ldM;
+  s.plBy = s.nk * 2 * d->nocc * (long)s.ldM;
+  s.nexp = s.nk * (d->nbas + 2L * d->nisdf + 2L * d->nocc);
   return s;
 }
 
@@ -82,12 +83,12 @@ size_t memory_bytes(const thc_dims* d, int precision) {
   size_t b = 0;
   b += s.v * s.el;               // prepared kernel
   b += 2 * s.psi * s.el;         // Psi, Y
-  b += s.v * s.el;               // D
+  b += 2 * s.v * s.el;           // D, M
   if (precision == THC_MIXED) {
-    b += 3 * 2 * (s.plXn + s.plXT + s.plM + s.plPs + s.plBc + s.plBd + s.plBp);
+    b += 4 * 2 * (s.plXn + s.plXT + s.plPs + s.plBc + s.plBd + s.plBy);   // bf16 slices
+    b += sizeof(int) * s.nexp + 64;                                         // exponents, error word
   } else {
     b += s.x * s.el;             // X copy
-    b += s.v * s.el;             // M
   }
   b += 2 * s.kc * sizeof(double2) + 2 * sizeof(double);  // host-build staging
   b += 2 * kPartials * sizeof(double) + 64 + 64;
@@ -97,7 +98,7 @@ size_t memory_bytes(const thc_dims* d, int precision) {
 void free_all(thc_ctx* c) {
   void* ptrs[] = {c->X64, c->Vh64, c->X32, c->Vh32, c->Psi, c->D, c->M, c->Y,
                   c->Cdev, c->KCdev, c->exdev, c->partial, c->flag, c->Xn_pl, c->XT_pl,
-                  c->M_pl, c->PsiA_pl, c->Bc_pl, c->Bd_pl, c->Bp_pl, c->tc_err};
+                  c->PsiA_pl, c->Bc_pl, c->Bd_pl, c->By_pl, c->ex_pl, c->tc_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 7; i++)
@@ -173,13 +174,14 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
     W(&c->M, s.v * s.el);
   } else {
     W((void**)&c->Vh32, s.v * s.el);
-    W((void**)&c->Xn_pl, 3 * 2 * s.plXn);
-    W((void**)&c->XT_pl, 3 * 2 * s.plXT);
-    W((void**)&c->M_pl, 3 * 2 * s.plM);
-    W((void**)&c->PsiA_pl, 3 * 2 * s.plPs);
-    W((void**)&c->Bc_pl, 3 * 2 * s.plBc);
-    W((void**)&c->Bd_pl, 3 * 2 * s.plBd);
-    W((void**)&c->Bp_pl, 3 * 2 * s.plBp);
+    W(&c->M, s.v * s.el);
+    W((void**)&c->Xn_pl, 4 * 2 * s.plXn);
+    W((void**)&c->XT_pl, 4 * 2 * s.plXT);
+    W((void**)&c->PsiA_pl, 4 * 2 * s.plPs);
+    W((void**)&c->Bc_pl, 4 * 2 * s.plBc);
+    W((void**)&c->Bd_pl, 4 * 2 * s.plBd);
+    W((void**)&c->By_pl, 4 * 2 * s.plBy);
+    W((void**)&c->ex_pl, sizeof(int) * s.nexp);
     W((void**)&c->tc_err, 64);
   }
   W(&c->Psi, s.psi * s.el);
@@ -206,21 +208,25 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
   }
   if (precision == THC_MIXED) {
     c->ldXT = s.ldXT; c->ldM = s.ldM; c->ldPs = s.ldPs;
-    c->plXn = s.plXn; c->plXT = s.plXT; c->plM = s.plM; c->plPs = s.plPs;
-    c->plBc = s.plBc; c->plBd = s.plBd; c->plBp = s.plBp;
+    c->plXn = s.plXn; c->plXT = s.plXT; c->plPs = s.plPs;
+    c->plBc = s.plBc; c->plBd = s.plBd; c->plBy = s.plBy;
     const int nk = (int)s.nk, N = d->nbas, n = d->nocc, P = d->nisdf;
+    c->eXn = c->ex_pl;
+    c->eXT = c->eXn + (long)nk * N;
+    c->ePsi = c->eXT + (long)nk * P;
+    c->eC = c->ePsi + (long)nk * P;
+    c->eY = c->eC + (long)nk * n;
     struct MapReq { TcOperand* op; uint16_t* base; long pl; int rows, cols, ld; };
     MapReq reqs[] = {
         {&c->opXT, c->XT_pl, s.plXT, P, 2 * N, s.ldXT},
         {&c->opPs, c->PsiA_pl, s.plPs, P, 2 * n, s.ldPs},
-        {&c->opM, c->M_pl, s.plM, P, 2 * P, s.ldM},
         {&c->opXn, c->Xn_pl, s.plXn, N, 2 * P, s.ldM},
         {&c->opBc, c->Bc_pl, s.plBc, 2 * n, 2 * N, s.ldXT},
         {&c->opBd, c->Bd_pl, s.plBd, 2 * P, 2 * n, s.ldPs},
-        {&c->opBp, c->Bp_pl, s.plBp, 2 * n, 2 * P, s.ldM},
+        {&c->opBy, c->By_pl, s.plBy, 2 * n, 2 * P, s.ldM},
     };
     for (auto& r : reqs)
-      for (int p = 0; p < 3; p++) {
+      for (int p = 0; p < 4; p++) {
         e = make_plane_map(r.op->map[p], r.base + p * r.pl, nk, r.rows, r.cols, r.ld);
         if (e != cudaSuccess) {
           g_create_error = std::string("cuTensorMapEncodeTiled: ") + cudaGetErrorString(e);
@@ -271,11 +277,14 @@ thc_status thc_set_collocation(thc_ctx* c, const double* X) {
   } else if (c->precision == THC_MIXED_SIMT) {
     CKC(c, convert_z2c(x, c->X32, n, c->stream));
   } else {
+    // X (rows mu, A of S4b) and X^T (rows P, A of S1) as fixed-point slices
     const long sb = (long)c->nbas * c->nisdf;
-    CKC(c, split_rows_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->Xn_pl, c->Xn_pl + c->plXn,
-                        c->Xn_pl + 2 * c->plXn, c->ldM, c->stream));
-    CKC(c, split_cols_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->XT_pl, c->XT_pl + c->plXT,
-                        c->XT_pl + 2 * c->plXT, c->ldXT, c->stream));
+    CKC(c, row_exponents_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->eXn, c->stream));
+    CKC(c, col_exponents_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->eXT, c->stream));
+    CKC(c, slice_rows_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->eXn, c->Xn_pl, c->plXn, c->ldM,
+                        c->stream));
+    CKC(c, slice_cols_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->eXT, c->XT_pl, c->plXT, c->ldXT,
+                        c->stream));
   }
   CKC(c, cudaStreamSynchronize(c->stream));
   c->have_x = true;
@@ -357,36 +366,38 @@ static thc_status build_mixed(thc_ctx* c, const double2* C, double2* KC, double*
 
 static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex) {
   const int nk = c->nk, N = c->nbas, n = c->nocc, P = c->nisdf;
-  const long PP = (long)P * P, Pn = (long)P * n;
+  const long PP = (long)P * P, Pn = (long)P * n, Nn = (long)N * n;
   float2* Psi = (float2*)c->Psi;
   float2* D = (float2*)c->D;
+  float2* M = (float2*)c->M;
   float2* Y = (float2*)c->Y;
-  uint16_t* Bc[3] = {c->Bc_pl, c->Bc_pl + c->plBc, c->Bc_pl + 2 * c->plBc};
-  uint16_t* Bd[3] = {c->Bd_pl, c->Bd_pl + c->plBd, c->Bd_pl + 2 * c->plBd};
-  uint16_t* Bp[3] = {c->Bp_pl, c->Bp_pl + c->plBp, c->Bp_pl + 2 * c->plBp};
-  uint16_t* Pa[3] = {c->PsiA_pl, c->PsiA_pl + c->plPs, c->PsiA_pl + 2 * c->plPs};
-  uint16_t* Mp[3] = {c->M_pl, c->M_pl + c->plM, c->M_pl + 2 * c->plM};
   cudaStream_t s = c->stream;
   CKC(c, cudaEventRecord(stage_event(c, 0), s));
-  // S1  Psi = X^T C
-  CKC(c, embed_b(C, true, (long)N * n, n, 1, false, false, nk, N, n, Bc[0], Bc[1], Bc[2], c->ldXT, s));
-  CKC(c, tc_gemm(c->opXT, c->opBc, P, 2 * n, 2 * N, nk, Psi, false, 2 * n, 2 * Pn, c->tc_err, s));
+  // S1  Psi = X^T C on tensor cores: B = embedded C, one exponent per orbital
+  CKC(c, col_exponents_z(C, Nn, n, nk, N, n, c->eC, s));
+  CKC(c, embed_b(C, true, Nn, n, 1, false, false, nk, N, n, c->eC, c->Bc_pl, c->plBc, c->ldXT, s));
+  CKC(c, tc_gemm(c->opXT, c->opBc, P, 2 * n, 2 * N, nk, c->eXT, P, c->eC, n, Psi, false, 2 * n, 2 * Pn,
+                 c->tc_err, s));
   CKC(c, cudaEventRecord(stage_event(c, 1), s));
-  // S2  D = Psi Psi^H
-  CKC(c, split_rows_c(Psi, Pn, n, nk, P, n, Pa[0], Pa[1], Pa[2], c->ldPs, s));
-  CKC(c, embed_b(Psi, false, Pn, 1, n, true, false, nk, n, P, Bd[0], Bd[1], Bd[2], c->ldPs, s));
-  CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, D, false, 2 * P, 2 * PP, c->tc_err, s));
+  // S2  D = Psi Psi^H on tensor cores: A = Psi and B = embedded Psi^H share the
+  // row exponents of Psi
+  CKC(c, row_exponents_c(Psi, Pn, n, nk, P, n, c->ePsi, s));
+  CKC(c, slice_rows_c(Psi, Pn, n, nk, P, n, c->ePsi, c->PsiA_pl, c->plPs, c->ldPs, s));
+  CKC(c, embed_b(Psi, false, Pn, 1, n, true, false, nk, n, P, c->ePsi, c->Bd_pl, c->plBd, c->ldPs, s));
+  CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
+                 c->tc_err, s));
   CKC(c, cudaEventRecord(stage_event(c, 2), s));
-  // S3  M = IDFT(DFT(D) o Vh), written as bf16 planes
-  CKC(c, kconv_c_planes(D, c->Vh32, Mp[0], Mp[1], Mp[2], PP, P, c->ldM, c->n1, c->n2, c->n3, s));
+  // S3  M = IDFT(DFT(D) o Vh)
+  CKC(c, kconv_c(D, c->Vh32, M, PP, c->n1, c->n2, c->n3, s));
   CKC(c, cudaEventRecord(stage_event(c, 3), s));
-  // S4a Y = M Psi
-  CKC(c, embed_b(Psi, false, Pn, n, 1, false, false, nk, P, n, Bp[0], Bp[1], Bp[2], c->ldM, s));
-  CKC(c, tc_gemm(c->opM, c->opBp, P, 2 * n, 2 * P, nk, Y, false, 2 * n, 2 * Pn, c->tc_err, s));
+  // S4a Y = M Psi (CUDA cores, compensated sums)
+  CKC(c, (gemm_c_comp<float2, float2, float2>(A_MK, B_KN, P, n, P, M, P, PP, Psi, n, Pn, Y, n, Pn, nk, s)));
   CKC(c, cudaEventRecord(stage_event(c, 4), s));
-  // S4b KC = conj(X) Y
-  CKC(c, embed_b(Y, false, Pn, n, 1, false, true, nk, P, n, Bp[0], Bp[1], Bp[2], c->ldM, s));
-  CKC(c, tc_gemm(c->opXn, c->opBp, N, 2 * n, 2 * P, nk, KC, true, 2 * n, 2L * N * n, c->tc_err, s));
+  // S4b KC = conj(X) Y on tensor cores: B = embedded Y (conj-A form)
+  CKC(c, col_exponents_c(Y, Pn, n, nk, P, n, c->eY, s));
+  CKC(c, embed_b(Y, false, Pn, n, 1, false, true, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
+  CKC(c, tc_gemm(c->opXn, c->opBy, N, 2 * n, 2 * P, nk, c->eXn, N, c->eY, n, KC, true, 2 * n, 2 * Nn,
+                 c->tc_err, s));
   CKC(c, cudaEventRecord(stage_event(c, 5), s));
   CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
   CKC(c, cudaEventRecord(stage_event(c, 6), s));
@@ -446,10 +457,7 @@ thc_status thc_get_intermediate(thc_ctx* c, int which, double* out) {
   const long n = (which == 0 || which == 3) ? (long)c->nk * c->nisdf * c->nocc
                                             : (long)c->nk * c->nisdf * c->nisdf;
   void* src = which == 0 ? c->Psi : which == 1 ? c->D : which == 2 ? c->M : c->Y;
-  if (c->precision == THC_MIXED && which == 2)
-    CKC(c, combine_planes(c->M_pl, c->M_pl + c->plM, c->M_pl + 2 * c->plM, c->nk, c->nisdf, c->nisdf,
-                          c->ldM, (double2*)out, c->stream));
-  else if (c->precision == THC_FP64)
+  if (c->precision == THC_FP64)
     CKC(c, cudaMemcpyAsync(out, src, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
   else
     CKC(c, convert_c2z((const float2*)src, (double2*)out, n, c->stream));
@@ -504,9 +512,9 @@ thc_status thc_profile_end(thc_ctx* c, float mean_ms[6], int* nbuilds) {
 thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   if (!c || !launches) return THC_ERR_ARG;
   // FP64 and CUDA-core forms: S1, S2, S3, S4a, S4b, E_x partial, E_x final.
-  // Tensor-core form adds the operand preparation: 2 (S1) + 3 (S2) + 1 (S3)
-  // + 2 (S4a) + 2 (S4b) + 2 (E_x).
-  *launches = c->precision == THC_MIXED ? 12 : 7;
+  // Tensor-core form: S1 3 (exponents, embed, GEMM), S2 4 (exponents, slices,
+  // embed, GEMM), S3 1, S4a 1, S4b 3, E_x 2.
+  *launches = c->precision == THC_MIXED ? 14 : 7;
   return THC_OK;
 }
 

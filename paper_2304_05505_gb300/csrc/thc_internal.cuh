@@ -63,18 +63,20 @@ struct thc_ctx {
   double* partial;  // reduction scratch
   int* flag;        // device flag word (finite checks)
   int n_partial;
-  // tensor-core operands (THC_MIXED): three bf16 planes each, plane p at
-  // base + p * plane elements; rows padded to a multiple of 8 elements
-  uint16_t* Xn_pl;    // [nk][nbas][ldM]     X, A of S4b
-  uint16_t* XT_pl;    // [nk][nisdf][ldXT]   X^T, A of S1
-  uint16_t* M_pl;     // [nk][nisdf][ldM]    M, A of S4a
-  uint16_t* PsiA_pl;  // [nk][nisdf][ldPs]   Psi, A of S2
-  uint16_t* Bc_pl;    // [nk][2 nocc][ldXT]  embedded C, B of S1
-  uint16_t* Bd_pl;    // [nk][2 nisdf][ldPs] embedded Psi^H, B of S2
-  uint16_t* Bp_pl;    // [nk][2 nocc][ldM]   embedded Psi (S4a) / Y (S4b)
-  long plXn, plXT, plM, plPs, plBc, plBd, plBp;
+  // tensor-core operands (THC_MIXED): four bf16 fixed-point planes each,
+  // plane p at base + p * plane elements, rows padded to 8 elements, and one
+  // power-of-two exponent per row
+  uint16_t* Xn_pl;    // [nk][nbas][ldM]     X, A of S4b          exponents eXn [nk][nbas]
+  uint16_t* XT_pl;    // [nk][nisdf][ldXT]   X^T, A of S1         eXT [nk][nisdf]
+  uint16_t* PsiA_pl;  // [nk][nisdf][ldPs]   Psi, A of S2         ePsi [nk][nisdf]
+  uint16_t* Bc_pl;    // [nk][2 nocc][ldXT]  embedded C, B of S1  eC [nk][nocc]
+  uint16_t* Bd_pl;    // [nk][2 nisdf][ldPs] embedded Psi^H, B of S2 (ePsi)
+  uint16_t* By_pl;    // [nk][2 nocc][ldM]   embedded Y, B of S4b eY [nk][nocc]
+  int* ex_pl;         // eXn | eXT | ePsi | eC | eY
+  int *eXn, *eXT, *ePsi, *eC, *eY;
+  long plXn, plXT, plPs, plBc, plBd, plBy;
   int ldXT, ldM, ldPs;
-  TcOperand opXT, opPs, opM, opXn, opBc, opBd, opBp;
+  TcOperand opXT, opPs, opXn, opBc, opBd, opBy;
   int* tc_err;        // device word: nonzero after a device wait gave up
   cudaEvent_t ev[7];               // stage boundaries of the last build
   std::vector<cudaEvent_t> prof;   // 7 per profiled build
@@ -113,9 +115,6 @@ cudaError_t kconv_z(const double2* D, const double2* Vh, double2* M, long npq, i
                     int n3, cudaStream_t s);
 cudaError_t kconv_c(const float2* D, const float2* Vh, float2* M, long npq, int n1, int n2,
                     int n3, cudaStream_t s);
-// As kconv_c, writing M as three bf16 planes [k][row][ldp] (row = e / ncols).
-cudaError_t kconv_c_planes(const float2* D, const float2* Vh, uint16_t* p0, uint16_t* p1, uint16_t* p2,
-                           long npq, int ncols, int ldp, int n1, int n2, int n3, cudaStream_t s);
 // Vh[a] = (1/N_k) sum_q V[q] w^{+a.q} in FP64; writes FP64 or FP32 output.
 cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long npq, int n1,
                              int n2, int n3, cudaStream_t s);
@@ -130,6 +129,4 @@ cudaError_t ex_reduce_c(const float2* Psi, const float2* Y, long n, int nk, doub
 cudaError_t convert_z2c(const double2* in, float2* out, long n, cudaStream_t s);
 cudaError_t convert_c2z(const float2* in, double2* out, long n, cudaStream_t s);
 cudaError_t check_finite_z(const double2* in, long n, int* flag, cudaStream_t s);
-// out[b][r][c] = p0 + p1 + p2 at [b][r][2c + d] (complex128), for tests.
-cudaError_t combine_planes(const uint16_t* p0, const uint16_t* p1, const uint16_t* p2, int batch, int rows,
-                           int cols, int ldp, double2* out, cudaStream_t s);
+

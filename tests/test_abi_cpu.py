@@ -58,9 +58,10 @@ def test_memory_bytes_arithmetic():
 
     def pad8(x):
         return (x + 7) // 8 * 8
-    planes = nk * (N * pad8(2 * P) + P * pad8(2 * N) + P * pad8(2 * P) + P * pad8(2 * n)
+    planes = nk * (N * pad8(2 * P) + P * pad8(2 * N) + P * pad8(2 * n)
                    + 2 * n * pad8(2 * N) + 2 * P * pad8(2 * n) + 2 * n * pad8(2 * P))
-    tc = 8 * (nk * P * P + 2 * nk * P * n + nk * P * P) + 3 * 2 * planes + common
+    exps = nk * (N + 2 * P + 2 * n)
+    tc = 8 * (nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + 4 * 2 * planes + 4 * exps + 64 + common
     assert thc.thc_memory_bytes(d, thc.THC_MIXED) == tc
 
 
