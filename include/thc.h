@@ -140,6 +140,26 @@ thc_status thc_launches_per_build(const thc_ctx* ctx, int* launches);
 
 thc_status thc_destroy(thc_ctx* ctx);
 
+/* The k-mesh convolution alone, M^k[P,Q] = sum_k' D^k'[P,Q] V^(k'-k)[P,Q] in
+ * FP64, for callers that cannot allocate device memory when they call: for
+ * example a host framework that has already reserved the device's memory in
+ * its own pool, or a caller that must not let cudaMalloc/cudaFree synchronise
+ * the device.  The paper has no counterpart; this is a deployment variant of
+ * step S3.
+ *
+ * D, V, M: device, [N_k][npq] complex128 (npq = elements per k, e.g. N_P^2),
+ * V indexed by q on the mesh index; M must not alias D or V.  Work is queued
+ * on `stream` (a cudaStream_t; NULL = legacy default stream).  It allocates
+ * nothing: its scratch (the DFT of V over the mesh) is one static device array
+ * of 2,097,152 complex128 elements (32 MiB) that every GPU loading the library
+ * holds until the process exits, so N_k * npq must be at most 2,097,152
+ * (THC_ERR_ARG otherwise, message in thc_last_error(NULL)).  The first call on
+ * each device looks up that array's device address, so make it before any
+ * stream capture.  All calls on a device share the array: calls that overlap
+ * on the GPU race and must be ordered by the caller. */
+thc_status thc_kconv_noalloc(const double* D, const double* V, double* M, int n1, int n2, int n3,
+                             long npq, void* stream);
+
 const char* thc_status_string(thc_status s);
 const char* thc_last_error(const thc_ctx* ctx);
 

@@ -111,6 +111,8 @@ constexpr int kStages = 6;
 
 }  // namespace
 
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+
 extern "C" {
 
 const char* thc_status_string(thc_status s) {

@@ -125,6 +125,9 @@ cudaError_t ex_reduce_z(const double2* Psi, const double2* Y, long n, int nk, do
 cudaError_t ex_reduce_c(const float2* Psi, const float2* Y, long n, int nk, double* partial,
                         int npartial, double* ex, cudaStream_t s);
 
+// Message returned by thc_last_error(NULL) for calls made without a context.
+void set_global_error(const std::string& msg);
+
 // conversions and checks
 cudaError_t convert_z2c(const double2* in, float2* out, long n, cudaStream_t s);
 cudaError_t convert_c2z(const float2* in, double2* out, long n, cudaStream_t s);

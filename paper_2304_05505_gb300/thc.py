@@ -28,7 +28,7 @@ STATUS = {0: "THC_OK", 1: "THC_ERR_ARG", 2: "THC_ERR_OOM", 3: "THC_ERR_CUDA",
 EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_kernel",
            "thc_build", "thc_build_host", "thc_get_intermediate", "thc_stage_times",
            "thc_launches_per_build", "thc_destroy", "thc_status_string", "thc_last_error",
-           "thc_profile_begin", "thc_profile_end", "thc_sync"]
+           "thc_profile_begin", "thc_profile_end", "thc_sync", "thc_kconv_noalloc"]
 
 
 class ThcDims(ctypes.Structure):
@@ -68,6 +68,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]
     lib.thc_destroy.argtypes = [vp]
     lib.thc_sync.argtypes = [vp]
+    lib.thc_kconv_noalloc.argtypes = [dp, dp, dp, ip, ip, ip, ctypes.c_long, vp]
     lib.thc_status_string.argtypes = [ip]
     lib.thc_status_string.restype = ctypes.c_char_p
     lib.thc_last_error.argtypes = [vp]
@@ -199,6 +200,16 @@ def thc_launches_per_build(ctx) -> int:
 
 def thc_sync(ctx) -> None:
     _check(load().thc_sync(ctx), "thc_sync", ctx)
+
+
+def thc_kconv_noalloc(D, V, M, mesh, npq: int, stream: int | None = None) -> None:
+    """k-mesh convolution without device allocation (see include/thc.h)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load().thc_kconv_noalloc(_dev_ptr(D, name="D"), _dev_ptr(V, name="V"), _dev_ptr(M, name="M"),
+                                    int(mesh[0]), int(mesh[1]), int(mesh[2]), int(npq), ctypes.c_void_p(stream)),
+           "thc_kconv_noalloc")
 
 
 def thc_destroy(ctx) -> None:
