@@ -23,15 +23,24 @@
 // accumulator; their rounding is at least 2^-8 smaller.  Classes with
 // s + t >= 4 (below 2^-32 of the row scales) are dropped.
 //
-// Kernel structure (one 128 x 128 output tile per CTA, 384 threads):
+// Work units: a 128 x 128 output tile and a chunk of at most 1024 real K (so
+// the leading sum of a unit is exact).  When K needs more than one chunk the
+// units write their exact int32 leading sums and FP32 remainders to a partial
+// buffer and tc_combine adds the chunks (split K); otherwise they write the
+// scaled result directly.
+//
+// Kernel structure (persistent: one CTA per SM loops over units, 384 threads):
 //   warp 0      TMA producer: 4 A planes + 4 B planes per 32-wide real-K block
-//               into a 3-stage ring (64 KB a stage, 64B swizzle)
-//   warp 1      allocates 512 TMEM columns; lane 0 issues tcgen05.mma
-//               (M = 128, N = 128, K = 16, bf16 x bf16 -> f32), 10 per K step
+//               into a 3-stage ring (64 KB a stage, 64B swizzle), running
+//               ahead across units
+//   warp 1      allocates 512 TMEM columns = two accumulator sets (leading
+//               class, classes 1..3; 128 columns each) so that the epilogue of
+//               one unit overlaps the MMAs of the next; lane 0 issues
+//               tcgen05.mma (M = 128, N = 128, K = 16, bf16 x bf16 -> f32),
+//               10 per K step
 //   warps 2-3   idle (they keep the block at 12 warps)
-//   warps 4-11  epilogue: move the exact leading class out of TMEM into int32
-//               registers every DRAIN blocks (1024 real K), then scale, combine
-//               and store
+//   warps 4-11  epilogue: read both accumulators, scale and store (or write
+//               the partial sums), release the accumulator set
 // Every mbarrier wait is bounded (about 2 s of clock64); on expiry the thread
 // sets the error word, stops issuing work and the CTA releases TMEM and exits.
 #include "thc_internal.cuh"
@@ -40,6 +49,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 namespace {
 
@@ -168,14 +179,31 @@ struct Maps {
   CUtensorMap b[NPL];
 };
 
-template <bool OUT_F64>
+// Exact powers of two built from the exponent bits (ldexp for the rare
+// exponents outside the normal range).
+__device__ __forceinline__ float pow2f(int e) {
+  return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : ldexpf(1.0f, e);
+}
+__device__ __forceinline__ double pow2d(int e) {
+  return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+}
+
+struct Geometry {
+  int M, Nr, Kr, batch;
+  int mt, nt, nchunk, nkb;   // tiles along M and N, K chunks, K blocks
+  long units;
+};
+
+// OUT: 0 = FP32 result, 1 = FP64 result, 2 = partial sums (split K)
+template <int OUT>
 __global__ void __launch_bounds__(NTHREADS, 1)
-tc_gemm_kernel(const __grid_constant__ Maps maps, int M, int Nr, int Kr, const int* __restrict__ eA,
-               long seA, const int* __restrict__ eB, long seB, void* out, long ldo, long sbo, int* err) {
+tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restrict__ eA, long seA,
+               const int* __restrict__ eB, long seB, void* out, long ldo, long sbo, int* __restrict__ ps0,
+               float* __restrict__ pbc, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-  // bars: full[3], empty[3], accA_full[2], accA_empty[2], done[1]
+  // bars: full[3], empty[3], acc_full[2], acc_empty[2]
   uint32_t* tmem_slot = (uint32_t*)(bars + 16);
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = smem_u32(bars);
@@ -183,17 +211,13 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, int M, int Nr, int Kr, const i
   auto EMPTY = [&](int s) { return bar0 + 8u * (3 + s); };
   auto AFULL = [&](int s) { return bar0 + 8u * (6 + s); };
   auto AEMPTY = [&](int s) { return bar0 + 8u * (8 + s); };
-  const uint32_t DONE = bar0 + 8u * 10;
 
   __shared__ int abort_flag;
   if (threadIdx.x == 0) abort_flag = *(volatile int*)err;
   __syncthreads();
-  if (abort_flag) return;   // an earlier CTA gave up a wait: skip the tile
+  if (abort_flag) return;   // an earlier CTA gave up a wait: skip the work
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, b = blockIdx.z;
-  const int nkb = (Kr + BKR - 1) / BKR;
-  const int nchunk = (nkb + DRAIN - 1) / DRAIN;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
@@ -204,7 +228,6 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, int M, int Nr, int Kr, const i
       mbar_init(AFULL(s), 1);
       mbar_init(AEMPTY(s), EPI_WARPS);
     }
-    mbar_init(DONE, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -219,121 +242,155 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, int M, int Nr, int Kr, const i
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  // unit u -> (b, m tile, n tile, K chunk); n fastest so CTAs running side by
+  // side share the A tile through L2
+  auto decode = [&](long u, int& b, int& mi, int& ni, int& kc) {
+    kc = (int)(u % g.nchunk);
+    long r = u / g.nchunk;
+    ni = (int)(r % g.nt);
+    r /= g.nt;
+    mi = (int)(r % g.mt);
+    b = (int)(r / g.mt);
+  };
+
   if (warp == 0) {
     if (lane == 0) {
       for (int s = 0; s < NPL; s++) {
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.a[s]) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.b[s]) : "memory");
       }
-      for (int kb = 0; kb < nkb; kb++) {
-        const int st = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(EMPTY(st), ph ^ 1, err, 2)) break;
-        mbar_expect_tx(FULL(st), STAGE_BYTES);
-        const uint32_t dst = sbase + st * STAGE_BYTES;
-        for (int p = 0; p < NPL; p++)
-          tma_load_3d(dst + p * TILE_BYTES, &maps.a[p], FULL(st), kb * BKR, m0, b);
-        for (int p = 0; p < NPL; p++)
-          tma_load_3d(dst + (NPL + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, n0, b);
+      uint32_t it = 0;
+      bool ok = true;
+      for (long u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+        int b, mi, ni, kc;
+        decode(u, b, mi, ni, kc);
+        const int kb1 = min(g.nkb, (kc + 1) * DRAIN);
+        for (int kb = kc * DRAIN; kb < kb1; kb++, it++) {
+          const int st = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1;
+          if (!mbar_wait(EMPTY(st), ph ^ 1, err, 2)) { ok = false; break; }
+          mbar_expect_tx(FULL(st), STAGE_BYTES);
+          const uint32_t dst = sbase + st * STAGE_BYTES;
+          for (int p = 0; p < NPL; p++)
+            tma_load_3d(dst + p * TILE_BYTES, &maps.a[p], FULL(st), kb * BKR, mi * BM, b);
+          for (int p = 0; p < NPL; p++)
+            tma_load_3d(dst + (NPL + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(BM, BN);
-      const uint32_t accBC = tmem + 256;
-      for (int kb = 0; kb < nkb; kb++) {
-        const int st = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
-        const int chunk = kb / DRAIN;
-        const int buf = chunk & 1;
-        const bool chunk_start = (kb % DRAIN) == 0;
-        if (chunk_start && !mbar_wait(AEMPTY(buf), ((chunk >> 1) & 1) ^ 1, err, 4)) break;
-        if (!mbar_wait(FULL(st), ph, err, 8)) break;
+      uint32_t it = 0, local = 0;
+      bool ok = true;
+      for (long u = blockIdx.x; u < g.units && ok; u += gridDim.x, local++) {
+        int b, mi, ni, kc;
+        decode(u, b, mi, ni, kc);
+        const int set = local & 1;
+        if (!mbar_wait(AEMPTY(set), ((local >> 1) & 1) ^ 1, err, 4)) break;
         fence_after();
-        const uint32_t accA = tmem + 128 * buf;
-        const uint32_t tA = sbase + st * STAGE_BYTES;
-        const uint32_t tB = tA + NPL * TILE_BYTES;
+        const uint32_t accA = tmem + 256 * set, accBC = accA + 128;
+        const int kb0 = kc * DRAIN, kb1 = min(g.nkb, (kc + 1) * DRAIN);
+        for (int kb = kb0; kb < kb1; kb++, it++) {
+          const int st = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1;
+          if (!mbar_wait(FULL(st), ph, err, 8)) { ok = false; break; }
+          fence_after();
+          const uint32_t tA = sbase + st * STAGE_BYTES;
+          const uint32_t tB = tA + NPL * TILE_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < BKR / 16; kk++) {
-          const uint32_t off = kk * 32;
-          const uint32_t firstA = (chunk_start && kk == 0) ? 0u : 1u;
-          const uint32_t firstBC = (kb == 0 && kk == 0) ? 0u : 1u;
-          auto da = [&](int s) { return smem_desc(tA + s * TILE_BYTES + off); };
-          auto db = [&](int t) { return smem_desc(tB + t * TILE_BYTES + off); };
-          mma_bf16(accA, da(0), db(0), idesc, firstA);          // exact leading class
-          // classes s + t = 3, 2, 1 (smallest first) into the second accumulator
-          mma_bf16(accBC, da(0), db(3), idesc, firstBC);
-          mma_bf16(accBC, da(1), db(2), idesc, 1u);
-          mma_bf16(accBC, da(2), db(1), idesc, 1u);
-          mma_bf16(accBC, da(3), db(0), idesc, 1u);
-          mma_bf16(accBC, da(0), db(2), idesc, 1u);
-          mma_bf16(accBC, da(1), db(1), idesc, 1u);
-          mma_bf16(accBC, da(2), db(0), idesc, 1u);
-          mma_bf16(accBC, da(0), db(1), idesc, 1u);
-          mma_bf16(accBC, da(1), db(0), idesc, 1u);
+          for (int kk = 0; kk < BKR / 16; kk++) {
+            const uint32_t off = kk * 32;
+            const uint32_t acc = (kb == kb0 && kk == 0) ? 0u : 1u;
+            auto da = [&](int q) { return smem_desc(tA + q * TILE_BYTES + off); };
+            auto db = [&](int q) { return smem_desc(tB + q * TILE_BYTES + off); };
+            mma_bf16(accA, da(0), db(0), idesc, acc);          // exact leading class
+            // classes s + t = 3, 2, 1 (smallest first) into the second accumulator
+            mma_bf16(accBC, da(0), db(3), idesc, acc);
+            mma_bf16(accBC, da(1), db(2), idesc, 1u);
+            mma_bf16(accBC, da(2), db(1), idesc, 1u);
+            mma_bf16(accBC, da(3), db(0), idesc, 1u);
+            mma_bf16(accBC, da(0), db(2), idesc, 1u);
+            mma_bf16(accBC, da(1), db(1), idesc, 1u);
+            mma_bf16(accBC, da(2), db(0), idesc, 1u);
+            mma_bf16(accBC, da(0), db(1), idesc, 1u);
+            mma_bf16(accBC, da(1), db(0), idesc, 1u);
+          }
+          mma_commit(EMPTY(st));
         }
-        mma_commit(EMPTY(st));
-        if ((kb % DRAIN) == DRAIN - 1 || kb == nkb - 1) mma_commit(AFULL(buf));
+        mma_commit(AFULL(set));
       }
-      mma_commit(DONE);
     }
   } else if (warp >= EPI_WARP0) {
     // epilogue warps: lane quadrant q, column half h
     const int q = warp & 3;
     const int h = (warp - EPI_WARP0) >> 2;
-    const int row = m0 + 32 * q + lane;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    int s0[64];   // exact leading-class sums, |s0| <= 2^14 K
-#pragma unroll
-    for (int j = 0; j < 64; j++) s0[j] = 0;
-    bool ok = true;
-    for (int c = 0; c < nchunk; c++) {
-      const int buf = c & 1;
-      if (!mbar_wait_warp(AFULL(buf), (c >> 1) & 1, err, 16)) { ok = false; break; }
+    uint32_t local = 0;
+    for (long u = blockIdx.x; u < g.units; u += gridDim.x, local++) {
+      int b, mi, ni, kc;
+      decode(u, b, mi, ni, kc);
+      const int set = local & 1;
+      if (!mbar_wait_warp(AFULL(set), (local >> 1) & 1, err, 16)) break;
       fence_after();
-#pragma unroll
+      const int row = mi * BM + 32 * q + lane;
+      const int ea = (OUT != 2 && row < g.M) ? eA[(long)b * seA + row] : 0;
+      const uint32_t accA = tmem + lane_off + 256 * set, accBC = accA + 128;
+#pragma unroll 1
       for (int qq = 0; qq < 4; qq++) {
-        float v[16];
-        tmem_ld16(tmem + lane_off + 128 * buf + 64 * h + 16 * qq, v);
+        float va[16], vb[16];
+        tmem_ld16(accA + 64 * h + 16 * qq, va);
+        tmem_ld16(accBC + 64 * h + 16 * qq, vb);
+        const int col0 = ni * BN + 64 * h + 16 * qq;   // even: complex pairs stay together
+        if (row >= g.M) continue;
+        if constexpr (OUT == 2) {
+          // exact leading sums and FP32 remainders of this K chunk
+          const long base = (((long)kc * g.batch + b) * g.M + row) * g.Nr;
 #pragma unroll
-        for (int j = 0; j < 16; j++) s0[16 * qq + j] += __float2int_rn(v[j]);
-      }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(AEMPTY(buf));
-    }
-    if (ok && mbar_wait_warp(DONE, 0, err, 32)) {
-      fence_after();
-      const int ea = (row < M) ? eA[(long)b * seA + row] : 0;
-#pragma unroll
-      for (int qq = 0; qq < 4; qq++) {
-        float v[16];
-        tmem_ld16(tmem + lane_off + 256 + 64 * h + 16 * qq, v);   // classes 1..3
-        const int col0 = n0 + 64 * h + 16 * qq;
-        if (row < M) {
-          if constexpr (OUT_F64) {
-            double* o = (double*)out + (long)b * sbo + (long)row * ldo;
-#pragma unroll
-            for (int j = 0; j < 16; j++) {
-              const int col = col0 + j;
-              if (col < Nr) {
-                const int e = ea + eB[(long)b * seB + (col >> 1)] - 14;
-                o[col] = ldexp((double)s0[16 * qq + j] + (double)v[j], e);
-              }
+          for (int j = 0; j < 16; j++)
+            if (col0 + j < g.Nr) {
+              ps0[base + col0 + j] = __float2int_rn(va[j]);
+              pbc[base + col0 + j] = vb[j];
             }
+        } else if constexpr (OUT == 1) {
+          double* o = (double*)out + (long)b * sbo + (long)row * ldo;
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            if (col0 + j >= g.Nr) break;
+            const double sc = pow2d(ea + eB[(long)b * seB + ((col0 + j) >> 1)] - 14);
+            const double x0 = ((double)__float2int_rn(va[j]) + (double)vb[j]) * sc;
+            const double x1 = ((double)__float2int_rn(va[j + 1]) + (double)vb[j + 1]) * sc;
+            if (col0 + j + 1 < g.Nr && (ldo % 2) == 0) {
+              *reinterpret_cast<double2*>(o + col0 + j) = make_double2(x0, x1);
+            } else {
+              o[col0 + j] = x0;
+              if (col0 + j + 1 < g.Nr) o[col0 + j + 1] = x1;
+            }
+          }
+        } else {
+          float w[16];
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const int jj = (col0 + j < g.Nr) ? ((col0 + j) >> 1) : 0;
+            const float sc = pow2f(ea + eB[(long)b * seB + jj] - 14);
+            w[j] = (va[j] + vb[j]) * sc;           // va holds an exact integer below 2^24
+            w[j + 1] = (va[j + 1] + vb[j + 1]) * sc;
+          }
+          float* o = (float*)out + (long)b * sbo + (long)row * ldo;
+          if (col0 + 16 <= g.Nr && (ldo % 4) == 0) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+              *reinterpret_cast<float4*>(o + col0 + j) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
           } else {
-            float* o = (float*)out + (long)b * sbo + (long)row * ldo;
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
-              const int col = col0 + j;
-              if (col < Nr) {
-                const int e = ea + eB[(long)b * seB + (col >> 1)] - 14;
-                o[col] = ldexpf((float)s0[16 * qq + j] + v[j], e);
-              }
-            }
+            for (int j = 0; j < 16; j++)
+              if (col0 + j < g.Nr) o[col0 + j] = w[j];
           }
         }
       }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(AEMPTY(set));
     }
   }
   fence_before();
@@ -342,6 +399,31 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, int M, int Nr, int Kr, const i
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
                  : "memory");
+  }
+}
+
+// Adds the K chunks of a split-K product: out = 2^(e_a + e_b - 14) (sum s0 + sum bc).
+template <bool OUT_F64>
+__global__ void tc_combine_kernel(const int* __restrict__ ps0, const float* __restrict__ pbc, int nchunk,
+                                  int batch, int M, int Nr, const int* __restrict__ eA, long seA,
+                                  const int* __restrict__ eB, long seB, void* out, long ldo, long sbo) {
+  const long total = (long)batch * M * Nr;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int col = (int)(i % Nr);
+    const long bm = i / Nr;
+    const int m = (int)(bm % M);
+    const int b = (int)(bm / M);
+    long s0 = 0;
+    float bc = 0.f;
+    for (int c = 0; c < nchunk; c++) {
+      s0 += ps0[(long)c * total + i];
+      bc += pbc[(long)c * total + i];
+    }
+    const int e = eA[(long)b * seA + m] + eB[(long)b * seB + (col >> 1)] - 14;
+    if (OUT_F64)
+      ((double*)out)[(long)b * sbo + (long)m * ldo + col] = ((double)s0 + (double)bc) * pow2d(e);
+    else
+      ((float*)out)[(long)b * sbo + (long)m * ldo + col] = (float)(((double)s0 + (double)bc) * pow2d(e));
   }
 }
 
@@ -375,30 +457,62 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+long tc_partial_elems(int M, int Nr, int Kr, int batch) {
+  const int nkb = (Kr + BKR - 1) / BKR;
+  const int nchunk = (nkb + DRAIN - 1) / DRAIN;
+  return nchunk > 1 ? (long)nchunk * batch * M * Nr : 0;
+}
+
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
-                    long sbo, int* err, cudaStream_t s) {
+                    long sbo, int* ps0, float* pbc, int* err, cudaStream_t s) {
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
-  if (Kr > 0x7fffffff / 16384) return cudaErrorInvalidValue;   // exact int32 leading sums
   Maps maps;
   for (int p = 0; p < NPL; p++) {
     memcpy(&maps.a[p], A.map[p], sizeof(CUtensorMap));
     memcpy(&maps.b[p], B.map[p], sizeof(CUtensorMap));
   }
-  dim3 grid((Nr + BN - 1) / BN, (M + BM - 1) / BM, batch);
-  cudaError_t e;
-  if (out_f64) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    tc_gemm_kernel<true><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps, M, Nr, Kr, eA, seA, eB, seB, out, ldo, sbo,
-                                                          err);
-  } else {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    tc_gemm_kernel<false><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps, M, Nr, Kr, eA, seA, eB, seB, out, ldo, sbo,
-                                                           err);
+  Geometry g;
+  g.M = M; g.Nr = Nr; g.Kr = Kr; g.batch = batch;
+  g.mt = (M + BM - 1) / BM;
+  g.nt = (Nr + BN - 1) / BN;
+  g.nkb = (Kr + BKR - 1) / BKR;
+  g.nchunk = (g.nkb + DRAIN - 1) / DRAIN;
+  g.units = (long)batch * g.mt * g.nt * g.nchunk;
+  if (g.units <= 0) return cudaSuccess;
+  const bool split = g.nchunk > 1;
+  if (split && (!ps0 || !pbc)) return cudaErrorInvalidValue;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
   }
+  const unsigned grid = (unsigned)std::min<long>(g.units, nsm);
+  cudaError_t e;
+#define LAUNCH(OUTK)                                                                                     \
+  e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                           (int)SMEM_BYTES);                                                             \
+  if (e != cudaSuccess) return e;                                                                        \
+  tc_gemm_kernel<OUTK><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, out, ldo, sbo, ps0, \
+                                                          pbc, err);
+  if (split) {
+    LAUNCH(2)
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long total = (long)batch * M * Nr;
+    const unsigned cg = (unsigned)std::min<long>((total + 255) / 256, 152L * 16);
+    if (out_f64)
+      tc_combine_kernel<true><<<cg, 256, 0, s>>>(ps0, pbc, g.nchunk, batch, M, Nr, eA, seA, eB, seB, out, ldo,
+                                                 sbo);
+    else
+      tc_combine_kernel<false><<<cg, 256, 0, s>>>(ps0, pbc, g.nchunk, batch, M, Nr, eA, seA, eB, seB, out, ldo,
+                                                  sbo);
+  } else if (out_f64) {
+    LAUNCH(1)
+  } else {
+    LAUNCH(0)
+  }
+#undef LAUNCH
   return cudaGetLastError();
 }

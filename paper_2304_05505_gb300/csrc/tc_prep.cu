@@ -72,16 +72,25 @@ __global__ void rowexp_kernel(const CT* __restrict__ src, long sbs, int lds, int
 }
 
 // Exponent of each column: e[b * cols + c] = max over r of src[b][r][c].
+// Block (b, column slab of 32): warp w scans rows w, w + 8, ..., lane = column.
 template <typename CT>
 __global__ void colexp_kernel(const CT* __restrict__ src, long sbs, int lds, int batch, int rows, int cols,
                               int* __restrict__ e) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long)batch * cols) return;
-  const int b = (int)(i / cols), c = (int)(i % cols);
-  const CT* p = src + (long)b * sbs + c;
+  __shared__ double red[8][32];
+  const int b = blockIdx.y;
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int w = threadIdx.x >> 5;
   double m = 0.0;
-  for (int r = 0; r < rows; r++) m = fmax(m, cmax(p[(long)r * lds]));
-  e[i] = row_exponent(m);
+  if (c < cols) {
+    const CT* p = src + (long)b * sbs + c;
+    for (int r = w; r < rows; r += 8) m = fmax(m, cmax(p[(long)r * lds]));
+  }
+  red[w][threadIdx.x & 31] = m;
+  __syncthreads();
+  if (w == 0) {
+    for (int i = 1; i < 8; i++) m = fmax(m, red[i][threadIdx.x]);
+    if (c < cols) e[(long)b * cols + c] = row_exponent(m);
+  }
 }
 
 // planes[p][b][r][2c + d] of src[b][r][c] with row exponents e[b][r].
@@ -186,15 +195,13 @@ cudaError_t row_exponents_c(const float2* src, long sbs, int lds, int batch, int
 
 cudaError_t col_exponents_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
                             cudaStream_t s) {
-  const long n = (long)batch * cols;
-  colexp_kernel<double2><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(src, sbs, lds, batch, rows, cols, e);
+  colexp_kernel<double2><<<dim3((cols + 31) / 32, batch), 256, 0, s>>>(src, sbs, lds, batch, rows, cols, e);
   return cudaGetLastError();
 }
 
 cudaError_t col_exponents_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
                             cudaStream_t s) {
-  const long n = (long)batch * cols;
-  colexp_kernel<float2><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(src, sbs, lds, batch, rows, cols, e);
+  colexp_kernel<float2><<<dim3((cols + 31) / 32, batch), 256, 0, s>>>(src, sbs, lds, batch, rows, cols, e);
   return cudaGetLastError();
 }
 
@@ -224,7 +231,7 @@ cudaError_t embed_b(const void* src, bool src_f64, long sbs, long ldk, long ldj,
                     cudaStream_t s) {
   const long n = (long)batch * J * K;
   if (src_f64)
-    embed_kernel<double2, double><<<grid1(n), 256, 0, s>>>((const double2*)src, sbs, ldk, ldj, conj_src, conj_a, batch,
+    embed_kernel<double2, float><<<grid1(n), 256, 0, s>>>((const double2*)src, sbs, ldk, ldj, conj_src, conj_a, batch,
                                                    K, J, e, planes, plane, ldp);
   else
     embed_kernel<float2, float><<<grid1(n), 256, 0, s>>>((const float2*)src, sbs, ldk, ldj, conj_src, conj_a, batch, K,

@@ -14,6 +14,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 namespace {
@@ -38,6 +39,7 @@ struct Sizes {
   int ldXT, ldM, ldPs;
   long plXn, plXT, plPs, plBc, plBd, plBy;
   long nexp;  // exponents: eXn + eXT + ePsi + eC + eY
+  long npart; // split-K partial elements (max over the tensor-core GEMMs)
 };
 
 int pad8(int x) { return (x + 7) & ~7; }
@@ -60,6 +62,9 @@ Sizes sizes_of(const thc_dims* d, int precision) {
   s.plBd = s.nk * 2L * d->nisdf * s.ldPs;
   s.plBy = s.nk * 2 * d->nocc * (long)s.ldM;
   s.nexp = s.nk * (d->nbas + 2L * d->nisdf + 2L * d->nocc);
+  s.npart = std::max({tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nbas, (int)s.nk),
+                      tc_partial_elems(d->nisdf, 2 * d->nisdf, 2 * d->nocc, (int)s.nk),
+                      tc_partial_elems(d->nbas, 2 * d->nocc, 2 * d->nisdf, (int)s.nk)});
   return s;
 }
 
@@ -87,6 +92,7 @@ size_t memory_bytes(const thc_dims* d, int precision) {
   if (precision == THC_MIXED) {
     b += 4 * 2 * (s.plXn + s.plXT + s.plPs + s.plBc + s.plBd + s.plBy);   // bf16 slices
     b += sizeof(int) * s.nexp + 64;                                         // exponents, error word
+    b += (sizeof(int) + sizeof(float)) * s.npart;                           // split-K partial sums
   } else {
     b += s.x * s.el;             // X copy
   }
@@ -98,7 +104,8 @@ size_t memory_bytes(const thc_dims* d, int precision) {
 void free_all(thc_ctx* c) {
   void* ptrs[] = {c->X64, c->Vh64, c->X32, c->Vh32, c->Psi, c->D, c->M, c->Y,
                   c->Cdev, c->KCdev, c->exdev, c->partial, c->flag, c->Xn_pl, c->XT_pl,
-                  c->PsiA_pl, c->Bc_pl, c->Bd_pl, c->By_pl, c->ex_pl, c->tc_err};
+                  c->PsiA_pl, c->Bc_pl, c->Bd_pl, c->By_pl, c->ex_pl, c->tc_err, c->part_s0,
+                  c->part_bc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 7; i++)
@@ -163,7 +170,7 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
   }
   Sizes s = sizes_of(d, precision);
   struct Want { void** p; size_t bytes; };
-  Want want[24];
+  Want want[32];
   int nw = 0;
   auto W = [&](void** p, size_t bytes) { want[nw++] = Want{p, bytes}; };
   if (precision == THC_FP64) {
@@ -185,6 +192,10 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
     W((void**)&c->By_pl, 4 * 2 * s.plBy);
     W((void**)&c->ex_pl, sizeof(int) * s.nexp);
     W((void**)&c->tc_err, 64);
+    if (s.npart > 0) {
+      W((void**)&c->part_s0, sizeof(int) * s.npart);
+      W((void**)&c->part_bc, sizeof(float) * s.npart);
+    }
   }
   W(&c->Psi, s.psi * s.el);
   W(&c->Y, s.psi * s.el);
@@ -379,7 +390,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, col_exponents_z(C, Nn, n, nk, N, n, c->eC, s));
   CKC(c, embed_b(C, true, Nn, n, 1, false, false, nk, N, n, c->eC, c->Bc_pl, c->plBc, c->ldXT, s));
   CKC(c, tc_gemm(c->opXT, c->opBc, P, 2 * n, 2 * N, nk, c->eXT, P, c->eC, n, Psi, false, 2 * n, 2 * Pn,
-                 c->tc_err, s));
+                 c->part_s0, c->part_bc, c->tc_err, s));
   CKC(c, cudaEventRecord(stage_event(c, 1), s));
   // S2  D = Psi Psi^H on tensor cores: A = Psi and B = embedded Psi^H share the
   // row exponents of Psi
@@ -387,7 +398,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, slice_rows_c(Psi, Pn, n, nk, P, n, c->ePsi, c->PsiA_pl, c->plPs, c->ldPs, s));
   CKC(c, embed_b(Psi, false, Pn, 1, n, true, false, nk, n, P, c->ePsi, c->Bd_pl, c->plBd, c->ldPs, s));
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
-                 c->tc_err, s));
+                 c->part_s0, c->part_bc, c->tc_err, s));
   CKC(c, cudaEventRecord(stage_event(c, 2), s));
   // S3  M = IDFT(DFT(D) o Vh)
   CKC(c, kconv_c(D, c->Vh32, M, PP, c->n1, c->n2, c->n3, s));
@@ -399,7 +410,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, col_exponents_c(Y, Pn, n, nk, P, n, c->eY, s));
   CKC(c, embed_b(Y, false, Pn, n, 1, false, true, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
   CKC(c, tc_gemm(c->opXn, c->opBy, N, 2 * n, 2 * P, nk, c->eXn, N, c->eY, n, KC, true, 2 * n, 2 * Nn,
-                 c->tc_err, s));
+                 c->part_s0, c->part_bc, c->tc_err, s));
   CKC(c, cudaEventRecord(stage_event(c, 5), s));
   CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
   CKC(c, cudaEventRecord(stage_event(c, 6), s));
@@ -515,8 +526,10 @@ thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   if (!c || !launches) return THC_ERR_ARG;
   // FP64 and CUDA-core forms: S1, S2, S3, S4a, S4b, E_x partial, E_x final.
   // Tensor-core form: S1 3 (exponents, embed, GEMM), S2 4 (exponents, slices,
-  // embed, GEMM), S3 1, S4a 1, S4b 3, E_x 2.
-  *launches = c->precision == THC_MIXED ? 14 : 7;
+  // embed, GEMM), S3 1, S4a 1, S4b 3 (+1 when split along K), E_x 2.
+  int extra = 0;
+  if (c->precision == THC_MIXED && tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk) > 0) extra = 1;
+  *launches = c->precision == THC_MIXED ? 14 + extra : 7;
   return THC_OK;
 }
 

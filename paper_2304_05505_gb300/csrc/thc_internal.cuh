@@ -73,6 +73,8 @@ struct thc_ctx {
   uint16_t* Bd_pl;    // [nk][2 nisdf][ldPs] embedded Psi^H, B of S2 (ePsi)
   uint16_t* By_pl;    // [nk][2 nocc][ldM]   embedded Y, B of S4b eY [nk][nocc]
   int* ex_pl;         // eXn | eXT | ePsi | eC | eY
+  int* part_s0;       // split-K partial sums of the tensor-core GEMMs (exact leading class)
+  float* part_bc;     // and their FP32 remainders
   int *eXn, *eXT, *ePsi, *eC, *eY;
   long plXn, plXT, plPs, plBc, plBd, plBy;
   int ldXT, ldM, ldPs;
