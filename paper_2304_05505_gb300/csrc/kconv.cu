@@ -254,3 +254,4 @@ cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long
   return cudaGetLastError();
 }
 
+

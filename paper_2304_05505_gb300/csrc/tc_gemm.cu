@@ -56,15 +56,16 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BKR = 32;
 constexpr int NPL = 4;                                       // slices per operand
-constexpr int STAGES = 3;
 constexpr uint32_t TILE_BYTES = BM * BKR * 2;                // 8 KB (one plane of A or B)
-constexpr uint32_t STAGE_BYTES = 2 * NPL * TILE_BYTES;       // 64 KB
 constexpr int EPI_WARPS = 8;
-constexpr int EPI_WARP0 = 4;
-constexpr int NTHREADS = (EPI_WARP0 + EPI_WARPS) * 32;
 constexpr int DRAIN = 32;                                    // K blocks per exact chunk (1024 real K)
 constexpr long long WAIT_LIMIT = 4000000000LL;               // clock64 cycles (~2 s)
 constexpr uint32_t TMEM_COLS = 512;
+
+constexpr int STAGES = 3;
+constexpr uint32_t STAGE_BYTES = 2 * NPL * TILE_BYTES;       // 64 KB
+constexpr int EPI_WARP0 = 4;
+constexpr int NTHREADS = (EPI_WARP0 + EPI_WARPS) * 32;
 constexpr size_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -106,11 +107,34 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
   }
 }
 
-// The same wait taken by a whole warp, with one answer for every lane.
+// The same wait taken by a whole warp, with one answer for every lane.  Lane
+// 0 polls with a growing sleep (up to 256 ns) so that waiting epilogue and
+// converter warps leave the issue slots to the warps doing work.
 __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, int* err, int code) {
-  bool ok = true;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, err, code);
-  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    const long long t0 = clock64();
+    uint32_t ns = 8;
+    for (uint32_t it = 0;; it++) {
+      uint32_t done;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(bar), "r"(parity)
+          : "memory");
+      if (done) break;
+      if ((it & 15) == 15 && *(volatile int*)err != 0) { ok = 0; break; }
+      if (clock64() - t0 > WAIT_LIMIT) {
+        atomicOr(err, code);
+        ok = 0;
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 256) ns <<= 1;
+    }
+  }
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
@@ -193,6 +217,12 @@ struct Geometry {
   int mt, nt, nchunk, nkb;   // tiles along M and N, K chunks, K blocks
   long units;
 };
+
+// Exponent sentinel of an all-zero row (the rows' atomicMax starts below it).
+__device__ __forceinline__ int row_exp(const int* e, long i) {
+  const int x = e[i];
+  return x < -1000 ? 0 : x;
+}
 
 // OUT: 0 = FP32 result, 1 = FP64 result, 2 = partial sums (split K)
 template <int OUT>
@@ -281,6 +311,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(BM, BN);
+      const uint64_t dbase = smem_desc(sbase);
       uint32_t it = 0, local = 0;
       bool ok = true;
       for (long u = blockIdx.x; u < g.units && ok; u += gridDim.x, local++) {
@@ -296,25 +327,26 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
           const uint32_t ph = (it / STAGES) & 1;
           if (!mbar_wait(FULL(st), ph, err, 8)) { ok = false; break; }
           fence_after();
-          const uint32_t tA = sbase + st * STAGE_BYTES;
-          const uint32_t tB = tA + NPL * TILE_BYTES;
+          // descriptors: one base per stage, planes and K steps are offsets of
+          // (bytes >> 4) in the start-address field (no carry: smem < 256 KB)
+          const uint64_t aBase = dbase + ((st * STAGE_BYTES) >> 4);
+          const uint64_t bBase = aBase + ((NPL * TILE_BYTES) >> 4);
+          constexpr uint64_t PL = TILE_BYTES >> 4;
 #pragma unroll
           for (int kk = 0; kk < BKR / 16; kk++) {
-            const uint32_t off = kk * 32;
+            const uint64_t a = aBase + 2 * kk, b2 = bBase + 2 * kk;   // 32 B per K step
             const uint32_t acc = (kb == kb0 && kk == 0) ? 0u : 1u;
-            auto da = [&](int q) { return smem_desc(tA + q * TILE_BYTES + off); };
-            auto db = [&](int q) { return smem_desc(tB + q * TILE_BYTES + off); };
-            mma_bf16(accA, da(0), db(0), idesc, acc);          // exact leading class
+            mma_bf16(accA, a, b2, idesc, acc);                          // exact leading class
             // classes s + t = 3, 2, 1 (smallest first) into the second accumulator
-            mma_bf16(accBC, da(0), db(3), idesc, acc);
-            mma_bf16(accBC, da(1), db(2), idesc, 1u);
-            mma_bf16(accBC, da(2), db(1), idesc, 1u);
-            mma_bf16(accBC, da(3), db(0), idesc, 1u);
-            mma_bf16(accBC, da(0), db(2), idesc, 1u);
-            mma_bf16(accBC, da(1), db(1), idesc, 1u);
-            mma_bf16(accBC, da(2), db(0), idesc, 1u);
-            mma_bf16(accBC, da(0), db(1), idesc, 1u);
-            mma_bf16(accBC, da(1), db(0), idesc, 1u);
+            mma_bf16(accBC, a, b2 + 3 * PL, idesc, acc);
+            mma_bf16(accBC, a + PL, b2 + 2 * PL, idesc, 1u);
+            mma_bf16(accBC, a + 2 * PL, b2 + PL, idesc, 1u);
+            mma_bf16(accBC, a + 3 * PL, b2, idesc, 1u);
+            mma_bf16(accBC, a, b2 + 2 * PL, idesc, 1u);
+            mma_bf16(accBC, a + PL, b2 + PL, idesc, 1u);
+            mma_bf16(accBC, a + 2 * PL, b2, idesc, 1u);
+            mma_bf16(accBC, a, b2 + PL, idesc, 1u);
+            mma_bf16(accBC, a + PL, b2, idesc, 1u);
           }
           mma_commit(EMPTY(st));
         }
@@ -334,7 +366,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
       if (!mbar_wait_warp(AFULL(set), (local >> 1) & 1, err, 16)) break;
       fence_after();
       const int row = mi * BM + 32 * q + lane;
-      const int ea = (OUT != 2 && row < g.M) ? eA[(long)b * seA + row] : 0;
+      const int ea = (OUT != 2 && row < g.M) ? row_exp(eA, (long)b * seA + row) : 0;
       const uint32_t accA = tmem + lane_off + 256 * set, accBC = accA + 128;
 #pragma unroll 1
       for (int qq = 0; qq < 4; qq++) {
@@ -346,12 +378,22 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
         if constexpr (OUT == 2) {
           // exact leading sums and FP32 remainders of this K chunk
           const long base = (((long)kc * g.batch + b) * g.M + row) * g.Nr;
+          if (col0 + 16 <= g.Nr && (g.Nr % 4) == 0) {
 #pragma unroll
-          for (int j = 0; j < 16; j++)
-            if (col0 + j < g.Nr) {
-              ps0[base + col0 + j] = __float2int_rn(va[j]);
-              pbc[base + col0 + j] = vb[j];
+            for (int j = 0; j < 16; j += 4) {
+              *reinterpret_cast<int4*>(ps0 + base + col0 + j) =
+                  make_int4(__float2int_rn(va[j]), __float2int_rn(va[j + 1]), __float2int_rn(va[j + 2]),
+                            __float2int_rn(va[j + 3]));
+              *reinterpret_cast<float4*>(pbc + base + col0 + j) = make_float4(vb[j], vb[j + 1], vb[j + 2], vb[j + 3]);
             }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; j++)
+              if (col0 + j < g.Nr) {
+                ps0[base + col0 + j] = __float2int_rn(va[j]);
+                pbc[base + col0 + j] = vb[j];
+              }
+          }
         } else if constexpr (OUT == 1) {
           double* o = (double*)out + (long)b * sbo + (long)row * ldo;
 #pragma unroll
@@ -419,7 +461,7 @@ __global__ void tc_combine_kernel(const int* __restrict__ ps0, const float* __re
       s0 += ps0[(long)c * total + i];
       bc += pbc[(long)c * total + i];
     }
-    const int e = eA[(long)b * seA + m] + eB[(long)b * seB + (col >> 1)] - 14;
+    const int e = row_exp(eA, (long)b * seA + m) + eB[(long)b * seB + (col >> 1)] - 14;
     if (OUT_F64)
       ((double*)out)[(long)b * sbo + (long)m * ldo + col] = ((double)s0 + (double)bc) * pow2d(e);
     else
@@ -489,30 +531,24 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
   }
   const unsigned grid = (unsigned)std::min<long>(g.units, nsm);
-  cudaError_t e;
-#define LAUNCH(OUTK)                                                                                     \
-  e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
-                           (int)SMEM_BYTES);                                                             \
-  if (e != cudaSuccess) return e;                                                                        \
-  tc_gemm_kernel<OUTK><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, out, ldo, sbo, ps0, \
-                                                          pbc, err);
-  if (split) {
-    LAUNCH(2)
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const long total = (long)batch * M * Nr;
-    const unsigned cg = (unsigned)std::min<long>((total + 255) / 256, 152L * 16);
-    if (out_f64)
-      tc_combine_kernel<true><<<cg, 256, 0, s>>>(ps0, pbc, g.nchunk, batch, M, Nr, eA, seA, eB, seB, out, ldo,
-                                                 sbo);
-    else
-      tc_combine_kernel<false><<<cg, 256, 0, s>>>(ps0, pbc, g.nchunk, batch, M, Nr, eA, seA, eB, seB, out, ldo,
-                                                  sbo);
-  } else if (out_f64) {
-    LAUNCH(1)
-  } else {
-    LAUNCH(0)
+  cudaError_t e = cudaSuccess;
+#define LAUNCH(OUTK)                                                                                      \
+  {                                                                                                       \
+    e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                             (int)SMEM_BYTES);                                                            \
+    if (e != cudaSuccess) return e;                                                                       \
+    tc_gemm_kernel<OUTK><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, out, ldo, sbo,     \
+                                                            ps0, pbc, err);                               \
   }
+  if (split) LAUNCH(2) else if (out_f64) LAUNCH(1) else LAUNCH(0)
 #undef LAUNCH
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !split) return e;
+  const long total = (long)batch * M * Nr;
+  const unsigned cg = (unsigned)std::min<long>((total + 255) / 256, 152L * 16);
+  if (out_f64)
+    tc_combine_kernel<true><<<cg, 256, 0, s>>>(ps0, pbc, g.nchunk, batch, M, Nr, eA, seA, eB, seB, out, ldo, sbo);
+  else
+    tc_combine_kernel<false><<<cg, 256, 0, s>>>(ps0, pbc, g.nchunk, batch, M, Nr, eA, seA, eB, seB, out, ldo, sbo);
   return cudaGetLastError();
 }

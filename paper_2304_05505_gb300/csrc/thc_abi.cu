@@ -403,7 +403,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   // S3  M = IDFT(DFT(D) o Vh)
   CKC(c, kconv_c(D, c->Vh32, M, PP, c->n1, c->n2, c->n3, s));
   CKC(c, cudaEventRecord(stage_event(c, 3), s));
-  // S4a Y = M Psi (CUDA cores, compensated sums)
+  // S4a Y = M Psi on CUDA cores with compensated FP32 sums
   CKC(c, (gemm_c_comp<float2, float2, float2>(A_MK, B_KN, P, n, P, M, P, PP, Psi, n, Pn, Y, n, Pn, nk, s)));
   CKC(c, cudaEventRecord(stage_event(c, 4), s));
   // S4b KC = conj(X) Y on tensor cores: B = embedded Y (conj-A form)
@@ -526,10 +526,14 @@ thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   if (!c || !launches) return THC_ERR_ARG;
   // FP64 and CUDA-core forms: S1, S2, S3, S4a, S4b, E_x partial, E_x final.
   // Tensor-core form: S1 3 (exponents, embed, GEMM), S2 4 (exponents, slices,
-  // embed, GEMM), S3 1, S4a 1, S4b 3 (+1 when split along K), E_x 2.
-  int extra = 0;
-  if (c->precision == THC_MIXED && tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk) > 0) extra = 1;
-  *launches = c->precision == THC_MIXED ? 14 + extra : 7;
+  // embed, GEMM), S3 1, S4a 1 (CUDA cores), S4b 3 (+1 combine kernel when
+  // split along K), E_x 2.
+  if (c->precision == THC_MIXED) {
+    const int split = tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk) > 0 ? 1 : 0;
+    *launches = 3 + 4 + 1 + 1 + 3 + split + 2;
+  } else {
+    *launches = 7;
+  }
   return THC_OK;
 }
 
