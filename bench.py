@@ -34,6 +34,9 @@ WORKLOAD = ("benzene-shaped orthorhombic cell 13.9x17.8x12.9 bohr, 48 centres, N
             "4x4x4 k (N_k=64), N_ISDF=1200, 40^3 grid (config C2)")
 CONFIG = "C2"
 SAMPLE_FRACTION = 8      # the CPU oracle sample is 1/8 of a build
+# stages of the mixed build that run on tensor cores (the others: S3 and S5
+# stream HBM, S4a runs on CUDA cores)
+TENSOR_STAGES = ("S1_collocate", "S2_density", "S4b_backproject")
 
 
 def parse():
@@ -166,7 +169,7 @@ def stage_work(d: dict) -> dict:
     }
 
 
-def kernel_roofline(stage: str, ms: float, work: dict, pk: dict, clocks: dict, tensor: bool = True) -> dict:
+def kernel_roofline(stage: str, ms: float, work: dict, pk: dict, clocks: dict, tensor: bool) -> dict:
     w = work[stage]
     traffic = measured_traffic(stage)
     if w["flops"] is None or stage == "S5_energy":
@@ -413,8 +416,9 @@ def run_ours(args, world, rank, local):
     names = thc.STAGES
     stages = {nm: ms for nm, ms in zip(names, stage_ms)}
     dominant = max(stages, key=stages.get)
-    roof = kernel_roofline(dominant, stages[dominant], work, pk, clocks)
-    per_stage = {nm: kernel_roofline(nm, stages[nm], work, pk, clocks) for nm in names}
+    roof = kernel_roofline(dominant, stages[dominant], work, pk, clocks, tensor=dominant in TENSOR_STAGES)
+    per_stage = {nm: kernel_roofline(nm, stages[nm], work, pk, clocks, tensor=nm in TENSOR_STAGES)
+                 for nm in names}
 
 
     line = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world, "steps": args.steps,

@@ -6,7 +6,8 @@
 // A is read as A[m*lda + k] (A_MK), A[k*lda + m] (A_KM, a transpose) or
 // conj(A[m*lda + k]) (A_MK_CONJ); B as B[k*ldb + n] (B_KN) or
 // conj(B[n*ldb + k]) (B_NK_CONJ).  Tiles of 64 x 64 outputs, 16-deep k slabs
-// staged in shared memory, 256 threads with 4 x 4 outputs each.
+// staged in shared memory.  FP64: 256 threads with 4 x 4 outputs each.  FP32:
+// 512 threads with 2 x 4 outputs each and double-buffered slabs.
 //
 // Three arithmetic forms:
 //  * FP64 (double2 throughout): the plain FP64 build.
@@ -154,6 +155,147 @@ gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int lda, long sA,
     }
 }
 
+// FP32 form, 512 threads, 2 x 4 complex outputs a thread (rows ty + 32 i,
+// columns tx + 16 j), and two shared-memory slabs: the next slab is fetched
+// into registers while the current one is multiplied.
+constexpr int NT2 = 512;
+
+template <int LA, int LB, bool COMP, typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(NT2)
+gemm_c_kernel(int M, int N, int K, const TA* __restrict__ A, int lda, long sA, const TB* __restrict__ B,
+              int ldb, long sB, TC* __restrict__ C, int ldc, long sC) {
+  __shared__ float2 As[2][BK][BM + 1];
+  __shared__ float2 Bs[2][BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const long b = blockIdx.z;
+  A += b * sA;
+  B += b * sB;
+  C += b * sC;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+
+  float2 acc[2][4], hi[2][4], lo[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      acc[i][j] = make_float2(0.f, 0.f);
+      hi[i][j] = make_float2(0.f, 0.f);
+      lo[i][j] = make_float2(0.f, 0.f);
+    }
+
+  // this thread's two A and two B elements of a slab
+  float2 pa[2], pb[2];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+      const int e = tid + r * NT2;
+      int mm, kk;
+      if (LA == A_KM) { kk = e / BM; mm = e % BM; }
+      else { mm = e / BK; kk = e % BK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (gm < M && gk < K) {
+        v = to_c((LA == A_KM) ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk], 0.f);
+        if (LA == A_MK_CONJ) v.y = -v.y;
+      }
+      pa[r] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+      const int e = tid + r * NT2;
+      int nn, kk;
+      if (LB == B_KN) { kk = e / BN; nn = e % BN; }
+      else { nn = e / BK; kk = e % BK; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (gn < N && gk < K) {
+        if (LB == B_KN) v = to_c(B[(long)gk * ldb + gn], 0.f);
+        else { v = to_c(B[(long)gn * ldb + gk], 0.f); v.y = -v.y; }
+      }
+      pb[r] = v;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+      const int e = tid + r * NT2;
+      if (LA == A_KM) As[buf][e / BM][e % BM] = pa[r];
+      else As[buf][e % BK][e / BK] = pa[r];
+      if (LB == B_KN) Bs[buf][e / BN][e % BN] = pb[r];
+      else Bs[buf][e % BK][e / BK] = pb[r];
+    }
+  };
+
+  fetch(0);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    const bool more = k0 + BK < K;
+    if (more) fetch(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; kk++) {
+      float2 a[2], bb[4];
+#pragma unroll
+      for (int i = 0; i < 2; i++) a[i] = As[buf][kk][ty + 32 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) bb[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          acc[i][j].x = fmaf(a[i].x, bb[j].x, acc[i][j].x);
+          acc[i][j].x = fmaf(-a[i].y, bb[j].y, acc[i][j].x);
+          acc[i][j].y = fmaf(a[i].x, bb[j].y, acc[i][j].y);
+          acc[i][j].y = fmaf(a[i].y, bb[j].x, acc[i][j].y);
+        }
+    }
+    if constexpr (COMP) {
+#pragma unroll
+      for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          float s, e;
+          two_sum(hi[i][j].x, acc[i][j].x, s, e);
+          hi[i][j].x = s; lo[i][j].x += e;
+          two_sum(hi[i][j].y, acc[i][j].y, s, e);
+          hi[i][j].y = s; lo[i][j].y += e;
+          acc[i][j] = make_float2(0.f, 0.f);
+        }
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int gm = m0 + ty + 32 * i, gn = n0 + tx + 16 * j;
+      if (gm < M && gn < N) {
+        if constexpr (COMP) store_out(&C[(long)gm * ldc + gn], hi[i][j], lo[i][j]);
+        else store_plain(&C[(long)gm * ldc + gn], acc[i][j]);
+      }
+    }
+}
+
+template <bool COMP, typename TA, typename TB, typename TC>
+cudaError_t launch_c(int la, int lb, int M, int N, int K, const TA* A, int lda, long sA, const TB* B, int ldb,
+                     long sB, TC* C, int ldc, long sC, int batch, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+#define L(LA_, LB_)                                                                                         \
+  if (la == LA_ && lb == LB_) {                                                                             \
+    gemm_c_kernel<LA_, LB_, COMP, TA, TB, TC><<<grid, NT2, 0, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, \
+                                                                   sC);                                     \
+    return cudaGetLastError();                                                                              \
+  }
+  L(A_MK, B_KN) L(A_KM, B_KN) L(A_MK_CONJ, B_KN) L(A_MK, B_NK_CONJ)
+#undef L
+  return cudaErrorInvalidValue;
+}
+
 template <typename R, bool COMP, typename TA, typename TB, typename TC>
 cudaError_t launch(int la, int lb, int M, int N, int K, const TA* A, int lda, long sA,
                    const TB* B, int ldb, long sB, TC* C, int ldc, long sC, int batch,
@@ -183,13 +325,13 @@ template <typename TA, typename TB, typename TC>
 cudaError_t gemm_c_comp(int la, int lb, int M, int N, int K, const TA* A, int lda, long sA,
                         const TB* B, int ldb, long sB, TC* C, int ldc, long sC, int batch,
                         cudaStream_t s) {
-  return launch<float, true>(la, lb, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, s);
+  return launch_c<true>(la, lb, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, s);
 }
 
 cudaError_t gemm_c_plain(int la, int lb, int M, int N, int K, const float2* A, int lda, long sA,
                          const float2* B, int ldb, long sB, float2* C, int ldc, long sC,
                          int batch, cudaStream_t s) {
-  return launch<float, false>(la, lb, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, s);
+  return launch_c<false>(la, lb, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, s);
 }
 
 template cudaError_t gemm_c_comp<float2, double2, float2>(int, int, int, int, int, const float2*,

@@ -144,8 +144,11 @@ __global__ void kconv_kernel(const typename cplx<R>::type* __restrict__ D,
   const long e = (long)blockIdx.x * T + tid;
   const bool ok = e < npq;
   CT* x = buf + tid;
+  // unrolled so that many independent loads are in flight per thread
+#pragma unroll 16
   for (int k = 0; k < nk; k++) x[(long)k * T] = ok ? D[(long)k * npq + e] : CT{(R)0, (R)0};
   dft3<R>(x, T, tw, -1);
+#pragma unroll 16
   for (int a = 0; a < nk; a++) {
     CT v = ok ? Vh[(long)a * npq + e] : CT{(R)0, (R)0};
     x[(long)a * T] = cmul(x[(long)a * T], v);

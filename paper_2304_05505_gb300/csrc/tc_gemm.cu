@@ -24,7 +24,8 @@
 // s + t >= 4 (below 2^-32 of the row scales) are dropped.
 //
 // Work units: a 128 x 128 output tile and a chunk of at most 1024 real K (so
-// the leading sum of a unit is exact).  When K needs more than one chunk the
+// the leading sum of a unit is exact; shorter chunks also shorten the FP32
+// sums of the other classes).  When K needs more than one chunk the
 // units write their exact int32 leading sums and FP32 remainders to a partial
 // buffer and tc_combine adds the chunks (split K); otherwise they write the
 // scaled result directly.
@@ -58,7 +59,7 @@ constexpr int BM = 128, BN = 128, BKR = 32;
 constexpr int NPL = 4;                                       // slices per operand
 constexpr uint32_t TILE_BYTES = BM * BKR * 2;                // 8 KB (one plane of A or B)
 constexpr int EPI_WARPS = 8;
-constexpr int DRAIN = 32;                                    // K blocks per exact chunk (1024 real K)
+constexpr int MAX_CHUNK_KB = 32;                             // K blocks per exact chunk, at most (1024 real K)
 constexpr long long WAIT_LIMIT = 4000000000LL;               // clock64 cycles (~2 s)
 constexpr uint32_t TMEM_COLS = 512;
 
@@ -215,6 +216,7 @@ __device__ __forceinline__ double pow2d(int e) {
 struct Geometry {
   int M, Nr, Kr, batch;
   int mt, nt, nchunk, nkb;   // tiles along M and N, K chunks, K blocks
+  int ckb;                   // K blocks per chunk
   long units;
 };
 
@@ -294,8 +296,8 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
       for (long u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
         int b, mi, ni, kc;
         decode(u, b, mi, ni, kc);
-        const int kb1 = min(g.nkb, (kc + 1) * DRAIN);
-        for (int kb = kc * DRAIN; kb < kb1; kb++, it++) {
+        const int kb1 = min(g.nkb, (kc + 1) * g.ckb);
+        for (int kb = kc * g.ckb; kb < kb1; kb++, it++) {
           const int st = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
           if (!mbar_wait(EMPTY(st), ph ^ 1, err, 2)) { ok = false; break; }
@@ -321,7 +323,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
         if (!mbar_wait(AEMPTY(set), ((local >> 1) & 1) ^ 1, err, 4)) break;
         fence_after();
         const uint32_t accA = tmem + 256 * set, accBC = accA + 128;
-        const int kb0 = kc * DRAIN, kb1 = min(g.nkb, (kc + 1) * DRAIN);
+        const int kb0 = kc * g.ckb, kb1 = min(g.nkb, (kc + 1) * g.ckb);
         for (int kb = kb0; kb < kb1; kb++, it++) {
           const int st = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
@@ -499,15 +501,16 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-long tc_partial_elems(int M, int Nr, int Kr, int batch) {
+long tc_partial_elems(int M, int Nr, int Kr, int batch, int chunk_k) {
+  const int ckb = std::max(1, std::min(MAX_CHUNK_KB, chunk_k / BKR));
   const int nkb = (Kr + BKR - 1) / BKR;
-  const int nchunk = (nkb + DRAIN - 1) / DRAIN;
+  const int nchunk = (nkb + ckb - 1) / ckb;
   return nchunk > 1 ? (long)nchunk * batch * M * Nr : 0;
 }
 
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
-                    long sbo, int* ps0, float* pbc, int* err, cudaStream_t s) {
+                    long sbo, int* ps0, float* pbc, int* err, cudaStream_t s, int chunk_k) {
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   Maps maps;
   for (int p = 0; p < NPL; p++) {
@@ -519,7 +522,8 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   g.mt = (M + BM - 1) / BM;
   g.nt = (Nr + BN - 1) / BN;
   g.nkb = (Kr + BKR - 1) / BKR;
-  g.nchunk = (g.nkb + DRAIN - 1) / DRAIN;
+  g.ckb = std::max(1, std::min(MAX_CHUNK_KB, chunk_k / BKR));
+  g.nchunk = (g.nkb + g.ckb - 1) / g.ckb;
   g.units = (long)batch * g.mt * g.nt * g.nchunk;
   if (g.units <= 0) return cudaSuccess;
   const bool split = g.nchunk > 1;

@@ -17,16 +17,17 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
 // out[b][m][n] (n < Nr real columns, interleaved complex) = A'[b] B'[b]^T for
 // sliced operands: A' has M rows with exponents eA[b * seA + m], B' has Nr rows
 // whose pair (2j, 2j + 1) shares the exponent eB[b * seB + j]; Kr real K.
-// FP32 output, or FP64 output when out_f64.  When Kr > 1024 the product is
-// split along K and ps0 / pbc (tc_partial_elems elements each) hold the exact
-// chunk sums until they are combined.  `err` receives a nonzero code if a
-// device wait gave up.
+// FP32 output, or FP64 output when out_f64.  K is taken in chunks of
+// chunk_k real elements (a multiple of 32, at most 1024); with more than one
+// chunk ps0 / pbc (tc_partial_elems elements each) hold the exact chunk sums
+// until they are combined.  `err` receives a nonzero code if a device wait
+// gave up.
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
-                    long sbo, int* ps0, float* pbc, int* err, cudaStream_t s);
+                    long sbo, int* ps0, float* pbc, int* err, cudaStream_t s, int chunk_k);
 
 // Elements of each split-K partial buffer tc_gemm needs for this shape (0 if none).
-long tc_partial_elems(int M, int Nr, int Kr, int batch);
+long tc_partial_elems(int M, int Nr, int Kr, int batch, int chunk_k);
 
 // Row exponents of src[b][r][0..cols) (contiguous rows): e[b * rows + r], the
 // smallest e with max_c max(|re|, |im|) < 2^e (0 for a zero row).

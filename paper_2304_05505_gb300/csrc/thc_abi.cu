@@ -44,6 +44,12 @@ struct Sizes {
 
 int pad8(int x) { return (x + 7) & ~7; }
 
+// K chunk (real elements) of the tensor-core GEMMs: 512 for the long
+// contractions S1 and S4b, so that the FP32 sums of the small product classes
+// stay short; S2's K (2 n_occ) fits one chunk.
+constexpr int kChunkLong = 512;
+constexpr int kChunkShort = 1024;
+
 Sizes sizes_of(const thc_dims* d, int precision) {
   Sizes s;
   s.nk = (long)d->n1 * d->n2 * d->n3;
@@ -62,9 +68,9 @@ Sizes sizes_of(const thc_dims* d, int precision) {
   s.plBd = s.nk * 2L * d->nisdf * s.ldPs;
   s.plBy = s.nk * 2 * d->nocc * (long)s.ldM;
   s.nexp = s.nk * (d->nbas + 2L * d->nisdf + 2L * d->nocc);
-  s.npart = std::max({tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nbas, (int)s.nk),
-                      tc_partial_elems(d->nisdf, 2 * d->nisdf, 2 * d->nocc, (int)s.nk),
-                      tc_partial_elems(d->nbas, 2 * d->nocc, 2 * d->nisdf, (int)s.nk)});
+  s.npart = std::max({tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nbas, (int)s.nk, kChunkLong),
+                      tc_partial_elems(d->nisdf, 2 * d->nisdf, 2 * d->nocc, (int)s.nk, kChunkShort),
+                      tc_partial_elems(d->nbas, 2 * d->nocc, 2 * d->nisdf, (int)s.nk, kChunkLong)});
   return s;
 }
 
@@ -390,7 +396,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, col_exponents_z(C, Nn, n, nk, N, n, c->eC, s));
   CKC(c, embed_b(C, true, Nn, n, 1, false, false, nk, N, n, c->eC, c->Bc_pl, c->plBc, c->ldXT, s));
   CKC(c, tc_gemm(c->opXT, c->opBc, P, 2 * n, 2 * N, nk, c->eXT, P, c->eC, n, Psi, false, 2 * n, 2 * Pn,
-                 c->part_s0, c->part_bc, c->tc_err, s));
+                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong));
   CKC(c, cudaEventRecord(stage_event(c, 1), s));
   // S2  D = Psi Psi^H on tensor cores: A = Psi and B = embedded Psi^H share the
   // row exponents of Psi
@@ -398,7 +404,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, slice_rows_c(Psi, Pn, n, nk, P, n, c->ePsi, c->PsiA_pl, c->plPs, c->ldPs, s));
   CKC(c, embed_b(Psi, false, Pn, 1, n, true, false, nk, n, P, c->ePsi, c->Bd_pl, c->plBd, c->ldPs, s));
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
-                 c->part_s0, c->part_bc, c->tc_err, s));
+                 c->part_s0, c->part_bc, c->tc_err, s, kChunkShort));
   CKC(c, cudaEventRecord(stage_event(c, 2), s));
   // S3  M = IDFT(DFT(D) o Vh)
   CKC(c, kconv_c(D, c->Vh32, M, PP, c->n1, c->n2, c->n3, s));
@@ -410,7 +416,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, col_exponents_c(Y, Pn, n, nk, P, n, c->eY, s));
   CKC(c, embed_b(Y, false, Pn, n, 1, false, true, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
   CKC(c, tc_gemm(c->opXn, c->opBy, N, 2 * n, 2 * P, nk, c->eXn, N, c->eY, n, KC, true, 2 * n, 2 * Nn,
-                 c->part_s0, c->part_bc, c->tc_err, s));
+                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong));
   CKC(c, cudaEventRecord(stage_event(c, 5), s));
   CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
   CKC(c, cudaEventRecord(stage_event(c, 6), s));
@@ -529,8 +535,9 @@ thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   // embed, GEMM), S3 1, S4a 1 (CUDA cores), S4b 3 (+1 combine kernel when
   // split along K), E_x 2.
   if (c->precision == THC_MIXED) {
-    const int split = tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk) > 0 ? 1 : 0;
-    *launches = 3 + 4 + 1 + 1 + 3 + split + 2;
+    const int s1 = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nbas, c->nk, kChunkLong) > 0 ? 1 : 0;
+    const int s4b = tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk, kChunkLong) > 0 ? 1 : 0;
+    *launches = 3 + s1 + 4 + 1 + 1 + 3 + s4b + 2;
   } else {
     *launches = 7;
   }

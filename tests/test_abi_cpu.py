@@ -61,8 +61,9 @@ def test_memory_bytes_arithmetic():
     planes = nk * (N * pad8(2 * P) + P * pad8(2 * N) + P * pad8(2 * n)
                    + 2 * n * pad8(2 * N) + 2 * P * pad8(2 * n) + 2 * n * pad8(2 * P))
     exps = nk * (N + 2 * P + 2 * n)
-    kchunks = -(-(2 * P) // 1024)                       # split-K chunks of S4b (K = 2 N_P real)
-    part = kchunks * nk * N * 2 * n if kchunks > 1 else 0
+    c4b = -(-(2 * P) // 512)                             # split-K chunks of S4b (K = 2 N_P real)
+    c1 = -(-(2 * N) // 512)                              # and of S1 (K = 2 N real)
+    part = max(c4b * nk * N * 2 * n if c4b > 1 else 0, c1 * nk * P * 2 * n if c1 > 1 else 0)
     tc = 8 * (nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + 4 * 2 * planes + 4 * exps + 64 \
         + 8 * part + common
     assert thc.thc_memory_bytes(d, thc.THC_MIXED) == tc
