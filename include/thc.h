@@ -2,7 +2,7 @@
  * thc.h -- C ABI of the GB300 THC-oo-K exact-exchange build.
  *
  * One build is the per-SCF-iteration exchange step of THC-oo-K
- * (Rettig, Lee, Head-Gordon, arXiv 2304.05505, Algorithm 2, the lines that
+ * (Rettig, Lee, Head-Gordon, arXiv 2304.05505, Algorithm 2: the steps that
  * form X^k_PQ by FFT convolution and K_ij):
  *
  *   S1  Psi^k[P,i] = sum_mu X^k[mu,P] C^k[mu,i]        orbitals at the points

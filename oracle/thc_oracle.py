@@ -68,7 +68,7 @@ def collocate(X: np.ndarray, C: np.ndarray) -> np.ndarray:
 def density(Psi: np.ndarray) -> np.ndarray:
     """Step 2: D^k[P, Q] = sum_i Psi^k[P, i] conj(Psi^k[Q, i]).
 
-    The inner sum over i of the convolution line of Algorithm 2."""
+    The inner sum over i in the convolution step of Algorithm 2."""
     nk = Psi.shape[0]
     return np.stack([Psi[k] @ Psi[k].conj().T for k in range(nk)])
 
@@ -102,14 +102,14 @@ def kconv_fft(D: np.ndarray, V: np.ndarray, mesh) -> np.ndarray:
 
 
 def apply_M(M: np.ndarray, Psi: np.ndarray) -> np.ndarray:
-    """Step 4a: Y^k = M^k Psi^k (first half of the K_ij line of Algorithm 2)."""
+    """Step 4a: Y^k = M^k Psi^k (first half of the K_ij step of Algorithm 2)."""
     return np.stack([M[k] @ Psi[k] for k in range(M.shape[0])])
 
 
 def backproject(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
     """Step 4b: (K C)^k[mu, i] = sum_P conj(X^k[mu, P]) Y^k[P, i].
 
-    With K^k = conj(X^k) M^k X^{kT} (Algorithm 1's K line), this is K^k C^k."""
+    With K^k = conj(X^k) M^k X^{kT} (the K step of Algorithm 1), this is K^k C^k."""
     return np.stack([X[k].conj() @ Y[k] for k in range(X.shape[0])])
 
 
