@@ -140,6 +140,25 @@ thc_status thc_launches_per_build(const thc_ctx* ctx, int* launches);
 
 thc_status thc_destroy(thc_ctx* ctx);
 
+/* Interpolation points (setup, outside the timed build).  Greedy pivoted
+ * Cholesky, in FP64, of the Gram matrix of occupied pair products
+ *   A(r, r') = | sum_f conj(U[f][r]) U[f][r'] |^2
+ * over candidate points r: the metric of the least-squares fit of Eq.
+ * pbcinterpvec restricted to occupied orbitals (Eq. orbprodoo); in exact
+ * arithmetic the points of the QR decomposition with column pivoting of
+ * Sec. 2.1.  Each step takes the candidate with the largest residual diagonal
+ * (the lowest index among equal ones).
+ * U: device, [nfunc][ncand] complex128, U[f][r] = u^k_i(r_c) for f = (k, i)
+ * (the cell-periodic parts of the occupied orbitals at the candidates).
+ * Stops after npts points or when the residual trace falls to rel_tol times
+ * trace(A).  points_host (host, npts ints) receives the candidate indices in
+ * selection order, -1 past the end; npoints_host the number chosen.
+ * resid_diag (device, ncand doubles, may be NULL) receives the residual
+ * diagonal.  Allocates its own scratch (npts * ncand doubles) and waits for
+ * `stream`. */
+thc_status thc_select_points(const double* U, int nfunc, int ncand, int npts, double rel_tol,
+                             int* points_host, int* npoints_host, double* resid_diag, void* stream);
+
 /* The k-mesh convolution alone, M^k[P,Q] = sum_k' D^k'[P,Q] V^(k'-k)[P,Q] in
  * FP64, for callers that cannot allocate device memory when they call: for
  * example a host framework that has already reserved the device's memory in

@@ -131,3 +131,58 @@ def brute_force_exchange(lattice, grid, mesh, Xgrid, C) -> dict:
                 hh = hh.reshape(nb, n, ng)[:, :, flat] / ng
                 KC[k] += (vol / nk) * w * np.einsum("mjg,g,ijg->mi", hh, v, gh.conj())
     return dict(Ex=float(Ex.real), Ex_imag=float(Ex.imag), KC=KC)
+
+
+# ----------------------------------------------------------------------------
+# interpolation points: pivoted Cholesky of the occupied-pair Gram matrix
+# ----------------------------------------------------------------------------
+
+def pair_gram(U: np.ndarray) -> np.ndarray:
+    """A(r, r') = |sum_f conj(U[f, r]) U[f, r']|^2 for U[f, r] = u^k_i(r),
+    f = (k, i): the Gram matrix of all occupied pair products
+    conj(u^k_i) u^k'_j (the metric of the fit in Eq. pbcinterpvec, restricted
+    to occupied orbitals as in Eq. orbprodoo)."""
+    B = U.conj().T @ U
+    return np.abs(B) ** 2
+
+
+def pivoted_cholesky(U: np.ndarray, npts: int, rel_tol: float = 1e-14) -> dict:
+    """Greedy pivoted Cholesky of pair_gram(U) without forming it: the pivot
+    is the largest residual diagonal (the lowest index among equal ones); stop
+    after npts pivots or when the residual trace falls to rel_tol times the
+    trace of A.  Returns pivots, the residual diagonal and the factor columns."""
+    rho = np.sum(np.abs(U) ** 2, axis=0)
+    d = rho ** 2                                   # A(r, r)
+    tr0 = d.sum()
+    cols, piv = [], []
+    for _ in range(npts):
+        if d.sum() <= rel_tol * tr0:
+            break
+        p = int(np.argmax(d))
+        a = np.abs(U.conj().T @ U[:, p]) ** 2      # column A(:, p)
+        for L in cols:
+            a = a - L * L[p]
+        ell = a / np.sqrt(d[p])
+        d = np.maximum(d - ell ** 2, 0.0)
+        d[p] = 0.0
+        cols.append(ell)
+        piv.append(p)
+    return dict(points=np.array(piv, dtype=np.int64), resid=d, L=np.array(cols))
+
+
+def isdf_fit(U: np.ndarray, points: np.ndarray) -> np.ndarray:
+    """Interpolation vectors xi[P, r] = sum_Q S^-1[P, Q] A(r_Q, r), S = A[points,
+    points] (the least-squares fit of Eq. orbprodoo; S is the ISDF metric)."""
+    A = pair_gram(U)
+    S = A[np.ix_(points, points)]
+    return np.linalg.solve(S, A[points, :])
+
+
+def fit_error(U: np.ndarray, points: np.ndarray) -> float:
+    """Relative residual sqrt(sum_r d_r / sum_r A_rr) of the pivoted-Cholesky
+    (Schur complement) diagonal after selecting `points`."""
+    A = pair_gram(U)
+    S = A[np.ix_(points, points)]
+    Ar = A[:, points]
+    d = np.diag(A) - np.einsum("rp,pq,rq->r", Ar, np.linalg.inv(S), Ar)
+    return float(np.sqrt(max(d.sum(), 0.0) / np.trace(A)))

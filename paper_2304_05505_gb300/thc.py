@@ -28,7 +28,8 @@ STATUS = {0: "THC_OK", 1: "THC_ERR_ARG", 2: "THC_ERR_OOM", 3: "THC_ERR_CUDA",
 EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_kernel",
            "thc_build", "thc_build_host", "thc_get_intermediate", "thc_stage_times",
            "thc_launches_per_build", "thc_destroy", "thc_status_string", "thc_last_error",
-           "thc_profile_begin", "thc_profile_end", "thc_sync", "thc_kconv_noalloc"]
+           "thc_profile_begin", "thc_profile_end", "thc_sync", "thc_kconv_noalloc",
+           "thc_select_points"]
 
 
 class ThcDims(ctypes.Structure):
@@ -69,6 +70,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_destroy.argtypes = [vp]
     lib.thc_sync.argtypes = [vp]
     lib.thc_kconv_noalloc.argtypes = [dp, dp, dp, ip, ip, ip, ctypes.c_long, vp]
+    lib.thc_select_points.argtypes = [dp, ip, ip, ip, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), dp, vp]
     lib.thc_status_string.argtypes = [ip]
     lib.thc_status_string.restype = ctypes.c_char_p
     lib.thc_last_error.argtypes = [vp]
@@ -210,6 +213,23 @@ def thc_kconv_noalloc(D, V, M, mesh, npq: int, stream: int | None = None) -> Non
     _check(load().thc_kconv_noalloc(_dev_ptr(D, name="D"), _dev_ptr(V, name="V"), _dev_ptr(M, name="M"),
                                     int(mesh[0]), int(mesh[1]), int(mesh[2]), int(npq), ctypes.c_void_p(stream)),
            "thc_kconv_noalloc")
+
+
+def thc_select_points(U, npts: int, rel_tol: float = 1e-14, stream: int | None = None):
+    """FP64 pivoted-Cholesky interpolation points (see include/thc.h).
+
+    U: CUDA complex128 tensor [nfunc][ncand].  Returns (points, residual diagonal)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    nfunc, ncand = U.shape
+    pts = (ctypes.c_int * int(npts))()
+    cnt = ctypes.c_int(0)
+    resid = torch.empty(ncand, dtype=torch.float64, device=U.device)
+    _check(load().thc_select_points(_dev_ptr(U, name="U"), int(nfunc), int(ncand), int(npts), float(rel_tol),
+                                    pts, ctypes.byref(cnt), resid.data_ptr(), ctypes.c_void_p(stream)),
+           "thc_select_points")
+    return np.array(pts[: cnt.value], dtype=np.int64), resid
 
 
 def thc_destroy(ctx) -> None:
