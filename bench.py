@@ -179,16 +179,18 @@ def kernel_roofline(stage: str, ms: float, work: dict, pk: dict, clocks: dict, t
                 "frac": achieved / peak, "traffic": traffic, "peak_source": pk["source"],
                 "algorithmic_bytes": w["bytes"], "ms": ms}
     if tensor:
-        # tcgen05 bf16 GEMM on three-plane split operands: six bf16 products per
-        # real product.  Achieved counts the algorithmic complex flops (8 per
-        # complex multiply-add); the issued bf16 flops are 6x that.
+        # tcgen05 bf16 GEMM on four-slice fixed-point operands: ten slice
+        # products (the classes s + t <= 3) per real product, and the real
+        # embedding of a complex product costs the same 8 flops as the
+        # algorithmic count.  Achieved counts the algorithmic complex flops
+        # (8 per complex multiply-add); the issued bf16 flops are 10x that.
         peak = pk["bf16_tflops_sustained"]
         achieved = w["flops"] / (ms * 1e-3) / 1e12
         return {"kernel": stage, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{pk['source']} bf16 sustained (cuBLAS)",
-                "algorithmic_flops": w["flops"], "issued_bf16_flops": 6 * w["flops"],
-                "issued_frac": 6 * achieved / peak, "ms": ms}
+                "algorithmic_flops": w["flops"], "issued_bf16_flops": 10 * w["flops"],
+                "issued_frac": 10 * achieved / peak, "ms": ms}
     # CUDA-core FP32 GEMM: bound by the FP32 pipe.  Peak = 152 SMs x 128 lanes
     # x 2 flop x the maximum SM clock (2070 MHz): 80.6 TFLOP/s.
     peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
