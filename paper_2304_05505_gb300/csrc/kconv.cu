@@ -18,6 +18,11 @@
 // additions; the only irrational twiddles (sqrt(3)/2 for lengths 3 and 6, the
 // table for lengths 5, 7, 8) are applied as an FP32 hi + lo pair so that the
 // forward and inverse transforms do not pick up a systematic scale error.
+//
+// For the tensor-core build the same kernel also finds, for every row P of
+// every M^k, the maximum of max(|Re|, |Im|) over Q (warp-segmented reduction,
+// one atomic per warp and row segment); the operand slicing of S4a takes its
+// row exponents from these maxima.
 #include "thc_internal.cuh"
 
 #include <math.h>
@@ -131,11 +136,15 @@ __device__ __forceinline__ void dft3(typename cplx<R>::type* x, int T, const Twi
   dft_axis<R>(x, T, tw, 2, sign);
 }
 
-// M = IDFT(DFT(D) o Vh), one element per thread.
+// M = IDFT(DFT(D) o Vh), one element per thread.  With rmax, also
+// rmax[k * np + P] = max over the row's Q of max(|Re|, |Im|) of M^k[P,Q], as
+// float bits (non-negative floats order as their bit patterns); rmax must be
+// zero on entry.
 template <typename R>
 __global__ void kconv_kernel(const typename cplx<R>::type* __restrict__ D,
                              const typename cplx<R>::type* __restrict__ Vh,
-                             typename cplx<R>::type* __restrict__ M, long npq, Twiddles tw) {
+                             typename cplx<R>::type* __restrict__ M, long npq, Twiddles tw,
+                             unsigned* __restrict__ rmax, int np) {
   typedef typename cplx<R>::type CT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* buf = reinterpret_cast<CT*>(smem_raw);
@@ -143,6 +152,7 @@ __global__ void kconv_kernel(const typename cplx<R>::type* __restrict__ D,
   const int nk = tw.n[0] * tw.n[1] * tw.n[2];
   const long e = (long)blockIdx.x * T + tid;
   const bool ok = e < npq;
+  const unsigned okmask = __ballot_sync(0xffffffffu, ok);   // T is a multiple of 32
   CT* x = buf + tid;
   // unrolled so that many independent loads are in flight per thread
 #pragma unroll 16
@@ -154,8 +164,22 @@ __global__ void kconv_kernel(const typename cplx<R>::type* __restrict__ D,
     x[(long)a * T] = cmul(x[(long)a * T], v);
   }
   dft3<R>(x, T, tw, +1);
-  if (ok)
+  if (!ok) return;
+  if (!rmax) {
     for (int k = 0; k < nk; k++) M[(long)k * npq + e] = x[(long)k * T];
+    return;
+  }
+  // lanes of this warp on the same row P (a warp spans at most a few rows)
+  const int P = (int)(e / np);
+  const unsigned same = __match_any_sync(okmask, P);
+  const bool leader = (threadIdx.x & 31) == __ffs(same) - 1;
+  for (int k = 0; k < nk; k++) {
+    const CT v = x[(long)k * T];
+    M[(long)k * npq + e] = v;
+    const float a = fmaxf(fabsf((float)v.x), fabsf((float)v.y));
+    const unsigned m = __reduce_max_sync(same, __float_as_uint(a));
+    if (leader) atomicMax(rmax + (long)k * np + P, m);
+  }
 }
 
 // Vh[a] = (1/N_k) sum_q w^{+a.q} V[q], FP64; stored FP64 and/or FP32.
@@ -218,17 +242,16 @@ int pick_threads(int nk, size_t elem) {
 
 template <typename R>
 cudaError_t kconv_launch(const typename cplx<R>::type* D, const typename cplx<R>::type* Vh,
-                         typename cplx<R>::type* M, long npq, int n1, int n2, int n3,
-                         cudaStream_t s) {
+                         typename cplx<R>::type* M, long npq, int n1, int n2, int n3, unsigned* rmax,
+                         int np, cudaStream_t s) {
   const int nk = n1 * n2 * n3;
   const size_t el = sizeof(typename cplx<R>::type);
   const int T = pick_threads(nk, el);
   const size_t sm = (size_t)T * nk * el;
-  cudaError_t e = cudaFuncSetAttribute(kconv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(kconv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const long blocks = (npq + T - 1) / T;
-  kconv_kernel<R><<<(unsigned)blocks, T, sm, s>>>(D, Vh, M, npq, make_twiddles(n1, n2, n3));
+  kconv_kernel<R><<<(unsigned)blocks, T, sm, s>>>(D, Vh, M, npq, make_twiddles(n1, n2, n3), rmax, np);
   return cudaGetLastError();
 }
 
@@ -236,12 +259,19 @@ cudaError_t kconv_launch(const typename cplx<R>::type* D, const typename cplx<R>
 
 cudaError_t kconv_z(const double2* D, const double2* Vh, double2* M, long npq, int n1, int n2,
                     int n3, cudaStream_t s) {
-  return kconv_launch<double>(D, Vh, M, npq, n1, n2, n3, s);
+  return kconv_launch<double>(D, Vh, M, npq, n1, n2, n3, nullptr, 0, s);
 }
 
 cudaError_t kconv_c(const float2* D, const float2* Vh, float2* M, long npq, int n1, int n2,
                     int n3, cudaStream_t s) {
-  return kconv_launch<float>(D, Vh, M, npq, n1, n2, n3, s);
+  return kconv_launch<float>(D, Vh, M, npq, n1, n2, n3, nullptr, 0, s);
+}
+
+cudaError_t kconv_c_rowmax(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
+                           unsigned* rmax, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(rmax, 0, sizeof(unsigned) * n1 * n2 * n3 * (size_t)np, s);
+  if (e != cudaSuccess) return e;
+  return kconv_launch<float>(D, Vh, M, (long)np * np, n1, n2, n3, rmax, np, s);
 }
 
 cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long npq, int n1,

@@ -11,44 +11,11 @@
 // the first 32 bits of x relative to its row scale.
 #include "thc_internal.cuh"
 #include "tc_gemm.cuh"
+#include "slices.cuh"
 
 #include <cuda_bf16.h>
 
 namespace {
-
-__device__ __forceinline__ void slice4(double x, int e, uint16_t* s) {
-  double y = ldexp(x, 7 - e);
-#pragma unroll
-  for (int p = 0; p < 4; p++) {
-    const double sp = rint(y);
-    s[p] = __bfloat16_as_ushort(__float2bfloat16_rn(ldexpf((float)sp, -8 * p)));   // exact, |sp| <= 128
-    y = (y - sp) * 256.0;
-  }
-}
-
-__device__ __forceinline__ void slice4(float x, int e, uint16_t* s) {
-  float y = ldexpf(x, 7 - e);
-#pragma unroll
-  for (int p = 0; p < 4; p++) {
-    const float sp = rintf(y);
-    s[p] = __bfloat16_as_ushort(__float2bfloat16_rn(ldexpf(sp, -8 * p)));
-    y = (y - sp) * 256.0f;
-  }
-}
-
-__device__ __forceinline__ int row_exponent(double m) {
-  if (!(m > 0.0)) return 0;
-  int e;
-  frexp(m, &e);
-  return e;   // m < 2^e
-}
-
-__device__ __forceinline__ void store4(uint16_t* base, long plane, long off, const uint16_t* re,
-                                       const uint16_t* im) {
-#pragma unroll
-  for (int p = 0; p < 4; p++)
-    *reinterpret_cast<uint32_t*>(base + p * plane + off) = (uint32_t)re[p] | ((uint32_t)im[p] << 16);
-}
 
 template <typename CT>
 __device__ __forceinline__ double cmax(CT v) {
@@ -171,6 +138,48 @@ __global__ void embed_kernel(const CT* __restrict__ src, long sbs, long ldk, lon
   }
 }
 
+// Slices of the rows of M[k][P][Q] (np x np per k) with the row exponent taken
+// from the row maximum rmax[k][P] (float bits); also writes e[k][P].  V = 2:
+// two consecutive complex values per thread (16-byte loads, np even).
+template <int V>
+__global__ void slice_max_kernel(const float2* __restrict__ src, int np, long rows, const unsigned* __restrict__ rmax,
+                                 int* __restrict__ e, uint16_t* planes, long plane, int ldp) {
+  const int per = np / V;
+  const long total = rows * per;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long row = i / per;
+    const int c = (int)(i - row * per) * V;
+    const int ex = row_exponent((double)__uint_as_float(__ldg(rmax + row)));
+    if (c == 0) e[row] = ex;
+    float2 v[V];
+    if constexpr (V == 2) {
+      const float4 w = __ldcs(reinterpret_cast<const float4*>(src + row * np + c));
+      v[0] = make_float2(w.x, w.y);
+      v[1] = make_float2(w.z, w.w);
+    } else {
+      v[0] = __ldcs(src + row * np + c);
+    }
+    uint16_t s[V][2][4];
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+      slice4(v[j].x, ex, s[j][0]);
+      slice4(v[j].y, ex, s[j][1]);
+    }
+    const long off = row * ldp + 2L * c;
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+      if constexpr (V == 2) {
+        const uint2 w = make_uint2((uint32_t)s[0][0][p] | ((uint32_t)s[0][1][p] << 16),
+                                   (uint32_t)s[1][0][p] | ((uint32_t)s[1][1][p] << 16));
+        *reinterpret_cast<uint2*>(planes + p * plane + off) = w;
+      } else {
+        *reinterpret_cast<uint32_t*>(planes + p * plane + off) =
+            (uint32_t)s[0][0][p] | ((uint32_t)s[0][1][p] << 16);
+      }
+    }
+  }
+}
+
 unsigned grid1(long n) {
   long b = (n + 255) / 256;
   if (b > 152L * 32) b = 152L * 32;
@@ -223,6 +232,16 @@ cudaError_t slice_cols_z(const double2* src, long sbs, int lds, int batch, int r
                          uint16_t* planes, long plane, int ldp, cudaStream_t s) {
   dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch);
   slice_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(src, sbs, lds, rows, cols, e, planes, plane, ldp);
+  return cudaGetLastError();
+}
+
+cudaError_t slice_rows_from_max(const float2* src, int np, long rows, const unsigned* rmax, int* e,
+                                uint16_t* planes, long plane, int ldp, cudaStream_t s) {
+  // 16-byte loads and 8-byte plane stores need even rows and 8-byte aligned plane rows
+  if (np % 2 == 0 && ldp % 4 == 0 && ((uintptr_t)src & 15) == 0)
+    slice_max_kernel<2><<<grid1(rows * (np / 2)), 256, 0, s>>>(src, np, rows, rmax, e, planes, plane, ldp);
+  else
+    slice_max_kernel<1><<<grid1(rows * np), 256, 0, s>>>(src, np, rows, rmax, e, planes, plane, ldp);
   return cudaGetLastError();
 }
 

@@ -37,16 +37,16 @@ struct Sizes {
   size_t el;  // bytes of a workspace complex element
   // tensor-core planes (elements of one plane)
   int ldXT, ldM, ldPs;
-  long plXn, plXT, plPs, plBc, plBd, plBy;
-  long nexp;  // exponents: eXn + eXT + ePsi + eC + eY
+  long plXn, plXT, plPs, plBc, plBd, plBy, plM;
+  long nexp;  // exponents: eXn + eXT + ePsi + eC + eY + eM
   long npart; // split-K partial elements (max over the tensor-core GEMMs)
 };
 
 int pad8(int x) { return (x + 7) & ~7; }
 
 // K chunk (real elements) of the tensor-core GEMMs: 512 for the long
-// contractions S1 and S4b, so that the FP32 sums of the small product classes
-// stay short; S2's K (2 n_occ) fits one chunk.
+// contractions S1, S4a and S4b, so that the FP32 sums of the small product
+// classes stay short; S2's K (2 n_occ) fits one chunk.
 constexpr int kChunkLong = 512;
 constexpr int kChunkShort = 1024;
 
@@ -67,9 +67,11 @@ Sizes sizes_of(const thc_dims* d, int precision) {
   s.plBc = s.nk * 2 * d->nocc * s.ldXT;
   s.plBd = s.nk * 2L * d->nisdf * s.ldPs;
   s.plBy = s.nk * 2 * d->nocc * (long)s.ldM;
-  s.nexp = s.nk * (d->nbas + 2L * d->nisdf + 2L * d->nocc);
+  s.plM = s.nk * d->nisdf * (long)s.ldM;
+  s.nexp = s.nk * (d->nbas + 3L * d->nisdf + 2L * d->nocc);
   s.npart = std::max({tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nbas, (int)s.nk, kChunkLong),
                       tc_partial_elems(d->nisdf, 2 * d->nisdf, 2 * d->nocc, (int)s.nk, kChunkShort),
+                      tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nisdf, (int)s.nk, kChunkLong),
                       tc_partial_elems(d->nbas, 2 * d->nocc, 2 * d->nisdf, (int)s.nk, kChunkLong)});
   return s;
 }
@@ -96,7 +98,8 @@ size_t memory_bytes(const thc_dims* d, int precision) {
   b += 2 * s.psi * s.el;         // Psi, Y
   b += 2 * s.v * s.el;           // D, M
   if (precision == THC_MIXED) {
-    b += 4 * 2 * (s.plXn + s.plXT + s.plPs + s.plBc + s.plBd + s.plBy);   // bf16 slices
+    b += 4 * 2 * (s.plXn + s.plXT + s.plPs + s.plBc + s.plBd + s.plBy + s.plM);   // bf16 slices (M too)
+    b += sizeof(unsigned) * s.nk * d->nisdf;                                      // row maxima of M
     b += sizeof(int) * s.nexp + 64;                                         // exponents, error word
     b += (sizeof(int) + sizeof(float)) * s.npart;                           // split-K partial sums
   } else {
@@ -111,7 +114,7 @@ void free_all(thc_ctx* c) {
   void* ptrs[] = {c->X64, c->Vh64, c->X32, c->Vh32, c->Psi, c->D, c->M, c->Y,
                   c->Cdev, c->KCdev, c->exdev, c->partial, c->flag, c->Xn_pl, c->XT_pl,
                   c->PsiA_pl, c->Bc_pl, c->Bd_pl, c->By_pl, c->ex_pl, c->tc_err, c->part_s0,
-                  c->part_bc};
+                  c->part_bc, c->M_pl, c->mrow};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 7; i++)
@@ -190,6 +193,8 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
   } else {
     W((void**)&c->Vh32, s.v * s.el);
     W(&c->M, s.v * s.el);
+    W((void**)&c->M_pl, 4 * 2 * s.plM);
+    W((void**)&c->mrow, sizeof(unsigned) * s.nk * d->nisdf);
     W((void**)&c->Xn_pl, 4 * 2 * s.plXn);
     W((void**)&c->XT_pl, 4 * 2 * s.plXT);
     W((void**)&c->PsiA_pl, 4 * 2 * s.plPs);
@@ -228,13 +233,14 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
   if (precision == THC_MIXED) {
     c->ldXT = s.ldXT; c->ldM = s.ldM; c->ldPs = s.ldPs;
     c->plXn = s.plXn; c->plXT = s.plXT; c->plPs = s.plPs;
-    c->plBc = s.plBc; c->plBd = s.plBd; c->plBy = s.plBy;
+    c->plBc = s.plBc; c->plBd = s.plBd; c->plBy = s.plBy; c->plM = s.plM;
     const int nk = (int)s.nk, N = d->nbas, n = d->nocc, P = d->nisdf;
     c->eXn = c->ex_pl;
     c->eXT = c->eXn + (long)nk * N;
     c->ePsi = c->eXT + (long)nk * P;
     c->eC = c->ePsi + (long)nk * P;
     c->eY = c->eC + (long)nk * n;
+    c->eM = c->eY + (long)nk * n;
     struct MapReq { TcOperand* op; uint16_t* base; long pl; int rows, cols, ld; };
     MapReq reqs[] = {
         {&c->opXT, c->XT_pl, s.plXT, P, 2 * N, s.ldXT},
@@ -243,6 +249,7 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
         {&c->opBc, c->Bc_pl, s.plBc, 2 * n, 2 * N, s.ldXT},
         {&c->opBd, c->Bd_pl, s.plBd, 2 * P, 2 * n, s.ldPs},
         {&c->opBy, c->By_pl, s.plBy, 2 * n, 2 * P, s.ldM},
+        {&c->opM, c->M_pl, s.plM, P, 2 * P, s.ldM},
     };
     for (auto& r : reqs)
       for (int p = 0; p < 4; p++) {
@@ -406,11 +413,16 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
                  c->part_s0, c->part_bc, c->tc_err, s, kChunkShort));
   CKC(c, cudaEventRecord(stage_event(c, 2), s));
-  // S3  M = IDFT(DFT(D) o Vh)
-  CKC(c, kconv_c(D, c->Vh32, M, PP, c->n1, c->n2, c->n3, s));
+  // S3  M = IDFT(DFT(D) o Vh) in FP32, with the row maxima of every M^k, then
+  // M's fixed-point slices (A of S4a) with the exact row exponents
+  CKC(c, kconv_c_rowmax(D, c->Vh32, M, P, c->n1, c->n2, c->n3, c->mrow, s));
+  CKC(c, slice_rows_from_max(M, P, (long)nk * P, c->mrow, c->eM, c->M_pl, c->plM, c->ldM, s));
   CKC(c, cudaEventRecord(stage_event(c, 3), s));
-  // S4a Y = M Psi on CUDA cores with compensated FP32 sums
-  CKC(c, (gemm_c_comp<float2, float2, float2>(A_MK, B_KN, P, n, P, M, P, PP, Psi, n, Pn, Y, n, Pn, nk, s)));
+  // S4a Y = M Psi on tensor cores: B = embedded Psi, one exponent per orbital
+  CKC(c, col_exponents_c(Psi, Pn, n, nk, P, n, c->eY, s));
+  CKC(c, embed_b(Psi, false, Pn, n, 1, false, false, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
+  CKC(c, tc_gemm(c->opM, c->opBy, P, 2 * n, 2 * P, nk, c->eM, P, c->eY, n, Y, false, 2 * n, 2 * Pn,
+                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong));
   CKC(c, cudaEventRecord(stage_event(c, 4), s));
   // S4b KC = conj(X) Y on tensor cores: B = embedded Y (conj-A form)
   CKC(c, col_exponents_c(Y, Pn, n, nk, P, n, c->eY, s));
@@ -532,12 +544,14 @@ thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   if (!c || !launches) return THC_ERR_ARG;
   // FP64 and CUDA-core forms: S1, S2, S3, S4a, S4b, E_x partial, E_x final.
   // Tensor-core form: S1 3 (exponents, embed, GEMM), S2 4 (exponents, slices,
-  // embed, GEMM), S3 1, S4a 1 (CUDA cores), S4b 3 (+1 combine kernel when
-  // split along K), E_x 2.
+  // embed, GEMM), S3 2 (convolution with row maxima, slices of M), S4a 3
+  // (exponents, embed, GEMM), S4b 3, E_x 2; S1, S4a and S4b add a combine
+  // kernel when split along K.
   if (c->precision == THC_MIXED) {
     const int s1 = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nbas, c->nk, kChunkLong) > 0 ? 1 : 0;
+    const int s4a = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nisdf, c->nk, kChunkLong) > 0 ? 1 : 0;
     const int s4b = tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk, kChunkLong) > 0 ? 1 : 0;
-    *launches = 3 + s1 + 4 + 1 + 1 + 3 + s4b + 2;
+    *launches = 3 + s1 + 4 + 2 + 3 + s4a + 3 + s4b + 2;
   } else {
     *launches = 7;
   }

@@ -71,14 +71,17 @@ struct thc_ctx {
   uint16_t* PsiA_pl;  // [nk][nisdf][ldPs]   Psi, A of S2         ePsi [nk][nisdf]
   uint16_t* Bc_pl;    // [nk][2 nocc][ldXT]  embedded C, B of S1  eC [nk][nocc]
   uint16_t* Bd_pl;    // [nk][2 nisdf][ldPs] embedded Psi^H, B of S2 (ePsi)
-  uint16_t* By_pl;    // [nk][2 nocc][ldM]   embedded Y, B of S4b eY [nk][nocc]
+  uint16_t* By_pl;    // [nk][2 nocc][ldM]   embedded Psi, B of S4a, then embedded Y, B of S4b
+                      //                     (column exponents of Psi, then of Y, in eY [nk][nocc])
+  uint16_t* M_pl;     // [nk][nisdf][ldM]    M, A of S4a                  eM [nk][nisdf]
+  unsigned* mrow;     // [nk][nisdf] row maxima of M (float bits), found by S3
   int* ex_pl;         // eXn | eXT | ePsi | eC | eY
   int* part_s0;       // split-K partial sums of the tensor-core GEMMs (exact leading class)
   float* part_bc;     // and their FP32 remainders
-  int *eXn, *eXT, *ePsi, *eC, *eY;
-  long plXn, plXT, plPs, plBc, plBd, plBy;
+  int *eXn, *eXT, *ePsi, *eC, *eY, *eM;
+  long plXn, plXT, plPs, plBc, plBd, plBy, plM;
   int ldXT, ldM, ldPs;
-  TcOperand opXT, opPs, opXn, opBc, opBd, opBy;
+  TcOperand opXT, opPs, opXn, opBc, opBd, opBy, opM;
   int* tc_err;        // device word: nonzero after a device wait gave up
   cudaEvent_t ev[7];               // stage boundaries of the last build
   std::vector<cudaEvent_t> prof;   // 7 per profiled build
@@ -117,6 +120,10 @@ cudaError_t kconv_z(const double2* D, const double2* Vh, double2* M, long npq, i
                     int n3, cudaStream_t s);
 cudaError_t kconv_c(const float2* D, const float2* Vh, float2* M, long npq, int n1, int n2,
                     int n3, cudaStream_t s);
+// The FP32 convolution that also finds the row maxima of M:
+// rmax[k * np + P] = max_Q max(|Re|, |Im|) of M^k[P,Q] as float bits.
+cudaError_t kconv_c_rowmax(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
+                           unsigned* rmax, cudaStream_t s);
 // Vh[a] = (1/N_k) sum_q V[q] w^{+a.q} in FP64; writes FP64 or FP32 output.
 cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long npq, int n1,
                              int n2, int n3, cudaStream_t s);

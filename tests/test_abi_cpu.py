@@ -59,13 +59,15 @@ def test_memory_bytes_arithmetic():
     def pad8(x):
         return (x + 7) // 8 * 8
     planes = nk * (N * pad8(2 * P) + P * pad8(2 * N) + P * pad8(2 * n)
-                   + 2 * n * pad8(2 * N) + 2 * P * pad8(2 * n) + 2 * n * pad8(2 * P))
-    exps = nk * (N + 2 * P + 2 * n)
-    c4b = -(-(2 * P) // 512)                             # split-K chunks of S4b (K = 2 N_P real)
+                   + 2 * n * pad8(2 * N) + 2 * P * pad8(2 * n) + 2 * n * pad8(2 * P)
+                   + P * pad8(2 * P))                    # M, written as slices by S3
+    exps = nk * (N + 3 * P + 2 * n)
+    c4 = -(-(2 * P) // 512)                              # split-K chunks of S4a and S4b (K = 2 N_P real)
     c1 = -(-(2 * N) // 512)                              # and of S1 (K = 2 N real)
-    part = max(c4b * nk * N * 2 * n if c4b > 1 else 0, c1 * nk * P * 2 * n if c1 > 1 else 0)
-    tc = 8 * (nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + 4 * 2 * planes + 4 * exps + 64 \
-        + 8 * part + common
+    part = max(c4 * nk * N * 2 * n if c4 > 1 else 0, c4 * nk * P * 2 * n if c4 > 1 else 0,
+               c1 * nk * P * 2 * n if c1 > 1 else 0)
+    tc = 8 * (nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + 4 * 2 * planes + 4 * nk * P \
+        + 4 * exps + 64 + 8 * part + common
     assert thc.thc_memory_bytes(d, thc.THC_MIXED) == tc
 
 
