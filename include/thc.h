@@ -159,6 +159,33 @@ thc_status thc_destroy(thc_ctx* ctx);
 thc_status thc_select_points(const double* U, int nfunc, int ncand, int npts, double rel_tol,
                              int* points_host, int* npoints_host, double* resid_diag, void* stream);
 
+/* The ISDF kernel of a set of interpolation points (setup, outside the timed
+ * build), in FP64.  The interpolation vectors are the least-squares fit of
+ * the occupied pair products (Eq. pbcinterpvec restricted to occupied
+ * orbitals, Eq. orbprodoo): xi = S^-1 R with R[P][r] = |B[P][r]|^2,
+ * B[P][r] = sum_f conj(U[f][r_P]) U[f][r] and S = R[:, points].  The kernel is
+ * their Coulomb interaction in reciprocal space (Sec. 2.2), with the pair phase
+ * folded in as thc_set_kernel expects:
+ *   V^q[P,Q] = 1/(N_k Omega) exp(-i q.(r_P - r_Q)) sum_G v(G + q) xh_P(G) conj(xh_Q(G)),
+ *   xh_P(G) = (Omega / N_g) sum_r xi_P(r) exp(-i G.r),  v(K) = 4 pi / |K|^2 (K = 0 left out),
+ * G over the grid's frequencies without the Nyquist planes of even sizes, and
+ * for a q on the zone boundary the mean over its minimum-image
+ * representatives.
+ * U: device, [nfunc][N_g] complex128, u^k_i(r) on the whole grid (f = (k, i);
+ * grid index r = (i1 * g2 + i2) * g3 + i3 for fractional position
+ * (i1/g1, i2/g2, i3/g3)).  grid_host[3] = (g1, g2, g3); lattice_host[9] the
+ * cell vectors a1, a2, a3 as rows (bohr); mesh_host[3] the k-mesh (each 1..8).
+ * points_host: npts distinct grid indices (host).  V_out: device,
+ * [N_k][npts][npts] complex128 (q on the mesh index).  xi_out: device,
+ * [npts][N_g] doubles, or NULL.  Allocates its own scratch (about
+ * 40 npts N_g bytes) and waits for `stream`.  THC_ERR_ARG for bad sizes,
+ * repeated or out-of-range points, or points whose metric S is numerically
+ * singular (a Cholesky pivot below 1e-12 of its diagonal entry; message in
+ * thc_last_error(NULL)). */
+thc_status thc_fit_kernel(const double* U, int nfunc, const int* grid_host, const double* lattice_host,
+                          const int* mesh_host, const int* points_host, int npts, double* V_out,
+                          double* xi_out, void* stream);
+
 /* The k-mesh convolution alone, M^k[P,Q] = sum_k' D^k'[P,Q] V^(k'-k)[P,Q] in
  * FP64, for callers that cannot allocate device memory when they call: for
  * example a host framework that has already reserved the device's memory in

@@ -186,3 +186,44 @@ def fit_error(U: np.ndarray, points: np.ndarray) -> float:
     Ar = A[:, points]
     d = np.diag(A) - np.einsum("rp,pq,rq->r", Ar, np.linalg.inv(S), Ar)
     return float(np.sqrt(max(d.sum(), 0.0) / np.trace(A)))
+
+
+# ----------------------------------------------------------------------------
+# the ISDF kernel from the interpolation vectors
+# ----------------------------------------------------------------------------
+
+def kernel_from_xi(lattice, grid, mesh, xi: np.ndarray, points: np.ndarray) -> np.ndarray:
+    """V[q, P, Q] of the interpolation vectors xi[P, r] (Sec. 2.2, the Coulomb
+    kernel between two interpolation vectors taken in reciprocal space):
+
+        V^q[P, Q] = 1/(N_k Omega) exp(-i q.(r_P - r_Q))
+                    sum_G v(G + q) xh_P(G) conj(xh_Q(G)),
+        xh_P(G) = (Omega / N_g) sum_r xi_P(r) exp(-i G.r),
+
+    with the pair phase folded in as for every kernel of the build, the
+    symmetric G set, and the mean over the minimum-image representatives of a
+    q on the zone boundary (as in full_grid_kernel)."""
+    B = recip_vectors(lattice)
+    vol = abs(np.linalg.det(lattice))
+    ng = int(np.prod(grid))
+    nk = int(np.prod(mesh))
+    npts = len(points)
+    rP = (grid_frac(grid) @ lattice)[points]
+    gm = symmetric_gset(grid)
+    flat = np.ravel_multi_index(tuple((gm % np.array(grid)).T), grid)
+    xh = np.fft.fftn(np.asarray(xi, dtype=np.complex128).reshape((npts,) + tuple(grid)), axes=(1, 2, 3))
+    xh = xh.reshape(npts, ng)[:, flat] * (vol / ng)
+    V = np.zeros((nk, npts, npts), dtype=np.complex128)
+    for q, qco in enumerate(mesh_coords(mesh)):
+        reps = representatives(qco, mesh)
+        for qr in reps:
+            qc = qr @ B
+            v = coulomb((gm + qr[None, :]) @ B)
+            A = xh * np.sqrt(v)[None, :] * np.exp(-1j * (rP @ qc))[:, None]
+            V[q] += (A @ A.conj().T) / len(reps)
+    return V / (nk * vol)
+
+
+def fit_kernel(lattice, grid, mesh, U: np.ndarray, points: np.ndarray) -> np.ndarray:
+    """The ISDF kernel of the occupied-pair fit: kernel_from_xi of isdf_fit."""
+    return kernel_from_xi(lattice, grid, mesh, isdf_fit(U, points), points)

@@ -1,0 +1,329 @@
+// ISDF kernel fit (setup, not part of the timed build), FP64 throughout.
+//
+// Given the occupied orbitals' periodic parts on the grid, U[f][r] = u^k_i(r)
+// with f = (k, i), and the interpolation points r_P:
+//   1. the fit's right-hand side and metric (the least-squares fit of
+//      Eq. pbcinterpvec restricted to occupied products, Eq. orbprodoo):
+//        B[P][r] = sum_f conj(U[f][r_P]) U[f][r],   R[P][r] = |B[P][r]|^2,
+//        S = R[:, points]
+//   2. the interpolation vectors xi = S^-1 R (Cholesky S = L L^T, then one
+//      forward and one backward substitution per grid column);
+//   3. their reciprocal-space form xh_P(G) = (Omega/N_g) sum_r xi_P(r) e^{-iG.r}
+//      (a separable 3-D DFT, one axis at a time, on the G set without the
+//      Nyquist planes);
+//   4. the kernel of every q (Sec. 2.2), with the pair phase folded in:
+//        V^q[P,Q] = 1/(N_k Omega) mean over the representatives q_r of q of
+//                   sum_G v(G + q_r) (xh_P(G) e^{-i q_r.r_P}) conj(xh_Q(G) e^{-i q_r.r_Q})
+//      one Hermitian product per representative (v(K) = 4 pi / |K|^2, K = 0
+//      left out).
+#include "thc_internal.cuh"
+
+#include <math.h>
+
+#include <vector>
+
+namespace {
+
+constexpr int TB = 256;
+
+unsigned blocks(long n) { return (unsigned)((n + TB - 1) / TB); }
+
+// Ugc[P][f] = conj(U[f][pts[P]])
+__global__ void gather_conj(const double2* __restrict__ U, int nf, long ng, const int* __restrict__ pts, int np,
+                            double2* __restrict__ Ugc) {
+  const long i = (long)blockIdx.x * TB + threadIdx.x;
+  if (i >= (long)np * nf) return;
+  const int P = (int)(i / nf), f = (int)(i % nf);
+  const double2 u = U[(long)f * ng + pts[P]];
+  Ugc[i] = make_double2(u.x, -u.y);
+}
+
+// R[i] = |B[i]|^2
+__global__ void abs2_kernel(const double2* __restrict__ B, long n, double* __restrict__ R) {
+  const long i = (long)blockIdx.x * TB + threadIdx.x;
+  if (i >= n) return;
+  const double2 b = B[i];
+  R[i] = b.x * b.x + b.y * b.y;
+}
+
+// S[P][Q] = R[P][pts[Q]]
+__global__ void gather_cols(const double* __restrict__ R, long ng, const int* __restrict__ pts, int np,
+                            double* __restrict__ S) {
+  const long i = (long)blockIdx.x * TB + threadIdx.x;
+  if (i >= (long)np * np) return;
+  const int P = (int)(i / np), Q = (int)(i % np);
+  S[i] = R[(long)P * ng + pts[Q]];
+}
+
+// Column j of the Cholesky factor L (row-major, lower), left-looking: every
+// thread recomputes the pivot d_j = S_jj - sum_t L_jt^2 and forms its L_ij.
+// A pivot below 1e-12 S_jj marks the metric numerically singular.
+__global__ void chol_column(const double* __restrict__ S, double* __restrict__ L, int n, int j, int* bad) {
+  const int i = j + (int)((long)blockIdx.x * TB + threadIdx.x);
+  if (i >= n) return;
+  double d = S[(long)j * n + j];
+  const double sjj = d;
+  for (int t = 0; t < j; t++) d -= L[(long)j * n + t] * L[(long)j * n + t];
+  if (!(d > 1e-12 * sjj)) {
+    if (i == j) atomicOr(bad, 1);
+    return;
+  }
+  const double ljj = sqrt(d);
+  if (i == j) {
+    L[(long)j * n + j] = ljj;
+    return;
+  }
+  double a = S[(long)i * n + j];
+  for (int t = 0; t < j; t++) a -= L[(long)i * n + t] * L[(long)j * n + t];
+  L[(long)i * n + j] = a / ljj;
+}
+
+// X = L^-T L^-1 X for every column r of X[n][ng], in place.
+__global__ void chol_solve(const double* __restrict__ L, double* __restrict__ X, int n, long ng) {
+  const long r = (long)blockIdx.x * TB + threadIdx.x;
+  if (r >= ng) return;
+  for (int j = 0; j < n; j++) {
+    double a = X[(long)j * ng + r];
+    for (int t = 0; t < j; t++) a -= L[(long)j * n + t] * X[(long)t * ng + r];
+    X[(long)j * ng + r] = a / L[(long)j * n + j];
+  }
+  for (int j = n - 1; j >= 0; j--) {
+    double a = X[(long)j * ng + r];
+    for (int t = j + 1; t < n; t++) a -= L[(long)t * n + j] * X[(long)t * ng + r];
+    X[(long)j * ng + r] = a / L[(long)j * n + j];
+  }
+}
+
+// One axis of the forward DFT of [np][g1][g2][g3]: out = sum_j in(j) tw[(j m) mod g].
+// `real_in` reads a real array (the vectors themselves) for the first axis.
+__global__ void dft_axis_kernel(const void* __restrict__ in, bool real_in, double2* __restrict__ out, long total,
+                                int g, long st, const double2* __restrict__ tw) {
+  const long i = (long)blockIdx.x * TB + threadIdx.x;
+  if (i >= total) return;
+  const int m = (int)((i / st) % g);
+  const long base = i - (long)m * st;
+  double re = 0.0, im = 0.0;
+  for (int j = 0, jm = 0; j < g; j++, jm = (jm + m) % g) {
+    const double2 w = tw[jm];
+    if (real_in) {
+      const double x = ((const double*)in)[base + (long)j * st];
+      re += x * w.x;
+      im += x * w.y;
+    } else {
+      const double2 x = ((const double2*)in)[base + (long)j * st];
+      re += x.x * w.x - x.y * w.y;
+      im += x.x * w.y + x.y * w.x;
+    }
+  }
+  out[i] = make_double2(re, im);
+}
+
+// Xq[P][G] = F[P][flat[G]] * sqrt(w v(G + q)) * exp(-i q.r_P), with
+// K = (gm[G] + qf) B (Cartesian) and v(K) = 4 pi / |K|^2 (0 for K = 0).
+struct Recip {
+  double b[9];   // rows b1, b2, b3
+};
+
+__global__ void scale_xi(const double2* __restrict__ F, long ng, const int* __restrict__ flat,
+                         const int* __restrict__ gm, int nG, const double* __restrict__ rP, int np, Recip B,
+                         double q0, double q1, double q2, double w, double2* __restrict__ Xq) {
+  const long i = (long)blockIdx.x * TB + threadIdx.x;
+  if (i >= (long)np * nG) return;
+  const int P = (int)(i / nG), G = (int)(i % nG);
+  const double f0 = gm[3 * G] + q0, f1 = gm[3 * G + 1] + q1, f2 = gm[3 * G + 2] + q2;
+  const double kx = f0 * B.b[0] + f1 * B.b[3] + f2 * B.b[6];
+  const double ky = f0 * B.b[1] + f1 * B.b[4] + f2 * B.b[7];
+  const double kz = f0 * B.b[2] + f1 * B.b[5] + f2 * B.b[8];
+  const double k2 = kx * kx + ky * ky + kz * kz;
+  const double sv = k2 > 1e-12 ? sqrt(w * 4.0 * M_PI / k2) : 0.0;
+  const double qx = q0 * B.b[0] + q1 * B.b[3] + q2 * B.b[6];
+  const double qy = q0 * B.b[1] + q1 * B.b[4] + q2 * B.b[7];
+  const double qz = q0 * B.b[2] + q1 * B.b[5] + q2 * B.b[8];
+  double s, c;
+  sincos(-(qx * rP[3 * P] + qy * rP[3 * P + 1] + qz * rP[3 * P + 2]), &s, &c);
+  const double2 x = F[(long)P * ng + flat[G]];
+  Xq[i] = make_double2(sv * (x.x * c - x.y * s), sv * (x.x * s + x.y * c));
+}
+
+// V += W (complex)
+__global__ void add_kernel(double2* __restrict__ V, const double2* __restrict__ W, long n) {
+  const long i = (long)blockIdx.x * TB + threadIdx.x;
+  if (i >= n) return;
+  V[i] = make_double2(V[i].x + W[i].x, V[i].y + W[i].y);
+}
+
+// Minimum-image fractional representatives of q = qco / mesh along one axis.
+std::vector<double> axis_reps(int qc, int n) {
+  const double f = (double)(((qc % n) + n) % n) / n;
+  if (fabs(f - 0.5) < 1e-12) return {0.5, -0.5};
+  if (f > 0.5) return {f - 1.0};
+  return {f};
+}
+
+}  // namespace
+
+extern "C" thc_status thc_fit_kernel(const double* U, int nfunc, const int* grid_host, const double* lattice_host,
+                                     const int* mesh_host, const int* points_host, int npts, double* V_out,
+                                     double* xi_out, void* stream) {
+  if (!U || !grid_host || !lattice_host || !mesh_host || !points_host || !V_out || nfunc < 1 || npts < 1)
+    return THC_ERR_ARG;
+  if (((uintptr_t)U & 15) || ((uintptr_t)V_out & 15) || ((uintptr_t)xi_out & 7)) return THC_ERR_ARG;
+  const int g1 = grid_host[0], g2 = grid_host[1], g3 = grid_host[2];
+  const int n1 = mesh_host[0], n2 = mesh_host[1], n3 = mesh_host[2];
+  if (g1 < 1 || g2 < 1 || g3 < 1 || n1 < 1 || n2 < 1 || n3 < 1 || n1 > 8 || n2 > 8 || n3 > 8) return THC_ERR_ARG;
+  const long ng = (long)g1 * g2 * g3;
+  if (npts > ng) return THC_ERR_ARG;
+  std::vector<char> seen(ng, 0);
+  for (int P = 0; P < npts; P++) {
+    const int p = points_host[P];
+    if (p < 0 || p >= ng || seen[p]) return THC_ERR_ARG;   // points must be distinct grid indices
+    seen[p] = 1;
+  }
+  const double* a = lattice_host;
+  const double vol = fabs(a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                          a[2] * (a[3] * a[7] - a[4] * a[6]));
+  if (!(vol > 0)) return THC_ERR_ARG;
+  // reciprocal rows b_i with a_i . b_j = 2 pi delta_ij
+  Recip B;
+  {
+    const double c = 2.0 * M_PI / (a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                                   a[2] * (a[3] * a[7] - a[4] * a[6]));
+    const double* a1 = a;
+    const double* a2 = a + 3;
+    const double* a3 = a + 6;
+    auto cross = [](const double* x, const double* y, double* o) {
+      o[0] = x[1] * y[2] - x[2] * y[1];
+      o[1] = x[2] * y[0] - x[0] * y[2];
+      o[2] = x[0] * y[1] - x[1] * y[0];
+    };
+    cross(a2, a3, B.b);
+    cross(a3, a1, B.b + 3);
+    cross(a1, a2, B.b + 6);
+    for (double& x : B.b) x *= c;
+  }
+  // G set without Nyquist planes, its flat grid index, point positions
+  const int h1 = (g1 - 1) / 2, h2 = (g2 - 1) / 2, h3 = (g3 - 1) / 2;
+  std::vector<int> gm, flat;
+  for (int i = -h1; i <= h1; i++)
+    for (int j = -h2; j <= h2; j++)
+      for (int l = -h3; l <= h3; l++) {
+        gm.push_back(i);
+        gm.push_back(j);
+        gm.push_back(l);
+        flat.push_back((((i % g1) + g1) % g1 * g2 + ((j % g2) + g2) % g2) * g3 + ((l % g3) + g3) % g3);
+      }
+  const int nG = (int)flat.size();
+  std::vector<double> rP(3 * (size_t)npts);
+  for (int P = 0; P < npts; P++) {
+    const int p = points_host[P];
+    const double f0 = (double)(p / (g2 * g3)) / g1, f1 = (double)((p / g3) % g2) / g2, f2 = (double)(p % g3) / g3;
+    for (int x = 0; x < 3; x++) rP[3 * P + x] = f0 * a[x] + f1 * a[3 + x] + f2 * a[6 + x];
+  }
+  std::vector<double2> tw(g1 + g2 + g3);
+  int off[3] = {0, g1, g1 + g2};
+  const int gs[3] = {g1, g2, g3};
+  for (int ax = 0; ax < 3; ax++)
+    for (int t = 0; t < gs[ax]; t++) {
+      const double ang = -2.0 * M_PI * t / gs[ax];
+      tw[off[ax] + t] = make_double2(cos(ang), sin(ang));
+    }
+
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nk = n1 * n2 * n3;
+  const long npq = (long)npts * npts;
+  double2 *Ugc = nullptr, *Bm = nullptr, *F = nullptr, *Xq = nullptr, *W = nullptr, *twd = nullptr;
+  double *R = nullptr, *S = nullptr, *L = nullptr, *rPd = nullptr;
+  int *ptsd = nullptr, *gmd = nullptr, *flatd = nullptr, *bad = nullptr;
+  cudaError_t e = cudaSuccess;
+  thc_status st = THC_OK;
+  int hbad = 0;
+  do {
+    if ((e = cudaMalloc(&ptsd, sizeof(int) * npts)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&Ugc, sizeof(double2) * (size_t)npts * nfunc)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&Bm, sizeof(double2) * (size_t)npts * ng)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&R, sizeof(double) * (size_t)npts * ng)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&S, sizeof(double) * npq)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&L, sizeof(double) * npq)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&bad, sizeof(int))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&twd, sizeof(double2) * tw.size())) != cudaSuccess) break;
+    if ((e = cudaMalloc(&gmd, sizeof(int) * gm.size())) != cudaSuccess) break;
+    if ((e = cudaMalloc(&flatd, sizeof(int) * flat.size())) != cudaSuccess) break;
+    if ((e = cudaMalloc(&rPd, sizeof(double) * rP.size())) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(ptsd, points_host, sizeof(int) * npts, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(twd, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      break;
+    if ((e = cudaMemcpyAsync(gmd, gm.data(), sizeof(int) * gm.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      break;
+    if ((e = cudaMemcpyAsync(flatd, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      break;
+    if ((e = cudaMemcpyAsync(rPd, rP.data(), sizeof(double) * rP.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      break;
+    if ((e = cudaMemsetAsync(bad, 0, sizeof(int), s)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(L, 0, sizeof(double) * npq, s)) != cudaSuccess) break;
+    // 1. B = conj(U[:, points])^T U, R = |B|^2, S = R[:, points]
+    gather_conj<<<blocks((long)npts * nfunc), TB, 0, s>>>((const double2*)U, nfunc, ng, ptsd, npts, Ugc);
+    if ((e = gemm_z(A_MK, B_KN, npts, (int)ng, nfunc, Ugc, nfunc, 0, (const double2*)U, (int)ng, 0, Bm, (int)ng,
+                    0, 1, s)) != cudaSuccess)
+      break;
+    abs2_kernel<<<blocks((long)npts * ng), TB, 0, s>>>(Bm, (long)npts * ng, R);
+    gather_cols<<<blocks(npq), TB, 0, s>>>(R, ng, ptsd, npts, S);
+    // 2. xi = S^-1 R
+    for (int j = 0; j < npts; j++) chol_column<<<blocks(npts - j), TB, 0, s>>>(S, L, npts, j, bad);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+    if (hbad) {
+      st = THC_ERR_ARG;   // the metric of these points is not positive definite
+      set_global_error("thc_fit_kernel: the Gram matrix of the points is not positive definite");
+      break;
+    }
+    chol_solve<<<blocks(ng), TB, 0, s>>>(L, R, npts, ng);
+    if (xi_out &&
+        (e = cudaMemcpyAsync(xi_out, R, sizeof(double) * npts * ng, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      break;
+    // 3. xh = DFT of xi, axis by axis (Bm holds the last two passes' input/output)
+    cudaFree(Ugc);
+    Ugc = nullptr;
+    if ((e = cudaMalloc(&F, sizeof(double2) * (size_t)npts * ng)) != cudaSuccess) break;
+    const long tot = (long)npts * ng;
+    dft_axis_kernel<<<blocks(tot), TB, 0, s>>>(R, true, F, tot, g3, 1, twd + off[2]);
+    dft_axis_kernel<<<blocks(tot), TB, 0, s>>>(F, false, Bm, tot, g2, g3, twd + off[1]);
+    dft_axis_kernel<<<blocks(tot), TB, 0, s>>>(Bm, false, F, tot, g1, (long)g2 * g3, twd + off[0]);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    // 4. V^q, one Hermitian product per representative of q
+    cudaFree(Bm);
+    Bm = nullptr;
+    if ((e = cudaMalloc(&Xq, sizeof(double2) * (size_t)npts * nG)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&W, sizeof(double2) * npq)) != cudaSuccess) break;
+    double2* V = (double2*)V_out;
+    if ((e = cudaMemsetAsync(V, 0, sizeof(double2) * nk * npq, s)) != cudaSuccess) break;
+    const double sc = vol / ng;   // xh = (Omega / N_g) DFT(xi)
+    for (int q = 0; q < nk && e == cudaSuccess; q++) {
+      const int qc[3] = {q / (n2 * n3), (q / n3) % n2, q % n3};
+      const std::vector<double> r0 = axis_reps(qc[0], n1), r1 = axis_reps(qc[1], n2), r2 = axis_reps(qc[2], n3);
+      const double nrep = (double)(r0.size() * r1.size() * r2.size());
+      const double w = sc * sc / (nrep * nk * vol);
+      for (double x0 : r0)
+        for (double x1 : r1)
+          for (double x2 : r2) {
+            scale_xi<<<blocks((long)npts * nG), TB, 0, s>>>(F, ng, flatd, gmd, nG, rPd, npts, B, x0, x1, x2, w, Xq);
+            if ((e = gemm_z(A_MK, B_NK_CONJ, npts, npts, nG, Xq, nG, 0, Xq, nG, 0, W, npts, 0, 1, s)) !=
+                cudaSuccess)
+              break;
+            add_kernel<<<blocks(npq), TB, 0, s>>>(V + (long)q * npq, W, npq);
+          }
+    }
+    if (e != cudaSuccess) break;
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    e = cudaStreamSynchronize(s);
+  } while (0);
+  if (e != cudaSuccess) {
+    set_global_error(std::string("thc_fit_kernel: ") + cudaGetErrorString(e));
+    st = e == cudaErrorMemoryAllocation ? THC_ERR_OOM : THC_ERR_CUDA;
+  }
+  void* ptrs[] = {Ugc, Bm, F, Xq, W, twd, R, S, L, rPd, ptsd, gmd, flatd, bad};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  return st;
+}

@@ -29,7 +29,7 @@ EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_ker
            "thc_build", "thc_build_host", "thc_get_intermediate", "thc_stage_times",
            "thc_launches_per_build", "thc_destroy", "thc_status_string", "thc_last_error",
            "thc_profile_begin", "thc_profile_end", "thc_sync", "thc_kconv_noalloc",
-           "thc_select_points"]
+           "thc_select_points", "thc_fit_kernel"]
 
 
 class ThcDims(ctypes.Structure):
@@ -72,6 +72,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_kconv_noalloc.argtypes = [dp, dp, dp, ip, ip, ip, ctypes.c_long, vp]
     lib.thc_select_points.argtypes = [dp, ip, ip, ip, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), dp, vp]
+    lib.thc_fit_kernel.argtypes = [dp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, dp, dp, vp]
     lib.thc_status_string.argtypes = [ip]
     lib.thc_status_string.restype = ctypes.c_char_p
     lib.thc_last_error.argtypes = [vp]
@@ -230,6 +232,31 @@ def thc_select_points(U, npts: int, rel_tol: float = 1e-14, stream: int | None =
                                     pts, ctypes.byref(cnt), resid.data_ptr(), ctypes.c_void_p(stream)),
            "thc_select_points")
     return np.array(pts[: cnt.value], dtype=np.int64), resid
+
+
+def thc_fit_kernel(U, grid, lattice, mesh, points, want_xi: bool = False, stream: int | None = None):
+    """FP64 ISDF kernel of the interpolation points (see include/thc.h).
+
+    U: CUDA complex128 tensor [nfunc][N_g] on the whole grid; grid, mesh:
+    3 ints; lattice: 3 x 3 (rows a1, a2, a3); points: grid indices.  Returns
+    V [N_k][npts][npts] complex128 (CUDA tensor), and xi [npts][N_g] if asked."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    nfunc, ng = U.shape
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    m = (ctypes.c_int * 3)(*[int(x) for x in mesh])
+    lat = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(lattice, dtype=np.float64).ravel()])
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int32))
+    npts = int(pts.size)
+    nk = int(np.prod([int(x) for x in mesh]))
+    V = torch.empty((nk, npts, npts), dtype=torch.complex128, device=U.device)
+    xi = torch.empty((npts, ng), dtype=torch.float64, device=U.device) if want_xi else None
+    _check(load().thc_fit_kernel(_dev_ptr(U, name="U"), int(nfunc), g, lat, m,
+                                 pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), npts, V.data_ptr(),
+                                 xi.data_ptr() if xi is not None else None, ctypes.c_void_p(stream)),
+           "thc_fit_kernel")
+    return (V, xi) if want_xi else V
 
 
 def thc_destroy(ctx) -> None:
