@@ -186,6 +186,58 @@ thc_status thc_fit_kernel(const double* U, int nfunc, const int* grid_host, cons
                           const int* mesh_host, const int* points_host, int npts, double* V_out,
                           double* xi_out, void* stream);
 
+/* Learned interpolation-point proposal (setup, outside the timed build).  The
+ * paper has no learned part (its points come from a QR decomposition with
+ * column pivoting, Sec. 2.1, or from k-means on the density, Sec. 4); these
+ * calls add a small network that scores grid points so that the pivoted
+ * Cholesky of thc_select_points_among only has to search a few candidates.
+ *
+ * Network: 3 -> 64 -> 64 -> 64 -> 1, SiLU, FP32, output a logit.  Parameters
+ * (device, THC_MLP_NPARAM floats): W1 [64][3], b1 [64], W2 [64][64], b2 [64],
+ * W3 [64][64], b3 [64], W4 [64], b4.  Features are standardised inside the
+ * calls with norm_host = {mean[3], std[3]} (host, std > 0). */
+#define THC_MLP_NPARAM 8641
+
+/* Per-grid-point features (device, [N_g][3] floats): log(rho + 1e-8),
+ * log(|grad rho| + 1e-8) and the minimum-image distance to the nearest of the
+ * ncent centres (host, [ncent][3] Cartesian bohr), with
+ * rho(r) = (1/nk) sum_f |U[f][r]|^2 (U as for thc_fit_kernel) and the gradient
+ * from periodic second-order central differences (each grid size >= 3).
+ * Waits for `stream`. */
+thc_status thc_mlp_features(const double* U, int nfunc, int nk, const int* grid_host, const double* lattice_host,
+                            const double* centres_host, int ncent, float* feat, void* stream);
+
+/* score[p] = network logit of feat[p] (device, n points).  Queued on `stream`. */
+thc_status thc_mlp_score(const float* params, const float* norm_host, const float* feat, int n, float* score,
+                         void* stream);
+
+/* Device workspace one thc_mlp_train_step over n points needs. */
+thc_status thc_mlp_workspace_bytes(int n, size_t* bytes);
+
+/* One training step over n points (labels: device floats, 1 for a point the
+ * full-grid pivoted Cholesky picks, else 0): the mean of the weighted binary
+ * cross-entropy with logits, pos_weight y softplus(-z) + (1 - y) softplus(z);
+ * its gradient by backpropagation (summed over fixed point chunks, in a fixed
+ * order, so repeated calls give identical results); then the Adam update
+ * (beta 0.9, 0.999, eps 1e-8, bias-corrected for step t >= 1) of params,
+ * adam_m and adam_v (device, THC_MLP_NPARAM floats each) with rate lr.
+ * lr = 0 computes the gradient only.  loss_out (device float) and grad_out
+ * (device, THC_MLP_NPARAM floats) may be NULL.  Queued on `stream`. */
+thc_status thc_mlp_train_step(float* params, float* adam_m, float* adam_v, int t, float lr, const float* norm_host,
+                              const float* feat, const float* labels, int n, float pos_weight, void* workspace,
+                              size_t ws_bytes, float* loss_out, float* grad_out, void* stream);
+
+/* The k highest of n scores (device), the lower index first among equal
+ * scores; cand_host (host, k ints) receives their indices in ascending order.
+ * Waits for `stream`. */
+thc_status thc_mlp_candidates(const float* score, int n, int k, int* cand_host, void* stream);
+
+/* thc_select_points restricted to the candidate columns cand_host[0..ncand)
+ * (host, indices into the ng columns of U, ascending for the lowest-index
+ * tie rule); points_host receives grid indices. */
+thc_status thc_select_points_among(const double* U, int nfunc, int ng, const int* cand_host, int ncand, int npts,
+                                   double rel_tol, int* points_host, int* npoints_host, void* stream);
+
 /* The k-mesh convolution alone, M^k[P,Q] = sum_k' D^k'[P,Q] V^(k'-k)[P,Q] in
  * FP64, for callers that cannot allocate device memory when they call: for
  * example a host framework that has already reserved the device's memory in

@@ -29,7 +29,10 @@ EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_ker
            "thc_build", "thc_build_host", "thc_get_intermediate", "thc_stage_times",
            "thc_launches_per_build", "thc_destroy", "thc_status_string", "thc_last_error",
            "thc_profile_begin", "thc_profile_end", "thc_sync", "thc_kconv_noalloc",
-           "thc_select_points", "thc_fit_kernel"]
+           "thc_select_points", "thc_fit_kernel", "thc_mlp_features", "thc_mlp_score",
+           "thc_mlp_workspace_bytes", "thc_mlp_train_step", "thc_mlp_candidates", "thc_select_points_among"]
+
+MLP_NPARAM = 8641
 
 
 class ThcDims(ctypes.Structure):
@@ -74,6 +77,16 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_int), dp, vp]
     lib.thc_fit_kernel.argtypes = [dp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, dp, dp, vp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.thc_mlp_features.argtypes = [dp, ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), ip, dp, vp]
+    lib.thc_mlp_score.argtypes = [dp, fp, dp, ip, dp, vp]
+    lib.thc_mlp_workspace_bytes.argtypes = [ip, ctypes.POINTER(ctypes.c_size_t)]
+    lib.thc_mlp_train_step.argtypes = [dp, dp, dp, ip, ctypes.c_float, fp, dp, dp, ip, ctypes.c_float, dp,
+                                       ctypes.c_size_t, dp, dp, vp]
+    lib.thc_mlp_candidates.argtypes = [dp, ip, ip, ctypes.POINTER(ctypes.c_int), vp]
+    lib.thc_select_points_among.argtypes = [dp, ip, ip, ctypes.POINTER(ctypes.c_int), ip, ip, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp]
     lib.thc_status_string.argtypes = [ip]
     lib.thc_status_string.restype = ctypes.c_char_p
     lib.thc_last_error.argtypes = [vp]
@@ -257,6 +270,103 @@ def thc_fit_kernel(U, grid, lattice, mesh, points, want_xi: bool = False, stream
                                  xi.data_ptr() if xi is not None else None, ctypes.c_void_p(stream)),
            "thc_fit_kernel")
     return (V, xi) if want_xi else V
+
+
+def _f32_dev(t, n=None, name="tensor") -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name}: expected a contiguous CUDA float32 tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name}: {t.numel()} elements, expected {n}")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    return torch.cuda.current_stream().cuda_stream if stream is None else stream
+
+
+def thc_mlp_features(U, nk: int, grid, lattice, centres, stream=None):
+    """[N_g][3] float32 CUDA tensor of point features (see include/thc.h)."""
+    import torch
+    nfunc, ng = U.shape
+    feat = torch.empty((ng, 3), dtype=torch.float32, device=U.device)
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    lat = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(lattice, dtype=np.float64).ravel()])
+    cen = np.ascontiguousarray(np.asarray(centres, dtype=np.float64))
+    _check(load().thc_mlp_features(_dev_ptr(U, name="U"), int(nfunc), int(nk), g, lat,
+                                   cen.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(cen.shape[0]),
+                                   feat.data_ptr(), ctypes.c_void_p(_stream(stream))), "thc_mlp_features")
+    return feat
+
+
+def _norm(norm):
+    return (ctypes.c_float * 6)(*[float(x) for x in np.asarray(norm).ravel()])
+
+
+def thc_mlp_score(params, norm, feat, stream=None):
+    """Logits [n] (float32 CUDA tensor) of features feat [n][3]."""
+    import torch
+    n = feat.shape[0]
+    score = torch.empty(n, dtype=torch.float32, device=feat.device)
+    _check(load().thc_mlp_score(_f32_dev(params, MLP_NPARAM, "params"), _norm(norm), _f32_dev(feat, name="feat"),
+                                int(n), score.data_ptr(), ctypes.c_void_p(_stream(stream))), "thc_mlp_score")
+    return score
+
+
+class MlpTrainer:
+    """Parameters, Adam moments and workspace of thc_mlp_train_step."""
+
+    def __init__(self, params, norm, n: int, device=None):
+        import torch
+        self.torch = torch
+        self.params = params.to(device or "cuda", dtype=torch.float32).contiguous().clone()
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.norm = np.asarray(norm, dtype=np.float32)
+        self.n = int(n)
+        b = ctypes.c_size_t(0)
+        _check(load().thc_mlp_workspace_bytes(self.n, ctypes.byref(b)), "thc_mlp_workspace_bytes")
+        self.ws = torch.empty(int(b.value), dtype=torch.uint8, device=self.params.device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.params.device)
+        self.grad = torch.zeros_like(self.params)
+        self.t = 0
+
+    def step(self, feat, labels, pos_weight: float, lr: float, stream=None):
+        """One Adam step (lr > 0) or the gradient alone (lr = 0, step count kept)."""
+        if feat.shape[0] != self.n or labels.numel() != self.n:
+            raise ValueError("batch size differs from the workspace's")
+        t = self.t + 1 if lr > 0 else max(self.t, 1)
+        _check(load().thc_mlp_train_step(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), int(t),
+                                         float(lr), _norm(self.norm), _f32_dev(feat, name="feat"),
+                                         _f32_dev(labels, name="labels"), self.n, float(pos_weight),
+                                         self.ws.data_ptr(), int(self.ws.numel()), self.loss.data_ptr(),
+                                         self.grad.data_ptr(), ctypes.c_void_p(_stream(stream))),
+               "thc_mlp_train_step")
+        if lr > 0:
+            self.t = t
+        return self.loss, self.grad
+
+
+def thc_mlp_candidates(score, k: int, stream=None):
+    """Indices (numpy, ascending) of the k highest scores."""
+    out = (ctypes.c_int * int(k))()
+    _check(load().thc_mlp_candidates(_f32_dev(score, name="score"), int(score.numel()), int(k), out,
+                                     ctypes.c_void_p(_stream(stream))), "thc_mlp_candidates")
+    return np.array(out[:], dtype=np.int64)
+
+
+def thc_select_points_among(U, cand, npts: int, rel_tol: float = 1e-14, stream=None):
+    """Pivoted-Cholesky points among the candidate grid indices `cand`."""
+    nfunc, ng = U.shape
+    c = np.ascontiguousarray(np.asarray(cand, dtype=np.int32))
+    pts = (ctypes.c_int * int(npts))()
+    cnt = ctypes.c_int(0)
+    _check(load().thc_select_points_among(_dev_ptr(U, name="U"), int(nfunc), int(ng),
+                                          c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(c.size), int(npts),
+                                          float(rel_tol), pts, ctypes.byref(cnt), ctypes.c_void_p(_stream(stream))),
+           "thc_select_points_among")
+    return np.array(pts[: cnt.value], dtype=np.int64)
 
 
 def thc_destroy(ctx) -> None:
