@@ -34,9 +34,12 @@ WORKLOAD = ("benzene-shaped orthorhombic cell 13.9x17.8x12.9 bohr, 48 centres, N
             "4x4x4 k (N_k=64), N_ISDF=1200, 40^3 grid (config C2)")
 CONFIG = "C2"
 SAMPLE_FRACTION = 8      # the CPU oracle sample is 1/8 of a build
-# stages of the mixed build that run on tensor cores (the others: S3 and S5
-# stream HBM, S4a runs on CUDA cores)
-TENSOR_STAGES = ("S1_collocate", "S2_density", "S4b_backproject")
+# the main kernel of each stage of the tensor-core build
+KERNEL_NAMES = {"S1_collocate": "tc_gemm_kernel<2> (S1, split-K)", "S2_density": "tc_gemm_kernel<0> (S2)",
+                "S3_kconv": "kconv_kernel<float> (S3, with row maxima)",
+                "S4a_apply_M": "tc_gemm_kernel<2> (S4a, split-K)",
+                "S4b_backproject": "tc_gemm_kernel<2> (S4b, split-K)",
+                "S5_energy": "ex_partial_c + ex_final (S5)"}
 
 
 def parse():
@@ -154,8 +157,9 @@ def peaks() -> dict:
 
 
 def stage_work(d: dict) -> dict:
-    """Algorithmic work of each stage of one build (complex MAC = 8 flops;
-    bytes are the arrays a stage must read and write once, complex64)."""
+    """Algorithmic work of each stage's main kernel in one build: complex
+    multiply-adds at 8 flops, and the arrays the step must read and write once
+    at complex64 (KC and the C input at complex128)."""
     nk = d["n1"] * d["n2"] * d["n3"]
     N, n, P = d["nbas"], d["nocc"], d["nisdf"]
     c64 = 8
@@ -165,40 +169,40 @@ def stage_work(d: dict) -> dict:
         "S3_kconv": dict(flops=None, bytes=3.0 * c64 * nk * P * P),
         "S4a_apply_M": dict(flops=8.0 * nk * P * P * n, bytes=c64 * nk * (P * P + 2 * P * n)),
         "S4b_backproject": dict(flops=8.0 * nk * N * n * P, bytes=c64 * nk * (N * P + P * n) + 16 * nk * N * n),
-        "S5_energy": dict(flops=8.0 * nk * P * n, bytes=2.0 * c64 * nk * P * n),
+        "S5_energy": dict(flops=None, bytes=2.0 * c64 * nk * P * n),
     }
 
 
-def kernel_roofline(stage: str, ms: float, work: dict, pk: dict, clocks: dict, tensor: bool) -> dict:
+def kernel_roofline(stage: str, ms: float, work: dict, pk: dict) -> dict:
+    """Roofline of one stage's main kernel (or the stage) at `ms` per build.
+
+    The bound is whichever lower limit is larger: algorithmic bytes over the
+    measured copy bandwidth, or algorithmic flops over the sustained bf16
+    tensor peak (the kernels run inside a multi-millisecond build).  The
+    tensor-core GEMMs issue 10 bf16 slice products per real product (the
+    classes s + t <= 3 of four-slice fixed-point operands), so their issued
+    tensor fraction is also given."""
     w = work[stage]
-    traffic = measured_traffic(stage)
-    if w["flops"] is None or stage == "S5_energy":
-        achieved = w["bytes"] / (ms * 1e-3) / 1e9
-        peak = pk["hbm_gbs"]
-        return {"kernel": stage, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_source": pk["source"],
-                "algorithmic_bytes": w["bytes"], "ms": ms}
-    if tensor:
-        # tcgen05 bf16 GEMM on four-slice fixed-point operands: ten slice
-        # products (the classes s + t <= 3) per real product, and the real
-        # embedding of a complex product costs the same 8 flops as the
-        # algorithmic count.  Achieved counts the algorithmic complex flops
-        # (8 per complex multiply-add); the issued bf16 flops are 10x that.
+    sec = ms * 1e-3
+    t_hbm = w["bytes"] / (pk["hbm_gbs"] * 1e9)
+    t_ten = (w["flops"] / (pk["bf16_tflops_sustained"] * 1e12)) if w["flops"] else 0.0
+    out = {"kernel": stage, "ms": ms, "algorithmic_bytes": w["bytes"], "traffic": measured_traffic(stage)}
+    if t_ten > t_hbm:
+        achieved = w["flops"] / sec / 1e12
         peak = pk["bf16_tflops_sustained"]
-        achieved = w["flops"] / (ms * 1e-3) / 1e12
-        return {"kernel": stage, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_source": f"{pk['source']} bf16 sustained (cuBLAS)",
-                "algorithmic_flops": w["flops"], "issued_bf16_flops": 10 * w["flops"],
-                "issued_frac": 10 * achieved / peak, "ms": ms}
-    # CUDA-core FP32 GEMM: bound by the FP32 pipe.  Peak = 152 SMs x 128 lanes
-    # x 2 flop x the maximum SM clock (2070 MHz): 80.6 TFLOP/s.
-    peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-    achieved = w["flops"] / (ms * 1e-3) / 1e12
-    return {"kernel": stage, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
-            "algorithmic_flops": w["flops"], "ms": ms}
+        out.update(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                   peak_source=f"{pk['source']} bf16 sustained (cuBLAS)")
+    else:
+        achieved = w["bytes"] / sec / 1e9
+        peak = pk["hbm_gbs"]
+        out.update(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                   peak_source=f"{pk['source']} copy bandwidth")
+    if w["flops"]:
+        tf = w["flops"] / sec / 1e12
+        out.update(algorithmic_flops=w["flops"], tensor_tflops=tf,
+                   tensor_frac=tf / pk["bf16_tflops_sustained"],
+                   issued_tensor_frac=10 * tf / pk["bf16_tflops_sustained"])
+    return out
 
 
 def source_hash() -> str:
@@ -344,6 +348,7 @@ def run_ours(args, world, rank, local):
     clocks = clk.stop()
     ms_total = max_over_ranks(world, e0.elapsed_time(e1))
     stage_ms, nprof = thc.thc_profile_end(eb.ctx)
+    kernel_ms = thc.thc_profile_kernels(eb.ctx)
     eb.sync()   # raises if a device-side wait gave up during the timed builds
     launches = thc.thc_launches_per_build(eb.ctx) * args.steps
     KC_mixed = KC.cpu().numpy()
@@ -417,24 +422,27 @@ def run_ours(args, world, rank, local):
     work = stage_work(d)
     names = thc.STAGES
     stages = {nm: ms for nm, ms in zip(names, stage_ms)}
-    dominant = max(stages, key=stages.get)
-    roof = kernel_roofline(dominant, stages[dominant], work, pk, clocks, tensor=dominant in TENSOR_STAGES)
-    per_stage = {nm: kernel_roofline(nm, stages[nm], work, pk, clocks, tensor=nm in TENSOR_STAGES)
-                 for nm in names}
+    kernels = {nm: ms for nm, ms in zip(names, kernel_ms)}
+    dominant = max(kernels, key=kernels.get)
+    roof = kernel_roofline(dominant, kernels[dominant], work, pk)
+    roof["name"] = KERNEL_NAMES[dominant]
+    per_kernel = {nm: kernel_roofline(nm, kernels[nm], work, pk) for nm in names}
 
 
     line = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16-slices/f32", "data": "synthetic",
             "config": {"workload": WORKLOAD,
-                       "precision": "mixed: S1/S2/S4b tcgen05 bf16 GEMMs on 4-slice fixed-point operands "
-                                    "(exact leading sums), S3 FP32, S4a FP32 compensated, E_x FP64 sum",
+                       "precision": "mixed: S1/S2/S4a/S4b tcgen05 bf16 GEMMs on 4-slice fixed-point operands "
+                                    "(exact leading sums, FP32 remainders), S3 FP32, E_x FP64 sum",
                        "l2": "inputs larger than L2 (prepared kernel 737 MB, X 265 MB complex64)",
                        "parallelism": f"{world} independent builds (one per GPU)"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-            "stages_ms": stages, "stage_roofline": {k: {"frac": v["frac"], "bound": v["bound"],
-                                                        "achieved": v["achieved"], "unit": v["unit"]}
-                                                    for k, v in per_stage.items()},
+            "stages_ms": stages, "kernels_ms": kernels,
+            "kernel_roofline": {k: {"frac": v["frac"], "bound": v["bound"], "achieved": v["achieved"],
+                                    "unit": v["unit"], **({"issued_tensor_frac": v["issued_tensor_frac"]}
+                                                          if "issued_tensor_frac" in v else {})}
+                                for k, v in per_kernel.items()},
             "fp64_gpu": {"value": world / (ms64 * 1e-3), "unit": "builds/s", "ms_per_step": ms64,
                          "stages_ms": {nm: ms for nm, ms in zip(names, st64)}},
             "mixed_cuda_cores": {"value": world / (ms_simt * 1e-3), "unit": "builds/s", "ms_per_step": ms_simt,

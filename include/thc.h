@@ -130,6 +130,14 @@ thc_status thc_stage_times(thc_ctx* ctx, float stage_ms[6]);
 thc_status thc_profile_begin(thc_ctx* ctx, int max_builds);
 thc_status thc_profile_end(thc_ctx* ctx, float mean_ms[6], int* nbuilds);
 
+/* Mean device time (ms) of each stage's main kernel over the builds of the
+ * last completed profile: the GEMM of S1, S2, S4a and S4b (without operand
+ * preparation or the combine of split-K partials), the convolution of S3, the
+ * two reduction kernels of S5.  In the FP64 and CUDA-core forms each stage is
+ * one kernel and this equals the stage time.  THC_ERR_STATE before a profile
+ * has completed. */
+thc_status thc_profile_kernels(const thc_ctx* ctx, float core_ms[6]);
+
 /* Wait for the context's stream.  Returns THC_ERR_TIMEOUT if a device-side
  * wait of a tensor-core kernel gave up since the last thc_sync (its outputs
  * are then invalid; the context stays usable), else THC_OK. */

@@ -510,7 +510,8 @@ long tc_partial_elems(int M, int Nr, int Kr, int batch, int chunk_k) {
 
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
-                    long sbo, int* ps0, float* pbc, int* err, cudaStream_t s, int chunk_k) {
+                    long sbo, int* ps0, float* pbc, int* err, cudaStream_t s, int chunk_k,
+                    cudaEvent_t gemm_done) {
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   Maps maps;
   for (int p = 0; p < NPL; p++) {
@@ -547,6 +548,7 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   if (split) LAUNCH(2) else if (out_f64) LAUNCH(1) else LAUNCH(0)
 #undef LAUNCH
   e = cudaGetLastError();
+  if (e == cudaSuccess && gemm_done) e = cudaEventRecord(gemm_done, s);
   if (e != cudaSuccess || !split) return e;
   const long total = (long)batch * M * Nr;
   const unsigned cg = (unsigned)std::min<long>((total + 255) / 256, 152L * 16);

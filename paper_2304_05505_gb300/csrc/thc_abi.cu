@@ -329,10 +329,35 @@ thc_status thc_set_kernel(thc_ctx* c, const double* V) {
   return THC_OK;
 }
 
+constexpr int kProfEv = 7 + 12;
+
+static bool profiling(const thc_ctx* c) { return c->prof_max > 0 && c->prof_n < c->prof_max; }
+
 // Event marking the start of stage i (i = 6: end of the build).
 static cudaEvent_t stage_event(thc_ctx* c, int i) {
-  if (c->prof_max > 0 && c->prof_n < c->prof_max) return c->prof[(size_t)c->prof_n * 7 + i];
+  if (profiling(c)) return c->prof[(size_t)c->prof_n * kProfEv + i];
   return c->ev[i];
+}
+
+// Start (which = 0) or end (1) of stage st's main kernel; null unless profiling.
+static cudaEvent_t core_event(thc_ctx* c, int st, int which) {
+  if (!profiling(c)) return nullptr;
+  return c->prof[(size_t)c->prof_n * kProfEv + 7 + 2 * st + which];
+}
+
+static cudaError_t record_core(thc_ctx* c, int st, int which, cudaStream_t s) {
+  cudaEvent_t e = core_event(c, st, which);
+  return e ? cudaEventRecord(e, s) : cudaSuccess;
+}
+
+// Stage boundary i.  In the one-kernel-per-stage forms (simple) the stage's
+// main kernel is the whole stage, so its core events sit on the boundaries.
+static cudaError_t mark(thc_ctx* c, int i, cudaStream_t s, bool simple) {
+  cudaError_t e = cudaSuccess;
+  if (simple && i > 0) e = record_core(c, i - 1, 1, s);
+  if (e == cudaSuccess) e = cudaEventRecord(stage_event(c, i), s);
+  if (e == cudaSuccess && simple && i < 6) e = record_core(c, i, 0, s);
+  return e;
 }
 
 static thc_status build_fp64(thc_ctx* c, const double2* C, double2* KC, double* ex) {
@@ -343,22 +368,22 @@ static thc_status build_fp64(thc_ctx* c, const double2* C, double2* KC, double* 
   double2* M = (double2*)c->M;
   double2* Y = (double2*)c->Y;
   cudaStream_t s = c->stream;
-  CKC(c, cudaEventRecord(stage_event(c, 0), s));
+  CKC(c, mark(c, 0, s, true));
   CKC(c, gemm_z(A_KM, B_KN, P, n, N, c->X64, P, (long)N * P, C, n, (long)N * n, Psi, n,
                 (long)P * n, nk, s));
-  CKC(c, cudaEventRecord(stage_event(c, 1), s));
+  CKC(c, mark(c, 1, s, true));
   CKC(c, gemm_z(A_MK, B_NK_CONJ, P, P, n, Psi, n, (long)P * n, Psi, n, (long)P * n, D, P, PP,
                 nk, s));
-  CKC(c, cudaEventRecord(stage_event(c, 2), s));
+  CKC(c, mark(c, 2, s, true));
   CKC(c, kconv_z(D, c->Vh64, M, PP, c->n1, c->n2, c->n3, s));
-  CKC(c, cudaEventRecord(stage_event(c, 3), s));
+  CKC(c, mark(c, 3, s, true));
   CKC(c, gemm_z(A_MK, B_KN, P, n, P, M, P, PP, Psi, n, (long)P * n, Y, n, (long)P * n, nk, s));
-  CKC(c, cudaEventRecord(stage_event(c, 4), s));
+  CKC(c, mark(c, 4, s, true));
   CKC(c, gemm_z(A_MK_CONJ, B_KN, N, n, P, c->X64, P, (long)N * P, Y, n, (long)P * n, KC, n,
                 (long)N * n, nk, s));
-  CKC(c, cudaEventRecord(stage_event(c, 5), s));
+  CKC(c, mark(c, 5, s, true));
   CKC(c, ex_reduce_z(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
-  CKC(c, cudaEventRecord(stage_event(c, 6), s));
+  CKC(c, mark(c, 6, s, true));
   return THC_OK;
 }
 
@@ -370,23 +395,23 @@ static thc_status build_mixed(thc_ctx* c, const double2* C, double2* KC, double*
   float2* M = (float2*)c->M;
   float2* Y = (float2*)c->Y;
   cudaStream_t s = c->stream;
-  CKC(c, cudaEventRecord(stage_event(c, 0), s));
+  CKC(c, mark(c, 0, s, true));
   CKC(c, (gemm_c_comp<float2, double2, float2>(A_KM, B_KN, P, n, N, c->X32, P, (long)N * P, C, n,
                                                (long)N * n, Psi, n, (long)P * n, nk, s)));
-  CKC(c, cudaEventRecord(stage_event(c, 1), s));
+  CKC(c, mark(c, 1, s, true));
   CKC(c, gemm_c_plain(A_MK, B_NK_CONJ, P, P, n, Psi, n, (long)P * n, Psi, n, (long)P * n, D, P,
                       PP, nk, s));
-  CKC(c, cudaEventRecord(stage_event(c, 2), s));
+  CKC(c, mark(c, 2, s, true));
   CKC(c, kconv_c(D, c->Vh32, M, PP, c->n1, c->n2, c->n3, s));
-  CKC(c, cudaEventRecord(stage_event(c, 3), s));
+  CKC(c, mark(c, 3, s, true));
   CKC(c, (gemm_c_comp<float2, float2, float2>(A_MK, B_KN, P, n, P, M, P, PP, Psi, n, (long)P * n,
                                               Y, n, (long)P * n, nk, s)));
-  CKC(c, cudaEventRecord(stage_event(c, 4), s));
+  CKC(c, mark(c, 4, s, true));
   CKC(c, (gemm_c_comp<float2, float2, double2>(A_MK_CONJ, B_KN, N, n, P, c->X32, P, (long)N * P,
                                                Y, n, (long)P * n, KC, n, (long)N * n, nk, s)));
-  CKC(c, cudaEventRecord(stage_event(c, 5), s));
+  CKC(c, mark(c, 5, s, true));
   CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
-  CKC(c, cudaEventRecord(stage_event(c, 6), s));
+  CKC(c, mark(c, 6, s, true));
   return THC_OK;
 }
 
@@ -398,40 +423,48 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   float2* M = (float2*)c->M;
   float2* Y = (float2*)c->Y;
   cudaStream_t s = c->stream;
-  CKC(c, cudaEventRecord(stage_event(c, 0), s));
+  CKC(c, mark(c, 0, s, false));
   // S1  Psi = X^T C on tensor cores: B = embedded C, one exponent per orbital
   CKC(c, col_exponents_z(C, Nn, n, nk, N, n, c->eC, s));
   CKC(c, embed_b(C, true, Nn, n, 1, false, false, nk, N, n, c->eC, c->Bc_pl, c->plBc, c->ldXT, s));
+  CKC(c, record_core(c, 0, 0, s));
   CKC(c, tc_gemm(c->opXT, c->opBc, P, 2 * n, 2 * N, nk, c->eXT, P, c->eC, n, Psi, false, 2 * n, 2 * Pn,
-                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong));
-  CKC(c, cudaEventRecord(stage_event(c, 1), s));
+                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong, core_event(c, 0, 1)));
+  CKC(c, mark(c, 1, s, false));
   // S2  D = Psi Psi^H on tensor cores: A = Psi and B = embedded Psi^H share the
   // row exponents of Psi
   CKC(c, row_exponents_c(Psi, Pn, n, nk, P, n, c->ePsi, s));
   CKC(c, slice_rows_c(Psi, Pn, n, nk, P, n, c->ePsi, c->PsiA_pl, c->plPs, c->ldPs, s));
   CKC(c, embed_b(Psi, false, Pn, 1, n, true, false, nk, n, P, c->ePsi, c->Bd_pl, c->plBd, c->ldPs, s));
+  CKC(c, record_core(c, 1, 0, s));
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
-                 c->part_s0, c->part_bc, c->tc_err, s, kChunkShort));
-  CKC(c, cudaEventRecord(stage_event(c, 2), s));
-  // S3  M = IDFT(DFT(D) o Vh) in FP32, with the row maxima of every M^k, then
-  // M's fixed-point slices (A of S4a) with the exact row exponents
+                 c->part_s0, c->part_bc, c->tc_err, s, kChunkShort, core_event(c, 1, 1)));
+  CKC(c, mark(c, 2, s, false));
+  // S3  M = IDFT(DFT(D) o Vh) in FP32, with the row maxima of every M^k
+  CKC(c, record_core(c, 2, 0, s));
   CKC(c, kconv_c_rowmax(D, c->Vh32, M, P, c->n1, c->n2, c->n3, c->mrow, s));
+  CKC(c, record_core(c, 2, 1, s));
+  CKC(c, mark(c, 3, s, false));
+  // S4a Y = M Psi on tensor cores: A = M's fixed-point slices with the exact
+  // row exponents, B = embedded Psi with one exponent per orbital
   CKC(c, slice_rows_from_max(M, P, (long)nk * P, c->mrow, c->eM, c->M_pl, c->plM, c->ldM, s));
-  CKC(c, cudaEventRecord(stage_event(c, 3), s));
-  // S4a Y = M Psi on tensor cores: B = embedded Psi, one exponent per orbital
   CKC(c, col_exponents_c(Psi, Pn, n, nk, P, n, c->eY, s));
   CKC(c, embed_b(Psi, false, Pn, n, 1, false, false, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
+  CKC(c, record_core(c, 3, 0, s));
   CKC(c, tc_gemm(c->opM, c->opBy, P, 2 * n, 2 * P, nk, c->eM, P, c->eY, n, Y, false, 2 * n, 2 * Pn,
-                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong));
-  CKC(c, cudaEventRecord(stage_event(c, 4), s));
+                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong, core_event(c, 3, 1)));
+  CKC(c, mark(c, 4, s, false));
   // S4b KC = conj(X) Y on tensor cores: B = embedded Y (conj-A form)
   CKC(c, col_exponents_c(Y, Pn, n, nk, P, n, c->eY, s));
   CKC(c, embed_b(Y, false, Pn, n, 1, false, true, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
+  CKC(c, record_core(c, 4, 0, s));
   CKC(c, tc_gemm(c->opXn, c->opBy, N, 2 * n, 2 * P, nk, c->eXn, N, c->eY, n, KC, true, 2 * n, 2 * Nn,
-                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong));
-  CKC(c, cudaEventRecord(stage_event(c, 5), s));
+                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong, core_event(c, 4, 1)));
+  CKC(c, mark(c, 5, s, false));
+  CKC(c, record_core(c, 5, 0, s));
   CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
-  CKC(c, cudaEventRecord(stage_event(c, 6), s));
+  CKC(c, record_core(c, 5, 1, s));
+  CKC(c, mark(c, 6, s, false));
   return THC_OK;
 }
 
@@ -509,7 +542,7 @@ thc_status thc_stage_times(thc_ctx* c, float ms[6]) {
 thc_status thc_profile_begin(thc_ctx* c, int max_builds) {
   if (!c || max_builds < 1 || max_builds > 4096) return THC_ERR_ARG;
   for (cudaEvent_t e : c->prof) cudaEventDestroy(e);
-  c->prof.assign((size_t)max_builds * 7, nullptr);
+  c->prof.assign((size_t)max_builds * kProfEv, nullptr);
   for (auto& e : c->prof) CKC(c, cudaEventCreate(&e));
   c->prof_max = max_builds;
   c->prof_n = 0;
@@ -521,22 +554,36 @@ thc_status thc_profile_end(thc_ctx* c, float mean_ms[6], int* nbuilds) {
   if (c->prof_max <= 0) return THC_ERR_STATE;
   for (int i = 0; i < kStages; i++) mean_ms[i] = 0.f;
   const int nb = c->prof_n;
+  float core[kStages] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int b = 0; b < nb; b++) {
-    cudaEvent_t* e = &c->prof[(size_t)b * 7];
+    cudaEvent_t* e = &c->prof[(size_t)b * kProfEv];
     CKC(c, cudaEventSynchronize(e[6]));
     for (int i = 0; i < kStages; i++) {
       float t = 0.f;
       CKC(c, cudaEventElapsedTime(&t, e[i], e[i + 1]));
       mean_ms[i] += t;
+      CKC(c, cudaEventElapsedTime(&t, e[7 + 2 * i], e[8 + 2 * i]));
+      core[i] += t;
     }
   }
   if (nb > 0)
-    for (int i = 0; i < kStages; i++) mean_ms[i] /= nb;
+    for (int i = 0; i < kStages; i++) {
+      mean_ms[i] /= nb;
+      c->core_ms[i] = core[i] / nb;
+    }
+  c->core_valid = nb > 0;
   *nbuilds = nb;
   for (cudaEvent_t e : c->prof) cudaEventDestroy(e);
   c->prof.clear();
   c->prof_max = 0;
   c->prof_n = 0;
+  return THC_OK;
+}
+
+thc_status thc_profile_kernels(const thc_ctx* c, float core_ms[6]) {
+  if (!c || !core_ms) return THC_ERR_ARG;
+  if (!c->core_valid) return THC_ERR_STATE;
+  for (int i = 0; i < kStages; i++) core_ms[i] = c->core_ms[i];
   return THC_OK;
 }
 

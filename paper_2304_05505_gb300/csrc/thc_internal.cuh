@@ -84,8 +84,11 @@ struct thc_ctx {
   TcOperand opXT, opPs, opXn, opBc, opBd, opBy, opM;
   int* tc_err;        // device word: nonzero after a device wait gave up
   cudaEvent_t ev[7];               // stage boundaries of the last build
-  std::vector<cudaEvent_t> prof;   // 7 per profiled build
+  std::vector<cudaEvent_t> prof;   // per profiled build: 7 stage boundaries, then the
+                                   // start and end of each stage's main kernel (12)
   int prof_max, prof_n;            // slots, builds recorded
+  float core_ms[6];                // mean main-kernel times of the last profile
+  bool core_valid;
   std::string last_error;
 };
 

@@ -29,7 +29,7 @@ EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_ker
            "thc_build", "thc_build_host", "thc_get_intermediate", "thc_stage_times",
            "thc_launches_per_build", "thc_destroy", "thc_status_string", "thc_last_error",
            "thc_profile_begin", "thc_profile_end", "thc_sync", "thc_kconv_noalloc",
-           "thc_select_points", "thc_fit_kernel", "thc_mlp_features", "thc_mlp_score",
+           "thc_select_points", "thc_fit_kernel", "thc_profile_kernels", "thc_mlp_features", "thc_mlp_score",
            "thc_mlp_workspace_bytes", "thc_mlp_train_step", "thc_mlp_candidates", "thc_select_points_among"]
 
 MLP_NPARAM = 8641
@@ -70,6 +70,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_launches_per_build.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.thc_profile_begin.argtypes = [vp, ip]
     lib.thc_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]
+    lib.thc_profile_kernels.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.thc_destroy.argtypes = [vp]
     lib.thc_sync.argtypes = [vp]
     lib.thc_kconv_noalloc.argtypes = [dp, dp, dp, ip, ip, ip, ctypes.c_long, vp]
@@ -202,6 +203,13 @@ def thc_profile_end(ctx) -> tuple:
     n = ctypes.c_int(0)
     _check(load().thc_profile_end(ctx, arr, ctypes.byref(n)), "thc_profile_end", ctx)
     return [float(x) for x in arr], int(n.value)
+
+
+def thc_profile_kernels(ctx) -> list:
+    """Mean ms of each stage's main kernel in the last completed profile."""
+    arr = (ctypes.c_float * 6)()
+    _check(load().thc_profile_kernels(ctx, arr), "thc_profile_kernels", ctx)
+    return [float(x) for x in arr]
 
 
 def thc_stage_times(ctx) -> list:

@@ -205,18 +205,25 @@ def test_error_paths(torch_cuda):
     eb.close()
 
 
-def test_profile_stage_times(torch_cuda):
+@pytest.mark.parametrize("precision", ["mixed", "mixed_simt", "fp64"])
+def test_profile_stage_times(torch_cuda, precision):
+    """Stage times and the times of each stage's main kernel: every main
+    kernel takes time and fits inside its stage."""
     from paper_2304_05505_gb300 import thc
     r = cells.random_problem((2, 2, 2), nbas=30, nocc=5, nisdf=100, seed=3)
     dims = dict(n1=2, n2=2, n3=2, nbas=30, nocc=5, nisdf=100)
-    eb = thc.ExchangeBuild(dims, "mixed")
+    eb = thc.ExchangeBuild(dims, precision)
     eb.set_collocation(r["X"])
     eb.set_kernel(r["V"])
+    with pytest.raises(thc.ThcError):
+        thc.thc_profile_kernels(eb.ctx)          # no profile has completed yet
     thc.thc_profile_begin(eb.ctx, 4)
     for _ in range(6):
         eb.build(r["C"])
     ms, n = thc.thc_profile_end(eb.ctx)
     assert n == 4 and all(t > 0 for t in ms)
+    core = thc.thc_profile_kernels(eb.ctx)
+    assert all(0 < c <= t * 1.001 + 1e-3 for c, t in zip(core, ms))
     last = thc.thc_stage_times(eb.ctx)
     assert all(t > 0 for t in last)
     eb.close()
