@@ -36,7 +36,7 @@ CONFIG = "C2"
 SAMPLE_FRACTION = 8      # the CPU oracle sample is 1/8 of a build
 # the main kernel of each stage of the tensor-core build
 KERNEL_NAMES = {"S1_collocate": "tc_gemm_kernel<2> (S1, split-K)", "S2_density": "tc_gemm_kernel<0> (S2)",
-                "S3_kconv": "kconv_kernel<float> (S3, with row maxima)",
+                "S3_kconv": "kconv_lanes_kernel<4, 4, 4> (S3)",
                 "S4a_apply_M": "tc_gemm_kernel<2> (S4a, split-K)",
                 "S4b_backproject": "tc_gemm_kernel<2> (S4b, split-K)",
                 "S5_energy": "ex_partial_c + ex_final (S5)"}

@@ -19,10 +19,6 @@
 // table for lengths 5, 7, 8) are applied as an FP32 hi + lo pair so that the
 // forward and inverse transforms do not pick up a systematic scale error.
 //
-// For the tensor-core build the same kernel also finds, for every row P of
-// every M^k, the maximum of max(|Re|, |Im|) over Q (warp-segmented reduction,
-// one atomic per warp and row segment); the operand slicing of S4a takes its
-// row exponents from these maxima.
 #include "thc_internal.cuh"
 
 #include <math.h>
@@ -136,15 +132,11 @@ __device__ __forceinline__ void dft3(typename cplx<R>::type* x, int T, const Twi
   dft_axis<R>(x, T, tw, 2, sign);
 }
 
-// M = IDFT(DFT(D) o Vh), one element per thread.  With rmax, also
-// rmax[k * np + P] = max over the row's Q of max(|Re|, |Im|) of M^k[P,Q], as
-// float bits (non-negative floats order as their bit patterns); rmax must be
-// zero on entry.
+// M = IDFT(DFT(D) o Vh), one element per thread, values in shared memory.
 template <typename R>
 __global__ void kconv_kernel(const typename cplx<R>::type* __restrict__ D,
                              const typename cplx<R>::type* __restrict__ Vh,
-                             typename cplx<R>::type* __restrict__ M, long npq, Twiddles tw,
-                             unsigned* __restrict__ rmax, int np) {
+                             typename cplx<R>::type* __restrict__ M, long npq, Twiddles tw) {
   typedef typename cplx<R>::type CT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* buf = reinterpret_cast<CT*>(smem_raw);
@@ -152,7 +144,6 @@ __global__ void kconv_kernel(const typename cplx<R>::type* __restrict__ D,
   const int nk = tw.n[0] * tw.n[1] * tw.n[2];
   const long e = (long)blockIdx.x * T + tid;
   const bool ok = e < npq;
-  const unsigned okmask = __ballot_sync(0xffffffffu, ok);   // T is a multiple of 32
   CT* x = buf + tid;
   // unrolled so that many independent loads are in flight per thread
 #pragma unroll 16
@@ -164,21 +155,73 @@ __global__ void kconv_kernel(const typename cplx<R>::type* __restrict__ D,
     x[(long)a * T] = cmul(x[(long)a * T], v);
   }
   dft3<R>(x, T, tw, +1);
-  if (!ok) return;
-  if (!rmax) {
+  if (ok)
     for (int k = 0; k < nk; k++) M[(long)k * npq + e] = x[(long)k * T];
-    return;
-  }
-  // lanes of this warp on the same row P (a warp spans at most a few rows)
-  const int P = (int)(e / np);
-  const unsigned same = __match_any_sync(okmask, P);
-  const bool leader = (threadIdx.x & 31) == __ffs(same) - 1;
-  for (int k = 0; k < nk; k++) {
-    const CT v = x[(long)k * T];
-    M[(long)k * npq + e] = v;
-    const float a = fmaxf(fabsf((float)v.x), fabsf((float)v.y));
-    const unsigned m = __reduce_max_sync(same, __float_as_uint(a));
-    if (leader) atomicMax(rmax + (long)k * np + P, m);
+}
+
+// Lane-split FP32 form for the meshes 2^3, 3^3 and 4^3 (compile-time N1, N2,
+// N3).  N1 lanes of a warp share one element: lane slot t holds the N2 N3
+// values with first mesh index t, in registers.  The DFT along the first axis
+// runs across the N1 lanes (each lane gathers the N1 values by shuffles and
+// keeps output t), the other two axes run locally.  Lane l of a warp is slot
+// l / EPW of element l % EPW, so the lanes of one slot read EPW consecutive
+// elements of one k plane.  Both D and Vh are loaded up front, so a warp
+// waits for DRAM once, and no shared memory holds the data.
+template <int N1, int N2, int N3>
+__global__ void __launch_bounds__(256, 2) kconv_lanes_kernel(const float2* __restrict__ D,
+                                                          const float2* __restrict__ Vh, float2* __restrict__ M,
+                                                          long npq, Twiddles tw) {
+  constexpr int L = N2 * N3, EPW = 32 / N1, EPB = EPW * 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / EPW;                       // first mesh index of this lane's values
+  const int el = lane - slot * EPW;                  // element within the warp
+  const bool live = slot < N1;                       // lanes past EPW N1 idle
+  const long e0 = (long)blockIdx.x * EPB;
+  const long e = e0 + warp * EPW + el;
+  const bool ok = live && e < npq;
+  const long off = (long)(live ? slot : 0) * L * npq + e;
+  float2 x[L], vh[L];
+#pragma unroll
+  for (int j = 0; j < L; j++) x[j] = ok ? __ldcs(D + off + (long)j * npq) : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < L; j++) vh[j] = ok ? __ldcs(Vh + off + (long)j * npq) : make_float2(0.f, 0.f);
+  // forward DFT: first axis across lanes, then the two local axes
+  auto across = [&](int sign) {
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+      float2 v[N1];
+#pragma unroll
+      for (int t = 0; t < N1; t++) {
+        v[t].x = __shfl_sync(0xffffffffu, x[j].x, t * EPW + el);
+        v[t].y = __shfl_sync(0xffffffffu, x[j].y, t * EPW + el);
+      }
+      line_dft<float, N1>(v, 1, tw, 0, sign);
+      float2 r = v[0];
+#pragma unroll
+      for (int t = 1; t < N1; t++)
+        if (slot == t) r = v[t];
+      x[j] = r;
+    }
+  };
+  auto local = [&](int sign) {
+    if constexpr (N2 > 1) {
+#pragma unroll
+      for (int i = 0; i < N3; i++) line_dft<float, N2>(x + i, N3, tw, 1, sign);
+    }
+    if constexpr (N3 > 1) {
+#pragma unroll
+      for (int i = 0; i < N2; i++) line_dft<float, N3>(x + i * N3, 1, tw, 2, sign);
+    }
+  };
+  across(-1);
+  local(-1);
+#pragma unroll
+  for (int j = 0; j < L; j++) x[j] = cmul(x[j], vh[j]);
+  local(+1);
+  across(+1);
+  if (ok) {
+#pragma unroll
+    for (int j = 0; j < L; j++) M[off + (long)j * npq] = x[j];
   }
 }
 
@@ -240,10 +283,24 @@ int pick_threads(int nk, size_t elem) {
   return T;
 }
 
+template <int N1, int N2, int N3>
+cudaError_t kconv_lanes_launch(const float2* D, const float2* Vh, float2* M, long npq, cudaStream_t s) {
+  constexpr int EPB = (32 / N1) * 8;
+  const long blocks = (npq + EPB - 1) / EPB;
+  kconv_lanes_kernel<N1, N2, N3><<<(unsigned)blocks, 256, 0, s>>>(D, Vh, M, npq, make_twiddles(N1, N2, N3));
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t kconv_launch(const typename cplx<R>::type* D, const typename cplx<R>::type* Vh,
-                         typename cplx<R>::type* M, long npq, int n1, int n2, int n3, unsigned* rmax,
-                         int np, cudaStream_t s) {
+                         typename cplx<R>::type* M, long npq, int n1, int n2, int n3, cudaStream_t s) {
+  if constexpr (sizeof(R) == sizeof(float)) {
+    if (n1 == n2 && n2 == n3) {
+      if (n1 == 4) return kconv_lanes_launch<4, 4, 4>(D, Vh, M, npq, s);
+      if (n1 == 3) return kconv_lanes_launch<3, 3, 3>(D, Vh, M, npq, s);
+      if (n1 == 2) return kconv_lanes_launch<2, 2, 2>(D, Vh, M, npq, s);
+    }
+  }
   const int nk = n1 * n2 * n3;
   const size_t el = sizeof(typename cplx<R>::type);
   const int T = pick_threads(nk, el);
@@ -251,7 +308,7 @@ cudaError_t kconv_launch(const typename cplx<R>::type* D, const typename cplx<R>
   cudaError_t e = cudaFuncSetAttribute(kconv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const long blocks = (npq + T - 1) / T;
-  kconv_kernel<R><<<(unsigned)blocks, T, sm, s>>>(D, Vh, M, npq, make_twiddles(n1, n2, n3), rmax, np);
+  kconv_kernel<R><<<(unsigned)blocks, T, sm, s>>>(D, Vh, M, npq, make_twiddles(n1, n2, n3));
   return cudaGetLastError();
 }
 
@@ -259,19 +316,12 @@ cudaError_t kconv_launch(const typename cplx<R>::type* D, const typename cplx<R>
 
 cudaError_t kconv_z(const double2* D, const double2* Vh, double2* M, long npq, int n1, int n2,
                     int n3, cudaStream_t s) {
-  return kconv_launch<double>(D, Vh, M, npq, n1, n2, n3, nullptr, 0, s);
+  return kconv_launch<double>(D, Vh, M, npq, n1, n2, n3, s);
 }
 
 cudaError_t kconv_c(const float2* D, const float2* Vh, float2* M, long npq, int n1, int n2,
                     int n3, cudaStream_t s) {
-  return kconv_launch<float>(D, Vh, M, npq, n1, n2, n3, nullptr, 0, s);
-}
-
-cudaError_t kconv_c_rowmax(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
-                           unsigned* rmax, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(rmax, 0, sizeof(unsigned) * n1 * n2 * n3 * (size_t)np, s);
-  if (e != cudaSuccess) return e;
-  return kconv_launch<float>(D, Vh, M, (long)np * np, n1, n2, n3, rmax, np, s);
+  return kconv_launch<float>(D, Vh, M, npq, n1, n2, n3, s);
 }
 
 cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long npq, int n1,

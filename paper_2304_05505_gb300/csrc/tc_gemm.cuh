@@ -50,11 +50,11 @@ cudaError_t slice_rows_z(const double2* src, long sbs, int lds, int batch, int r
                          uint16_t* planes, long plane, int ldp, cudaStream_t s);
 cudaError_t slice_rows_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
                          uint16_t* planes, long plane, int ldp, cudaStream_t s);
-// Slices of the rows of src[row][0..np) (rows = batch x rows per batch,
-// contiguous) with exponents from the row maxima rmax[row] (float bits of
-// max(|re|, |im|)); writes the exponents to e[row].
-cudaError_t slice_rows_from_max(const float2* src, int np, long rows, const unsigned* rmax, int* e,
-                                uint16_t* planes, long plane, int ldp, cudaStream_t s);
+// Slices of the contiguous rows src[row][0..np) (rows = batch x rows per
+// batch) with each row's exact exponent, found by the same kernel; writes the
+// exponents to e[row].
+cudaError_t slice_rows_exact(const float2* src, int np, long rows, int* e, uint16_t* planes, long plane, int ldp,
+                             cudaStream_t s);
 // Transposed: planes[p][b][c][2r + d] of src[b][r][c] with column exponents e[b][c].
 cudaError_t slice_cols_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
                          uint16_t* planes, long plane, int ldp, cudaStream_t s);

@@ -15,6 +15,8 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 namespace {
 
 template <typename CT>
@@ -138,43 +140,58 @@ __global__ void embed_kernel(const CT* __restrict__ src, long sbs, long ldk, lon
   }
 }
 
-// Slices of the rows of M[k][P][Q] (np x np per k) with the row exponent taken
-// from the row maximum rmax[k][P] (float bits); also writes e[k][P].  V = 2:
-// two consecutive complex values per thread (16-byte loads, np even).
+// Slices of the contiguous rows src[row][0..np) with the exact row exponent,
+// one warp per row: the warp first reduces max(|re|, |im|) over its row, then
+// reads the row again (from cache) and writes the four planes.  V = 2: two
+// consecutive complex values per lane access (16-byte loads, np even).
 template <int V>
-__global__ void slice_max_kernel(const float2* __restrict__ src, int np, long rows, const unsigned* __restrict__ rmax,
-                                 int* __restrict__ e, uint16_t* planes, long plane, int ldp) {
+__global__ void slice_rowmax_kernel(const float2* __restrict__ src, int np, long rows, int* __restrict__ e,
+                                    uint16_t* planes, long plane, int ldp) {
+  const long w0 = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long nw = ((long)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
   const int per = np / V;
-  const long total = rows * per;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const long row = i / per;
-    const int c = (int)(i - row * per) * V;
-    const int ex = row_exponent((double)__uint_as_float(__ldg(rmax + row)));
-    if (c == 0) e[row] = ex;
-    float2 v[V];
-    if constexpr (V == 2) {
-      const float4 w = __ldcs(reinterpret_cast<const float4*>(src + row * np + c));
-      v[0] = make_float2(w.x, w.y);
-      v[1] = make_float2(w.z, w.w);
-    } else {
-      v[0] = __ldcs(src + row * np + c);
-    }
-    uint16_t s[V][2][4];
-#pragma unroll
-    for (int j = 0; j < V; j++) {
-      slice4(v[j].x, ex, s[j][0]);
-      slice4(v[j].y, ex, s[j][1]);
-    }
-    const long off = row * ldp + 2L * c;
-#pragma unroll
-    for (int p = 0; p < 4; p++) {
+  for (long row = w0; row < rows; row += nw) {
+    const float2* r = src + row * np;
+    float m = 0.f;
+    for (int c = lane; c < per; c += 32) {
       if constexpr (V == 2) {
-        const uint2 w = make_uint2((uint32_t)s[0][0][p] | ((uint32_t)s[0][1][p] << 16),
-                                   (uint32_t)s[1][0][p] | ((uint32_t)s[1][1][p] << 16));
-        *reinterpret_cast<uint2*>(planes + p * plane + off) = w;
+        const float4 w = *reinterpret_cast<const float4*>(r + 2 * c);
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(w.x), fabsf(w.y)), fmaxf(fabsf(w.z), fabsf(w.w))));
       } else {
-        *reinterpret_cast<uint32_t*>(planes + p * plane + off) =
-            (uint32_t)s[0][0][p] | ((uint32_t)s[0][1][p] << 16);
+        const float2 w = r[c];
+        m = fmaxf(m, fmaxf(fabsf(w.x), fabsf(w.y)));
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int ex = row_exponent((double)m);
+    if (lane == 0) e[row] = ex;
+    for (int c = lane; c < per; c += 32) {
+      float2 v[V];
+      if constexpr (V == 2) {
+        const float4 w = __ldcs(reinterpret_cast<const float4*>(r + 2 * c));
+        v[0] = make_float2(w.x, w.y);
+        v[1] = make_float2(w.z, w.w);
+      } else {
+        v[0] = __ldcs(r + c);
+      }
+      uint16_t sl[V][2][4];
+#pragma unroll
+      for (int j = 0; j < V; j++) {
+        slice4(v[j].x, ex, sl[j][0]);
+        slice4(v[j].y, ex, sl[j][1]);
+      }
+      const long off = row * ldp + 2L * c * V;
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        if constexpr (V == 2) {
+          *reinterpret_cast<uint2*>(planes + p * plane + off) =
+              make_uint2((uint32_t)sl[0][0][p] | ((uint32_t)sl[0][1][p] << 16),
+                         (uint32_t)sl[1][0][p] | ((uint32_t)sl[1][1][p] << 16));
+        } else {
+          *reinterpret_cast<uint32_t*>(planes + p * plane + off) =
+              (uint32_t)sl[0][0][p] | ((uint32_t)sl[0][1][p] << 16);
+        }
       }
     }
   }
@@ -235,13 +252,14 @@ cudaError_t slice_cols_z(const double2* src, long sbs, int lds, int batch, int r
   return cudaGetLastError();
 }
 
-cudaError_t slice_rows_from_max(const float2* src, int np, long rows, const unsigned* rmax, int* e,
-                                uint16_t* planes, long plane, int ldp, cudaStream_t s) {
+cudaError_t slice_rows_exact(const float2* src, int np, long rows, int* e, uint16_t* planes, long plane, int ldp,
+                             cudaStream_t s) {
+  const long nb = std::min<long>((rows + 7) / 8, 152L * 64);
   // 16-byte loads and 8-byte plane stores need even rows and 8-byte aligned plane rows
   if (np % 2 == 0 && ldp % 4 == 0 && ((uintptr_t)src & 15) == 0)
-    slice_max_kernel<2><<<grid1(rows * (np / 2)), 256, 0, s>>>(src, np, rows, rmax, e, planes, plane, ldp);
+    slice_rowmax_kernel<2><<<(unsigned)nb, 256, 0, s>>>(src, np, rows, e, planes, plane, ldp);
   else
-    slice_max_kernel<1><<<grid1(rows * np), 256, 0, s>>>(src, np, rows, rmax, e, planes, plane, ldp);
+    slice_rowmax_kernel<1><<<(unsigned)nb, 256, 0, s>>>(src, np, rows, e, planes, plane, ldp);
   return cudaGetLastError();
 }
 

@@ -99,7 +99,6 @@ size_t memory_bytes(const thc_dims* d, int precision) {
   b += 2 * s.v * s.el;           // D, M
   if (precision == THC_MIXED) {
     b += 4 * 2 * (s.plXn + s.plXT + s.plPs + s.plBc + s.plBd + s.plBy + s.plM);   // bf16 slices (M too)
-    b += sizeof(unsigned) * s.nk * d->nisdf;                                      // row maxima of M
     b += sizeof(int) * s.nexp + 64;                                         // exponents, error word
     b += (sizeof(int) + sizeof(float)) * s.npart;                           // split-K partial sums
   } else {
@@ -114,7 +113,7 @@ void free_all(thc_ctx* c) {
   void* ptrs[] = {c->X64, c->Vh64, c->X32, c->Vh32, c->Psi, c->D, c->M, c->Y,
                   c->Cdev, c->KCdev, c->exdev, c->partial, c->flag, c->Xn_pl, c->XT_pl,
                   c->PsiA_pl, c->Bc_pl, c->Bd_pl, c->By_pl, c->ex_pl, c->tc_err, c->part_s0,
-                  c->part_bc, c->M_pl, c->mrow};
+                  c->part_bc, c->M_pl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 7; i++)
@@ -194,7 +193,6 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
     W((void**)&c->Vh32, s.v * s.el);
     W(&c->M, s.v * s.el);
     W((void**)&c->M_pl, 4 * 2 * s.plM);
-    W((void**)&c->mrow, sizeof(unsigned) * s.nk * d->nisdf);
     W((void**)&c->Xn_pl, 4 * 2 * s.plXn);
     W((void**)&c->XT_pl, 4 * 2 * s.plXT);
     W((void**)&c->PsiA_pl, 4 * 2 * s.plPs);
@@ -440,14 +438,14 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
                  c->part_s0, c->part_bc, c->tc_err, s, kChunkShort, core_event(c, 1, 1)));
   CKC(c, mark(c, 2, s, false));
-  // S3  M = IDFT(DFT(D) o Vh) in FP32, with the row maxima of every M^k
+  // S3  M = IDFT(DFT(D) o Vh) in FP32
   CKC(c, record_core(c, 2, 0, s));
-  CKC(c, kconv_c_rowmax(D, c->Vh32, M, P, c->n1, c->n2, c->n3, c->mrow, s));
+  CKC(c, kconv_c(D, c->Vh32, M, PP, c->n1, c->n2, c->n3, s));
   CKC(c, record_core(c, 2, 1, s));
   CKC(c, mark(c, 3, s, false));
   // S4a Y = M Psi on tensor cores: A = M's fixed-point slices with the exact
   // row exponents, B = embedded Psi with one exponent per orbital
-  CKC(c, slice_rows_from_max(M, P, (long)nk * P, c->mrow, c->eM, c->M_pl, c->plM, c->ldM, s));
+  CKC(c, slice_rows_exact(M, P, (long)nk * P, c->eM, c->M_pl, c->plM, c->ldM, s));
   CKC(c, col_exponents_c(Psi, Pn, n, nk, P, n, c->eY, s));
   CKC(c, embed_b(Psi, false, Pn, n, 1, false, false, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
   CKC(c, record_core(c, 3, 0, s));
@@ -591,14 +589,14 @@ thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   if (!c || !launches) return THC_ERR_ARG;
   // FP64 and CUDA-core forms: S1, S2, S3, S4a, S4b, E_x partial, E_x final.
   // Tensor-core form: S1 3 (exponents, embed, GEMM), S2 4 (exponents, slices,
-  // embed, GEMM), S3 2 (convolution with row maxima, slices of M), S4a 3
-  // (exponents, embed, GEMM), S4b 3, E_x 2; S1, S4a and S4b add a combine
-  // kernel when split along K.
+  // embed, GEMM), S3 1 (convolution), S4a 4 (slices of M with their row
+  // exponents, exponents of Psi, embed, GEMM), S4b 3, E_x 2; S1, S4a and S4b
+  // add a combine kernel when split along K.
   if (c->precision == THC_MIXED) {
     const int s1 = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nbas, c->nk, kChunkLong) > 0 ? 1 : 0;
     const int s4a = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nisdf, c->nk, kChunkLong) > 0 ? 1 : 0;
     const int s4b = tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk, kChunkLong) > 0 ? 1 : 0;
-    *launches = 3 + s1 + 4 + 2 + 3 + s4a + 3 + s4b + 2;
+    *launches = 3 + s1 + 4 + 1 + 4 + s4a + 3 + s4b + 2;
   } else {
     *launches = 7;
   }

@@ -74,7 +74,6 @@ struct thc_ctx {
   uint16_t* By_pl;    // [nk][2 nocc][ldM]   embedded Psi, B of S4a, then embedded Y, B of S4b
                       //                     (column exponents of Psi, then of Y, in eY [nk][nocc])
   uint16_t* M_pl;     // [nk][nisdf][ldM]    M, A of S4a                  eM [nk][nisdf]
-  unsigned* mrow;     // [nk][nisdf] row maxima of M (float bits), found by S3
   int* ex_pl;         // eXn | eXT | ePsi | eC | eY
   int* part_s0;       // split-K partial sums of the tensor-core GEMMs (exact leading class)
   float* part_bc;     // and their FP32 remainders
@@ -123,10 +122,6 @@ cudaError_t kconv_z(const double2* D, const double2* Vh, double2* M, long npq, i
                     int n3, cudaStream_t s);
 cudaError_t kconv_c(const float2* D, const float2* Vh, float2* M, long npq, int n1, int n2,
                     int n3, cudaStream_t s);
-// The FP32 convolution that also finds the row maxima of M:
-// rmax[k * np + P] = max_Q max(|Re|, |Im|) of M^k[P,Q] as float bits.
-cudaError_t kconv_c_rowmax(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
-                           unsigned* rmax, cudaStream_t s);
 // Vh[a] = (1/N_k) sum_q V[q] w^{+a.q} in FP64; writes FP64 or FP32 output.
 cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long npq, int n1,
                              int n2, int n3, cudaStream_t s);

@@ -66,7 +66,7 @@ def test_memory_bytes_arithmetic():
     c1 = -(-(2 * N) // 512)                              # and of S1 (K = 2 N real)
     part = max(c4 * nk * N * 2 * n if c4 > 1 else 0, c4 * nk * P * 2 * n if c4 > 1 else 0,
                c1 * nk * P * 2 * n if c1 > 1 else 0)
-    tc = 8 * (nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + 4 * 2 * planes + 4 * nk * P \
+    tc = 8 * (nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + 4 * 2 * planes \
         + 4 * exps + 64 + 8 * part + common
     assert thc.thc_memory_bytes(d, thc.THC_MIXED) == tc
 
