@@ -1,6 +1,6 @@
 // Batched complex GEMMs of the mixed build on the 5th-generation tensor cores
 // (tcgen05, sm_103a): the dense contractions S1 (Psi = X^T C), S2
-// (D = Psi Psi^H) and S4b (KC = conj(X) Y) of the build.
+// (D = Psi Psi^H), S4a (Y = M Psi) and S4b (KC = conj(X) Y) of the build.
 //
 // Complex via a real embedding.  C[m][n] = sum_k A[m][k] B[k][n] with A stored
 // as interleaved complex rows is the real product C' = A' B'^T where
@@ -41,7 +41,11 @@
 //               10 per K step
 //   warps 2-3   idle (they keep the block at 12 warps)
 //   warps 4-11  epilogue: read both accumulators, scale and store (or write
-//               the partial sums), release the accumulator set
+//               the partial sums), release the accumulator set.  Each warp
+//               turns its 32-row x 16-column blocks around in a small shared
+//               tile so that every store instruction writes whole 64-byte row
+//               segments, and reads the column exponents of a block with one
+//               load spread by shuffles
 // Every mbarrier wait is bounded (about 2 s of clock64); on expiry the thread
 // sets the error word, stops issuing work and the CTA releases TMEM and exits.
 #include "thc_internal.cuh"
@@ -67,7 +71,9 @@ constexpr int STAGES = 3;
 constexpr uint32_t STAGE_BYTES = 2 * NPL * TILE_BYTES;       // 64 KB
 constexpr int EPI_WARP0 = 4;
 constexpr int NTHREADS = (EPI_WARP0 + EPI_WARPS) * 32;
-constexpr size_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int EPI_LD = 20;                                   // floats per staged row (16 + 4: no bank conflicts)
+constexpr uint32_t EPI_TILE = 32 * EPI_LD;                   // floats per epilogue warp
+constexpr size_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + EPI_WARPS * EPI_TILE * 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -237,6 +243,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
   uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   // bars: full[3], empty[3], acc_full[2], acc_empty[2]
   uint32_t* tmem_slot = (uint32_t*)(bars + 16);
+  float* epi_stage = (float*)(smem + STAGES * STAGE_BYTES + 256);   // EPI_WARPS tiles of EPI_TILE floats
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = smem_u32(bars);
   auto FULL = [&](int s) { return bar0 + 8u * s; };
@@ -370,33 +377,18 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
       const int row = mi * BM + 32 * q + lane;
       const int ea = (OUT != 2 && row < g.M) ? row_exp(eA, (long)b * seA + row) : 0;
       const uint32_t accA = tmem + lane_off + 256 * set, accBC = accA + 128;
+      float* stg = epi_stage + (warp - EPI_WARP0) * EPI_TILE;
+      const int row0 = mi * BM + 32 * q;          // first row of this warp's blocks
 #pragma unroll 1
       for (int qq = 0; qq < 4; qq++) {
         float va[16], vb[16];
         tmem_ld16(accA + 64 * h + 16 * qq, va);
         tmem_ld16(accBC + 64 * h + 16 * qq, vb);
         const int col0 = ni * BN + 64 * h + 16 * qq;   // even: complex pairs stay together
-        if (row >= g.M) continue;
-        if constexpr (OUT == 2) {
-          // exact leading sums and FP32 remainders of this K chunk
-          const long base = (((long)kc * g.batch + b) * g.M + row) * g.Nr;
-          if (col0 + 16 <= g.Nr && (g.Nr % 4) == 0) {
-#pragma unroll
-            for (int j = 0; j < 16; j += 4) {
-              *reinterpret_cast<int4*>(ps0 + base + col0 + j) =
-                  make_int4(__float2int_rn(va[j]), __float2int_rn(va[j + 1]), __float2int_rn(va[j + 2]),
-                            __float2int_rn(va[j + 3]));
-              *reinterpret_cast<float4*>(pbc + base + col0 + j) = make_float4(vb[j], vb[j + 1], vb[j + 2], vb[j + 3]);
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 16; j++)
-              if (col0 + j < g.Nr) {
-                ps0[base + col0 + j] = __float2int_rn(va[j]);
-                pbc[base + col0 + j] = vb[j];
-              }
-          }
-        } else if constexpr (OUT == 1) {
+        if (col0 >= g.Nr) continue;                   // the whole block is padding (warp-uniform)
+        if constexpr (OUT == 1) {
+          const int row = row0 + lane;
+          if (row >= g.M) continue;
           double* o = (double*)out + (long)b * sbo + (long)row * ldo;
 #pragma unroll
           for (int j = 0; j < 16; j += 2) {
@@ -412,24 +404,65 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
             }
           }
         } else {
-          float w[16];
-#pragma unroll
-          for (int j = 0; j < 16; j += 2) {
-            const int jj = (col0 + j < g.Nr) ? ((col0 + j) >> 1) : 0;
-            const float sc = pow2f(ea + eB[(long)b * seB + jj] - 14);
-            w[j] = (va[j] + vb[j]) * sc;           // va holds an exact integer below 2^24
-            w[j + 1] = (va[j + 1] + vb[j + 1]) * sc;
-          }
-          float* o = (float*)out + (long)b * sbo + (long)row * ldo;
-          if (col0 + 16 <= g.Nr && (ldo % 4) == 0) {
+          // values of this lane's row into the staging tile
+          if constexpr (OUT == 2) {
 #pragma unroll
             for (int j = 0; j < 16; j += 4)
-              *reinterpret_cast<float4*>(o + col0 + j) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+              *reinterpret_cast<float4*>(stg + lane * EPI_LD + j) =
+                  make_float4(__int_as_float(__float2int_rn(va[j])), __int_as_float(__float2int_rn(va[j + 1])),
+                              __int_as_float(__float2int_rn(va[j + 2])), __int_as_float(__float2int_rn(va[j + 3])));
           } else {
+            // column exponents of the block's 8 complex pairs: one load, shuffled
+            const int jp = (col0 >> 1) + (lane & 7);
+            const int ebl = (col0 + 2 * (lane & 7) < g.Nr) ? eB[(long)b * seB + jp] : 0;
 #pragma unroll
-            for (int j = 0; j < 16; j++)
-              if (col0 + j < g.Nr) o[col0 + j] = w[j];
+            for (int j = 0; j < 16; j += 4) {
+              const float s0 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, j >> 1) - 14);
+              const float s1 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, (j >> 1) + 1) - 14);
+              // va holds an exact integer below 2^24
+              *reinterpret_cast<float4*>(stg + lane * EPI_LD + j) =
+                  make_float4((va[j] + vb[j]) * s0, (va[j + 1] + vb[j + 1]) * s0, (va[j + 2] + vb[j + 2]) * s1,
+                              (va[j + 3] + vb[j + 3]) * s1);
+            }
           }
+          __syncwarp();
+          // write out: lane -> (row rr, 4 columns f); 8 rows x 64 B per instruction
+          const int f = lane >> 3;
+          const int col = col0 + 4 * f;
+          const bool vec = (OUT == 2) ? (g.Nr % 4 == 0) : ((ldo % 4) == 0 && (sbo % 4) == 0);
+#pragma unroll
+          for (int pass = 0; pass < (OUT == 2 ? 2 : 1); pass++) {
+            if (pass == 1) {   // FP32 remainders of the chunk through the same tile
+              __syncwarp();
+#pragma unroll
+              for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4*>(stg + lane * EPI_LD + j) = make_float4(vb[j], vb[j + 1], vb[j + 2], vb[j + 3]);
+              __syncwarp();
+            }
+#pragma unroll
+            for (int it = 0; it < 4; it++) {
+              const int rr = (lane & 7) + 8 * it;
+              const int row = row0 + rr;
+              if (row >= g.M || col >= g.Nr) continue;
+              const float4 v = *reinterpret_cast<const float4*>(stg + rr * EPI_LD + 4 * f);
+              float* o;
+              if constexpr (OUT == 2) {
+                const long base = (((long)kc * g.batch + b) * g.M + row) * g.Nr;
+                o = pass == 0 ? reinterpret_cast<float*>(ps0 + base) : pbc + base;
+              } else {
+                o = (float*)out + (long)b * sbo + (long)row * ldo;
+              }
+              if (vec && col + 4 <= g.Nr) {
+                *reinterpret_cast<float4*>(o + col) = v;
+              } else {
+                const float w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                  if (col + i < g.Nr) o[col + i] = w4[i];
+              }
+            }
+          }
+          __syncwarp();   // the tile is rewritten by the next block
         }
       }
       fence_before();
