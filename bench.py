@@ -34,11 +34,13 @@ WORKLOAD = ("benzene-shaped orthorhombic cell 13.9x17.8x12.9 bohr, 48 centres, N
             "4x4x4 k (N_k=64), N_ISDF=1200, 40^3 grid (config C2)")
 CONFIG = "C2"
 SAMPLE_FRACTION = 8      # the CPU oracle sample is 1/8 of a build
+# bf16 slice products per real product of each tensor-core GEMM
+SLICE_PRODUCTS = {"S1_collocate": 10, "S2_density": 6, "S4a_apply_M": 10, "S4b_backproject": 10}
 # the main kernel of each stage of the tensor-core build
-KERNEL_NAMES = {"S1_collocate": "tc_gemm_kernel<2> (S1, split-K)", "S2_density": "tc_gemm_kernel<0> (S2)",
+KERNEL_NAMES = {"S1_collocate": "tc_gemm_kernel<2, 4> (S1, split-K)", "S2_density": "tc_gemm_kernel<0, 3> (S2)",
                 "S3_kconv": "kconv_lanes_kernel<4, 4, 4> (S3)",
-                "S4a_apply_M": "tc_gemm_kernel<2> (S4a, split-K)",
-                "S4b_backproject": "tc_gemm_kernel<2> (S4b, split-K)",
+                "S4a_apply_M": "tc_gemm_kernel<2, 4> (S4a, split-K)",
+                "S4b_backproject": "tc_gemm_kernel<2, 4> (S4b, split-K)",
                 "S5_energy": "ex_partial_c + ex_final (S5)"}
 
 
@@ -179,9 +181,9 @@ def kernel_roofline(stage: str, ms: float, work: dict, pk: dict) -> dict:
     The bound is whichever lower limit is larger: algorithmic bytes over the
     measured copy bandwidth, or algorithmic flops over the sustained bf16
     tensor peak (the kernels run inside a multi-millisecond build).  The
-    tensor-core GEMMs issue 10 bf16 slice products per real product (the
-    classes s + t <= 3 of four-slice fixed-point operands), so their issued
-    tensor fraction is also given."""
+    tensor-core GEMMs issue several bf16 slice products per real product (10
+    for four-slice operands, 6 for S2's three-slice operands), so their
+    issued tensor fraction is also given."""
     w = work[stage]
     sec = ms * 1e-3
     t_hbm = w["bytes"] / (pk["hbm_gbs"] * 1e9)
@@ -199,9 +201,10 @@ def kernel_roofline(stage: str, ms: float, work: dict, pk: dict) -> dict:
                    peak_source=f"{pk['source']} copy bandwidth")
     if w["flops"]:
         tf = w["flops"] / sec / 1e12
+        issued = SLICE_PRODUCTS.get(stage, 10)
         out.update(algorithmic_flops=w["flops"], tensor_tflops=tf,
-                   tensor_frac=tf / pk["bf16_tflops_sustained"],
-                   issued_tensor_frac=10 * tf / pk["bf16_tflops_sustained"])
+                   tensor_frac=tf / pk["bf16_tflops_sustained"], slice_products=issued,
+                   issued_tensor_frac=issued * tf / pk["bf16_tflops_sustained"])
     return out
 
 
@@ -433,8 +436,8 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16-slices/f32", "data": "synthetic",
             "config": {"workload": WORKLOAD,
-                       "precision": "mixed: S1/S2/S4a/S4b tcgen05 bf16 GEMMs on 4-slice fixed-point operands "
-                                    "(exact leading sums, FP32 remainders), S3 FP32, E_x FP64 sum",
+                       "precision": "mixed: S1/S4a/S4b tcgen05 bf16 GEMMs on 4-slice fixed-point operands, S2 on "
+                                    "3 slices (exact leading sums, FP32 remainders), S3 FP32, E_x FP64 sum",
                        "l2": "inputs larger than L2 (prepared kernel 737 MB, X 265 MB complex64)",
                        "parallelism": f"{world} independent builds (one per GPU)"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,

@@ -21,7 +21,9 @@
 // is an integer below 2^24, which the FP32 accumulator holds exactly whatever
 // its rounding.  The nine classes with s + t = 1..3 go to a second
 // accumulator; their rounding is at least 2^-8 smaller.  Classes with
-// s + t >= 4 (below 2^-32 of the row scales) are dropped.
+// s + t >= 4 (below 2^-32 of the row scales) are dropped.  A GEMM whose
+// result is rounded to FP32 anyway may take three slices (24 bits) and the
+// six classes s + t <= 2.
 //
 // Work units: a 128 x 128 output tile and a chunk of at most 1024 real K (so
 // the leading sum of a unit is exact; shorter chunks also shorten the FP32
@@ -31,14 +33,14 @@
 // scaled result directly.
 //
 // Kernel structure (persistent: one CTA per SM loops over units, 384 threads):
-//   warp 0      TMA producer: 4 A planes + 4 B planes per 32-wide real-K block
-//               into a 3-stage ring (64 KB a stage, 64B swizzle), running
-//               ahead across units
+//   warp 0      TMA producer: NS A planes + NS B planes per 32-wide real-K
+//               block into a ring of 3 stages of 64 KB (NS = 4) or 4 of 48 KB
+//               (NS = 3), 64B swizzle, running ahead across units
 //   warp 1      allocates 512 TMEM columns = two accumulator sets (leading
 //               class, classes 1..3; 128 columns each) so that the epilogue of
 //               one unit overlaps the MMAs of the next; lane 0 issues
 //               tcgen05.mma (M = 128, N = 128, K = 16, bf16 x bf16 -> f32),
-//               10 per K step
+//               10 (NS = 4) or 6 (NS = 3) per K step
 //   warps 2-3   idle (they keep the block at 12 warps)
 //   warps 4-11  epilogue: read both accumulators, scale and store (or write
 //               the partial sums), release the accumulator set.  Each warp
@@ -67,13 +69,21 @@ constexpr int MAX_CHUNK_KB = 32;                             // K blocks per exa
 constexpr long long WAIT_LIMIT = 4000000000LL;               // clock64 cycles (~2 s)
 constexpr uint32_t TMEM_COLS = 512;
 
-constexpr int STAGES = 3;
-constexpr uint32_t STAGE_BYTES = 2 * NPL * TILE_BYTES;       // 64 KB
+// Operands in NS slices: 4 (10 products per real product) or 3 (6 products,
+// classes s + t <= 2; used where the output is rounded to FP32 anyway and K is
+// short).  The ring holds 3 stages of 64 KB or 4 of 48 KB.
+template <int NS> struct Ring {
+  static constexpr int STAGES = NS == 4 ? 3 : 4;
+  static constexpr uint32_t STAGE_BYTES = 2 * NS * TILE_BYTES;
+};
+constexpr uint32_t RING_BYTES = 3 * 2 * 4 * TILE_BYTES;     // 192 KB either way
+static_assert(Ring<4>::STAGES * Ring<4>::STAGE_BYTES == RING_BYTES, "ring size");
+static_assert(Ring<3>::STAGES * Ring<3>::STAGE_BYTES == RING_BYTES, "ring size");
 constexpr int EPI_WARP0 = 4;
 constexpr int NTHREADS = (EPI_WARP0 + EPI_WARPS) * 32;
 constexpr int EPI_LD = 20;                                   // floats per staged row (16 + 4: no bank conflicts)
 constexpr uint32_t EPI_TILE = 32 * EPI_LD;                   // floats per epilogue warp
-constexpr size_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + EPI_WARPS * EPI_TILE * 4;
+constexpr size_t SMEM_BYTES = RING_BYTES + 1024 + 256 + EPI_WARPS * EPI_TILE * 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -233,23 +243,25 @@ __device__ __forceinline__ int row_exp(const int* e, long i) {
 }
 
 // OUT: 0 = FP32 result, 1 = FP64 result, 2 = partial sums (split K)
-template <int OUT>
+template <int OUT, int NS>
 __global__ void __launch_bounds__(NTHREADS, 1)
 tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restrict__ eA, long seA,
                const int* __restrict__ eB, long seB, void* out, long ldo, long sbo, int* __restrict__ ps0,
                float* __restrict__ pbc, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-  // bars: full[3], empty[3], acc_full[2], acc_empty[2]
+  constexpr int STAGES = Ring<NS>::STAGES;
+  constexpr uint32_t STAGE_BYTES = Ring<NS>::STAGE_BYTES;
+  uint64_t* bars = (uint64_t*)(smem + RING_BYTES);
+  // bars: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2]
   uint32_t* tmem_slot = (uint32_t*)(bars + 16);
-  float* epi_stage = (float*)(smem + STAGES * STAGE_BYTES + 256);   // EPI_WARPS tiles of EPI_TILE floats
+  float* epi_stage = (float*)(smem + RING_BYTES + 256);   // EPI_WARPS tiles of EPI_TILE floats
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = smem_u32(bars);
   auto FULL = [&](int s) { return bar0 + 8u * s; };
-  auto EMPTY = [&](int s) { return bar0 + 8u * (3 + s); };
-  auto AFULL = [&](int s) { return bar0 + 8u * (6 + s); };
-  auto AEMPTY = [&](int s) { return bar0 + 8u * (8 + s); };
+  auto EMPTY = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto AFULL = [&](int s) { return bar0 + 8u * (2 * STAGES + s); };
+  auto AEMPTY = [&](int s) { return bar0 + 8u * (2 * STAGES + 2 + s); };
 
   __shared__ int abort_flag;
   if (threadIdx.x == 0) abort_flag = *(volatile int*)err;
@@ -294,7 +306,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int s = 0; s < NPL; s++) {
+      for (int s = 0; s < NS; s++) {
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.a[s]) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.b[s]) : "memory");
       }
@@ -310,10 +322,10 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
           if (!mbar_wait(EMPTY(st), ph ^ 1, err, 2)) { ok = false; break; }
           mbar_expect_tx(FULL(st), STAGE_BYTES);
           const uint32_t dst = sbase + st * STAGE_BYTES;
-          for (int p = 0; p < NPL; p++)
+          for (int p = 0; p < NS; p++)
             tma_load_3d(dst + p * TILE_BYTES, &maps.a[p], FULL(st), kb * BKR, mi * BM, b);
-          for (int p = 0; p < NPL; p++)
-            tma_load_3d(dst + (NPL + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
+          for (int p = 0; p < NS; p++)
+            tma_load_3d(dst + (NS + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
         }
       }
     }
@@ -339,19 +351,24 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
           // descriptors: one base per stage, planes and K steps are offsets of
           // (bytes >> 4) in the start-address field (no carry: smem < 256 KB)
           const uint64_t aBase = dbase + ((st * STAGE_BYTES) >> 4);
-          const uint64_t bBase = aBase + ((NPL * TILE_BYTES) >> 4);
+          const uint64_t bBase = aBase + ((NS * TILE_BYTES) >> 4);
           constexpr uint64_t PL = TILE_BYTES >> 4;
 #pragma unroll
           for (int kk = 0; kk < BKR / 16; kk++) {
             const uint64_t a = aBase + 2 * kk, b2 = bBase + 2 * kk;   // 32 B per K step
             const uint32_t acc = (kb == kb0 && kk == 0) ? 0u : 1u;
             mma_bf16(accA, a, b2, idesc, acc);                          // exact leading class
-            // classes s + t = 3, 2, 1 (smallest first) into the second accumulator
-            mma_bf16(accBC, a, b2 + 3 * PL, idesc, acc);
-            mma_bf16(accBC, a + PL, b2 + 2 * PL, idesc, 1u);
-            mma_bf16(accBC, a + 2 * PL, b2 + PL, idesc, 1u);
-            mma_bf16(accBC, a + 3 * PL, b2, idesc, 1u);
-            mma_bf16(accBC, a, b2 + 2 * PL, idesc, 1u);
+            // classes s + t = 3 (four slices only), 2, 1 (smallest first) into
+            // the second accumulator
+            if constexpr (NS == 4) {
+              mma_bf16(accBC, a, b2 + 3 * PL, idesc, acc);
+              mma_bf16(accBC, a + PL, b2 + 2 * PL, idesc, 1u);
+              mma_bf16(accBC, a + 2 * PL, b2 + PL, idesc, 1u);
+              mma_bf16(accBC, a + 3 * PL, b2, idesc, 1u);
+              mma_bf16(accBC, a, b2 + 2 * PL, idesc, 1u);
+            } else {
+              mma_bf16(accBC, a, b2 + 2 * PL, idesc, acc);
+            }
             mma_bf16(accBC, a + PL, b2 + PL, idesc, 1u);
             mma_bf16(accBC, a + 2 * PL, b2, idesc, 1u);
             mma_bf16(accBC, a, b2 + PL, idesc, 1u);
@@ -544,7 +561,8 @@ long tc_partial_elems(int M, int Nr, int Kr, int batch, int chunk_k) {
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s, int chunk_k,
-                    cudaEvent_t gemm_done) {
+                    cudaEvent_t gemm_done, int slices) {
+  if (slices != 3 && slices != 4) return cudaErrorInvalidValue;
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   Maps maps;
   for (int p = 0; p < NPL; p++) {
@@ -570,15 +588,19 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   }
   const unsigned grid = (unsigned)std::min<long>(g.units, nsm);
   cudaError_t e = cudaSuccess;
-#define LAUNCH(OUTK)                                                                                      \
+#define LAUNCH(OUTK, NSK)                                                                                 \
   {                                                                                                       \
-    e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+    e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK, NSK>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                              (int)SMEM_BYTES);                                                            \
     if (e != cudaSuccess) return e;                                                                       \
-    tc_gemm_kernel<OUTK><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, out, ldo, sbo,     \
-                                                            ps0, pbc, err);                               \
+    tc_gemm_kernel<OUTK, NSK><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, out, ldo,     \
+                                                                 sbo, ps0, pbc, err);                     \
   }
-  if (split) LAUNCH(2) else if (out_f64) LAUNCH(1) else LAUNCH(0)
+  if (slices == 4) {
+    if (split) LAUNCH(2, 4) else if (out_f64) LAUNCH(1, 4) else LAUNCH(0, 4)
+  } else {
+    if (split) LAUNCH(2, 3) else if (out_f64) LAUNCH(1, 3) else LAUNCH(0, 3)
+  }
 #undef LAUNCH
   e = cudaGetLastError();
   if (e == cudaSuccess && gemm_done) e = cudaEventRecord(gemm_done, s);

@@ -23,11 +23,13 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
 // until they are combined.  `err` receives a nonzero code if a device wait
 // gave up.
 // gemm_done (may be null) is recorded on `s` right after the GEMM kernel,
-// before any combine kernel, so that the GEMM alone can be timed.
+// before any combine kernel, so that the GEMM alone can be timed.  slices: 4
+// (all four planes, 10 slice products) or 3 (the first three planes, the 6
+// products s + t <= 2: about 2^-24 of the row scales).
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s, int chunk_k,
-                    cudaEvent_t gemm_done = nullptr);
+                    cudaEvent_t gemm_done = nullptr, int slices = 4);
 
 // Elements of each split-K partial buffer tc_gemm needs for this shape (0 if none).
 long tc_partial_elems(int M, int Nr, int Kr, int batch, int chunk_k);

@@ -435,8 +435,9 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, slice_rows_c(Psi, Pn, n, nk, P, n, c->ePsi, c->PsiA_pl, c->plPs, c->ldPs, s));
   CKC(c, embed_b(Psi, false, Pn, 1, n, true, false, nk, n, P, c->ePsi, c->Bd_pl, c->plBd, c->ldPs, s));
   CKC(c, record_core(c, 1, 0, s));
+  // D is rounded to FP32 on output and K = 2 n is short: three slices
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
-                 c->part_s0, c->part_bc, c->tc_err, s, kChunkShort, core_event(c, 1, 1)));
+                 c->part_s0, c->part_bc, c->tc_err, s, kChunkShort, core_event(c, 1, 1), 3));
   CKC(c, mark(c, 2, s, false));
   // S3  M = IDFT(DFT(D) o Vh) in FP32
   CKC(c, record_core(c, 2, 0, s));
