@@ -497,27 +497,54 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
 }
 
 // Adds the K chunks of a split-K product: out = 2^(e_a + e_b - 14) (sum s0 + sum bc).
-template <bool OUT_F64>
+// V = 4: four consecutive columns per thread (16-byte partial loads; Nr, ldo
+// and sbo multiples of 4), V = 1 otherwise.
+template <bool OUT_F64, int V>
 __global__ void tc_combine_kernel(const int* __restrict__ ps0, const float* __restrict__ pbc, int nchunk,
                                   int batch, int M, int Nr, const int* __restrict__ eA, long seA,
                                   const int* __restrict__ eB, long seB, void* out, long ldo, long sbo) {
   const long total = (long)batch * M * Nr;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+  const long nv = total / V;
+  for (long iv = (long)blockIdx.x * blockDim.x + threadIdx.x; iv < nv; iv += (long)gridDim.x * blockDim.x) {
+    const long i = iv * V;
     const int col = (int)(i % Nr);
     const long bm = i / Nr;
     const int m = (int)(bm % M);
     const int b = (int)(bm / M);
-    long s0 = 0;
-    float bc = 0.f;
-    for (int c = 0; c < nchunk; c++) {
-      s0 += ps0[(long)c * total + i];
-      bc += pbc[(long)c * total + i];
+    long s0[V];
+    float bc[V];
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+      s0[j] = 0;
+      bc[j] = 0.f;
     }
-    const int e = row_exp(eA, (long)b * seA + m) + eB[(long)b * seB + (col >> 1)] - 14;
-    if (OUT_F64)
-      ((double*)out)[(long)b * sbo + (long)m * ldo + col] = ((double)s0 + (double)bc) * pow2d(e);
-    else
-      ((float*)out)[(long)b * sbo + (long)m * ldo + col] = (float)(((double)s0 + (double)bc) * pow2d(e));
+    for (int c = 0; c < nchunk; c++) {
+      if constexpr (V == 4) {
+        const int4 a = __ldcs(reinterpret_cast<const int4*>(ps0 + (long)c * total + i));
+        const float4 f = __ldcs(reinterpret_cast<const float4*>(pbc + (long)c * total + i));
+        s0[0] += a.x; s0[1] += a.y; s0[2] += a.z; s0[3] += a.w;
+        bc[0] += f.x; bc[1] += f.y; bc[2] += f.z; bc[3] += f.w;
+      } else {
+        s0[0] += ps0[(long)c * total + i];
+        bc[0] += pbc[(long)c * total + i];
+      }
+    }
+    const int ea = row_exp(eA, (long)b * seA + m) - 14;
+    double x[V];
+#pragma unroll
+    for (int j = 0; j < V; j++) x[j] = ((double)s0[j] + (double)bc[j]) * pow2d(ea + eB[(long)b * seB + ((col + j) >> 1)]);
+    const long o = (long)b * sbo + (long)m * ldo + col;
+    if constexpr (V == 4) {
+      if (OUT_F64) {
+        reinterpret_cast<double2*>((double*)out + o)[0] = make_double2(x[0], x[1]);
+        reinterpret_cast<double2*>((double*)out + o)[1] = make_double2(x[2], x[3]);
+      } else {
+        *reinterpret_cast<float4*>((float*)out + o) = make_float4((float)x[0], (float)x[1], (float)x[2], (float)x[3]);
+      }
+    } else {
+      if (OUT_F64) ((double*)out)[o] = x[0];
+      else ((float*)out)[o] = (float)x[0];
+    }
   }
 }
 
@@ -606,10 +633,15 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   if (e == cudaSuccess && gemm_done) e = cudaEventRecord(gemm_done, s);
   if (e != cudaSuccess || !split) return e;
   const long total = (long)batch * M * Nr;
-  const unsigned cg = (unsigned)std::min<long>((total + 255) / 256, 152L * 16);
-  if (out_f64)
-    tc_combine_kernel<true><<<cg, 256, 0, s>>>(ps0, pbc, g.nchunk, batch, M, Nr, eA, seA, eB, seB, out, ldo, sbo);
-  else
-    tc_combine_kernel<false><<<cg, 256, 0, s>>>(ps0, pbc, g.nchunk, batch, M, Nr, eA, seA, eB, seB, out, ldo, sbo);
+  const bool v4 = Nr % 4 == 0 && ldo % 4 == 0 && sbo % 4 == 0 && ((uintptr_t)out & 31) == 0;
+  const unsigned cg = (unsigned)std::min<long>((total / (v4 ? 4 : 1) + 255) / 256, 152L * 16);
+#define COMBINE(F64, V) \
+  tc_combine_kernel<F64, V><<<cg, 256, 0, s>>>(ps0, pbc, g.nchunk, batch, M, Nr, eA, seA, eB, seB, out, ldo, sbo)
+  if (out_f64) {
+    if (v4) COMBINE(true, 4); else COMBINE(true, 1);
+  } else {
+    if (v4) COMBINE(false, 4); else COMBINE(false, 1);
+  }
+#undef COMBINE
   return cudaGetLastError();
 }

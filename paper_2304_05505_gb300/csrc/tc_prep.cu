@@ -41,23 +41,31 @@ __global__ void rowexp_kernel(const CT* __restrict__ src, long sbs, int lds, int
 }
 
 // Exponent of each column: e[b * cols + c] = max over r of src[b][r][c].
-// Block (b, column slab of 32): warp w scans rows w, w + 8, ..., lane = column.
+// Block (b, column slab of 32) of 32 warps: warp w scans rows w, w + 32, ...
+// four at a time (lane = column), then the warps' maxima are combined.
+constexpr int CE_WARPS = 32;
 template <typename CT>
-__global__ void colexp_kernel(const CT* __restrict__ src, long sbs, int lds, int batch, int rows, int cols,
-                              int* __restrict__ e) {
-  __shared__ double red[8][32];
+__global__ void __launch_bounds__(CE_WARPS * 32) colexp_kernel(const CT* __restrict__ src, long sbs, int lds,
+                                                               int batch, int rows, int cols, int* __restrict__ e) {
+  __shared__ double red[CE_WARPS][32];
   const int b = blockIdx.y;
   const int c = blockIdx.x * 32 + (threadIdx.x & 31);
   const int w = threadIdx.x >> 5;
   double m = 0.0;
   if (c < cols) {
     const CT* p = src + (long)b * sbs + c;
-    for (int r = w; r < rows; r += 8) m = fmax(m, cmax(p[(long)r * lds]));
+    int r = w;
+    for (; r + 3 * CE_WARPS < rows; r += 4 * CE_WARPS) {
+      const CT v0 = p[(long)r * lds], v1 = p[(long)(r + CE_WARPS) * lds];
+      const CT v2 = p[(long)(r + 2 * CE_WARPS) * lds], v3 = p[(long)(r + 3 * CE_WARPS) * lds];
+      m = fmax(m, fmax(fmax(cmax(v0), cmax(v1)), fmax(cmax(v2), cmax(v3))));
+    }
+    for (; r < rows; r += CE_WARPS) m = fmax(m, cmax(p[(long)r * lds]));
   }
   red[w][threadIdx.x & 31] = m;
   __syncthreads();
   if (w == 0) {
-    for (int i = 1; i < 8; i++) m = fmax(m, red[i][threadIdx.x]);
+    for (int i = 1; i < CE_WARPS; i++) m = fmax(m, red[i][threadIdx.x]);
     if (c < cols) e[(long)b * cols + c] = row_exponent(m);
   }
 }
@@ -221,13 +229,15 @@ cudaError_t row_exponents_c(const float2* src, long sbs, int lds, int batch, int
 
 cudaError_t col_exponents_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
                             cudaStream_t s) {
-  colexp_kernel<double2><<<dim3((cols + 31) / 32, batch), 256, 0, s>>>(src, sbs, lds, batch, rows, cols, e);
+  colexp_kernel<double2><<<dim3((cols + 31) / 32, batch), CE_WARPS * 32, 0, s>>>(src, sbs, lds, batch, rows, cols,
+                                                                                 e);
   return cudaGetLastError();
 }
 
 cudaError_t col_exponents_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
                             cudaStream_t s) {
-  colexp_kernel<float2><<<dim3((cols + 31) / 32, batch), 256, 0, s>>>(src, sbs, lds, batch, rows, cols, e);
+  colexp_kernel<float2><<<dim3((cols + 31) / 32, batch), CE_WARPS * 32, 0, s>>>(src, sbs, lds, batch, rows, cols,
+                                                                                e);
   return cudaGetLastError();
 }
 

@@ -431,8 +431,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, mark(c, 1, s, false));
   // S2  D = Psi Psi^H on tensor cores: A = Psi and B = embedded Psi^H share the
   // row exponents of Psi
-  CKC(c, row_exponents_c(Psi, Pn, n, nk, P, n, c->ePsi, s));
-  CKC(c, slice_rows_c(Psi, Pn, n, nk, P, n, c->ePsi, c->PsiA_pl, c->plPs, c->ldPs, s));
+  CKC(c, slice_rows_exact(Psi, n, (long)nk * P, c->ePsi, c->PsiA_pl, c->plPs, c->ldPs, s));
   CKC(c, embed_b(Psi, false, Pn, 1, n, true, false, nk, n, P, c->ePsi, c->Bd_pl, c->plBd, c->ldPs, s));
   CKC(c, record_core(c, 1, 0, s));
   // D is rounded to FP32 on output and K = 2 n is short: three slices
@@ -589,15 +588,15 @@ thc_status thc_profile_kernels(const thc_ctx* c, float core_ms[6]) {
 thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   if (!c || !launches) return THC_ERR_ARG;
   // FP64 and CUDA-core forms: S1, S2, S3, S4a, S4b, E_x partial, E_x final.
-  // Tensor-core form: S1 3 (exponents, embed, GEMM), S2 4 (exponents, slices,
-  // embed, GEMM), S3 1 (convolution), S4a 4 (slices of M with their row
+  // Tensor-core form: S1 3 (exponents, embed, GEMM), S2 3 (slices with their
+  // row exponents, embed, GEMM), S3 1 (convolution), S4a 4 (slices of M with their row
   // exponents, exponents of Psi, embed, GEMM), S4b 3, E_x 2; S1, S4a and S4b
   // add a combine kernel when split along K.
   if (c->precision == THC_MIXED) {
     const int s1 = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nbas, c->nk, kChunkLong) > 0 ? 1 : 0;
     const int s4a = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nisdf, c->nk, kChunkLong) > 0 ? 1 : 0;
     const int s4b = tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk, kChunkLong) > 0 ? 1 : 0;
-    *launches = 3 + s1 + 4 + 1 + 4 + s4a + 3 + s4b + 2;
+    *launches = 3 + s1 + 3 + 1 + 4 + s4a + 3 + s4b + 2;
   } else {
     *launches = 7;
   }
