@@ -41,13 +41,14 @@
 //               one unit overlaps the MMAs of the next; lane 0 issues
 //               tcgen05.mma (M = 128, N = 128, K = 16, bf16 x bf16 -> f32),
 //               10 (NS = 4) or 6 (NS = 3) per K step
-//   warps 2-3   idle (they keep the block at 12 warps)
-//   warps 4-11  epilogue: read both accumulators, scale and store (or write
-//               the partial sums), release the accumulator set.  Each warp
-//               turns its 32-row x 16-column blocks around in a small shared
-//               tile so that every store instruction writes whole 64-byte row
-//               segments, and reads the column exponents of a block with one
-//               load spread by shuffles
+//   warps 2-3   idle
+//   warps 4-19  epilogue (4 per TMEM lane quadrant, 32 columns each): read
+//               both accumulators, scale and store (or write the partial
+//               sums), release the accumulator set.  Each warp turns its
+//               32-row x 16-column blocks around in a 2 KB shared tile so that
+//               every store instruction writes whole 64-byte row segments; the
+//               unit's row and column exponents are loaded before its
+//               accumulator is ready
 // Every mbarrier wait is bounded (about 2 s of clock64); on expiry the thread
 // sets the error word, stops issuing work and the CTA releases TMEM and exits.
 #include "thc_internal.cuh"
@@ -64,7 +65,7 @@ namespace {
 constexpr int BM = 128, BN = 128, BKR = 32;
 constexpr int NPL = 4;                                       // slices per operand
 constexpr uint32_t TILE_BYTES = BM * BKR * 2;                // 8 KB (one plane of A or B)
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;
 constexpr int MAX_CHUNK_KB = 32;                             // K blocks per exact chunk, at most (1024 real K)
 constexpr long long WAIT_LIMIT = 4000000000LL;               // clock64 cycles (~2 s)
 constexpr uint32_t TMEM_COLS = 512;
@@ -81,8 +82,8 @@ static_assert(Ring<4>::STAGES * Ring<4>::STAGE_BYTES == RING_BYTES, "ring size")
 static_assert(Ring<3>::STAGES * Ring<3>::STAGE_BYTES == RING_BYTES, "ring size");
 constexpr int EPI_WARP0 = 4;
 constexpr int NTHREADS = (EPI_WARP0 + EPI_WARPS) * 32;
-constexpr int EPI_LD = 20;                                   // floats per staged row (16 + 4: no bank conflicts)
-constexpr uint32_t EPI_TILE = 32 * EPI_LD;                   // floats per epilogue warp
+constexpr uint32_t EPI_TILE = 32 * 16;                       // floats per epilogue warp (32 rows x 16)
+constexpr int EPI_COLS = 4 * BN / EPI_WARPS;                 // columns of a unit per epilogue warp
 constexpr size_t SMEM_BYTES = RING_BYTES + 1024 + 256 + EPI_WARPS * EPI_TILE * 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -215,6 +216,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// Float offset of 16-byte chunk c (0..3) of row r in a 32 x 16 staging tile;
+// the chunk index is XORed with bits 1-2 of the row so that 8 lanes writing
+// one chunk of 8 rows, or reading 8 rows of one chunk, hit distinct banks.
+__device__ __forceinline__ int stage_off(int r, int c) { return r * 16 + 4 * (c ^ ((r >> 1) & 3)); }
+
 struct Maps {
   CUtensorMap a[NPL];
   CUtensorMap b[NPL];
@@ -243,15 +249,24 @@ __device__ __forceinline__ int row_exp(const int* e, long i) {
 }
 
 // OUT: 0 = FP32 result, 1 = FP64 result, 2 = partial sums (split K)
-template <int OUT, int NS>
+// AR (A resident, short K in one chunk, three slices): the A tile of all K
+// (4 blocks x 3 planes, 96 KB) stays in shared memory while the CTA runs the
+// N tiles of one (batch, M tile) one after another; only B streams through a
+// 4-stage ring of 24 KB.  Each CTA takes a contiguous range of units so that
+// consecutive units share their A tile.
+template <int OUT, int NS, bool AR>
 __global__ void __launch_bounds__(NTHREADS, 1)
 tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restrict__ eA, long seA,
                const int* __restrict__ eB, long seB, void* out, long ldo, long sbo, int* __restrict__ ps0,
                float* __restrict__ pbc, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int STAGES = Ring<NS>::STAGES;
-  constexpr uint32_t STAGE_BYTES = Ring<NS>::STAGE_BYTES;
+  static_assert(!AR || NS == 3, "A-resident mode uses three slices");
+  constexpr int AKB = 4;                                           // K blocks the resident A tile holds
+  constexpr int STAGES = AR ? 4 : Ring<NS>::STAGES;
+  constexpr uint32_t A_BYTES = AR ? AKB * NS * TILE_BYTES : 0;     // resident A region (offset 0)
+  constexpr uint32_t STAGE_BYTES = AR ? NS * TILE_BYTES : Ring<NS>::STAGE_BYTES;
+  static_assert(A_BYTES + STAGES * STAGE_BYTES <= RING_BYTES, "ring size");
   uint64_t* bars = (uint64_t*)(smem + RING_BYTES);
   // bars: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2]
   uint32_t* tmem_slot = (uint32_t*)(bars + 16);
@@ -262,6 +277,8 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
   auto EMPTY = [&](int s) { return bar0 + 8u * (STAGES + s); };
   auto AFULL = [&](int s) { return bar0 + 8u * (2 * STAGES + s); };
   auto AEMPTY = [&](int s) { return bar0 + 8u * (2 * STAGES + 2 + s); };
+  const uint32_t AOP_FULL = bar0 + 8u * (2 * STAGES + 4);    // resident A tile loaded
+  const uint32_t AOP_EMPTY = bar0 + 8u * (2 * STAGES + 5);   // MMAs on the resident A tile done
 
   __shared__ int abort_flag;
   if (threadIdx.x == 0) abort_flag = *(volatile int*)err;
@@ -279,6 +296,10 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
       mbar_init(AFULL(s), 1);
       mbar_init(AEMPTY(s), EPI_WARPS);
     }
+    if (AR) {
+      mbar_init(AOP_FULL, 1);
+      mbar_init(AOP_EMPTY, 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -293,8 +314,12 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // unit u -> (b, m tile, n tile, K chunk); n fastest so CTAs running side by
-  // side share the A tile through L2
+  // units of this CTA: strided (CTAs running side by side share the A tile
+  // through L2) or, A resident, one contiguous range
+  const long u_begin = AR ? g.units * blockIdx.x / gridDim.x : (long)blockIdx.x;
+  const long u_end = AR ? g.units * (blockIdx.x + 1) / gridDim.x : g.units;
+  const long u_step = AR ? 1 : gridDim.x;
+  // unit u -> (b, m tile, n tile, K chunk), K chunk fastest, then n
   auto decode = [&](long u, int& b, int& mi, int& ni, int& kc) {
     kc = (int)(u % g.nchunk);
     long r = u / g.nchunk;
@@ -310,22 +335,41 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.a[s]) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.b[s]) : "memory");
       }
-      uint32_t it = 0;
+      uint32_t it = 0, agen = 0;
+      long gprev = -1;
       bool ok = true;
-      for (long u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+      for (long u = u_begin; u < u_end && ok; u += u_step) {
         int b, mi, ni, kc;
         decode(u, b, mi, ni, kc);
+        if constexpr (AR) {
+          const long grp = (long)b * g.mt + mi;
+          if (grp != gprev) {
+            // reload the resident A tile once the MMAs on the previous one are done
+            if (agen > 0 && !mbar_wait(AOP_EMPTY, (agen - 1) & 1, err, 32)) { ok = false; break; }
+            mbar_expect_tx(AOP_FULL, g.nkb * NS * TILE_BYTES);
+            for (int kb = 0; kb < g.nkb; kb++)
+              for (int p = 0; p < NS; p++)
+                tma_load_3d(sbase + (kb * NS + p) * TILE_BYTES, &maps.a[p], AOP_FULL, kb * BKR, mi * BM, b);
+            gprev = grp;
+            agen++;
+          }
+        }
         const int kb1 = min(g.nkb, (kc + 1) * g.ckb);
         for (int kb = kc * g.ckb; kb < kb1; kb++, it++) {
           const int st = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
           if (!mbar_wait(EMPTY(st), ph ^ 1, err, 2)) { ok = false; break; }
           mbar_expect_tx(FULL(st), STAGE_BYTES);
-          const uint32_t dst = sbase + st * STAGE_BYTES;
-          for (int p = 0; p < NS; p++)
-            tma_load_3d(dst + p * TILE_BYTES, &maps.a[p], FULL(st), kb * BKR, mi * BM, b);
-          for (int p = 0; p < NS; p++)
-            tma_load_3d(dst + (NS + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
+          const uint32_t dst = sbase + A_BYTES + st * STAGE_BYTES;
+          if constexpr (AR) {
+            for (int p = 0; p < NS; p++)
+              tma_load_3d(dst + p * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
+          } else {
+            for (int p = 0; p < NS; p++)
+              tma_load_3d(dst + p * TILE_BYTES, &maps.a[p], FULL(st), kb * BKR, mi * BM, b);
+            for (int p = 0; p < NS; p++)
+              tma_load_3d(dst + (NS + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
+          }
         }
       }
     }
@@ -333,11 +377,22 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(BM, BN);
       const uint64_t dbase = smem_desc(sbase);
-      uint32_t it = 0, local = 0;
+      uint32_t it = 0, local = 0, agen = 0;
+      long gprev = -1;
       bool ok = true;
-      for (long u = blockIdx.x; u < g.units && ok; u += gridDim.x, local++) {
+      for (long u = u_begin; u < u_end && ok; u += u_step, local++) {
         int b, mi, ni, kc;
         decode(u, b, mi, ni, kc);
+        if constexpr (AR) {
+          const long grp = (long)b * g.mt + mi;
+          if (grp != gprev) {
+            if (agen > 0) mma_commit(AOP_EMPTY);      // arrives when the MMAs issued so far are done
+            if (!mbar_wait(AOP_FULL, agen & 1, err, 64)) break;
+            fence_after();
+            gprev = grp;
+            agen++;
+          }
+        }
         const int set = local & 1;
         if (!mbar_wait(AEMPTY(set), ((local >> 1) & 1) ^ 1, err, 4)) break;
         fence_after();
@@ -350,8 +405,10 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
           fence_after();
           // descriptors: one base per stage, planes and K steps are offsets of
           // (bytes >> 4) in the start-address field (no carry: smem < 256 KB)
-          const uint64_t aBase = dbase + ((st * STAGE_BYTES) >> 4);
-          const uint64_t bBase = aBase + ((NS * TILE_BYTES) >> 4);
+          const uint64_t aBase = AR ? dbase + (((uint32_t)kb * NS * TILE_BYTES) >> 4)
+                                    : dbase + ((st * STAGE_BYTES) >> 4);
+          const uint64_t bBase = AR ? dbase + ((A_BYTES + st * STAGE_BYTES) >> 4)
+                                    : aBase + ((NS * TILE_BYTES) >> 4);
           constexpr uint64_t PL = TILE_BYTES >> 4;
 #pragma unroll
           for (int kk = 0; kk < BKR / 16; kk++) {
@@ -380,37 +437,46 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
       }
     }
   } else if (warp >= EPI_WARP0) {
-    // epilogue warps: lane quadrant q, column half h
+    // epilogue warps: lane quadrant q, column quarter h (EPI_COLS columns)
     const int q = warp & 3;
     const int h = (warp - EPI_WARP0) >> 2;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    float* stg = epi_stage + (warp - EPI_WARP0) * EPI_TILE;
     uint32_t local = 0;
-    for (long u = blockIdx.x; u < g.units; u += gridDim.x, local++) {
+    for (long u = u_begin; u < u_end; u += u_step, local++) {
       int b, mi, ni, kc;
       decode(u, b, mi, ni, kc);
+      const int row0 = mi * BM + 32 * q;          // first row of this warp's blocks
+      const int cbase = ni * BN + EPI_COLS * h;   // first column of this warp
+      // exponents before the accumulator is ready: this lane's row, and the
+      // column pairs of the warp's columns (lane l < EPI_COLS / 2 holds pair l)
+      int ea = 0, ebl = 0;
+      if constexpr (OUT != 2) {
+        if (row0 + lane < g.M) ea = row_exp(eA, (long)b * seA + row0 + lane);
+        if (lane < EPI_COLS / 2 && cbase + 2 * lane < g.Nr) ebl = eB[(long)b * seB + (cbase >> 1) + lane];
+      }
       const int set = local & 1;
       if (!mbar_wait_warp(AFULL(set), (local >> 1) & 1, err, 16)) break;
       fence_after();
-      const int row = mi * BM + 32 * q + lane;
-      const int ea = (OUT != 2 && row < g.M) ? row_exp(eA, (long)b * seA + row) : 0;
       const uint32_t accA = tmem + lane_off + 256 * set, accBC = accA + 128;
-      float* stg = epi_stage + (warp - EPI_WARP0) * EPI_TILE;
-      const int row0 = mi * BM + 32 * q;          // first row of this warp's blocks
 #pragma unroll 1
-      for (int qq = 0; qq < 4; qq++) {
+      for (int qq = 0; qq < EPI_COLS / 16; qq++) {
         float va[16], vb[16];
-        tmem_ld16(accA + 64 * h + 16 * qq, va);
-        tmem_ld16(accBC + 64 * h + 16 * qq, vb);
-        const int col0 = ni * BN + 64 * h + 16 * qq;   // even: complex pairs stay together
+        tmem_ld16(accA + EPI_COLS * h + 16 * qq, va);
+        tmem_ld16(accBC + EPI_COLS * h + 16 * qq, vb);
+        const int col0 = cbase + 16 * qq;             // even: complex pairs stay together
         if (col0 >= g.Nr) continue;                   // the whole block is padding (warp-uniform)
         if constexpr (OUT == 1) {
+          int ep[8];   // the block's column-pair exponents, shuffled while all lanes are here
+#pragma unroll
+          for (int j = 0; j < 8; j++) ep[j] = __shfl_sync(0xffffffffu, ebl, 8 * qq + j);
           const int row = row0 + lane;
           if (row >= g.M) continue;
           double* o = (double*)out + (long)b * sbo + (long)row * ldo;
 #pragma unroll
           for (int j = 0; j < 16; j += 2) {
             if (col0 + j >= g.Nr) break;
-            const double sc = pow2d(ea + eB[(long)b * seB + ((col0 + j) >> 1)] - 14);
+            const double sc = pow2d(ea + ep[j >> 1] - 14);
             const double x0 = ((double)__float2int_rn(va[j]) + (double)vb[j]) * sc;
             const double x1 = ((double)__float2int_rn(va[j + 1]) + (double)vb[j + 1]) * sc;
             if (col0 + j + 1 < g.Nr && (ldo % 2) == 0) {
@@ -425,19 +491,16 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
           if constexpr (OUT == 2) {
 #pragma unroll
             for (int j = 0; j < 16; j += 4)
-              *reinterpret_cast<float4*>(stg + lane * EPI_LD + j) =
+              *reinterpret_cast<float4*>(stg + stage_off(lane, j >> 2)) =
                   make_float4(__int_as_float(__float2int_rn(va[j])), __int_as_float(__float2int_rn(va[j + 1])),
                               __int_as_float(__float2int_rn(va[j + 2])), __int_as_float(__float2int_rn(va[j + 3])));
           } else {
-            // column exponents of the block's 8 complex pairs: one load, shuffled
-            const int jp = (col0 >> 1) + (lane & 7);
-            const int ebl = (col0 + 2 * (lane & 7) < g.Nr) ? eB[(long)b * seB + jp] : 0;
 #pragma unroll
             for (int j = 0; j < 16; j += 4) {
-              const float s0 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, j >> 1) - 14);
-              const float s1 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, (j >> 1) + 1) - 14);
+              const float s0 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, 8 * qq + (j >> 1)) - 14);
+              const float s1 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, 8 * qq + (j >> 1) + 1) - 14);
               // va holds an exact integer below 2^24
-              *reinterpret_cast<float4*>(stg + lane * EPI_LD + j) =
+              *reinterpret_cast<float4*>(stg + stage_off(lane, j >> 2)) =
                   make_float4((va[j] + vb[j]) * s0, (va[j + 1] + vb[j + 1]) * s0, (va[j + 2] + vb[j + 2]) * s1,
                               (va[j + 3] + vb[j + 3]) * s1);
             }
@@ -453,7 +516,8 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
               __syncwarp();
 #pragma unroll
               for (int j = 0; j < 16; j += 4)
-                *reinterpret_cast<float4*>(stg + lane * EPI_LD + j) = make_float4(vb[j], vb[j + 1], vb[j + 2], vb[j + 3]);
+                *reinterpret_cast<float4*>(stg + stage_off(lane, j >> 2)) =
+                    make_float4(vb[j], vb[j + 1], vb[j + 2], vb[j + 3]);
               __syncwarp();
             }
 #pragma unroll
@@ -461,7 +525,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
               const int rr = (lane & 7) + 8 * it;
               const int row = row0 + rr;
               if (row >= g.M || col >= g.Nr) continue;
-              const float4 v = *reinterpret_cast<const float4*>(stg + rr * EPI_LD + 4 * f);
+              const float4 v = *reinterpret_cast<const float4*>(stg + stage_off(rr, f));
               float* o;
               if constexpr (OUT == 2) {
                 const long base = (((long)kc * g.batch + b) * g.M + row) * g.Nr;
@@ -615,18 +679,22 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   }
   const unsigned grid = (unsigned)std::min<long>(g.units, nsm);
   cudaError_t e = cudaSuccess;
-#define LAUNCH(OUTK, NSK)                                                                                 \
+#define LAUNCH(OUTK, NSK, ARK)                                                                            \
   {                                                                                                       \
-    e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK, NSK>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+    e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK, NSK, ARK>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)SMEM_BYTES);                                                            \
     if (e != cudaSuccess) return e;                                                                       \
-    tc_gemm_kernel<OUTK, NSK><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, out, ldo,     \
-                                                                 sbo, ps0, pbc, err);                     \
+    tc_gemm_kernel<OUTK, NSK, ARK><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, out,     \
+                                                                      ldo, sbo, ps0, pbc, err);           \
   }
+  // A resident when all K fits the resident tile (one chunk of at most 4 K blocks)
+  const bool ar = slices == 3 && !split && g.nkb <= 4;
   if (slices == 4) {
-    if (split) LAUNCH(2, 4) else if (out_f64) LAUNCH(1, 4) else LAUNCH(0, 4)
+    if (split) LAUNCH(2, 4, false) else if (out_f64) LAUNCH(1, 4, false) else LAUNCH(0, 4, false)
+  } else if (ar) {
+    if (out_f64) LAUNCH(1, 3, true) else LAUNCH(0, 3, true)
   } else {
-    if (split) LAUNCH(2, 3) else if (out_f64) LAUNCH(1, 3) else LAUNCH(0, 3)
+    if (split) LAUNCH(2, 3, false) else if (out_f64) LAUNCH(1, 3, false) else LAUNCH(0, 3, false)
   }
 #undef LAUNCH
   e = cudaGetLastError();
