@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 namespace {
 
@@ -149,58 +150,77 @@ __global__ void embed_kernel(const CT* __restrict__ src, long sbs, long ldk, lon
 }
 
 // Slices of the contiguous rows src[row][0..np) with the exact row exponent,
-// one warp per row: the warp first reduces max(|re|, |im|) over its row, then
-// reads the row again (from cache) and writes the four planes.  V = 2: two
-// consecutive complex values per lane access (16-byte loads, np even).
-template <int V>
+// one warp per row: the warp reduces max(|re|, |im|) over its row, then
+// writes the four planes.  V = 2: two consecutive complex values per lane
+// access (16-byte loads, np even).  R > 0: the row stays in registers (R
+// accesses per lane, np / V <= 32 R; used for short rows); R = 0: the row is
+// read twice, the second time mostly from cache (long rows: holding a row of
+// 1200 complex values in registers costs more residency than the re-read).
+template <int V, int R>
 __global__ void slice_rowmax_kernel(const float2* __restrict__ src, int np, long rows, int* __restrict__ e,
                                     uint16_t* planes, long plane, int ldp) {
+  typedef typename std::conditional<V == 2, float4, float2>::type VT;
   const long w0 = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long nw = ((long)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int per = np / V;
-  for (long row = w0; row < rows; row += nw) {
-    const float2* r = src + row * np;
-    float m = 0.f;
-    for (int c = lane; c < per; c += 32) {
+  auto amax = [](VT w) {
+    if constexpr (V == 2) return fmaxf(fmaxf(fabsf(w.x), fabsf(w.y)), fmaxf(fabsf(w.z), fabsf(w.w)));
+    else return fmaxf(fabsf(w.x), fabsf(w.y));
+  };
+  auto put = [&](long row, int c, VT w, int ex) {
+    float2 v[V];
+    if constexpr (V == 2) {
+      v[0] = make_float2(w.x, w.y);
+      v[1] = make_float2(w.z, w.w);
+    } else {
+      v[0] = w;
+    }
+    uint16_t sl[V][2][4];
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+      slice4(v[j].x, ex, sl[j][0]);
+      slice4(v[j].y, ex, sl[j][1]);
+    }
+    const long off = row * ldp + 2L * c * V;
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
       if constexpr (V == 2) {
-        const float4 w = *reinterpret_cast<const float4*>(r + 2 * c);
-        m = fmaxf(m, fmaxf(fmaxf(fabsf(w.x), fabsf(w.y)), fmaxf(fabsf(w.z), fabsf(w.w))));
+        *reinterpret_cast<uint2*>(planes + p * plane + off) =
+            make_uint2((uint32_t)sl[0][0][p] | ((uint32_t)sl[0][1][p] << 16),
+                       (uint32_t)sl[1][0][p] | ((uint32_t)sl[1][1][p] << 16));
       } else {
-        const float2 w = r[c];
-        m = fmaxf(m, fmaxf(fabsf(w.x), fabsf(w.y)));
+        *reinterpret_cast<uint32_t*>(planes + p * plane + off) = (uint32_t)sl[0][0][p] | ((uint32_t)sl[0][1][p] << 16);
       }
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const int ex = row_exponent((double)m);
-    if (lane == 0) e[row] = ex;
-    for (int c = lane; c < per; c += 32) {
-      float2 v[V];
-      if constexpr (V == 2) {
-        const float4 w = __ldcs(reinterpret_cast<const float4*>(r + 2 * c));
-        v[0] = make_float2(w.x, w.y);
-        v[1] = make_float2(w.z, w.w);
-      } else {
-        v[0] = __ldcs(r + c);
-      }
-      uint16_t sl[V][2][4];
+  };
+  for (long row = w0; row < rows; row += nw) {
+    const VT* r = reinterpret_cast<const VT*>(src + row * np);
+    float m = 0.f;
+    if constexpr (R > 0) {
+      VT buf[R];
 #pragma unroll
-      for (int j = 0; j < V; j++) {
-        slice4(v[j].x, ex, sl[j][0]);
-        slice4(v[j].y, ex, sl[j][1]);
-      }
-      const long off = row * ldp + 2L * c * V;
-#pragma unroll
-      for (int p = 0; p < 4; p++) {
-        if constexpr (V == 2) {
-          *reinterpret_cast<uint2*>(planes + p * plane + off) =
-              make_uint2((uint32_t)sl[0][0][p] | ((uint32_t)sl[0][1][p] << 16),
-                         (uint32_t)sl[1][0][p] | ((uint32_t)sl[1][1][p] << 16));
-        } else {
-          *reinterpret_cast<uint32_t*>(planes + p * plane + off) =
-              (uint32_t)sl[0][0][p] | ((uint32_t)sl[0][1][p] << 16);
+      for (int t = 0; t < R; t++) {
+        const int c = lane + 32 * t;
+        if (c < per) {
+          buf[t] = __ldcs(r + c);
+          m = fmaxf(m, amax(buf[t]));
         }
       }
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      const int ex = row_exponent((double)m);
+      if (lane == 0) e[row] = ex;
+#pragma unroll
+      for (int t = 0; t < R; t++) {
+        const int c = lane + 32 * t;
+        if (c < per) put(row, c, buf[t], ex);
+      }
+    } else {
+      for (int c = lane; c < per; c += 32) m = fmaxf(m, amax(r[c]));
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      const int ex = row_exponent((double)m);
+      if (lane == 0) e[row] = ex;
+      for (int c = lane; c < per; c += 32) put(row, c, __ldcs(r + c), ex);
     }
   }
 }
@@ -264,12 +284,17 @@ cudaError_t slice_cols_z(const double2* src, long sbs, int lds, int batch, int r
 
 cudaError_t slice_rows_exact(const float2* src, int np, long rows, int* e, uint16_t* planes, long plane, int ldp,
                              cudaStream_t s) {
-  const long nb = std::min<long>((rows + 7) / 8, 152L * 64);
+  const long nb = std::min<long>((rows + 3) / 4, 152L * 128);   // 4 warps (rows) per block
   // 16-byte loads and 8-byte plane stores need even rows and 8-byte aligned plane rows
-  if (np % 2 == 0 && ldp % 4 == 0 && ((uintptr_t)src & 15) == 0)
-    slice_rowmax_kernel<2><<<(unsigned)nb, 256, 0, s>>>(src, np, rows, e, planes, plane, ldp);
-  else
-    slice_rowmax_kernel<1><<<(unsigned)nb, 256, 0, s>>>(src, np, rows, e, planes, plane, ldp);
+  const bool v2 = np % 2 == 0 && ldp % 4 == 0 && ((uintptr_t)src & 15) == 0;
+  const int per = v2 ? np / 2 : np;   // lane accesses of a row
+#define SR(V_, R_) slice_rowmax_kernel<V_, R_><<<(unsigned)nb, 128, 0, s>>>(src, np, rows, e, planes, plane, ldp)
+  if (v2) {
+    if (per <= 32) SR(2, 1); else if (per <= 128) SR(2, 4); else SR(2, 0);
+  } else {
+    if (per <= 32) SR(1, 1); else if (per <= 128) SR(1, 4); else SR(1, 0);
+  }
+#undef SR
   return cudaGetLastError();
 }
 
