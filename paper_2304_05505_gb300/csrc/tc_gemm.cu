@@ -53,6 +53,7 @@
 // sets the error word, stops issuing work and the CTA releases TMEM and exits.
 #include "thc_internal.cuh"
 #include "tc_gemm.cuh"
+#include "slices.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -80,11 +81,18 @@ template <int NS> struct Ring {
 constexpr uint32_t RING_BYTES = 3 * 2 * 4 * TILE_BYTES;     // 192 KB either way
 static_assert(Ring<4>::STAGES * Ring<4>::STAGE_BYTES == RING_BYTES, "ring size");
 static_assert(Ring<3>::STAGES * Ring<3>::STAGE_BYTES == RING_BYTES, "ring size");
-constexpr int EPI_WARP0 = 4;
-constexpr int NTHREADS = (EPI_WARP0 + EPI_WARPS) * 32;
 constexpr uint32_t EPI_TILE = 32 * 16;                       // floats per epilogue warp (32 rows x 16)
-constexpr int EPI_COLS = 4 * BN / EPI_WARPS;                 // columns of a unit per epilogue warp
 constexpr size_t SMEM_BYTES = RING_BYTES + 1024 + 256 + EPI_WARPS * EPI_TILE * 4;
+// Warp roles: 0 TMA, 1 MMA, then (CV) 8 converter warps, then the epilogue.
+// The converted-A form has the longer K per unit and takes 8 epilogue warps;
+// the others take 16.
+template <bool CV> struct Roles {
+  static constexpr int CONV_WARPS = CV ? 8 : 0;                 // warps 2 .. 2 + CONV_WARPS - 1
+  static constexpr int EPI = CV ? 8 : EPI_WARPS;                // epilogue warps
+  static constexpr int EPI0 = CV ? 2 + CONV_WARPS : 4;          // first epilogue warp
+  static constexpr int NT = (EPI0 + EPI) * 32;                  // threads
+  static constexpr int COLS = 4 * BN / EPI;                     // columns of a unit per epilogue warp
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -235,6 +243,19 @@ __device__ __forceinline__ double pow2d(int e) {
   return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
 
+// The four fixed-point slices of y = 2^(7 - e) x (|y| <= 128) as bf16 bit
+// patterns: each slice is an integer of at most 8 significant bits times
+// 2^-8p, exact in bf16, so its bf16 bits are the top half of its FP32 bits.
+__device__ __forceinline__ void slice4_bits(float y, uint32_t* bits) {
+  const float inv[4] = {1.0f, 0x1p-8f, 0x1p-16f, 0x1p-24f};
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    const float sp = rintf(y);
+    bits[p] = __float_as_uint(sp * inv[p]) >> 16;
+    y = (y - sp) * 256.0f;
+  }
+}
+
 struct Geometry {
   int M, Nr, Kr, batch;
   int mt, nt, nchunk, nkb;   // tiles along M and N, K chunks, K blocks
@@ -254,17 +275,30 @@ __device__ __forceinline__ int row_exp(const int* e, long i) {
 // N tiles of one (batch, M tile) one after another; only B streams through a
 // 4-stage ring of 24 KB.  Each CTA takes a contiguous range of units so that
 // consecutive units share their A tile.
-template <int OUT, int NS, bool AR>
-__global__ void __launch_bounds__(NTHREADS, 1)
+// CV (A converted in shared memory): A is an FP32 (interleaved complex)
+// matrix.  TMA brings 128 x 32 FP32 tiles into a 3-stage staging ring
+// (128B swizzle); warps 2-3 cut each tile into the four bf16 slices with the
+// rows' exponents and write them in the 64B-swizzled K-major layout the MMA
+// reads, then fence the generic-proxy writes for the async proxy and arrive
+// on the stage's full barrier beside the TMA bytes of the B planes.  No slice
+// planes of A ever go through HBM.
+template <int OUT, int NS, bool AR, bool CV>
+__global__ void __launch_bounds__(Roles<CV>::NT, 1)
 tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restrict__ eA, long seA,
                const int* __restrict__ eB, long seB, void* out, long ldo, long sbo, int* __restrict__ ps0,
                float* __restrict__ pbc, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   static_assert(!AR || NS == 3, "A-resident mode uses three slices");
+  static_assert(!CV || (NS == 4 && !AR), "converted A uses four slices");
   constexpr int AKB = 4;                                           // K blocks the resident A tile holds
-  constexpr int STAGES = AR ? 4 : Ring<NS>::STAGES;
-  constexpr uint32_t A_BYTES = AR ? AKB * NS * TILE_BYTES : 0;     // resident A region (offset 0)
+  constexpr int SA_STAGES = 3;                                     // FP32 staging ring of CV
+  constexpr uint32_t SA_BYTES = BM * BKR * 4;                      // 16 KB
+  constexpr int CONV_WARPS = Roles<CV>::CONV_WARPS;
+  constexpr int EPI_W = Roles<CV>::EPI, EPI_W0 = Roles<CV>::EPI0, EPI_COLS = Roles<CV>::COLS;
+  constexpr int STAGES = AR ? 4 : CV ? 2 : Ring<NS>::STAGES;
+  // what precedes the plane ring: the resident A tile, or the FP32 staging ring
+  constexpr uint32_t A_BYTES = AR ? AKB * NS * TILE_BYTES : CV ? SA_STAGES * SA_BYTES : 0;
   constexpr uint32_t STAGE_BYTES = AR ? NS * TILE_BYTES : Ring<NS>::STAGE_BYTES;
   static_assert(A_BYTES + STAGES * STAGE_BYTES <= RING_BYTES, "ring size");
   uint64_t* bars = (uint64_t*)(smem + RING_BYTES);
@@ -279,6 +313,9 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
   auto AEMPTY = [&](int s) { return bar0 + 8u * (2 * STAGES + 2 + s); };
   const uint32_t AOP_FULL = bar0 + 8u * (2 * STAGES + 4);    // resident A tile loaded
   const uint32_t AOP_EMPTY = bar0 + 8u * (2 * STAGES + 5);   // MMAs on the resident A tile done
+  auto SFULL = [&](int s) { return bar0 + 8u * (2 * STAGES + 6 + s); };    // CV: FP32 tile landed
+  auto SEMPTY = [&](int s) { return bar0 + 8u * (2 * STAGES + 9 + s); };   // CV: FP32 tile converted
+  static_assert(!CV || 2 * STAGES + 9 + SA_STAGES <= 16, "barrier slots");
 
   __shared__ int abort_flag;
   if (threadIdx.x == 0) abort_flag = *(volatile int*)err;
@@ -289,12 +326,18 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
-      mbar_init(FULL(s), 1);
+      mbar_init(FULL(s), CV ? 1 + CONV_WARPS : 1);   // CV: B bytes + the converter warps
       mbar_init(EMPTY(s), 1);
+    }
+    if (CV) {
+      for (int s = 0; s < SA_STAGES; s++) {
+        mbar_init(SFULL(s), 1);
+        mbar_init(SEMPTY(s), CONV_WARPS);
+      }
     }
     for (int s = 0; s < 2; s++) {
       mbar_init(AFULL(s), 1);
-      mbar_init(AEMPTY(s), EPI_WARPS);
+      mbar_init(AEMPTY(s), EPI_W);
     }
     if (AR) {
       mbar_init(AOP_FULL, 1);
@@ -358,6 +401,19 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
         for (int kb = kc * g.ckb; kb < kb1; kb++, it++) {
           const int st = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
+          if constexpr (CV) {
+            // the FP32 A tile into the staging ring, the B planes into the plane ring
+            const int sa = it % SA_STAGES;
+            if (!mbar_wait(SEMPTY(sa), ((it / SA_STAGES) & 1) ^ 1, err, 2)) { ok = false; break; }
+            mbar_expect_tx(SFULL(sa), SA_BYTES);
+            tma_load_3d(sbase + sa * SA_BYTES, &maps.a[0], SFULL(sa), kb * BKR, mi * BM, b);
+            if (!mbar_wait(EMPTY(st), ph ^ 1, err, 2)) { ok = false; break; }
+            mbar_expect_tx(FULL(st), NS * TILE_BYTES);
+            const uint32_t dst = sbase + A_BYTES + st * STAGE_BYTES;
+            for (int p = 0; p < NS; p++)
+              tma_load_3d(dst + (NS + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
+            continue;
+          }
           if (!mbar_wait(EMPTY(st), ph ^ 1, err, 2)) { ok = false; break; }
           mbar_expect_tx(FULL(st), STAGE_BYTES);
           const uint32_t dst = sbase + A_BYTES + st * STAGE_BYTES;
@@ -406,7 +462,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
           // descriptors: one base per stage, planes and K steps are offsets of
           // (bytes >> 4) in the start-address field (no carry: smem < 256 KB)
           const uint64_t aBase = AR ? dbase + (((uint32_t)kb * NS * TILE_BYTES) >> 4)
-                                    : dbase + ((st * STAGE_BYTES) >> 4);
+                                    : dbase + ((A_BYTES + st * STAGE_BYTES) >> 4);
           const uint64_t bBase = AR ? dbase + ((A_BYTES + st * STAGE_BYTES) >> 4)
                                     : aBase + ((NS * TILE_BYTES) >> 4);
           constexpr uint64_t PL = TILE_BYTES >> 4;
@@ -436,12 +492,63 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
         mma_commit(AFULL(set));
       }
     }
-  } else if (warp >= EPI_WARP0) {
-    // epilogue warps: lane quadrant q, column quarter h (EPI_COLS columns)
+  } else if (CV && warp >= 2 && warp < 2 + CONV_WARPS) {
+    // converter warps: thread t converts half a row (16 reals) of each tile:
+    // row t / 2, plane chunks 2 (t & 1) and 2 (t & 1) + 1
+    const int t = (warp - 2) * 32 + lane;
+    const int r = t >> 1, hf = t & 1;
+    uint32_t it = 0;
+    bool ok = true;
+    for (long u = u_begin; u < u_end && ok; u += u_step) {
+      int b, mi, ni, kc;
+      decode(u, b, mi, ni, kc);
+      const int row = mi * BM + r;
+      // 2^(7 - e): the row's scale, exact (e of a normal FP32 row maximum)
+      const float sc = pow2f(7 - (row < g.M ? row_exp(eA, (long)b * seA + row) : 0));
+      const int kb1 = min(g.nkb, (kc + 1) * g.ckb);
+      for (int kb = kc * g.ckb; kb < kb1; kb++, it++) {
+        const int sa = it % SA_STAGES, st = it % STAGES;
+        if (!mbar_wait(SFULL(sa), (it / SA_STAGES) & 1, err, 128)) { ok = false; break; }
+        if (!mbar_wait(EMPTY(st), ((it / STAGES) & 1) ^ 1, err, 256)) { ok = false; break; }
+        const unsigned char* src = smem + sa * SA_BYTES;
+        unsigned char* dstp = smem + A_BYTES + st * STAGE_BYTES;
+#pragma unroll
+        for (int k2 = 0; k2 < 2; k2++) {
+          const int pc = 2 * hf + k2;               // 8 reals = one 16-byte chunk of each plane
+          // FP32 row r, 128B swizzle: 16-byte chunk c at r * 128 + 16 (c ^ (r & 7))
+          const float4 f0 = *reinterpret_cast<const float4*>(src + r * 128 + 16 * ((2 * pc) ^ (r & 7)));
+          const float4 f1 = *reinterpret_cast<const float4*>(src + r * 128 + 16 * ((2 * pc + 1) ^ (r & 7)));
+          const float x[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+          uint32_t w[4][4];   // [plane][pair of reals]
+#pragma unroll
+          for (int j = 0; j < 8; j += 2) {
+            uint32_t lo[4], hi[4];
+            slice4_bits(x[j] * sc, lo);
+            slice4_bits(x[j + 1] * sc, hi);
+#pragma unroll
+            for (int p = 0; p < 4; p++) w[p][j >> 1] = lo[p] | (hi[p] << 16);
+          }
+          // bf16 row r of each plane, 64B swizzle: chunk pc at r * 64 + 16 (pc ^ ((r >> 1) & 3))
+          const uint32_t off = r * 64 + 16 * (pc ^ ((r >> 1) & 3));
+#pragma unroll
+          for (int p = 0; p < 4; p++)
+            *reinterpret_cast<uint4*>(dstp + p * TILE_BYTES + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+        }
+        // the planes were written by the generic proxy; the MMA reads them through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(SEMPTY(sa));
+          mbar_arrive(FULL(st));
+        }
+      }
+    }
+  } else if (warp >= EPI_W0) {
+    // epilogue warps: lane quadrant q, column part h (EPI_COLS columns)
     const int q = warp & 3;
-    const int h = (warp - EPI_WARP0) >> 2;
+    const int h = (warp - EPI_W0) >> 2;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    float* stg = epi_stage + (warp - EPI_WARP0) * EPI_TILE;
+    float* stg = epi_stage + (warp - EPI_W0) * EPI_TILE;
     uint32_t local = 0;
     for (long u = u_begin; u < u_end; u += u_step, local++) {
       int b, mi, ni, kc;
@@ -642,6 +749,20 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t make_f32_map(void* map_out, const void* base, int batch, int rows, int cols, int ld) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  if (((uintptr_t)base & 15) || (ld * 4) % 16) return cudaErrorInvalidValue;
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)ld * 4 * rows};
+  cuuint32_t box[3] = {BKR, 128, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 long tc_partial_elems(int M, int Nr, int Kr, int batch, int chunk_k) {
   const int ckb = std::max(1, std::min(MAX_CHUNK_KB, chunk_k / BKR));
   const int nkb = (Kr + BKR - 1) / BKR;
@@ -652,7 +773,7 @@ long tc_partial_elems(int M, int Nr, int Kr, int batch, int chunk_k) {
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s, int chunk_k,
-                    cudaEvent_t gemm_done, int slices) {
+                    cudaEvent_t gemm_done, int slices, bool a_f32) {
   if (slices != 3 && slices != 4) return cudaErrorInvalidValue;
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   Maps maps;
@@ -679,17 +800,21 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   }
   const unsigned grid = (unsigned)std::min<long>(g.units, nsm);
   cudaError_t e = cudaSuccess;
-#define LAUNCH(OUTK, NSK, ARK)                                                                            \
+#define LAUNCH4(OUTK, NSK, ARK, CVK)                                                                      \
   {                                                                                                       \
-    e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK, NSK, ARK>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)SMEM_BYTES);                                                            \
+    e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK, NSK, ARK, CVK>,                                         \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);               \
     if (e != cudaSuccess) return e;                                                                       \
-    tc_gemm_kernel<OUTK, NSK, ARK><<<grid, NTHREADS, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, out,     \
-                                                                      ldo, sbo, ps0, pbc, err);           \
+    tc_gemm_kernel<OUTK, NSK, ARK, CVK><<<grid, Roles<CVK>::NT, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, \
+                                                                           out, ldo, sbo, ps0, pbc, err); \
   }
+#define LAUNCH(OUTK, NSK, ARK) LAUNCH4(OUTK, NSK, ARK, false)
   // A resident when all K fits the resident tile (one chunk of at most 4 K blocks)
   const bool ar = slices == 3 && !split && g.nkb <= 4;
-  if (slices == 4) {
+  if (a_f32) {
+    if (slices != 4) return cudaErrorInvalidValue;
+    if (split) LAUNCH4(2, 4, false, true) else if (out_f64) LAUNCH4(1, 4, false, true) else LAUNCH4(0, 4, false, true)
+  } else if (slices == 4) {
     if (split) LAUNCH(2, 4, false) else if (out_f64) LAUNCH(1, 4, false) else LAUNCH(0, 4, false)
   } else if (ar) {
     if (out_f64) LAUNCH(1, 3, true) else LAUNCH(0, 3, true)
@@ -697,6 +822,7 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
     if (split) LAUNCH(2, 3, false) else if (out_f64) LAUNCH(1, 3, false) else LAUNCH(0, 3, false)
   }
 #undef LAUNCH
+#undef LAUNCH4
   e = cudaGetLastError();
   if (e == cudaSuccess && gemm_done) e = cudaEventRecord(gemm_done, s);
   if (e != cudaSuccess || !split) return e;

@@ -25,11 +25,17 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
 // gemm_done (may be null) is recorded on `s` right after the GEMM kernel,
 // before any combine kernel, so that the GEMM alone can be timed.  slices: 4
 // (all four planes, 10 slice products) or 3 (the first three planes, the 6
-// products s + t <= 2: about 2^-24 of the row scales).
+// products s + t <= 2: about 2^-24 of the row scales).  a_f32: A.map[0] is an
+// FP32 map (make_f32_map) of the interleaved complex A, cut into its four
+// slices inside the kernel with the row exponents eA.
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s, int chunk_k,
-                    cudaEvent_t gemm_done = nullptr, int slices = 4);
+                    cudaEvent_t gemm_done = nullptr, int slices = 4, bool a_f32 = false);
+
+// Map of an FP32 matrix [batch][rows][ld floats] (cols valid) in 32-float K
+// boxes of 128 rows with 128B swizzle (ld * 4 bytes a multiple of 16).
+cudaError_t make_f32_map(void* map_out, const void* base, int batch, int rows, int cols, int ld);
 
 // Elements of each split-K partial buffer tc_gemm needs for this shape (0 if none).
 long tc_partial_elems(int M, int Nr, int Kr, int batch, int chunk_k);
@@ -57,6 +63,9 @@ cudaError_t slice_rows_c(const float2* src, long sbs, int lds, int batch, int ro
 // exponents to e[row].
 cudaError_t slice_rows_exact(const float2* src, int np, long rows, int* e, uint16_t* planes, long plane, int ldp,
                              cudaStream_t s);
+// Exponents alone of the contiguous rows src[row][0..np): one warp per row,
+// 16-byte loads when np is even.
+cudaError_t row_exponents_rows(const float2* src, int np, long rows, int* e, cudaStream_t s);
 // Transposed: planes[p][b][c][2r + d] of src[b][r][c] with column exponents e[b][c].
 cudaError_t slice_cols_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
                          uint16_t* planes, long plane, int ldp, cudaStream_t s);

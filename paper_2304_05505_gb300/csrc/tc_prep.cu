@@ -156,7 +156,7 @@ __global__ void embed_kernel(const CT* __restrict__ src, long sbs, long ldk, lon
 // accesses per lane, np / V <= 32 R; used for short rows); R = 0: the row is
 // read twice, the second time mostly from cache (long rows: holding a row of
 // 1200 complex values in registers costs more residency than the re-read).
-template <int V, int R>
+template <int V, int R, bool PLANES = true>
 __global__ void slice_rowmax_kernel(const float2* __restrict__ src, int np, long rows, int* __restrict__ e,
                                     uint16_t* planes, long plane, int ldp) {
   typedef typename std::conditional<V == 2, float4, float2>::type VT;
@@ -216,11 +216,13 @@ __global__ void slice_rowmax_kernel(const float2* __restrict__ src, int np, long
         if (c < per) put(row, c, buf[t], ex);
       }
     } else {
-      for (int c = lane; c < per; c += 32) m = fmaxf(m, amax(r[c]));
+#pragma unroll 4
+      for (int c = lane; c < per; c += 32) m = fmaxf(m, amax(PLANES ? r[c] : __ldcs(r + c)));
       for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
       const int ex = row_exponent((double)m);
       if (lane == 0) e[row] = ex;
-      for (int c = lane; c < per; c += 32) put(row, c, __ldcs(r + c), ex);
+      if constexpr (PLANES)
+        for (int c = lane; c < per; c += 32) put(row, c, __ldcs(r + c), ex);
     }
   }
 }
@@ -295,6 +297,15 @@ cudaError_t slice_rows_exact(const float2* src, int np, long rows, int* e, uint1
     if (per <= 32) SR(1, 1); else if (per <= 128) SR(1, 4); else SR(1, 0);
   }
 #undef SR
+  return cudaGetLastError();
+}
+
+cudaError_t row_exponents_rows(const float2* src, int np, long rows, int* e, cudaStream_t s) {
+  const long nb = std::min<long>((rows + 3) / 4, 152L * 128);   // 4 warps (rows) per block
+  if (np % 2 == 0 && ((uintptr_t)src & 15) == 0)
+    slice_rowmax_kernel<2, 0, false><<<(unsigned)nb, 128, 0, s>>>(src, np, rows, e, nullptr, 0, 0);
+  else
+    slice_rowmax_kernel<1, 0, false><<<(unsigned)nb, 128, 0, s>>>(src, np, rows, e, nullptr, 0, 0);
   return cudaGetLastError();
 }
 

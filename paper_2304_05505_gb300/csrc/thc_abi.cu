@@ -67,7 +67,7 @@ Sizes sizes_of(const thc_dims* d, int precision) {
   s.plBc = s.nk * 2 * d->nocc * s.ldXT;
   s.plBd = s.nk * 2L * d->nisdf * s.ldPs;
   s.plBy = s.nk * 2 * d->nocc * (long)s.ldM;
-  s.plM = s.nk * d->nisdf * (long)s.ldM;
+  s.plM = (d->nisdf % 2) ? s.nk * d->nisdf * (long)s.ldM : 0;   // M's slices only for odd N_P
   s.nexp = s.nk * (d->nbas + 3L * d->nisdf + 2L * d->nocc);
   s.npart = std::max({tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nbas, (int)s.nk, kChunkLong),
                       tc_partial_elems(d->nisdf, 2 * d->nisdf, 2 * d->nocc, (int)s.nk, kChunkShort),
@@ -98,7 +98,7 @@ size_t memory_bytes(const thc_dims* d, int precision) {
   b += 2 * s.psi * s.el;         // Psi, Y
   b += 2 * s.v * s.el;           // D, M
   if (precision == THC_MIXED) {
-    b += 4 * 2 * (s.plXn + s.plXT + s.plPs + s.plBc + s.plBd + s.plBy + s.plM);   // bf16 slices (M too)
+    b += 4 * 2 * (s.plXn + s.plXT + s.plPs + s.plBc + s.plBd + s.plBy + s.plM);   // bf16 slices
     b += sizeof(int) * s.nexp + 64;                                         // exponents, error word
     b += (sizeof(int) + sizeof(float)) * s.npart;                           // split-K partial sums
   } else {
@@ -192,7 +192,7 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
   } else {
     W((void**)&c->Vh32, s.v * s.el);
     W(&c->M, s.v * s.el);
-    W((void**)&c->M_pl, 4 * 2 * s.plM);
+    if (s.plM) W((void**)&c->M_pl, 4 * 2 * s.plM);
     W((void**)&c->Xn_pl, 4 * 2 * s.plXn);
     W((void**)&c->XT_pl, 4 * 2 * s.plXT);
     W((void**)&c->PsiA_pl, 4 * 2 * s.plPs);
@@ -247,7 +247,6 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
         {&c->opBc, c->Bc_pl, s.plBc, 2 * n, 2 * N, s.ldXT},
         {&c->opBd, c->Bd_pl, s.plBd, 2 * P, 2 * n, s.ldPs},
         {&c->opBy, c->By_pl, s.plBy, 2 * n, 2 * P, s.ldM},
-        {&c->opM, c->M_pl, s.plM, P, 2 * P, s.ldM},
     };
     for (auto& r : reqs)
       for (int p = 0; p < 4; p++) {
@@ -259,6 +258,17 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
           return e == cudaErrorNotSupported ? THC_ERR_UNSUPPORTED : THC_ERR_CUDA;
         }
       }
+    if (s.plM)
+      for (int p = 0; p < 4 && e == cudaSuccess; p++)
+        e = make_plane_map(c->opM.map[p], c->M_pl + p * s.plM, nk, P, 2 * P, s.ldM);
+    else
+      e = make_f32_map(c->opMf.map[0], c->M, nk, P, 2 * P, 2 * P);
+    if (e != cudaSuccess) {
+      g_create_error = std::string("cuTensorMapEncodeTiled: ") + cudaGetErrorString(e);
+      free_all(c);
+      delete c;
+      return e == cudaErrorNotSupported ? THC_ERR_UNSUPPORTED : THC_ERR_CUDA;
+    }
   }
   for (int i = 0; i < 7; i++) {
     e = cudaEventCreate(&c->ev[i]);
@@ -443,14 +453,20 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, kconv_c(D, c->Vh32, M, PP, c->n1, c->n2, c->n3, s));
   CKC(c, record_core(c, 2, 1, s));
   CKC(c, mark(c, 3, s, false));
-  // S4a Y = M Psi on tensor cores: A = M's fixed-point slices with the exact
-  // row exponents, B = embedded Psi with one exponent per orbital
-  CKC(c, slice_rows_exact(M, P, (long)nk * P, c->eM, c->M_pl, c->plM, c->ldM, s));
+  // S4a Y = M Psi on tensor cores: A = M in FP32, cut into its slices inside
+  // the GEMM with the exact row exponents of M; B = embedded Psi with one
+  // exponent per orbital
+  // (odd N_P: M's slices go through HBM, written by the warp-per-row kernel)
+  const bool a_f32 = c->plM == 0;
+  if (a_f32)
+    CKC(c, row_exponents_rows(M, P, (long)nk * P, c->eM, s));
+  else
+    CKC(c, slice_rows_exact(M, P, (long)nk * P, c->eM, c->M_pl, c->plM, c->ldM, s));
   CKC(c, col_exponents_c(Psi, Pn, n, nk, P, n, c->eY, s));
   CKC(c, embed_b(Psi, false, Pn, n, 1, false, false, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
   CKC(c, record_core(c, 3, 0, s));
-  CKC(c, tc_gemm(c->opM, c->opBy, P, 2 * n, 2 * P, nk, c->eM, P, c->eY, n, Y, false, 2 * n, 2 * Pn,
-                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong, core_event(c, 3, 1)));
+  CKC(c, tc_gemm(a_f32 ? c->opMf : c->opM, c->opBy, P, 2 * n, 2 * P, nk, c->eM, P, c->eY, n, Y, false, 2 * n,
+                 2 * Pn, c->part_s0, c->part_bc, c->tc_err, s, kChunkLong, core_event(c, 3, 1), 4, a_f32));
   CKC(c, mark(c, 4, s, false));
   // S4b KC = conj(X) Y on tensor cores: B = embedded Y (conj-A form)
   CKC(c, col_exponents_c(Y, Pn, n, nk, P, n, c->eY, s));

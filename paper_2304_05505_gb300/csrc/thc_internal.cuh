@@ -73,14 +73,18 @@ struct thc_ctx {
   uint16_t* Bd_pl;    // [nk][2 nisdf][ldPs] embedded Psi^H, B of S2 (ePsi)
   uint16_t* By_pl;    // [nk][2 nocc][ldM]   embedded Psi, B of S4a, then embedded Y, B of S4b
                       //                     (column exponents of Psi, then of Y, in eY [nk][nocc])
-  uint16_t* M_pl;     // [nk][nisdf][ldM]    M, A of S4a                  eM [nk][nisdf]
+                      // M (FP32 workspace) is A of S4a, sliced inside the GEMM   eM [nk][nisdf]
+  uint16_t* M_pl;     // [nk][nisdf][ldM] M's slices, only for odd nisdf (FP32 rows of 8 nisdf
+                      // bytes are not 16-byte strided, which the FP32 tensor map needs)
   int* ex_pl;         // eXn | eXT | ePsi | eC | eY
   int* part_s0;       // split-K partial sums of the tensor-core GEMMs (exact leading class)
   float* part_bc;     // and their FP32 remainders
   int *eXn, *eXT, *ePsi, *eC, *eY, *eM;
   long plXn, plXT, plPs, plBc, plBd, plBy, plM;
   int ldXT, ldM, ldPs;
-  TcOperand opXT, opPs, opXn, opBc, opBd, opBy, opM;
+  TcOperand opXT, opPs, opXn, opBc, opBd, opBy;
+  TcOperand opMf;     // map[0]: FP32 map of M (A of S4a, converted in the GEMM), even nisdf
+  TcOperand opM;      // M's slices, odd nisdf
   int* tc_err;        // device word: nonzero after a device wait gave up
   cudaEvent_t ev[7];               // stage boundaries of the last build
   std::vector<cudaEvent_t> prof;   // per profiled build: 7 stage boundaries, then the

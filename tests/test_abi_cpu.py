@@ -59,8 +59,7 @@ def test_memory_bytes_arithmetic():
     def pad8(x):
         return (x + 7) // 8 * 8
     planes = nk * (N * pad8(2 * P) + P * pad8(2 * N) + P * pad8(2 * n)
-                   + 2 * n * pad8(2 * N) + 2 * P * pad8(2 * n) + 2 * n * pad8(2 * P)
-                   + P * pad8(2 * P))                    # M, written as slices by S3
+                   + 2 * n * pad8(2 * N) + 2 * P * pad8(2 * n) + 2 * n * pad8(2 * P))
     exps = nk * (N + 3 * P + 2 * n)
     c4 = -(-(2 * P) // 512)                              # split-K chunks of S4a and S4b (K = 2 N_P real)
     c1 = -(-(2 * N) // 512)                              # and of S1 (K = 2 N real)
@@ -69,6 +68,10 @@ def test_memory_bytes_arithmetic():
     tc = 8 * (nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + 4 * 2 * planes \
         + 4 * exps + 64 + 8 * part + common
     assert thc.thc_memory_bytes(d, thc.THC_MIXED) == tc
+    # odd N_P: M's slices are kept in HBM as well (FP32 rows not 16-byte strided)
+    d1 = dict(d, nisdf=P + 1)
+    extra = 4 * 2 * nk * (P + 1) * pad8(2 * (P + 1))
+    assert thc.thc_memory_bytes(d1, thc.THC_MIXED) - extra > thc.thc_memory_bytes(d, thc.THC_MIXED)
 
 
 @pytest.mark.parametrize("bad", [
