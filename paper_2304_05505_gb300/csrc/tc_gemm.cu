@@ -26,8 +26,8 @@
 // six classes s + t <= 2.
 //
 // Work units: a 128 x 128 output tile and a chunk of at most 1024 real K (so
-// the leading sum of a unit is exact; shorter chunks also shorten the FP32
-// sums of the other classes).  When K needs more than one chunk the
+// the leading sum of a unit is exact), the chunks of one product of equal
+// length (tc_chunk_blocks).  When K needs more than one chunk the
 // units write their exact int32 leading sums and FP32 remainders to a partial
 // buffer and tc_combine adds the chunks (split K); otherwise they write the
 // scaled result directly.
@@ -763,16 +763,26 @@ cudaError_t make_f32_map(void* map_out, const void* base, int batch, int rows, i
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-long tc_partial_elems(int M, int Nr, int Kr, int batch, int chunk_k) {
-  const int ckb = std::max(1, std::min(MAX_CHUNK_KB, chunk_k / BKR));
+int tc_chunk_blocks(int M, int Nr, int Kr, int batch) {
+  const int nkb = std::max(1, (Kr + BKR - 1) / BKR);
+  int nchunk = (nkb + MAX_CHUNK_KB - 1) / MAX_CHUNK_KB;
+  const long tiles = (long)batch * ((M + BM - 1) / BM) * ((Nr + BN - 1) / BN);
+  // split products pay a partial write and a combine whatever the count, so
+  // only they buy tail balance with a shorter chunk
+  if (nchunk > 1 && nchunk < nkb && tiles * nchunk < 6L * 152) nchunk++;
+  return (nkb + nchunk - 1) / nchunk;
+}
+
+long tc_partial_elems(int M, int Nr, int Kr, int batch) {
   const int nkb = (Kr + BKR - 1) / BKR;
+  const int ckb = tc_chunk_blocks(M, Nr, Kr, batch);
   const int nchunk = (nkb + ckb - 1) / ckb;
   return nchunk > 1 ? (long)nchunk * batch * M * Nr : 0;
 }
 
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
-                    long sbo, int* ps0, float* pbc, int* err, cudaStream_t s, int chunk_k,
+                    long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
                     cudaEvent_t gemm_done, int slices, bool a_f32) {
   if (slices != 3 && slices != 4) return cudaErrorInvalidValue;
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
@@ -786,7 +796,7 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   g.mt = (M + BM - 1) / BM;
   g.nt = (Nr + BN - 1) / BN;
   g.nkb = (Kr + BKR - 1) / BKR;
-  g.ckb = std::max(1, std::min(MAX_CHUNK_KB, chunk_k / BKR));
+  g.ckb = tc_chunk_blocks(M, Nr, Kr, batch);
   g.nchunk = (g.nkb + g.ckb - 1) / g.ckb;
   g.units = (long)batch * g.mt * g.nt * g.nchunk;
   if (g.units <= 0) return cudaSuccess;

@@ -17,10 +17,9 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
 // out[b][m][n] (n < Nr real columns, interleaved complex) = A'[b] B'[b]^T for
 // sliced operands: A' has M rows with exponents eA[b * seA + m], B' has Nr rows
 // whose pair (2j, 2j + 1) shares the exponent eB[b * seB + j]; Kr real K.
-// FP32 output, or FP64 output when out_f64.  K is taken in chunks of
-// chunk_k real elements (a multiple of 32, at most 1024); with more than one
-// chunk ps0 / pbc (tc_partial_elems elements each) hold the exact chunk sums
-// until they are combined.  `err` receives a nonzero code if a device wait
+// FP32 output, or FP64 output when out_f64.  K is taken in the chunks
+// tc_chunk_blocks gives; with more than one chunk ps0 / pbc (tc_partial_elems
+// elements each) hold the exact chunk sums until they are combined.  `err` receives a nonzero code if a device wait
 // gave up.
 // gemm_done (may be null) is recorded on `s` right after the GEMM kernel,
 // before any combine kernel, so that the GEMM alone can be timed.  slices: 4
@@ -30,15 +29,21 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
 // slices inside the kernel with the row exponents eA.
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
-                    long sbo, int* ps0, float* pbc, int* err, cudaStream_t s, int chunk_k,
+                    long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
                     cudaEvent_t gemm_done = nullptr, int slices = 4, bool a_f32 = false);
 
 // Map of an FP32 matrix [batch][rows][ld floats] (cols valid) in 32-float K
 // boxes of 128 rows with 128B swizzle (ld * 4 bytes a multiple of 16).
 cudaError_t make_f32_map(void* map_out, const void* base, int batch, int rows, int cols, int ld);
 
+// 32-wide real-K blocks per chunk of a product of this shape: the fewest
+// chunks of at most 32 blocks (the exact leading sums), of equal length; a
+// product split anyway takes one chunk more when it would otherwise have
+// fewer than six 128 x 128 x chunk units per SM of a 152-SM part.
+int tc_chunk_blocks(int M, int Nr, int Kr, int batch);
+
 // Elements of each split-K partial buffer tc_gemm needs for this shape (0 if none).
-long tc_partial_elems(int M, int Nr, int Kr, int batch, int chunk_k);
+long tc_partial_elems(int M, int Nr, int Kr, int batch);
 
 // Row exponents of src[b][r][0..cols) (contiguous rows): e[b * rows + r], the
 // smallest e with max_c max(|re|, |im|) < 2^e (0 for a zero row).

@@ -44,12 +44,6 @@ struct Sizes {
 
 int pad8(int x) { return (x + 7) & ~7; }
 
-// K chunk (real elements) of the tensor-core GEMMs: 512 for the long
-// contractions S1, S4a and S4b, so that the FP32 sums of the small product
-// classes stay short; S2's K (2 n_occ) fits one chunk.
-constexpr int kChunkLong = 512;
-constexpr int kChunkShort = 1024;
-
 Sizes sizes_of(const thc_dims* d, int precision) {
   Sizes s;
   s.nk = (long)d->n1 * d->n2 * d->n3;
@@ -69,10 +63,10 @@ Sizes sizes_of(const thc_dims* d, int precision) {
   s.plBy = s.nk * 2 * d->nocc * (long)s.ldM;
   s.plM = (d->nisdf % 2) ? s.nk * d->nisdf * (long)s.ldM : 0;   // M's slices only for odd N_P
   s.nexp = s.nk * (d->nbas + 3L * d->nisdf + 2L * d->nocc);
-  s.npart = std::max({tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nbas, (int)s.nk, kChunkLong),
-                      tc_partial_elems(d->nisdf, 2 * d->nisdf, 2 * d->nocc, (int)s.nk, kChunkShort),
-                      tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nisdf, (int)s.nk, kChunkLong),
-                      tc_partial_elems(d->nbas, 2 * d->nocc, 2 * d->nisdf, (int)s.nk, kChunkLong)});
+  s.npart = std::max({tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nbas, (int)s.nk),
+                      tc_partial_elems(d->nisdf, 2 * d->nisdf, 2 * d->nocc, (int)s.nk),
+                      tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nisdf, (int)s.nk),
+                      tc_partial_elems(d->nbas, 2 * d->nocc, 2 * d->nisdf, (int)s.nk)});
   return s;
 }
 
@@ -437,7 +431,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, embed_b(C, true, Nn, n, 1, false, false, nk, N, n, c->eC, c->Bc_pl, c->plBc, c->ldXT, s));
   CKC(c, record_core(c, 0, 0, s));
   CKC(c, tc_gemm(c->opXT, c->opBc, P, 2 * n, 2 * N, nk, c->eXT, P, c->eC, n, Psi, false, 2 * n, 2 * Pn,
-                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong, core_event(c, 0, 1)));
+                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 0, 1)));
   CKC(c, mark(c, 1, s, false));
   // S2  D = Psi Psi^H on tensor cores: A = Psi and B = embedded Psi^H share the
   // row exponents of Psi
@@ -446,7 +440,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, record_core(c, 1, 0, s));
   // D is rounded to FP32 on output and K = 2 n is short: three slices
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
-                 c->part_s0, c->part_bc, c->tc_err, s, kChunkShort, core_event(c, 1, 1), 3));
+                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 1, 1), 3));
   CKC(c, mark(c, 2, s, false));
   // S3  M = IDFT(DFT(D) o Vh) in FP32
   CKC(c, record_core(c, 2, 0, s));
@@ -466,14 +460,14 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, embed_b(Psi, false, Pn, n, 1, false, false, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
   CKC(c, record_core(c, 3, 0, s));
   CKC(c, tc_gemm(a_f32 ? c->opMf : c->opM, c->opBy, P, 2 * n, 2 * P, nk, c->eM, P, c->eY, n, Y, false, 2 * n,
-                 2 * Pn, c->part_s0, c->part_bc, c->tc_err, s, kChunkLong, core_event(c, 3, 1), 4, a_f32));
+                 2 * Pn, c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 3, 1), 4, a_f32));
   CKC(c, mark(c, 4, s, false));
   // S4b KC = conj(X) Y on tensor cores: B = embedded Y (conj-A form)
   CKC(c, col_exponents_c(Y, Pn, n, nk, P, n, c->eY, s));
   CKC(c, embed_b(Y, false, Pn, n, 1, false, true, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
   CKC(c, record_core(c, 4, 0, s));
   CKC(c, tc_gemm(c->opXn, c->opBy, N, 2 * n, 2 * P, nk, c->eXn, N, c->eY, n, KC, true, 2 * n, 2 * Nn,
-                 c->part_s0, c->part_bc, c->tc_err, s, kChunkLong, core_event(c, 4, 1)));
+                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 4, 1)));
   CKC(c, mark(c, 5, s, false));
   CKC(c, record_core(c, 5, 0, s));
   CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
@@ -609,9 +603,9 @@ thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   // exponents, exponents of Psi, embed, GEMM), S4b 3, E_x 2; S1, S4a and S4b
   // add a combine kernel when split along K.
   if (c->precision == THC_MIXED) {
-    const int s1 = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nbas, c->nk, kChunkLong) > 0 ? 1 : 0;
-    const int s4a = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nisdf, c->nk, kChunkLong) > 0 ? 1 : 0;
-    const int s4b = tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk, kChunkLong) > 0 ? 1 : 0;
+    const int s1 = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nbas, c->nk) > 0 ? 1 : 0;
+    const int s4a = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nisdf, c->nk) > 0 ? 1 : 0;
+    const int s4b = tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk) > 0 ? 1 : 0;
     *launches = 3 + s1 + 3 + 1 + 4 + s4a + 3 + s4b + 2;
   } else {
     *launches = 7;

@@ -61,10 +61,18 @@ def test_memory_bytes_arithmetic():
     planes = nk * (N * pad8(2 * P) + P * pad8(2 * N) + P * pad8(2 * n)
                    + 2 * n * pad8(2 * N) + 2 * P * pad8(2 * n) + 2 * n * pad8(2 * P))
     exps = nk * (N + 3 * P + 2 * n)
-    c4 = -(-(2 * P) // 512)                              # split-K chunks of S4a and S4b (K = 2 N_P real)
-    c1 = -(-(2 * N) // 512)                              # and of S1 (K = 2 N real)
-    part = max(c4 * nk * N * 2 * n if c4 > 1 else 0, c4 * nk * P * 2 * n if c4 > 1 else 0,
-               c1 * nk * P * 2 * n if c1 > 1 else 0)
+    def chunks(rows, kr):
+        # split-K chunks: the fewest of at most 32 K blocks of 32 reals, one
+        # more when a split product has fewer than 6 x 152 tile-chunk units
+        nkb = -(-kr // 32)
+        c = -(-nkb // 32)
+        if 1 < c < nkb and nk * -(-rows // 128) * -(-(2 * n) // 128) * c < 6 * 152:
+            c += 1
+        return -(-nkb // -(-nkb // c))
+
+    assert (chunks(P, 2 * N), chunks(P, 2 * P), chunks(N, 2 * P)) == (1, 3, 4)   # S1, S4a, S4b
+    part = max(c * nk * rows * 2 * n if c > 1 else 0
+               for rows, c in ((P, chunks(P, 2 * N)), (P, chunks(P, 2 * P)), (N, chunks(N, 2 * P))))
     tc = 8 * (nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + 4 * 2 * planes \
         + 4 * exps + 64 + 8 * part + common
     assert thc.thc_memory_bytes(d, thc.THC_MIXED) == tc
