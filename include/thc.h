@@ -113,7 +113,11 @@ thc_status thc_build_host(thc_ctx* ctx, const double* C_host, double* KC_host, d
 /* Intermediates of the last build, copied to device buffers the caller owns
  * (for tests).  which: 0 = Psi [N_k][nisdf][nocc], 1 = D [N_k][nisdf][nisdf],
  * 2 = M [N_k][nisdf][nisdf], 3 = Y = M Psi [N_k][nisdf][nocc].  Written as
- * complex128 whatever the precision.  Synchronises the stream. */
+ * complex128 whatever the precision.  which = 4 (THC_MIXED only): the row
+ * exponents of M that S4a slices it with, [N_k][nisdf] doubles, each the
+ * smallest e with max_Q max(|Re|, |Im|) of M^k[P][Q] < 2^e (0 for a zero
+ * row; a row whose maximum is below 2^-133 may also get 0, which still bounds
+ * it).  Synchronises the stream. */
 thc_status thc_get_intermediate(thc_ctx* ctx, int which, double* out);
 
 /* Per-stage device time of the last build in milliseconds (CUDA events on

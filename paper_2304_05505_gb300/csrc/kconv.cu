@@ -20,8 +20,16 @@
 // forward and inverse transforms do not pick up a systematic scale error.
 //
 #include "thc_internal.cuh"
+#include "mbarrier.cuh"
+#include "tc_gemm.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <math.h>
+
+#include <algorithm>
+#include <cstring>
 
 namespace {
 
@@ -167,24 +175,12 @@ __global__ void kconv_kernel(const typename cplx<R>::type* __restrict__ D,
 // l / EPW of element l % EPW, so the lanes of one slot read EPW consecutive
 // elements of one k plane.  Both D and Vh are loaded up front, so a warp
 // waits for DRAM once, and no shared memory holds the data.
+// The convolution of one element on N1 lanes: x (this lane's N2 N3 values of
+// D, first mesh index = slot) becomes this lane's values of M.
 template <int N1, int N2, int N3>
-__global__ void __launch_bounds__(256, 2) kconv_lanes_kernel(const float2* __restrict__ D,
-                                                          const float2* __restrict__ Vh, float2* __restrict__ M,
-                                                          long npq, Twiddles tw) {
-  constexpr int L = N2 * N3, EPW = 32 / N1, EPB = EPW * 8;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int slot = lane / EPW;                       // first mesh index of this lane's values
-  const int el = lane - slot * EPW;                  // element within the warp
-  const bool live = slot < N1;                       // lanes past EPW N1 idle
-  const long e0 = (long)blockIdx.x * EPB;
-  const long e = e0 + warp * EPW + el;
-  const bool ok = live && e < npq;
-  const long off = (long)(live ? slot : 0) * L * npq + e;
-  float2 x[L], vh[L];
-#pragma unroll
-  for (int j = 0; j < L; j++) x[j] = ok ? __ldcs(D + off + (long)j * npq) : make_float2(0.f, 0.f);
-#pragma unroll
-  for (int j = 0; j < L; j++) vh[j] = ok ? __ldcs(Vh + off + (long)j * npq) : make_float2(0.f, 0.f);
+__device__ __forceinline__ void lanes_convolve(float2* x, const float2* vh, const Twiddles& tw, int slot,
+                                               int el) {
+  constexpr int L = N2 * N3, EPW = 32 / N1;
   // forward DFT: first axis across lanes, then the two local axes
   auto across = [&](int sign) {
 #pragma unroll
@@ -219,9 +215,170 @@ __global__ void __launch_bounds__(256, 2) kconv_lanes_kernel(const float2* __res
   for (int j = 0; j < L; j++) x[j] = cmul(x[j], vh[j]);
   local(+1);
   across(+1);
+}
+
+template <int N1, int N2, int N3>
+__global__ void __launch_bounds__(256, 2) kconv_lanes_kernel(const float2* __restrict__ D,
+                                                          const float2* __restrict__ Vh, float2* __restrict__ M,
+                                                          long npq, Twiddles tw) {
+  constexpr int L = N2 * N3, EPW = 32 / N1, EPB = EPW * 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / EPW;                       // first mesh index of this lane's values
+  const int el = lane - slot * EPW;                  // element within the warp
+  const bool live = slot < N1;                       // lanes past EPW N1 idle
+  const long e = (long)blockIdx.x * EPB + warp * EPW + el;
+  const bool ok = live && e < npq;
+  const long off = (long)(live ? slot : 0) * L * npq + e;
+  float2 x[L], vh[L];
+#pragma unroll
+  for (int j = 0; j < L; j++) x[j] = ok ? __ldcs(D + off + (long)j * npq) : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < L; j++) vh[j] = ok ? __ldcs(Vh + off + (long)j * npq) : make_float2(0.f, 0.f);
+  lanes_convolve<N1, N2, N3>(x, vh, tw, slot, el);
   if (ok) {
 #pragma unroll
     for (int j = 0; j < L; j++) M[off + (long)j * npq] = x[j];
+  }
+}
+
+// Row-exponent key of a value pair's max(|re|, |im|): the top 16 bits of its
+// FP32 pattern (sign 0, exponent, 7 mantissa bits), which orders as the value
+// does and fixes its frexp exponent whenever the value is at least 2^-133.
+__device__ __forceinline__ uint32_t abs_bits(float2 v) {
+  return max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu);
+}
+
+// Persistent, TMA-fed form of the lane-split convolution (N_P^2 even).  A
+// batch is EPB consecutive elements of all N_k planes; one 2-D box of D and
+// one of Vh ([N_k][EPB] complex, zero past the end) land in shared memory
+// while the block convolves the batch before, so each SM keeps two boxes in
+// flight instead of waiting on DRAM once per element.  Each block takes a
+// contiguous range of batches.
+//
+// With rowkey (np rows of np elements per k), it also folds the row
+// exponents of M: rowkey[k * np + p] = the largest abs_bits key over
+// M^k[p][q], q < np.  The EPW lanes of one slot reduce the keys of a warp
+// whose elements lie in one row by shuffles (two keys per word); the slot's
+// first lane keeps the running maximum of its row across the block's batches
+// in registers and adds it to memory by atomicMax when the row changes.
+// Every mbarrier wait is bounded; on expiry the block sets the error word,
+// waits (bounded) for its copy in flight and returns.
+template <int N1, int N2, int N3>
+__global__ void __launch_bounds__(256, 2) kconv_pipe_kernel(const __grid_constant__ CUtensorMap mapD,
+                                                         const __grid_constant__ CUtensorMap mapV,
+                                                         float2* __restrict__ M, long npq, long nbatch,
+                                                         Twiddles tw, unsigned* __restrict__ rowkey, int np,
+                                                         int* err) {
+  constexpr int L = N2 * N3, NK = N1 * L, EPW = 32 / N1, EPB = EPW * 8, LP = (L + 1) / 2;
+  constexpr uint32_t BOX = NK * EPB * sizeof(float2);
+  extern __shared__ __align__(128) unsigned char kc_smem[];   // [D box][Vh box][mbarrier]
+  const float2* sD = reinterpret_cast<const float2*>(kc_smem);
+  const float2* sV = reinterpret_cast<const float2*>(kc_smem + BOX);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / EPW, el = lane - slot * EPW;
+  const bool live = slot < N1;
+  const int sbase = (live ? slot : 0) * L * EPB + warp * EPW + el;   // this lane's first value in a box
+  const long b0 = nbatch * blockIdx.x / gridDim.x, b1 = nbatch * (blockIdx.x + 1) / gridDim.x;
+  const uint32_t bar = smem_u32(kc_smem + 2 * BOX);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](long bt) {
+    mbar_expect_tx(bar, 2 * BOX);
+    tma_load_2d(smem_u32(sD), &mapD, bar, (int)(2 * bt * EPB), 0);
+    tma_load_2d(smem_u32(sV), &mapV, bar, (int)(2 * bt * EPB), 0);
+  };
+  if (threadIdx.x == 0 && b0 < b1) issue(b0);
+  uint32_t acc[LP];
+#pragma unroll
+  for (int i = 0; i < LP; i++) acc[i] = 0u;
+  long acc_row = -1;
+  auto flush = [&]() {
+    if (acc_row >= 0) {
+#pragma unroll
+      for (int i = 0; i < LP; i++) {
+        const uint32_t lo = acc[i] & 0xffffu, hi = acc[i] >> 16;
+        if (lo) atomicMax(rowkey + (long)(slot * L + 2 * i) * np + acc_row, lo);
+        if (hi) atomicMax(rowkey + (long)(slot * L + 2 * i + 1) * np + acc_row, hi);
+      }
+    }
+  };
+  bool good = true;
+  uint32_t fail_parity = 0;
+  for (long bt = b0; bt < b1; bt++) {
+    fail_parity = (uint32_t)((bt - b0) & 1);
+    good = mbar_wait_warp(bar, fail_parity, err, 1024);
+    good = __syncthreads_and(good);
+    if (!good) break;
+    float2 x[L], vh[L];
+#pragma unroll
+    for (int j = 0; j < L; j++) x[j] = live ? sD[sbase + j * EPB] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < L; j++) vh[j] = live ? sV[sbase + j * EPB] : make_float2(0.f, 0.f);
+    __syncthreads();                                   // the boxes are free for the next batch
+    if (threadIdx.x == 0 && bt + 1 < b1) issue(bt + 1);
+    lanes_convolve<N1, N2, N3>(x, vh, tw, slot, el);
+    const long ew = bt * EPB + warp * EPW;             // the warp's first element
+    const long e = ew + el;
+    const bool ok = live && e < npq;
+    if (ok) {
+      const long off = (long)slot * L * npq + e;
+#pragma unroll
+      for (int j = 0; j < L; j++) __stcs(M + off + (long)j * npq, x[j]);
+    }
+    if (rowkey) {
+      uint32_t w[LP];
+#pragma unroll
+      for (int i = 0; i < LP; i++)
+        w[i] = __byte_perm(abs_bits(x[2 * i]), 2 * i + 1 < L ? abs_bits(x[2 * i + 1 < L ? 2 * i + 1 : 0]) : 0u,
+                           0x7632);
+      const bool one = ew < npq && ew / np == (std::min(ew + EPW, npq) - 1) / np;   // warp-uniform
+      if (one) {
+#pragma unroll
+        for (int o = 1; o < EPW; o <<= 1) {
+#pragma unroll
+          for (int i = 0; i < LP; i++) {
+            const uint32_t t = __shfl_down_sync(0xffffffffu, w[i], o);
+            if (el + o < EPW) w[i] = __vmaxu2(w[i], t);
+          }
+        }
+        if (el == 0 && live) {
+          const long row = ew / np;
+          if (row != acc_row) {
+            flush();
+            acc_row = row;
+#pragma unroll
+            for (int i = 0; i < LP; i++) acc[i] = w[i];
+          } else {
+#pragma unroll
+            for (int i = 0; i < LP; i++) acc[i] = __vmaxu2(acc[i], w[i]);
+          }
+        }
+      } else if (ok) {                                 // a warp across rows: one atomic per value
+        const long row = e / np;
+#pragma unroll
+        for (int i = 0; i < LP; i++) {
+          if (w[i] & 0xffffu) atomicMax(rowkey + (long)(slot * L + 2 * i) * np + row, w[i] & 0xffffu);
+          if (w[i] >> 16) atomicMax(rowkey + (long)(slot * L + 2 * i + 1) * np + row, w[i] >> 16);
+        }
+      }
+    }
+  }
+  if (rowkey && el == 0 && live) flush();
+  // the copy of the batch whose wait gave up may still be in flight
+  if (!good && threadIdx.x == 0) mbar_drain(bar, fail_parity);
+}
+
+// e[i] = the exponent a row key stands for, in place: for a key of a value of
+// at least 2^-133 its frexp exponent (normal: biased exponent - 126;
+// subnormal: bit length of the 7 kept mantissa bits - 133), else 0.
+__global__ void rowkey_to_exponents(unsigned* v, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const unsigned k = v[i];
+    const int e = k >= 0x80u ? (int)(k >> 7) - 126 : k ? (32 - __clz((int)k)) - 133 : 0;
+    reinterpret_cast<int*>(v)[i] = e;
   }
 }
 
@@ -312,7 +469,67 @@ cudaError_t kconv_launch(const typename cplx<R>::type* D, const typename cplx<R>
   return cudaGetLastError();
 }
 
+template <int N1, int N2, int N3>
+cudaError_t kconv_pipe_launch(const float2* D, const float2* Vh, float2* M, int np, unsigned* rowkey, int* err,
+                              cudaStream_t s) {
+  constexpr int NK = N1 * N2 * N3, EPB = (32 / N1) * 8;
+  constexpr uint32_t BOX = NK * EPB * sizeof(float2);
+  const long npq = (long)np * np;
+  alignas(64) unsigned char mD[128], mV[128];
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  cudaError_t e = make_f32_map_2d(mD, D, 2 * npq, NK, 8 * npq, 2 * EPB, NK);
+  if (e == cudaSuccess) e = make_f32_map_2d(mV, Vh, 2 * npq, NK, 8 * npq, 2 * EPB, NK);
+  if (e != cudaSuccess) return e;
+  CUtensorMap mapD, mapV;
+  memcpy(&mapD, mD, sizeof mapD);
+  memcpy(&mapV, mV, sizeof mapV);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
+  }
+  constexpr uint32_t SMEM = 2 * BOX + 16;
+  static_assert(BOX % 128 == 0, "boxes start on 128-byte boundaries");
+  e = cudaFuncSetAttribute(kconv_pipe_kernel<N1, N2, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+  if (e != cudaSuccess) return e;
+  const long nbatch = (npq + EPB - 1) / EPB;
+  const unsigned grid = (unsigned)std::min<long>(nbatch, 2L * nsm);
+  kconv_pipe_kernel<N1, N2, N3><<<grid, 256, SMEM, s>>>(mapD, mapV, M, npq, nbatch, make_twiddles(N1, N2, N3),
+                                                         rowkey, np, err);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t kconv_c_rowexp(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3, int* e,
+                           bool* done, int* err, cudaEvent_t started, cudaEvent_t conv_done, cudaStream_t s) {
+  *done = false;
+  const long npq = (long)np * np;
+  const bool pipe = n1 == n2 && n2 == n3 && n1 >= 2 && n1 <= 4 && np >= 1 && npq % 2 == 0 && npq < (1L << 29) &&
+                    ((uintptr_t)D & 15) == 0 && ((uintptr_t)Vh & 15) == 0 && err;
+  cudaError_t r = cudaSuccess;
+  if (!pipe) {
+    if (started) r = cudaEventRecord(started, s);
+    if (r == cudaSuccess) r = kconv_c(D, Vh, M, npq, n1, n2, n3, s);
+    if (r == cudaSuccess && conv_done) r = cudaEventRecord(conv_done, s);
+    return r;
+  }
+  const long rows = (long)n1 * n2 * n3 * np;
+  unsigned* key = reinterpret_cast<unsigned*>(e);
+  r = cudaMemsetAsync(key, 0, rows * sizeof(unsigned), s);
+  if (r == cudaSuccess && started) r = cudaEventRecord(started, s);
+  if (r != cudaSuccess) return r;
+  if (n1 == 4) r = kconv_pipe_launch<4, 4, 4>(D, Vh, M, np, key, err, s);
+  else if (n1 == 3) r = kconv_pipe_launch<3, 3, 3>(D, Vh, M, np, key, err, s);
+  else r = kconv_pipe_launch<2, 2, 2>(D, Vh, M, np, key, err, s);
+  if (r == cudaSuccess && conv_done) r = cudaEventRecord(conv_done, s);
+  if (r != cudaSuccess) return r;
+  rowkey_to_exponents<<<(unsigned)std::min<long>((rows + 255) / 256, 152L * 8), 256, 0, s>>>(key, rows);
+  r = cudaGetLastError();
+  *done = r == cudaSuccess;
+  return r;
+}
 
 cudaError_t kconv_z(const double2* D, const double2* Vh, double2* M, long npq, int n1, int n2,
                     int n3, cudaStream_t s) {

@@ -54,6 +54,7 @@
 #include "thc_internal.cuh"
 #include "tc_gemm.cuh"
 #include "slices.cuh"
+#include "mbarrier.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -68,7 +69,6 @@ constexpr int NPL = 4;                                       // slices per opera
 constexpr uint32_t TILE_BYTES = BM * BKR * 2;                // 8 KB (one plane of A or B)
 constexpr int EPI_WARPS = 16;
 constexpr int MAX_CHUNK_KB = 32;                             // K blocks per exact chunk, at most (1024 real K)
-constexpr long long WAIT_LIMIT = 4000000000LL;               // clock64 cycles (~2 s)
 constexpr uint32_t TMEM_COLS = 512;
 
 // Operands in NS slices: 4 (10 products per real product) or 3 (6 products,
@@ -93,75 +93,6 @@ template <bool CV> struct Roles {
   static constexpr int NT = (EPI0 + EPI) * 32;                  // threads
   static constexpr int COLS = 4 * BN / EPI;                     // columns of a unit per epilogue warp
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Bounded wait for the phase of parity `parity` to complete.  Gives up after
-// WAIT_LIMIT cycles (setting `code` in the error word) or as soon as another
-// CTA has set the error word.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
-  const long long t0 = clock64();
-  for (uint32_t it = 0;; it++) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 255) == 255 && *(volatile int*)err != 0) return false;
-    if (clock64() - t0 > WAIT_LIMIT) {
-      atomicOr(err, code);
-      return false;
-    }
-  }
-}
-
-// The same wait taken by a whole warp, with one answer for every lane.  Lane
-// 0 polls with a growing sleep (up to 256 ns) so that waiting epilogue and
-// converter warps leave the issue slots to the warps doing work.
-__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, int* err, int code) {
-  int ok = 1;
-  if ((threadIdx.x & 31) == 0) {
-    const long long t0 = clock64();
-    uint32_t ns = 8;
-    for (uint32_t it = 0;; it++) {
-      uint32_t done;
-      asm volatile(
-          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-          " selp.u32 %0, 1, 0, p;\n}"
-          : "=r"(done)
-          : "r"(bar), "r"(parity)
-          : "memory");
-      if (done) break;
-      if ((it & 15) == 15 && *(volatile int*)err != 0) { ok = 0; break; }
-      if (clock64() - t0 > WAIT_LIMIT) {
-        atomicOr(err, code);
-        ok = 0;
-        break;
-      }
-      __nanosleep(ns);
-      if (ns < 256) ns <<= 1;
-    }
-  }
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
                                             int c1, int c2) {
@@ -759,6 +690,22 @@ cudaError_t make_f32_map(void* map_out, const void* base, int batch, int rows, i
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t make_f32_map_2d(void* map_out, const void* base, long inner, long outer, long stride_bytes, int box0,
+                            int box1) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  if (((uintptr_t)base & 15) || stride_bytes % 16 || (box0 * 4) % 16 || box0 > 256 || box1 > 256)
+    return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)stride_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)box0, (cuuint32_t)box1};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }

@@ -36,6 +36,12 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
 // boxes of 128 rows with 128B swizzle (ld * 4 bytes a multiple of 16).
 cudaError_t make_f32_map(void* map_out, const void* base, int batch, int rows, int cols, int ld);
 
+// Map of a 2-D FP32 array [outer][inner] (rows stride_bytes apart, a multiple
+// of 16) read as boxes of box0 (inner, box0 * 4 bytes a multiple of 16) by
+// box1 rows, no swizzle, zero past the ends.
+cudaError_t make_f32_map_2d(void* map_out, const void* base, long inner, long outer, long stride_bytes, int box0,
+                            int box1);
+
 // 32-wide real-K blocks per chunk of a product of this shape: the fewest
 // chunks of at most 32 blocks (the exact leading sums), of equal length; a
 // product split anyway takes one chunk more when it would otherwise have

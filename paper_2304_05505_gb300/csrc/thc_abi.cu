@@ -443,19 +443,28 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
                  c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 1, 1), 3));
   CKC(c, mark(c, 2, s, false));
   // S3  M = IDFT(DFT(D) o Vh) in FP32
-  CKC(c, record_core(c, 2, 0, s));
-  CKC(c, kconv_c(D, c->Vh32, M, PP, c->n1, c->n2, c->n3, s));
-  CKC(c, record_core(c, 2, 1, s));
+  // (2^3, 3^3 and 4^3 meshes: the convolution also finds the exact row
+  // exponents of M that S4a slices it with)
+  const bool a_f32 = c->plM == 0;
+  bool have_eM = false;
+  if (a_f32) {
+    CKC(c, kconv_c_rowexp(D, c->Vh32, M, P, c->n1, c->n2, c->n3, c->eM, &have_eM, c->tc_err,
+                          core_event(c, 2, 0), core_event(c, 2, 1), s));
+  } else {
+    CKC(c, record_core(c, 2, 0, s));
+    CKC(c, kconv_c(D, c->Vh32, M, PP, c->n1, c->n2, c->n3, s));
+    CKC(c, record_core(c, 2, 1, s));
+  }
   CKC(c, mark(c, 3, s, false));
   // S4a Y = M Psi on tensor cores: A = M in FP32, cut into its slices inside
   // the GEMM with the exact row exponents of M; B = embedded Psi with one
   // exponent per orbital
   // (odd N_P: M's slices go through HBM, written by the warp-per-row kernel)
-  const bool a_f32 = c->plM == 0;
-  if (a_f32)
-    CKC(c, row_exponents_rows(M, P, (long)nk * P, c->eM, s));
-  else
+  if (a_f32) {
+    if (!have_eM) CKC(c, row_exponents_rows(M, P, (long)nk * P, c->eM, s));
+  } else {
     CKC(c, slice_rows_exact(M, P, (long)nk * P, c->eM, c->M_pl, c->plM, c->ldM, s));
+  }
   CKC(c, col_exponents_c(Psi, Pn, n, nk, P, n, c->eY, s));
   CKC(c, embed_b(Psi, false, Pn, n, 1, false, false, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
   CKC(c, record_core(c, 3, 0, s));
@@ -523,9 +532,22 @@ thc_status thc_sync(thc_ctx* c) {
   return THC_OK;
 }
 
+__global__ void ints_to_doubles(const int* __restrict__ v, double* __restrict__ out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = (double)v[i];
+}
+
 thc_status thc_get_intermediate(thc_ctx* c, int which, double* out) {
-  if (!c || !out || !aligned16(out) || which < 0 || which > 3) return THC_ERR_ARG;
+  if (!c || !out || !aligned16(out) || which < 0 || which > 4) return THC_ERR_ARG;
+  if (which == 4 && c->precision != THC_MIXED) return THC_ERR_ARG;
   if (!c->built) return THC_ERR_STATE;
+  if (which == 4) {
+    const long n = (long)c->nk * c->nisdf;
+    ints_to_doubles<<<(unsigned)std::min<long>((n + 255) / 256, 152L * 8), 256, 0, c->stream>>>(c->eM, out, n);
+    CKC(c, cudaGetLastError());
+    CKC(c, cudaStreamSynchronize(c->stream));
+    return THC_OK;
+  }
   const long n = (which == 0 || which == 3) ? (long)c->nk * c->nisdf * c->nocc
                                             : (long)c->nk * c->nisdf * c->nisdf;
   void* src = which == 0 ? c->Psi : which == 1 ? c->D : which == 2 ? c->M : c->Y;
@@ -599,9 +621,11 @@ thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   if (!c || !launches) return THC_ERR_ARG;
   // FP64 and CUDA-core forms: S1, S2, S3, S4a, S4b, E_x partial, E_x final.
   // Tensor-core form: S1 3 (exponents, embed, GEMM), S2 3 (slices with their
-  // row exponents, embed, GEMM), S3 1 (convolution), S4a 4 (slices of M with their row
-  // exponents, exponents of Psi, embed, GEMM), S4b 3, E_x 2; S1, S4a and S4b
-  // add a combine kernel when split along K.
+  // row exponents, embed, GEMM), S3 + S4a 5 (the convolution, the row
+  // exponents of M: in the convolution plus a conversion kernel on the
+  // 2^3 .. 4^3 meshes, else a kernel of their own; exponents of Psi, embed,
+  // GEMM), S4b 3, E_x 2; S1, S4a and S4b add a combine kernel when split
+  // along K.
   if (c->precision == THC_MIXED) {
     const int s1 = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nbas, c->nk) > 0 ? 1 : 0;
     const int s4a = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nisdf, c->nk) > 0 ? 1 : 0;

@@ -126,6 +126,16 @@ cudaError_t kconv_z(const double2* D, const double2* Vh, double2* M, long npq, i
                     int n3, cudaStream_t s);
 cudaError_t kconv_c(const float2* D, const float2* Vh, float2* M, long npq, int n1, int n2,
                     int n3, cudaStream_t s);
+// As kconv_c with npq = np^2.  On the 2^3, 3^3 and 4^3 meshes with npq even
+// (and err non-null) it runs the TMA-fed convolution, which also writes the
+// row exponents of M: e[k * np + p] = the smallest e with
+// max_q max(|re|, |im|) of M^k[p][q] < 2^e when that maximum is at least
+// 2^-133, else 0; *done tells whether e was written.  err receives a nonzero
+// code if a device wait gave up.  started / conv_done (may be null) are
+// recorded on s right before and right after the convolution kernel.
+cudaError_t kconv_c_rowexp(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
+                           int* e, bool* done, int* err, cudaEvent_t started, cudaEvent_t conv_done,
+                           cudaStream_t s);
 // Vh[a] = (1/N_k) sum_q V[q] w^{+a.q} in FP64; writes FP64 or FP32 output.
 cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long npq, int n1,
                              int n2, int n3, cudaStream_t s);

@@ -115,12 +115,13 @@ def _dims(d: dict) -> ThcDims:
                    int(d["nisdf"]))
 
 
-def _dev_ptr(t, shape=None, name="tensor") -> int:
+def _dev_ptr(t, shape=None, name="tensor", dtype=None) -> int:
     import torch
+    dtype = torch.complex128 if dtype is None else dtype
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name}: expected a CUDA tensor")
-    if t.dtype != torch.complex128:
-        raise TypeError(f"{name}: expected complex128, got {t.dtype}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name}: must be contiguous")
     if shape is not None and tuple(t.shape) != tuple(shape):
@@ -187,7 +188,9 @@ def thc_build_host(ctx, C_host, KC_host, ex_host) -> None:
 
 
 def thc_get_intermediate(ctx, which: int, out) -> None:
-    _check(load().thc_get_intermediate(ctx, int(which), _dev_ptr(out, name="out")),
+    import torch
+    dt = torch.float64 if int(which) == 4 else torch.complex128
+    _check(load().thc_get_intermediate(ctx, int(which), _dev_ptr(out, name="out", dtype=dt)),
            "thc_get_intermediate", ctx)
 
 
@@ -429,6 +432,10 @@ class ExchangeBuild:
     def intermediate(self, which: int):
         t = self.torch
         d = self.dims
+        if which == 4:
+            out = t.empty((self.nk, d["nisdf"]), dtype=t.float64, device=self.device)
+            thc_get_intermediate(self.ctx, which, out)
+            return out
         shape = (self.nk, d["nisdf"], d["nocc"]) if which in (0, 3) else (self.nk, d["nisdf"], d["nisdf"])
         out = t.empty(shape, dtype=t.complex128, device=self.device)
         thc_get_intermediate(self.ctx, which, out)

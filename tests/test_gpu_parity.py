@@ -227,3 +227,44 @@ def test_profile_stage_times(torch_cuda, precision):
     last = thc.thc_stage_times(eb.ctx)
     assert all(t > 0 for t in last)
     eb.close()
+
+
+@pytest.mark.parametrize("mesh,nisdf", [
+    ((4, 4, 4), 150),      # 64-element blocks inside one row or across two
+    ((4, 4, 4), 40),       # blocks across two rows, ragged tail
+    ((4, 4, 4), 10),       # blocks across up to eight rows
+    ((3, 3, 3), 130),      # 80-element blocks, two idle lanes per warp
+    ((3, 3, 3), 2),
+    ((2, 2, 2), 150),
+    ((2, 2, 2), 6),
+    ((4, 4, 4), 65),       # odd N_P: the slices of M go through HBM
+    ((3, 2, 4), 60),       # a mesh without the lane-split convolution
+])
+def test_row_exponents_of_M(torch_cuda, mesh, nisdf):
+    """The row exponents S4a slices M with, from the TMA-fed convolution
+    (2^3 .. 4^3 meshes, even N_P) or from a row pass over M: integers,
+    compared exactly with the smallest e such that every max(|Re|, |Im|) of
+    the row of the GPU's own FP32 M is below 2^e (0 for a zero row; no row
+    here has a maximum below 2^-133, where 0 is also allowed)."""
+    from paper_2304_05505_gb300 import thc
+    r = cells.random_problem(mesh, nbas=9, nocc=3, nisdf=nisdf, seed=nisdf)
+    nk = int(np.prod(mesh))
+    for V in (r["V"], np.zeros_like(r["V"])):
+        dims = dict(n1=mesh[0], n2=mesh[1], n3=mesh[2], nbas=9, nocc=3, nisdf=nisdf)
+        eb = thc.ExchangeBuild(dims, "mixed")
+        try:
+            eb.set_collocation(r["X"])
+            eb.set_kernel(V)
+            eb.build(r["C"])
+            eb.sync()
+            M = eb.intermediate(2).cpu().numpy()
+            got = eb.intermediate(4).cpu().numpy()
+        finally:
+            eb.close()
+        m = np.maximum(np.abs(M.real), np.abs(M.imag)).max(axis=2)
+        assert not ((m > 0) & (m < 2.0 ** -133)).any()
+        ref = np.where(m > 0, np.frexp(m)[1], 0)
+        assert got.shape == (nk, nisdf)
+        assert np.array_equal(got, ref.astype(np.float64))
+        if not V.any():
+            assert not got.any()
