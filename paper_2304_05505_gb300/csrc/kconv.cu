@@ -175,13 +175,46 @@ __global__ void kconv_kernel(const typename cplx<R>::type* __restrict__ D,
 // l / EPW of element l % EPW, so the lanes of one slot read EPW consecutive
 // elements of one k plane.  Both D and Vh are loaded up front, so a warp
 // waits for DRAM once, and no shared memory holds the data.
+// Output m of the N1-point DFT of v (the same operations as line_dft).
+template <int N1>
+__device__ __forceinline__ float2 dft_one(const float2* v, int m, int sign, const Twiddles& tw) {
+  if constexpr (N1 == 2) {
+    return m ? csub(v[0], v[1]) : cadd(v[0], v[1]);
+  } else if constexpr (N1 == 3) {
+    const float2 t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    const float2 h = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+    const float2 r = Tw<float>::mul_s3(d, sign);
+    return m == 0 ? cadd(v[0], t) : m == 1 ? cadd(h, r) : csub(h, r);
+  } else {
+    static_assert(N1 == 4, "lane-split meshes are 2^3, 3^3 and 4^3");
+    const bool odd = m & 1;
+    const float2 a = odd ? csub(v[0], v[2]) : cadd(v[0], v[2]);
+    const float2 b = odd ? csub(v[1], v[3]) : cadd(v[1], v[3]);
+    const float2 bb = odd ? make_float2(-sign * b.y, sign * b.x) : b;   // i * sign * b for odd m
+    return (m & 2) ? csub(a, bb) : cadd(a, bb);
+  }
+}
+
+// The DFTs along the second and third mesh axes of one lane's N2 N3 values.
+template <int N2, int N3>
+__device__ __forceinline__ void local_dfts(float2* x, const Twiddles& tw, int sign) {
+  if constexpr (N2 > 1) {
+#pragma unroll
+    for (int i = 0; i < N3; i++) line_dft<float, N2>(x + i, N3, tw, 1, sign);
+  }
+  if constexpr (N3 > 1) {
+#pragma unroll
+    for (int i = 0; i < N2; i++) line_dft<float, N3>(x + i * N3, 1, tw, 2, sign);
+  }
+}
+
 // The convolution of one element on N1 lanes: x (this lane's N2 N3 values of
 // D, first mesh index = slot) becomes this lane's values of M.
 template <int N1, int N2, int N3>
 __device__ __forceinline__ void lanes_convolve(float2* x, const float2* vh, const Twiddles& tw, int slot,
                                                int el) {
   constexpr int L = N2 * N3, EPW = 32 / N1;
-  // forward DFT: first axis across lanes, then the two local axes
+  // DFT along the first axis across the lanes: gather the N1 values by shuffles
   auto across = [&](int sign) {
 #pragma unroll
     for (int j = 0; j < L; j++) {
@@ -191,29 +224,14 @@ __device__ __forceinline__ void lanes_convolve(float2* x, const float2* vh, cons
         v[t].x = __shfl_sync(0xffffffffu, x[j].x, t * EPW + el);
         v[t].y = __shfl_sync(0xffffffffu, x[j].y, t * EPW + el);
       }
-      line_dft<float, N1>(v, 1, tw, 0, sign);
-      float2 r = v[0];
-#pragma unroll
-      for (int t = 1; t < N1; t++)
-        if (slot == t) r = v[t];
-      x[j] = r;
-    }
-  };
-  auto local = [&](int sign) {
-    if constexpr (N2 > 1) {
-#pragma unroll
-      for (int i = 0; i < N3; i++) line_dft<float, N2>(x + i, N3, tw, 1, sign);
-    }
-    if constexpr (N3 > 1) {
-#pragma unroll
-      for (int i = 0; i < N2; i++) line_dft<float, N3>(x + i * N3, 1, tw, 2, sign);
+      x[j] = dft_one<N1>(v, slot, sign, tw);
     }
   };
   across(-1);
-  local(-1);
+  local_dfts<N2, N3>(x, tw, -1);
 #pragma unroll
   for (int j = 0; j < L; j++) x[j] = cmul(x[j], vh[j]);
-  local(+1);
+  local_dfts<N2, N3>(x, tw, +1);
   across(+1);
 }
 
@@ -253,7 +271,12 @@ __device__ __forceinline__ uint32_t abs_bits(float2 v) {
 // one of Vh ([N_k][EPB] complex, zero past the end) land in shared memory
 // while the block convolves the batch before, so each SM keeps two boxes in
 // flight instead of waiting on DRAM once per element.  Each block takes a
-// contiguous range of batches.
+// contiguous range of batches.  The DFT along the first mesh axis reads the
+// N1 values of an element straight from the D box (one broadcast load each,
+// every lane keeping its own output) and, on the way back, from a scratch
+// area where the warp's lanes left their values ([j][element][slot], the
+// slot index XORed so that the loads of one value index hit distinct banks):
+// no shuffles.
 //
 // With rowkey (np rows of np elements per k), it also folds the row
 // exponents of M: rowkey[k * np + p] = the largest abs_bits key over
@@ -271,15 +294,20 @@ __global__ void __launch_bounds__(256, 2) kconv_pipe_kernel(const __grid_constan
                                                          int* err) {
   constexpr int L = N2 * N3, NK = N1 * L, EPW = 32 / N1, EPB = EPW * 8, LP = (L + 1) / 2;
   constexpr uint32_t BOX = NK * EPB * sizeof(float2);
-  extern __shared__ __align__(128) unsigned char kc_smem[];   // [D box][Vh box][mbarrier]
+  extern __shared__ __align__(128) unsigned char kc_smem[];   // [D box][Vh box][scratch][mbarrier]
   const float2* sD = reinterpret_cast<const float2*>(kc_smem);
   const float2* sV = reinterpret_cast<const float2*>(kc_smem + BOX);
+  float2* scr = reinterpret_cast<float2*>(kc_smem + 2 * BOX);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int slot = lane / EPW, el = lane - slot * EPW;
   const bool live = slot < N1;
-  const int sbase = (live ? slot : 0) * L * EPB + warp * EPW + el;   // this lane's first value in a box
+  const int eloc = warp * EPW + el;                                  // element within the batch
+  const int sbase = (live ? slot : 0) * L * EPB + eloc;               // this lane's first value in a box
+  // scratch slot swizzle: the second half of a warp's elements XORs the slot
+  constexpr int SW = N1 == 4 ? 2 : N1 == 2 ? 1 : 0;
+  const int sw = el >= EPW / 2 ? SW : 0;
   const long b0 = nbatch * blockIdx.x / gridDim.x, b1 = nbatch * (blockIdx.x + 1) / gridDim.x;
-  const uint32_t bar = smem_u32(kc_smem + 2 * BOX);
+  const uint32_t bar = smem_u32(kc_smem + 3 * BOX);
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     mbar_fence_init();
@@ -313,13 +341,35 @@ __global__ void __launch_bounds__(256, 2) kconv_pipe_kernel(const __grid_constan
     good = __syncthreads_and(good);
     if (!good) break;
     float2 x[L], vh[L];
+    // forward DFT along the first axis, this lane's output, from the D box
 #pragma unroll
-    for (int j = 0; j < L; j++) x[j] = live ? sD[sbase + j * EPB] : make_float2(0.f, 0.f);
+    for (int j = 0; j < L; j++) {
+      float2 v[N1];
+#pragma unroll
+      for (int t = 0; t < N1; t++) v[t] = sD[(t * L + j) * EPB + eloc];
+      x[j] = dft_one<N1>(v, live ? slot : 0, -1, tw);
+    }
 #pragma unroll
     for (int j = 0; j < L; j++) vh[j] = live ? sV[sbase + j * EPB] : make_float2(0.f, 0.f);
     __syncthreads();                                   // the boxes are free for the next batch
     if (threadIdx.x == 0 && bt + 1 < b1) issue(bt + 1);
-    lanes_convolve<N1, N2, N3>(x, vh, tw, slot, el);
+    local_dfts<N2, N3>(x, tw, -1);
+#pragma unroll
+    for (int j = 0; j < L; j++) x[j] = cmul(x[j], vh[j]);
+    local_dfts<N2, N3>(x, tw, +1);
+    // inverse DFT along the first axis through the scratch (the warp's own elements)
+    if (live) {
+#pragma unroll
+      for (int j = 0; j < L; j++) scr[(j * EPB + eloc) * N1 + (slot ^ sw)] = x[j];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+      float2 v[N1];
+#pragma unroll
+      for (int t = 0; t < N1; t++) v[t] = scr[(j * EPB + eloc) * N1 + (t ^ sw)];
+      x[j] = dft_one<N1>(v, live ? slot : 0, +1, tw);
+    }
     const long ew = bt * EPB + warp * EPW;             // the warp's first element
     const long e = ew + el;
     const bool ok = live && e < npq;
@@ -489,7 +539,7 @@ cudaError_t kconv_pipe_launch(const float2* D, const float2* Vh, float2* M, int 
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
   }
-  constexpr uint32_t SMEM = 2 * BOX + 16;
+  constexpr uint32_t SMEM = 3 * BOX + 16;
   static_assert(BOX % 128 == 0, "boxes start on 128-byte boundaries");
   e = cudaFuncSetAttribute(kconv_pipe_kernel<N1, N2, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
   if (e != cudaSuccess) return e;
