@@ -632,20 +632,34 @@ __global__ void tc_combine_kernel(const int* __restrict__ ps0, const float* __re
       }
     }
     const int ea = row_exp(eA, (long)b * seA + m) - 14;
-    double x[V];
-#pragma unroll
-    for (int j = 0; j < V; j++) x[j] = ((double)s0[j] + (double)bc[j]) * pow2d(ea + eB[(long)b * seB + ((col + j) >> 1)]);
     const long o = (long)b * sbo + (long)m * ldo + col;
-    if constexpr (V == 4) {
-      if (OUT_F64) {
+    if constexpr (OUT_F64) {
+      double x[V];
+#pragma unroll
+      for (int j = 0; j < V; j++)
+        x[j] = ((double)s0[j] + (double)bc[j]) * pow2d(ea + eB[(long)b * seB + ((col + j) >> 1)]);
+      if constexpr (V == 4) {
         reinterpret_cast<double2*>((double*)out + o)[0] = make_double2(x[0], x[1]);
         reinterpret_cast<double2*>((double*)out + o)[1] = make_double2(x[2], x[3]);
       } else {
-        *reinterpret_cast<float4*>((float*)out + o) = make_float4((float)x[0], (float)x[1], (float)x[2], (float)x[3]);
+        ((double*)out)[o] = x[0];
       }
     } else {
-      if (OUT_F64) ((double*)out)[o] = x[0];
-      else ((float*)out)[o] = (float)x[0];
+      // FP32 result without the FP64 pipe: the integer sum (|s0| < 2^31) as
+      // its rounded float sh plus the exact remainder s0 - sh (at most 2^6),
+      // the FP32 classes added to the remainder first, so that the one
+      // remaining rounding is the final add
+      float x[V];
+#pragma unroll
+      for (int j = 0; j < V; j++) {
+        const int si = (int)s0[j];
+        const float sh = __int2float_rn(si);
+        const float lo = __int2float_rn(si - __float2int_rz(sh)) + bc[j];
+        const int e = ea + eB[(long)b * seB + ((col + j) >> 1)];
+        x[j] = (e >= -126 && e <= 127) ? (sh + lo) * pow2f(e) : ldexpf(sh + lo, e);
+      }
+      if constexpr (V == 4) *reinterpret_cast<float4*>((float*)out + o) = make_float4(x[0], x[1], x[2], x[3]);
+      else ((float*)out)[o] = x[0];
     }
   }
 }
@@ -749,6 +763,7 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   if (g.units <= 0) return cudaSuccess;
   const bool split = g.nchunk > 1;
   if (split && (!ps0 || !pbc)) return cudaErrorInvalidValue;
+  if (g.nchunk > 127) return cudaErrorInvalidValue;   // the combined leading sums stay below 2^31
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
