@@ -192,7 +192,16 @@ struct Geometry {
   int mt, nt, nchunk, nkb;   // tiles along M and N, K chunks, K blocks
   int ckb;                   // K blocks per chunk
   long units;
+  int herm;                  // Hermitian product: tiles on or above the diagonal only
+  long upb;                  // units per batch entry when herm
 };
+
+// First n tile of m tile mi that reaches the diagonal of a Hermitian product
+// (its last complex column >= the tile's first row).
+__host__ __device__ __forceinline__ int herm_n0(int mi) {
+  const int x = mi * BM - (BN / 2 - 1);
+  return x > 0 ? (x + BN / 2 - 1) / (BN / 2) : 0;
+}
 
 // Exponent sentinel of an all-zero row (the rows' atomicMax starts below it).
 __device__ __forceinline__ int row_exp(const int* e, long i) {
@@ -295,6 +304,20 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
   const long u_step = AR ? 1 : gridDim.x;
   // unit u -> (b, m tile, n tile, K chunk), K chunk fastest, then n
   auto decode = [&](long u, int& b, int& mi, int& ni, int& kc) {
+    if (g.herm) {   // one chunk; per batch entry the tiles n >= herm_n0(m), m ascending
+      kc = 0;
+      b = (int)(u / g.upb);
+      long r = u - (long)b * g.upb;
+      int m = 0;
+      for (; m < g.mt - 1; m++) {
+        const long cnt = g.nt - herm_n0(m);
+        if (r < cnt) break;
+        r -= cnt;
+      }
+      mi = m;
+      ni = herm_n0(m) + (int)r;
+      return;
+    }
     kc = (int)(u % g.nchunk);
     long r = u / g.nchunk;
     ni = (int)(r % g.nt);
@@ -533,14 +556,31 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
                   make_float4(__int_as_float(__float2int_rn(va[j])), __int_as_float(__float2int_rn(va[j + 1])),
                               __int_as_float(__float2int_rn(va[j + 2])), __int_as_float(__float2int_rn(va[j + 3])));
           } else {
+            float y[16];
 #pragma unroll
             for (int j = 0; j < 16; j += 4) {
               const float s0 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, 8 * qq + (j >> 1)) - 14);
               const float s1 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, 8 * qq + (j >> 1) + 1) - 14);
               // va holds an exact integer below 2^24
-              *reinterpret_cast<float4*>(stg + stage_off(lane, j >> 2)) =
-                  make_float4((va[j] + vb[j]) * s0, (va[j + 1] + vb[j + 1]) * s0, (va[j + 2] + vb[j + 2]) * s1,
-                              (va[j + 3] + vb[j + 3]) * s1);
+              y[j] = (va[j] + vb[j]) * s0;
+              y[j + 1] = (va[j + 1] + vb[j + 1]) * s0;
+              y[j + 2] = (va[j + 2] + vb[j + 2]) * s1;
+              y[j + 3] = (va[j + 3] + vb[j + 3]) * s1;
+              *reinterpret_cast<float4*>(stg + stage_off(lane, j >> 2)) = make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]);
+            }
+            if (g.herm) {
+              // the mirror image below the diagonal: out[Q][P] = conj(out[P][Q]) for Q > P,
+              // lanes = consecutive P, so each store instruction writes 256 contiguous bytes
+              const int P = row0 + lane;
+              if (P < g.M) {
+                float* ob = (float*)out + (long)b * sbo + 2L * P;
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                  const int Q = (col0 >> 1) + j;
+                  if (Q > P && 2 * Q < g.Nr)
+                    *reinterpret_cast<float2*>(ob + (long)Q * ldo) = make_float2(y[2 * j], -y[2 * j + 1]);
+                }
+              }
             }
           }
           __syncwarp();
@@ -570,6 +610,10 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
                 o = pass == 0 ? reinterpret_cast<float*>(ps0 + base) : pbc + base;
               } else {
                 o = (float*)out + (long)b * sbo + (long)row * ldo;
+              }
+              if (OUT == 0 && g.herm && (col >> 1) + 1 <= row) {   // on or below the diagonal
+                if ((col >> 1) + 1 == row) *reinterpret_cast<float2*>(o + col + 2) = make_float2(v.z, v.w);
+                continue;
               }
               if (vec && col + 4 <= g.Nr) {
                 *reinterpret_cast<float4*>(o + col) = v;
@@ -744,7 +788,7 @@ long tc_partial_elems(int M, int Nr, int Kr, int batch) {
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
-                    cudaEvent_t gemm_done, int slices, bool a_f32) {
+                    cudaEvent_t gemm_done, int slices, bool a_f32, bool herm) {
   if (slices != 3 && slices != 4) return cudaErrorInvalidValue;
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   Maps maps;
@@ -760,6 +804,14 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   g.ckb = tc_chunk_blocks(M, Nr, Kr, batch);
   g.nchunk = (g.nkb + g.ckb - 1) / g.ckb;
   g.units = (long)batch * g.mt * g.nt * g.nchunk;
+  g.herm = herm ? 1 : 0;
+  g.upb = 0;
+  if (herm) {
+    // a Hermitian FP32 product written whole: square, one chunk, FP32 interleaved output
+    if (Nr != 2 * M || g.nchunk != 1 || out_f64 || a_f32 || (ldo % 2) || (sbo % 2)) return cudaErrorInvalidValue;
+    for (int mi = 0; mi < g.mt; mi++) g.upb += g.nt - herm_n0(mi);
+    g.units = (long)batch * g.upb;
+  }
   if (g.units <= 0) return cudaSuccess;
   const bool split = g.nchunk > 1;
   if (split && (!ps0 || !pbc)) return cudaErrorInvalidValue;

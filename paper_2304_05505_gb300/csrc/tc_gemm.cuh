@@ -26,11 +26,14 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
 // (all four planes, 10 slice products) or 3 (the first three planes, the 6
 // products s + t <= 2: about 2^-24 of the row scales).  a_f32: A.map[0] is an
 // FP32 map (make_f32_map) of the interleaved complex A, cut into its four
-// slices inside the kernel with the row exponents eA.
+// slices inside the kernel with the row exponents eA.  herm: the product is
+// Hermitian (B built from conj(A), Nr = 2 M, one K chunk, FP32 output): only
+// the tiles that reach the diagonal are computed, and each writes its values
+// on or above the diagonal and their conjugates at the mirrored positions.
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
-                    cudaEvent_t gemm_done = nullptr, int slices = 4, bool a_f32 = false);
+                    cudaEvent_t gemm_done = nullptr, int slices = 4, bool a_f32 = false, bool herm = false);
 
 // Map of an FP32 matrix [batch][rows][ld floats] (cols valid) in 32-float K
 // boxes of 128 rows with 128B swizzle (ld * 4 bytes a multiple of 16).

@@ -438,9 +438,10 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, slice_rows_exact(Psi, n, (long)nk * P, c->ePsi, c->PsiA_pl, c->plPs, c->ldPs, s));
   CKC(c, embed_b(Psi, false, Pn, 1, n, true, false, nk, n, P, c->ePsi, c->Bd_pl, c->plBd, c->ldPs, s));
   CKC(c, record_core(c, 1, 0, s));
-  // D is rounded to FP32 on output and K = 2 n is short: three slices
+  // D is rounded to FP32 on output and K = 2 n is short: three slices; D is
+  // Hermitian, so only the tiles that reach the diagonal are multiplied
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
-                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 1, 1), 3));
+                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 1, 1), 3, false, true));
   CKC(c, mark(c, 2, s, false));
   // S3  M = IDFT(DFT(D) o Vh) in FP32
   // (2^3, 3^3 and 4^3 meshes: the convolution also finds the exact row
