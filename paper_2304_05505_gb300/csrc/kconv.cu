@@ -421,6 +421,243 @@ __global__ void __launch_bounds__(256, 2) kconv_pipe_kernel(const __grid_constan
   if (!good && threadIdx.x == 0) mbar_drain(bar, fail_parity);
 }
 
+// Exponent of a 16-bit row key (abs_bits >> 16): the frexp exponent of any
+// value of at least 2^-133 with that key, else 0.
+__device__ __forceinline__ int key_exponent(unsigned k) {
+  return k >= 0x80u ? (int)(k >> 7) - 126 : k ? (32 - __clz((int)k)) - 133 : 0;
+}
+
+// First column tile of row tile pb that reaches the diagonal (its last column
+// >= the tile's first row); tiles are 8 rows by EPW columns.
+__host__ __device__ __forceinline__ int herm_qb0(int pb, int epw) {
+  const int x = 8 * pb - (epw - 1);
+  return x > 0 ? (x + epw - 1) / epw : 0;
+}
+
+// Hermitian form of the TMA-fed convolution, for D^k and V^q Hermitian (so
+// that M^k is too): only the tiles of 8 rows P by EPW columns Q that reach the
+// diagonal are loaded (3-D boxes [N_k][8][EPW] of D and Vh, zero past the
+// ends), which halves the bytes read; each lane writes its value of M for
+// Q >= P and the conjugate at (Q, P) for Q > P.  Warp w holds row 8 pb + w,
+// so the box layout [k][w * EPW + el] is that of the flat form.  Row
+// exponents: every tile stores, with plain coalesced stores, the row keys of
+// its rows (max over its elements with Q >= P) in rowk[P][qb][..] and the
+// column keys of its columns (max over its elements with Q > P, the mirrored
+// part of row Q) in colk[Q][pb][..], KWR words per row ([slot][LP] pairs of
+// 16-bit keys); herm_keys_to_exponents takes the maxima.
+template <int N1, int N2, int N3>
+__global__ void __launch_bounds__(256, 2) kconv_herm_kernel(const __grid_constant__ CUtensorMap mapD,
+                                                         const __grid_constant__ CUtensorMap mapV,
+                                                         float2* __restrict__ M, int np, long ntile, Twiddles tw,
+                                                         uint32_t* __restrict__ rowk, uint32_t* __restrict__ colk,
+                                                         const int* __restrict__ tcum, int* err) {
+  constexpr int L = N2 * N3, NK = N1 * L, EPW = 32 / N1, EPB = EPW * 8, LP = (L + 1) / 2, KWR = N1 * LP;
+  constexpr uint32_t BOX = NK * EPB * sizeof(float2);
+  extern __shared__ __align__(128) unsigned char kc_smem[];   // [D box][Vh box][scratch][column keys][mbarrier]
+  const float2* sD = reinterpret_cast<const float2*>(kc_smem);
+  const float2* sV = reinterpret_cast<const float2*>(kc_smem + BOX);
+  float2* scr = reinterpret_cast<float2*>(kc_smem + 2 * BOX);
+  uint32_t* ckey = reinterpret_cast<uint32_t*>(kc_smem + 3 * BOX);   // [warp][lane][LP]
+  const uint32_t bar = smem_u32(kc_smem + 3 * BOX + 8 * 32 * LP * 4);
+  int* tnext = reinterpret_cast<int*>(kc_smem + 3 * BOX + 8 * 32 * LP * 4 + 8);   // (pb, qb) of the next tile
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / EPW, el = lane - slot * EPW;
+  const bool live = slot < N1;
+  const int eloc = warp * EPW + el;
+  const int sbase = (live ? slot : 0) * L * EPB + eloc;
+  constexpr int SW = N1 == 4 ? 2 : N1 == 2 ? 1 : 0;
+  const int sw = el >= EPW / 2 ? SW : 0;
+  auto tsw = [](int k, int c) { return (EPW == 8 ? (c >> 1) + 2 * (k / L) : (k * EPW + c) >> 1) & 7; };
+  const int npb = (np + 7) / 8, nqb = (np + EPW - 1) / EPW;
+  // tiles are dealt round robin, so that the blocks running side by side read
+  // neighbouring tiles (DRAM pages) at the same time; tile t is (pb, qb) with
+  // tcum[pb] <= t < tcum[pb + 1], found by bisection
+  auto locate = [&](long t, int& lpb, int& lqb) {
+    int lo = 0, hi = npb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tcum[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    lpb = lo;
+    lqb = herm_qb0(lo, EPW) + (int)(t - tcum[lo]);
+  };
+  auto issue = [&](int tpb, int tqb) {
+    mbar_expect_tx(bar, 2 * BOX);
+    tma_load_3d(smem_u32(sD), &mapD, bar, 2 * EPW * tqb, 8 * tpb, 0);
+    tma_load_3d(smem_u32(sV), &mapV, bar, 2 * EPW * tqb, 8 * tpb, 0);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+    if ((long)blockIdx.x < ntile) {
+      int a, b;
+      locate(blockIdx.x, a, b);
+      tnext[0] = a;
+      tnext[1] = b;
+      issue(a, b);
+    }
+  }
+  __syncthreads();
+  const long npq = (long)np * np;
+  bool good = true;
+  uint32_t fail_parity = 0;
+  long it = 0;
+  for (long t = blockIdx.x; t < ntile; t += gridDim.x, it++) {
+    fail_parity = (uint32_t)(it & 1);
+    good = mbar_wait_warp(bar, fail_parity, err, 2048);
+    good = __syncthreads_and(good);
+    if (!good) break;
+    const int pb = tnext[0], qb = tnext[1];
+    float2 x[L], vh[L];
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+      float2 v[N1];
+#pragma unroll
+      for (int u = 0; u < N1; u++) v[u] = sD[(u * L + j) * EPB + eloc];
+      x[j] = dft_one<N1>(v, live ? slot : 0, -1, tw);
+    }
+#pragma unroll
+    for (int j = 0; j < L; j++) vh[j] = live ? sV[sbase + j * EPB] : make_float2(0.f, 0.f);
+    __syncthreads();                                   // the boxes (and tnext) are free for the next tile
+    if (threadIdx.x == 0 && t + gridDim.x < ntile) {
+      int a, b;
+      locate(t + gridDim.x, a, b);
+      tnext[0] = a;
+      tnext[1] = b;
+      issue(a, b);
+    }
+    local_dfts<N2, N3>(x, tw, -1);
+#pragma unroll
+    for (int j = 0; j < L; j++) x[j] = cmul(x[j], vh[j]);
+    local_dfts<N2, N3>(x, tw, +1);
+    if (live) {
+#pragma unroll
+      for (int j = 0; j < L; j++) scr[(j * EPB + eloc) * N1 + (slot ^ sw)] = x[j];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+      float2 v[N1];
+#pragma unroll
+      for (int u = 0; u < N1; u++) v[u] = scr[(j * EPB + eloc) * N1 + (u ^ sw)];
+      x[j] = dft_one<N1>(v, live ? slot : 0, +1, tw);
+    }
+    const int P = 8 * pb + warp, Q = EPW * qb + el;
+    const bool valid = live && P < np && Q < np;
+    const bool direct = valid && Q >= P, mirror = valid && Q > P;   // mirror: its conjugate at (Q, P)
+    if (direct) {
+      const long off = (long)slot * L * npq + (long)P * np + Q;
+#pragma unroll
+      for (int j = 0; j < L; j++) __stcs(M + off + (long)j * npq, x[j]);
+    }
+    // keys: the row's (Q >= P) reduced over the warp's lanes of each slot, the
+    // column's (Q > P) over the warps through shared memory
+    uint32_t w[LP];
+#pragma unroll
+    for (int i = 0; i < LP; i++) {
+      const uint32_t k = __byte_perm(abs_bits(x[2 * i]), 2 * i + 1 < L ? abs_bits(x[2 * i + 1 < L ? 2 * i + 1 : 0]) : 0u,
+                                     0x7632);
+      w[i] = direct ? k : 0u;
+      ckey[(warp * 32 + lane) * LP + i] = mirror ? k : 0u;
+    }
+#pragma unroll
+    for (int o = 1; o < EPW; o <<= 1) {
+#pragma unroll
+      for (int i = 0; i < LP; i++) {
+        const uint32_t u = __shfl_down_sync(0xffffffffu, w[i], o);
+        if (el + o < EPW) w[i] = __vmaxu2(w[i], u);
+      }
+    }
+    if (el == 0 && live && P < np) {
+      uint32_t* dst = rowk + ((long)P * nqb + qb) * KWR + slot * LP;
+#pragma unroll
+      for (int i = 0; i < LP; i++) dst[i] = w[i];
+    }
+    // the mirror image goes out row by row: the tile is transposed through the
+    // scratch ([k][column][row], the row index XORed by tsw so that the stores
+    // of a warp and the loads of 8 consecutive rows hit distinct banks)
+    __syncthreads();                                   // every warp has read its part of the scratch
+    if (live) {
+#pragma unroll
+      for (int j = 0; j < L; j++) {
+        const int k = slot * L + j;
+        scr[(k * EPW + el) * 8 + (warp ^ tsw(k, el))] = x[j];
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NK * EPW * 8; idx += blockDim.x) {
+      const int r = idx & 7, c = (idx >> 3) % EPW, k = idx / (8 * EPW);
+      const int mP = 8 * pb + r, mQ = EPW * qb + c;
+      if (mQ > mP && mQ < np) {
+        const float2 v = scr[(k * EPW + c) * 8 + (r ^ tsw(k, c))];
+        __stcs(M + ((long)k * np + mQ) * np + mP, make_float2(v.x, -v.y));
+      }
+    }
+    for (int idx = threadIdx.x; idx < N1 * EPW * LP; idx += blockDim.x) {
+      const int i = idx % LP, ln = idx / LP;          // ln = slot * EPW + column
+      const int cs = ln / EPW, cq = EPW * qb + (ln - cs * EPW);
+      if (cq >= np) continue;
+      uint32_t m = 0u;
+#pragma unroll
+      for (int v = 0; v < 8; v++) m = __vmaxu2(m, ckey[(v * 32 + ln) * LP + i]);
+      colk[((long)cq * npb + pb) * KWR + cs * LP + i] = m;
+    }
+  }
+  if (!good && threadIdx.x == 0) mbar_drain(bar, fail_parity);
+}
+
+// e[k * np + P] from the keys of the tiles that hold row P (rowk[P][qb], qb
+// from the first tile of row band P / 8 that reaches the diagonal) and of
+// those whose mirrored part lands in row P (colk[P][pb], the tiles of column
+// band P / EPW): one block of four warps per row, lanes over the key words.
+template <int N1, int N2, int N3>
+__global__ void __launch_bounds__(128) herm_keys_to_exponents(const uint32_t* __restrict__ rowk,
+                                                              const uint32_t* __restrict__ colk, int np,
+                                                              int* __restrict__ e) {
+  constexpr int L = N2 * N3, EPW = 32 / N1, LP = (L + 1) / 2, KWR = N1 * LP;
+  __shared__ uint32_t part[4][32];
+  const int nqb = (np + EPW - 1) / EPW, npb = (np + 7) / 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int P = blockIdx.x; P < np; P += gridDim.x) {
+    uint32_t m0 = 0u, m1 = 0u;
+    if (lane < KWR) {
+      const uint32_t* r = rowk + (long)P * nqb * KWR + lane;
+      int qb = herm_qb0(P / 8, EPW) + warp;
+      for (; qb + 4 < nqb; qb += 8) {
+        m0 = __vmaxu2(m0, r[(long)qb * KWR]);
+        m1 = __vmaxu2(m1, r[(long)(qb + 4) * KWR]);
+      }
+      if (qb < nqb) m0 = __vmaxu2(m0, r[(long)qb * KWR]);
+      const uint32_t* c = colk + (long)P * npb * KWR + lane;
+      const int qbP = P / EPW;
+      for (int pb = warp; pb < npb && herm_qb0(pb, EPW) <= qbP; pb += 4) m1 = __vmaxu2(m1, c[(long)pb * KWR]);
+    }
+    part[warp][lane] = __vmaxu2(m0, m1);
+    __syncthreads();
+    if (warp == 0 && lane < KWR) {
+      const uint32_t m = __vmaxu2(__vmaxu2(part[0][lane], part[1][lane]), __vmaxu2(part[2][lane], part[3][lane]));
+      const int s = lane / LP, i = lane - s * LP;
+      e[(long)(s * L + 2 * i) * np + P] = key_exponent(m & 0xffffu);
+      if (2 * i + 1 < L) e[(long)(s * L + 2 * i + 1) * np + P] = key_exponent(m >> 16);
+    }
+    __syncthreads();
+  }
+}
+
+// tcum[pb] = the tiles of the row bands before pb that reach the diagonal
+// (tcum[npb] = all of them).
+__global__ void herm_tile_prefix(int* tcum, int np, int epw) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int npb = (np + 7) / 8, nqb = (np + epw - 1) / epw;
+  int c = 0;
+  for (int pb = 0; pb < npb; pb++) {
+    tcum[pb] = c;
+    c += nqb - herm_qb0(pb, epw);
+  }
+  tcum[npb] = c;
+}
+
 // e[i] = the exponent a row key stands for, in place: for a key of a value of
 // at least 2^-133 its frexp exponent (normal: biased exponent - 126;
 // subnormal: bit length of the 7 kept mantissa bits - 133), else 0.
@@ -550,7 +787,73 @@ cudaError_t kconv_pipe_launch(const float2* D, const float2* Vh, float2* M, int 
   return cudaGetLastError();
 }
 
+template <int N1, int N2, int N3>
+cudaError_t kconv_herm_launch(const float2* D, const float2* Vh, float2* M, int np, uint32_t* keys, int* e,
+                              int* err, cudaEvent_t conv_done, cudaStream_t s) {
+  constexpr int L = N2 * N3, NK = N1 * L, EPW = 32 / N1, EPB = EPW * 8, LP = (L + 1) / 2, KWR = N1 * LP;
+  constexpr uint32_t BOX = NK * EPB * sizeof(float2);
+  constexpr uint32_t SMEM = 3 * BOX + 8 * 32 * LP * 4 + 16;   // + mbarrier and the next tile's (pb, qb)
+  static_assert(BOX % 128 == 0, "boxes start on 128-byte boundaries");
+  const long npq = (long)np * np;
+  alignas(64) unsigned char mD[128], mV[128];
+  cudaError_t r = make_f32_map_3d(mD, D, 2L * np, np, NK, 8L * np, 8 * npq, 2 * EPW, 8, NK);
+  if (r == cudaSuccess) r = make_f32_map_3d(mV, Vh, 2L * np, np, NK, 8L * np, 8 * npq, 2 * EPW, 8, NK);
+  if (r != cudaSuccess) return r;
+  CUtensorMap mapD, mapV;
+  memcpy(&mapD, mD, sizeof mapD);
+  memcpy(&mapV, mV, sizeof mapV);
+  const int npb = (np + 7) / 8, nqb = (np + EPW - 1) / EPW;
+  long ntile = 0;
+  for (int pb = 0; pb < npb; pb++) ntile += nqb - herm_qb0(pb, EPW);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
+  }
+  r = cudaFuncSetAttribute(kconv_herm_kernel<N1, N2, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+  if (r != cudaSuccess) return r;
+  uint32_t* rowk = keys;
+  uint32_t* colk = keys + (long)nqb * np * KWR;
+  const int* tcum = reinterpret_cast<const int*>(colk + (long)npb * np * KWR);
+  const unsigned grid = (unsigned)std::min<long>(ntile, 2L * nsm);
+  kconv_herm_kernel<N1, N2, N3><<<grid, 256, SMEM, s>>>(mapD, mapV, M, np, ntile, make_twiddles(N1, N2, N3), rowk,
+                                                      colk, tcum, err);
+  r = cudaGetLastError();
+  if (r == cudaSuccess && conv_done) r = cudaEventRecord(conv_done, s);
+  if (r != cudaSuccess) return r;
+  herm_keys_to_exponents<N1, N2, N3><<<(unsigned)std::min(np, 152 * 16), 128, 0, s>>>(rowk, colk, np, e);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+long kconv_herm_key_words(int np, int n1, int n2, int n3) {
+  if (!(n1 == n2 && n2 == n3 && n1 >= 2 && n1 <= 4) || np < 2 || np % 2) return 0;
+  const int L = n2 * n3, EPW = 32 / n1, LP = (L + 1) / 2, KWR = n1 * LP;
+  const long nqb = (np + EPW - 1) / EPW, npb = (np + 7) / 8;
+  return (nqb + npb) * np * KWR + npb + 1;   // row keys, column keys, tile prefix
+}
+
+cudaError_t kconv_herm_prepare(uint32_t* keys, int np, int n1, int n2, int n3, cudaStream_t s) {
+  if (kconv_herm_key_words(np, n1, n2, n3) == 0 || !keys) return cudaErrorInvalidValue;
+  const int L = n2 * n3, EPW = 32 / n1, LP = (L + 1) / 2, KWR = n1 * LP;
+  const long nqb = (np + EPW - 1) / EPW, npb = (np + 7) / 8;
+  herm_tile_prefix<<<1, 32, 0, s>>>(reinterpret_cast<int*>(keys + (nqb + npb) * np * KWR), np, EPW);
+  return cudaGetLastError();
+}
+
+cudaError_t kconv_c_herm(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
+                         uint32_t* keys, int* e, int* err, cudaEvent_t started, cudaEvent_t conv_done,
+                         cudaStream_t s) {
+  if (kconv_herm_key_words(np, n1, n2, n3) == 0 || !keys || !err || ((uintptr_t)D & 15) || ((uintptr_t)Vh & 15))
+    return cudaErrorInvalidValue;
+  cudaError_t r = started ? cudaEventRecord(started, s) : cudaSuccess;
+  if (r != cudaSuccess) return r;
+  if (n1 == 4) return kconv_herm_launch<4, 4, 4>(D, Vh, M, np, keys, e, err, conv_done, s);
+  if (n1 == 3) return kconv_herm_launch<3, 3, 3>(D, Vh, M, np, keys, e, err, conv_done, s);
+  return kconv_herm_launch<2, 2, 2>(D, Vh, M, np, keys, e, err, conv_done, s);
+}
 
 cudaError_t kconv_c_rowexp(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3, int* e,
                            bool* done, int* err, cudaEvent_t started, cudaEvent_t conv_done, cudaStream_t s) {

@@ -127,6 +127,46 @@ cudaError_t ex_reduce_c(const float2* Psi, const float2* Y, long n, int nk, doub
   return cudaGetLastError();
 }
 
+__global__ void herm_dev_kernel(const double2* __restrict__ V, int np, long n, unsigned long long* out) {
+  double dev = 0.0, mx = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long k = i / ((long)np * np), r = i - k * np * np;
+    const int p = (int)(r / np), q = (int)(r - (long)p * np);
+    const double2 a = V[i], b = V[k * np * np + (long)q * np + p];
+    dev = fmax(dev, fmax(fabs(a.x - b.x), fabs(a.y + b.y)));
+    mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, (unsigned long long)__double_as_longlong(dev));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+__global__ void herm_fill_kernel(const float2* __restrict__ D, double2* __restrict__ out, int np, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long k = i / ((long)np * np), r = i - k * np * np;
+    const int p = (int)(r / np), q = (int)(r - (long)p * np);
+    const float2 v = q >= p ? D[i] : D[k * np * np + (long)q * np + p];
+    out[i] = make_double2(v.x, q >= p ? v.y : -v.y);
+  }
+}
+
+cudaError_t hermitian_deviation_z(const double2* V, int np, int nk, unsigned long long* out, cudaStream_t s) {
+  const long n = (long)nk * np * np;
+  herm_dev_kernel<<<grid_for(n, 256), 256, 0, s>>>(V, np, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t hermitian_fill_c2z(const float2* D, double2* out, int np, int nk, cudaStream_t s) {
+  const long n = (long)nk * np * np;
+  herm_fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(D, out, np, n);
+  return cudaGetLastError();
+}
+
 cudaError_t convert_z2c(const double2* in, float2* out, long n, cudaStream_t s) {
   z2c_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
   return cudaGetLastError();

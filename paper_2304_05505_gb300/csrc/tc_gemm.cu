@@ -94,15 +94,6 @@ template <bool CV> struct Roles {
   static constexpr int COLS = 4 * BN / EPI;                     // columns of a unit per epilogue warp
 };
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
-                                            int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
-      "%4, %5}], [%2];" ::"r"(dst),
-      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
-
 // K-major operand tile, 64B swizzle: rows of 64 B, 8-row groups 512 B apart.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
@@ -192,7 +183,7 @@ struct Geometry {
   int mt, nt, nchunk, nkb;   // tiles along M and N, K chunks, K blocks
   int ckb;                   // K blocks per chunk
   long units;
-  int herm;                  // Hermitian product: tiles on or above the diagonal only
+  int herm;                  // Hermitian product: tiles reaching the diagonal only (1: mirrored, 2: upper part)
   long upb;                  // units per batch entry when herm
 };
 
@@ -568,7 +559,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
               y[j + 3] = (va[j + 3] + vb[j + 3]) * s1;
               *reinterpret_cast<float4*>(stg + stage_off(lane, j >> 2)) = make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]);
             }
-            if (g.herm) {
+            if (g.herm == 1) {
               // the mirror image below the diagonal: out[Q][P] = conj(out[P][Q]) for Q > P,
               // lanes = consecutive P, so each store instruction writes 256 contiguous bytes
               const int P = row0 + lane;
@@ -752,6 +743,23 @@ cudaError_t make_f32_map(void* map_out, const void* base, int batch, int rows, i
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t make_f32_map_3d(void* map_out, const void* base, long d0, long d1, long d2, long s1_bytes,
+                            long s2_bytes, int b0, int b1, int b2) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  if (((uintptr_t)base & 15) || s1_bytes % 16 || s2_bytes % 16 || (b0 * 4) % 16 || b0 > 256 || b1 > 256 ||
+      b2 > 256)
+    return cudaErrorInvalidValue;
+  cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+  cuuint64_t strides[2] = {(cuuint64_t)s1_bytes, (cuuint64_t)s2_bytes};
+  cuuint32_t box[3] = {(cuuint32_t)b0, (cuuint32_t)b1, (cuuint32_t)b2};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t make_f32_map_2d(void* map_out, const void* base, long inner, long outer, long stride_bytes, int box0,
                             int box1) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
@@ -788,7 +796,7 @@ long tc_partial_elems(int M, int Nr, int Kr, int batch) {
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
-                    cudaEvent_t gemm_done, int slices, bool a_f32, bool herm) {
+                    cudaEvent_t gemm_done, int slices, bool a_f32, int herm) {
   if (slices != 3 && slices != 4) return cudaErrorInvalidValue;
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   Maps maps;
@@ -804,7 +812,8 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   g.ckb = tc_chunk_blocks(M, Nr, Kr, batch);
   g.nchunk = (g.nkb + g.ckb - 1) / g.ckb;
   g.units = (long)batch * g.mt * g.nt * g.nchunk;
-  g.herm = herm ? 1 : 0;
+  if (herm < 0 || herm > 2) return cudaErrorInvalidValue;
+  g.herm = herm;
   g.upb = 0;
   if (herm) {
     // a Hermitian FP32 product written whole: square, one chunk, FP32 interleaved output

@@ -26,14 +26,16 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
 // (all four planes, 10 slice products) or 3 (the first three planes, the 6
 // products s + t <= 2: about 2^-24 of the row scales).  a_f32: A.map[0] is an
 // FP32 map (make_f32_map) of the interleaved complex A, cut into its four
-// slices inside the kernel with the row exponents eA.  herm: the product is
-// Hermitian (B built from conj(A), Nr = 2 M, one K chunk, FP32 output): only
-// the tiles that reach the diagonal are computed, and each writes its values
-// on or above the diagonal and their conjugates at the mirrored positions.
+// slices inside the kernel with the row exponents eA.  herm (1 or 2): the
+// product is Hermitian (B built from conj(A), Nr = 2 M, one K chunk, FP32
+// output): only the tiles that reach the diagonal are computed, and each
+// writes its values on or above the diagonal, and with herm = 1 also their
+// conjugates at the mirrored positions (herm = 2 leaves the part below the
+// diagonal unwritten).
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
-                    cudaEvent_t gemm_done = nullptr, int slices = 4, bool a_f32 = false, bool herm = false);
+                    cudaEvent_t gemm_done = nullptr, int slices = 4, bool a_f32 = false, int herm = 0);
 
 // Map of an FP32 matrix [batch][rows][ld floats] (cols valid) in 32-float K
 // boxes of 128 rows with 128B swizzle (ld * 4 bytes a multiple of 16).
@@ -44,6 +46,12 @@ cudaError_t make_f32_map(void* map_out, const void* base, int batch, int rows, i
 // box1 rows, no swizzle, zero past the ends.
 cudaError_t make_f32_map_2d(void* map_out, const void* base, long inner, long outer, long stride_bytes, int box0,
                             int box1);
+
+// Map of a 3-D FP32 array [d2][d1][d0] (strides s1_bytes, s2_bytes, multiples
+// of 16) read as boxes b0 x b1 x b2 (b0 * 4 bytes a multiple of 16), no
+// swizzle, zero past the ends.
+cudaError_t make_f32_map_3d(void* map_out, const void* base, long d0, long d1, long d2, long s1_bytes,
+                            long s2_bytes, int b0, int b1, int b2);
 
 // 32-wide real-K blocks per chunk of a product of this shape: the fewest
 // chunks of at most 32 blocks (the exact leading sums), of equal length; a

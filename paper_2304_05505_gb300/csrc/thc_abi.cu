@@ -40,6 +40,7 @@ struct Sizes {
   long plXn, plXT, plPs, plBc, plBd, plBy, plM;
   long nexp;  // exponents: eXn + eXT + ePsi + eC + eY + eM
   long npart; // split-K partial elements (max over the tensor-core GEMMs)
+  long hkey;  // key words of the Hermitian convolution (0 where it does not apply)
 };
 
 int pad8(int x) { return (x + 7) & ~7; }
@@ -67,6 +68,7 @@ Sizes sizes_of(const thc_dims* d, int precision) {
                       tc_partial_elems(d->nisdf, 2 * d->nisdf, 2 * d->nocc, (int)s.nk),
                       tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nisdf, (int)s.nk),
                       tc_partial_elems(d->nbas, 2 * d->nocc, 2 * d->nisdf, (int)s.nk)});
+  s.hkey = precision == THC_MIXED ? kconv_herm_key_words(d->nisdf, d->n1, d->n2, d->n3) : 0;
   return s;
 }
 
@@ -95,6 +97,7 @@ size_t memory_bytes(const thc_dims* d, int precision) {
     b += 4 * 2 * (s.plXn + s.plXT + s.plPs + s.plBc + s.plBd + s.plBy + s.plM);   // bf16 slices
     b += sizeof(int) * s.nexp + 64;                                         // exponents, error word
     b += (sizeof(int) + sizeof(float)) * s.npart;                           // split-K partial sums
+    b += sizeof(uint32_t) * s.hkey;                                          // Hermitian convolution keys
   } else {
     b += s.x * s.el;             // X copy
   }
@@ -107,7 +110,7 @@ void free_all(thc_ctx* c) {
   void* ptrs[] = {c->X64, c->Vh64, c->X32, c->Vh32, c->Psi, c->D, c->M, c->Y,
                   c->Cdev, c->KCdev, c->exdev, c->partial, c->flag, c->Xn_pl, c->XT_pl,
                   c->PsiA_pl, c->Bc_pl, c->Bd_pl, c->By_pl, c->ex_pl, c->tc_err, c->part_s0,
-                  c->part_bc, c->M_pl};
+                  c->part_bc, c->M_pl, c->hkeys};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 7; i++)
@@ -199,6 +202,7 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
       W((void**)&c->part_s0, sizeof(int) * s.npart);
       W((void**)&c->part_bc, sizeof(float) * s.npart);
     }
+    if (s.hkey > 0) W((void**)&c->hkeys, sizeof(uint32_t) * s.hkey);
   }
   W(&c->Psi, s.psi * s.el);
   W(&c->Y, s.psi * s.el);
@@ -257,6 +261,10 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
         e = make_plane_map(c->opM.map[p], c->M_pl + p * s.plM, nk, P, 2 * P, s.ldM);
     else
       e = make_f32_map(c->opMf.map[0], c->M, nk, P, 2 * P, 2 * P);
+    if (e == cudaSuccess && c->hkeys) {
+      e = kconv_herm_prepare(c->hkeys, P, d->n1, d->n2, d->n3, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
     if (e != cudaSuccess) {
       g_create_error = std::string("cuTensorMapEncodeTiled: ") + cudaGetErrorString(e);
       free_all(c);
@@ -326,6 +334,21 @@ thc_status thc_set_kernel(thc_ctx* c, const double* V) {
   thc_status st = finite_check(c, v, npq * c->nk);
   if (st != THC_OK) return st;
   CKC(c, prepare_kernel_z(v, c->Vh64, c->Vh32, npq, c->n1, c->n2, c->n3, c->stream));
+  c->herm_v = false;
+  if (c->hkeys) {
+    // every V^q Hermitian to 1e-12 of max |V|: then M^k is Hermitian and the
+    // build convolves the part of D on and above the diagonal only
+    unsigned long long* dv = reinterpret_cast<unsigned long long*>(c->partial);
+    CKC(c, cudaMemsetAsync(dv, 0, 2 * sizeof(unsigned long long), c->stream));
+    CKC(c, hermitian_deviation_z(v, c->nisdf, c->nk, dv, c->stream));
+    unsigned long long h[2] = {0, 0};
+    CKC(c, cudaMemcpyAsync(h, dv, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CKC(c, cudaStreamSynchronize(c->stream));
+    double dev, mx;
+    memcpy(&dev, &h[0], sizeof dev);
+    memcpy(&mx, &h[1], sizeof mx);
+    c->herm_v = dev <= 1e-12 * mx;
+  }
   CKC(c, cudaStreamSynchronize(c->stream));
   c->have_v = true;
   return THC_OK;
@@ -440,15 +463,23 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, record_core(c, 1, 0, s));
   // D is rounded to FP32 on output and K = 2 n is short: three slices; D is
   // Hermitian, so only the tiles that reach the diagonal are multiplied
+  // (Hermitian V: M^k is Hermitian too, and S3 reads D on and above the
+  // diagonal only, so S2 leaves the part below it unwritten)
+  const bool a_f32 = c->plM == 0;
+  const bool herm = c->herm_v && c->hkeys && a_f32;
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
-                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 1, 1), 3, false, true));
+                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 1, 1), 3, false, herm ? 2 : 1));
+  c->d_upper = herm;
   CKC(c, mark(c, 2, s, false));
   // S3  M = IDFT(DFT(D) o Vh) in FP32
   // (2^3, 3^3 and 4^3 meshes: the convolution also finds the exact row
   // exponents of M that S4a slices it with)
-  const bool a_f32 = c->plM == 0;
   bool have_eM = false;
-  if (a_f32) {
+  if (herm) {
+    CKC(c, kconv_c_herm(D, c->Vh32, M, P, c->n1, c->n2, c->n3, c->hkeys, c->eM, c->tc_err, core_event(c, 2, 0),
+                        core_event(c, 2, 1), s));
+    have_eM = true;
+  } else if (a_f32) {
     CKC(c, kconv_c_rowexp(D, c->Vh32, M, P, c->n1, c->n2, c->n3, c->eM, &have_eM, c->tc_err,
                           core_event(c, 2, 0), core_event(c, 2, 1), s));
   } else {
@@ -552,7 +583,9 @@ thc_status thc_get_intermediate(thc_ctx* c, int which, double* out) {
   const long n = (which == 0 || which == 3) ? (long)c->nk * c->nisdf * c->nocc
                                             : (long)c->nk * c->nisdf * c->nisdf;
   void* src = which == 0 ? c->Psi : which == 1 ? c->D : which == 2 ? c->M : c->Y;
-  if (c->precision == THC_FP64)
+  if (which == 1 && c->precision == THC_MIXED && c->d_upper)
+    CKC(c, hermitian_fill_c2z((const float2*)src, (double2*)out, c->nisdf, c->nk, c->stream));
+  else if (c->precision == THC_FP64)
     CKC(c, cudaMemcpyAsync(out, src, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
   else
     CKC(c, convert_c2z((const float2*)src, (double2*)out, n, c->stream));

@@ -86,6 +86,9 @@ struct thc_ctx {
   TcOperand opMf;     // map[0]: FP32 map of M (A of S4a, converted in the GEMM), even nisdf
   TcOperand opM;      // M's slices, odd nisdf
   int* tc_err;        // device word: nonzero after a device wait gave up
+  uint32_t* hkeys;    // row and column keys of the Hermitian convolution (when its form applies)
+  bool herm_v;        // every V^q Hermitian (to 1e-12 of max |V|): S2 writes D's upper part, S3 mirrors M
+  bool d_upper;       // the last build left D's part below the diagonal unwritten
   cudaEvent_t ev[7];               // stage boundaries of the last build
   std::vector<cudaEvent_t> prof;   // per profiled build: 7 stage boundaries, then the
                                    // start and end of each stage's main kernel (12)
@@ -133,12 +136,32 @@ cudaError_t kconv_c(const float2* D, const float2* Vh, float2* M, long npq, int 
 // 2^-133, else 0; *done tells whether e was written.  err receives a nonzero
 // code if a device wait gave up.  started / conv_done (may be null) are
 // recorded on s right before and right after the convolution kernel.
+// Key scratch (32-bit words) of kconv_c_herm for this shape; 0 where the
+// Hermitian form does not apply (meshes other than 2^3, 3^3, 4^3, odd np).
+long kconv_herm_key_words(int np, int n1, int n2, int n3);
+// Writes the tile table of the Hermitian convolution into its key scratch
+// (once, when the context is made).
+cudaError_t kconv_herm_prepare(uint32_t* keys, int np, int n1, int n2, int n3, cudaStream_t s);
+// The convolution for Hermitian D^k and V^q (M^k Hermitian): reads the
+// tiles of D and Vh that reach the diagonal only (D's part below it is never
+// read), writes all of M, and the row exponents e of M as kconv_c_rowexp.
+// keys: kconv_herm_key_words words of scratch.
+cudaError_t kconv_c_herm(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
+                         uint32_t* keys, int* e, int* err, cudaEvent_t started, cudaEvent_t conv_done,
+                         cudaStream_t s);
 cudaError_t kconv_c_rowexp(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
                            int* e, bool* done, int* err, cudaEvent_t started, cudaEvent_t conv_done,
                            cudaStream_t s);
 // Vh[a] = (1/N_k) sum_q V[q] w^{+a.q} in FP64; writes FP64 or FP32 output.
 cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long npq, int n1,
                              int n2, int n3, cudaStream_t s);
+
+// max |V - V^H| and max |V| over the nk matrices [np][np] of V: out[0], out[1]
+// as the bits of non-negative doubles (atomicMax; the caller zeroes out).
+cudaError_t hermitian_deviation_z(const double2* V, int np, int nk, unsigned long long* out, cudaStream_t s);
+// out (complex128) = D, with the part below each diagonal filled from the
+// conjugate of the part above (D written by a herm = 2 GEMM).
+cudaError_t hermitian_fill_c2z(const float2* D, double2* out, int np, int nk, cudaStream_t s);
 
 // E_x = -(1/nk) sum conj(Psi) Y, FP64 accumulation, deterministic two-pass.
 cudaError_t ex_reduce_z(const double2* Psi, const double2* Y, long n, int nk, double* partial,

@@ -274,3 +274,20 @@ def test_row_exponents_of_M(torch_cuda, mesh, nisdf):
         assert np.array_equal(got, ref.astype(np.float64))
         if not V.any():
             assert not got.any()
+
+
+@pytest.mark.parametrize("mesh,nisdf", [((4, 4, 4), 70), ((3, 3, 3), 52), ((2, 2, 2), 130)])
+def test_non_hermitian_kernel_parity(torch_cuda, mesh, nisdf):
+    """The build does not assume a Hermitian V: with V^q made non-Hermitian the
+    mixed build takes the full convolution (every element of D read) and still
+    matches the oracle; with the Hermitian V of the same problem it takes the
+    form that reads D and Vh on and above the diagonal only."""
+    r = cells.random_problem(mesh, nbas=11, nocc=4, nisdf=nisdf, seed=nisdf + 1)
+    rng = np.random.default_rng(nisdf)
+    Vn = r["V"] + 0.05 * np.abs(r["V"]).max() * (rng.normal(size=r["V"].shape) + 1j * rng.normal(size=r["V"].shape))
+    for V in (Vn, r["V"]):
+        ref = O.build(r["X"], r["C"], V, r["mesh"], keep=True)
+        got = gpu_build(torch_cuda, r["X"], r["C"], V, r["mesh"], "mixed", keep=True)
+        assert_close(ref, got, "mixed")
+        err = np.abs(got["M"] - ref["M"]).max() / np.abs(ref["M"]).max()
+        assert err < 2e-6, err
