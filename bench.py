@@ -37,10 +37,11 @@ SAMPLE_FRACTION = 8      # the CPU oracle sample is 1/8 of a build
 # bf16 slice products per real product of each tensor-core GEMM
 SLICE_PRODUCTS = {"S1_collocate": 10, "S2_density": 6, "S4a_apply_M": 10, "S4b_backproject": 10}
 # the main kernel of each stage of the tensor-core build
-KERNEL_NAMES = {"S1_collocate": "tc_gemm_kernel<2, 4> (S1, split-K)", "S2_density": "tc_gemm_kernel<0, 3> (S2)",
-                "S3_kconv": "kconv_lanes_kernel<4, 4, 4> (S3)",
-                "S4a_apply_M": "tc_gemm_kernel<2, 4> (S4a, split-K)",
-                "S4b_backproject": "tc_gemm_kernel<2, 4> (S4b, split-K)",
+KERNEL_NAMES = {"S1_collocate": "tc_gemm_kernel<0, 4, 0, 0> (S1)",
+                "S2_density": "tc_gemm_kernel<0, 3, 1, 0> (S2, Hermitian tiles)",
+                "S3_kconv": "kconv_herm_kernel<4, 4, 4> (S3, Hermitian tiles)",
+                "S4a_apply_M": "tc_gemm_kernel<2, 4, 0, 1> (S4a, split-K, M sliced in the GEMM)",
+                "S4b_backproject": "tc_gemm_kernel<2, 4, 0, 0> (S4b, split-K)",
                 "S5_energy": "ex_partial_c + ex_final (S5)"}
 
 
@@ -158,17 +159,21 @@ def peaks() -> dict:
                 source="fallback")
 
 
-def stage_work(d: dict) -> dict:
+def stage_work(d: dict, hermitian: bool = False) -> dict:
     """Algorithmic work of each stage's main kernel in one build: complex
     multiply-adds at 8 flops, and the arrays the step must read and write once
-    at complex64 (KC and the C input at complex128)."""
+    at complex64 (KC and the C input at complex128).  In the Hermitian form
+    (every V^q Hermitian, so D^k and M^k are) S2 forms and writes the
+    P (P + 1) / 2 elements of D on and above the diagonal, and S3 reads that
+    half of D and of the prepared kernel and writes all of M."""
     nk = d["n1"] * d["n2"] * d["n3"]
     N, n, P = d["nbas"], d["nocc"], d["nisdf"]
     c64 = 8
+    half = P * (P + 1) / 2 if hermitian else P * P
     return {
         "S1_collocate": dict(flops=8.0 * nk * P * n * N, bytes=c64 * nk * (N * P + P * n) + 16 * nk * N * n),
-        "S2_density": dict(flops=8.0 * nk * P * P * n, bytes=c64 * nk * (P * n + P * P)),
-        "S3_kconv": dict(flops=None, bytes=3.0 * c64 * nk * P * P),
+        "S2_density": dict(flops=8.0 * nk * half * n, bytes=c64 * nk * (P * n + half)),
+        "S3_kconv": dict(flops=None, bytes=c64 * nk * (2.0 * half + P * P)),
         "S4a_apply_M": dict(flops=8.0 * nk * P * P * n, bytes=c64 * nk * (P * P + 2 * P * n)),
         "S4b_backproject": dict(flops=8.0 * nk * N * n * P, bytes=c64 * nk * (N * P + P * n) + 16 * nk * N * n),
         "S5_energy": dict(flops=None, bytes=2.0 * c64 * nk * P * n),
@@ -327,6 +332,7 @@ def run_ours(args, world, rank, local):
     eb = thc.ExchangeBuild(d, "mixed", device=dev, stream=stream)
     eb.set_collocation(p.X)
     eb.set_kernel(p.V)
+    hermitian = thc.thc_hermitian_kernel(eb.ctx)
     C = torch.from_numpy(p.C).to(dev)
     KC = torch.empty(eb.kc_shape, dtype=torch.complex128, device=dev)
     ex = torch.empty(2, dtype=torch.float64, device=dev)
@@ -422,7 +428,7 @@ def run_ours(args, world, rank, local):
     if rank != 0:
         return
     pk = peaks()
-    work = stage_work(d)
+    work = stage_work(d, hermitian)
     names = thc.STAGES
     stages = {nm: ms for nm, ms in zip(names, stage_ms)}
     kernels = {nm: ms for nm, ms in zip(names, kernel_ms)}
@@ -438,6 +444,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": WORKLOAD,
                        "precision": "mixed: S1/S4a/S4b tcgen05 bf16 GEMMs on 4-slice fixed-point operands, S2 on "
                                     "3 slices (exact leading sums, FP32 remainders), S3 FP32, E_x FP64 sum",
+                       "hermitian_form": hermitian,
                        "l2": "inputs larger than L2 (prepared kernel 737 MB, X 265 MB complex64)",
                        "parallelism": f"{world} independent builds (one per GPU)"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,

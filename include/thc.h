@@ -150,6 +150,13 @@ thc_status thc_sync(thc_ctx* ctx);
 /* Number of kernel launches one thc_build makes. */
 thc_status thc_launches_per_build(const thc_ctx* ctx, int* launches);
 
+/* *hermitian = 1 when the builds take the Hermitian form (THC_MIXED on a
+ * 2^3, 3^3 or 4^3 mesh with even nisdf, and the V of the last thc_set_kernel
+ * Hermitian for every q to 1e-12 of max |V|): then M^k is Hermitian, S2
+ * writes D on and above the diagonal only and S3 reads that half of D and of
+ * the prepared kernel; else 0.  THC_ERR_STATE before thc_set_kernel. */
+thc_status thc_hermitian_kernel(const thc_ctx* ctx, int* hermitian);
+
 thc_status thc_destroy(thc_ctx* ctx);
 
 /* Interpolation points (setup, outside the timed build).  Greedy pivoted

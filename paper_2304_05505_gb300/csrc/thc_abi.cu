@@ -651,6 +651,13 @@ thc_status thc_profile_kernels(const thc_ctx* c, float core_ms[6]) {
   return THC_OK;
 }
 
+thc_status thc_hermitian_kernel(const thc_ctx* c, int* hermitian) {
+  if (!c || !hermitian) return THC_ERR_ARG;
+  if (!c->have_v) return THC_ERR_STATE;
+  *hermitian = (c->precision == THC_MIXED && c->herm_v && c->hkeys && c->plM == 0) ? 1 : 0;
+  return THC_OK;
+}
+
 thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   if (!c || !launches) return THC_ERR_ARG;
   // FP64 and CUDA-core forms: S1, S2, S3, S4a, S4b, E_x partial, E_x final.

@@ -27,7 +27,7 @@ STATUS = {0: "THC_OK", 1: "THC_ERR_ARG", 2: "THC_ERR_OOM", 3: "THC_ERR_CUDA",
 
 EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_kernel",
            "thc_build", "thc_build_host", "thc_get_intermediate", "thc_stage_times",
-           "thc_launches_per_build", "thc_destroy", "thc_status_string", "thc_last_error",
+           "thc_launches_per_build", "thc_hermitian_kernel", "thc_destroy", "thc_status_string", "thc_last_error",
            "thc_profile_begin", "thc_profile_end", "thc_sync", "thc_kconv_noalloc",
            "thc_select_points", "thc_fit_kernel", "thc_profile_kernels", "thc_mlp_features", "thc_mlp_score",
            "thc_mlp_workspace_bytes", "thc_mlp_train_step", "thc_mlp_candidates", "thc_select_points_among"]
@@ -68,6 +68,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_get_intermediate.argtypes = [vp, ip, dp]
     lib.thc_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.thc_launches_per_build.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.thc_hermitian_kernel.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.thc_profile_begin.argtypes = [vp, ip]
     lib.thc_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]
     lib.thc_profile_kernels.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
@@ -219,6 +220,13 @@ def thc_stage_times(ctx) -> list:
     arr = (ctypes.c_float * 6)()
     _check(load().thc_stage_times(ctx, arr), "thc_stage_times", ctx)
     return [float(x) for x in arr]
+
+
+def thc_hermitian_kernel(ctx) -> bool:
+    """Whether the builds take the Hermitian form (see include/thc.h)."""
+    n = ctypes.c_int(0)
+    _check(load().thc_hermitian_kernel(ctx, ctypes.byref(n)), "thc_hermitian_kernel", ctx)
+    return bool(n.value)
 
 
 def thc_launches_per_build(ctx) -> int:

@@ -43,7 +43,8 @@ def gpu_build(torch, X, C, V, mesh, precision, keep=False):
         eb.set_kernel(V)
         KC, ex = eb.build(C)
         eb.sync()      # raises on a device-side wait that gave up
-        out = dict(KC=KC.cpu().numpy(), Ex=float(ex[0]), Ex_imag=float(ex[1]))
+        out = dict(KC=KC.cpu().numpy(), Ex=float(ex[0]), Ex_imag=float(ex[1]),
+                   hermitian=thc.thc_hermitian_kernel(eb.ctx))
         if keep:
             for i, nm in enumerate(["Psi", "D", "M", "Y"]):
                 out[nm] = eb.intermediate(i).cpu().numpy()
@@ -285,9 +286,10 @@ def test_non_hermitian_kernel_parity(torch_cuda, mesh, nisdf):
     r = cells.random_problem(mesh, nbas=11, nocc=4, nisdf=nisdf, seed=nisdf + 1)
     rng = np.random.default_rng(nisdf)
     Vn = r["V"] + 0.05 * np.abs(r["V"]).max() * (rng.normal(size=r["V"].shape) + 1j * rng.normal(size=r["V"].shape))
-    for V in (Vn, r["V"]):
+    for V, herm in ((Vn, False), (r["V"], True)):
         ref = O.build(r["X"], r["C"], V, r["mesh"], keep=True)
         got = gpu_build(torch_cuda, r["X"], r["C"], V, r["mesh"], "mixed", keep=True)
+        assert got["hermitian"] is herm
         assert_close(ref, got, "mixed")
         err = np.abs(got["M"] - ref["M"]).max() / np.abs(ref["M"]).max()
         assert err < 2e-6, err
