@@ -165,16 +165,18 @@ __device__ __forceinline__ double pow2d(int e) {
   return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
 
-// The four fixed-point slices of y = 2^(7 - e) x (|y| <= 128) as bf16 bit
-// patterns: each slice is an integer of at most 8 significant bits times
-// 2^-8p, exact in bf16, so its bf16 bits are the top half of its FP32 bits.
-__device__ __forceinline__ void slice4_bits(float y, uint32_t* bits) {
-  const float inv[4] = {1.0f, 0x1p-8f, 0x1p-16f, 0x1p-24f};
+// The four fixed-point slices P_s = S_s 2^-8s of y = 2^(7 - e) x (|y| <= 255)
+// as FP32 values: the rounding of the remainder to a multiple of 2^-8s (to
+// nearest, ties to even, as rint) is an add and a subtract of
+// 1.5 * 2^(23 - 8s), exact for these magnitudes, and each remainder y - P_s is
+// exact.  Each P_s is an integer of at most 8 significant bits times 2^-8s,
+// exact in bf16, so its bf16 bits are the top half of its FP32 bits.
+__device__ __forceinline__ void slice4_planes(float y, float* p) {
+  const float magic[4] = {0x1.8p23f, 0x1.8p15f, 0x1.8p7f, 0x1.8p-1f};
 #pragma unroll
-  for (int p = 0; p < 4; p++) {
-    const float sp = rintf(y);
-    bits[p] = __float_as_uint(sp * inv[p]) >> 16;
-    y = (y - sp) * 256.0f;
+  for (int s = 0; s < 4; s++) {
+    p[s] = __fsub_rn(__fadd_rn(y, magic[s]), magic[s]);
+    y = __fsub_rn(y, p[s]);
   }
 }
 
@@ -464,14 +466,14 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
           const float4 f0 = *reinterpret_cast<const float4*>(src + r * 128 + 16 * ((2 * pc) ^ (r & 7)));
           const float4 f1 = *reinterpret_cast<const float4*>(src + r * 128 + 16 * ((2 * pc + 1) ^ (r & 7)));
           const float x[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-          uint32_t w[4][4];   // [plane][pair of reals]
+          uint32_t w[4][4];   // [plane][pair of reals]: the bf16 halves of two FP32 slices
 #pragma unroll
           for (int j = 0; j < 8; j += 2) {
-            uint32_t lo[4], hi[4];
-            slice4_bits(x[j] * sc, lo);
-            slice4_bits(x[j + 1] * sc, hi);
+            float lo[4], hi[4];
+            slice4_planes(x[j] * sc, lo);
+            slice4_planes(x[j + 1] * sc, hi);
 #pragma unroll
-            for (int p = 0; p < 4; p++) w[p][j >> 1] = lo[p] | (hi[p] << 16);
+            for (int p = 0; p < 4; p++) w[p][j >> 1] = __byte_perm(__float_as_uint(lo[p]), __float_as_uint(hi[p]), 0x7632);
           }
           // bf16 row r of each plane, 64B swizzle: chunk pc at r * 64 + 16 (pc ^ ((r >> 1) & 3))
           const uint32_t off = r * 64 + 16 * (pc ^ ((r >> 1) & 3));
