@@ -137,8 +137,8 @@ __global__ void embed_kernel(const CT* __restrict__ src, long sbs, long ldk, lon
     uint16_t s_br[4], s_bi[4], s_nbr[4], s_nbi[4];
     slice4(br, ex, s_br);
     slice4(bi, ex, s_bi);
-    slice4(-br, ex, s_nbr);
-    slice4(-bi, ex, s_nbi);
+    negate4(s_br, s_nbr);
+    negate4(s_bi, s_nbi);
     if (!conj_a) {
       store4(planes, plane, row0, s_br, s_nbi);
       store4(planes, plane, row0 + ldp, s_bi, s_br);
