@@ -123,12 +123,12 @@ template <typename CT, typename R>
 __global__ void embed_kernel(const CT* __restrict__ src, long sbs, long ldk, long ldj, bool conj_src,
                              bool conj_a, int batch, int K, int J, const int* __restrict__ e, uint16_t* planes,
                              long plane, int ldp) {
-  const long total = (long)batch * J * K;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int k = (int)(i % K);
-    const long bj = i / K;
-    const int j = (int)(bj % J);
-    const int b = (int)(bj / J);
+  // grid: x over K, y over the rows j (blockDim.y per block), z over the batch
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int b = blockIdx.z;
+  if (k < K && j < J) {
+    const long bj = (long)b * J + j;
     const CT v = src[(long)b * sbs + (long)k * ldk + (long)j * ldj];
     const R br = (R)v.x;
     const R bi = conj_src ? -(R)v.y : (R)v.y;
@@ -312,13 +312,18 @@ cudaError_t row_exponents_rows(const float2* src, int np, long rows, int* e, cud
 cudaError_t embed_b(const void* src, bool src_f64, long sbs, long ldk, long ldj, bool conj_src, bool conj_a,
                     int batch, int K, int J, const int* e, uint16_t* planes, long plane, int ldp,
                     cudaStream_t s) {
-  const long n = (long)batch * J * K;
+  if ((long)batch * J * K == 0) return cudaSuccess;
+  // 256 threads: up to 128 consecutive K (one write segment per plane row), the rest over rows
+  const int kw = K > 64 ? 128 : K > 32 ? 64 : 32;
+  const dim3 blk(kw, 256 / kw);
+  if (batch > 65535 || (J + (int)blk.y - 1) / (int)blk.y > 65535) return cudaErrorInvalidValue;
+  const dim3 grid((K + kw - 1) / kw, (J + blk.y - 1) / blk.y, batch);
   if (src_f64)
-    embed_kernel<double2, float><<<grid1(n), 256, 0, s>>>((const double2*)src, sbs, ldk, ldj, conj_src, conj_a, batch,
-                                                   K, J, e, planes, plane, ldp);
+    embed_kernel<double2, float><<<grid, blk, 0, s>>>((const double2*)src, sbs, ldk, ldj, conj_src, conj_a, batch, K,
+                                                   J, e, planes, plane, ldp);
   else
-    embed_kernel<float2, float><<<grid1(n), 256, 0, s>>>((const float2*)src, sbs, ldk, ldj, conj_src, conj_a, batch, K,
-                                                  J, e, planes, plane, ldp);
+    embed_kernel<float2, float><<<grid, blk, 0, s>>>((const float2*)src, sbs, ldk, ldj, conj_src, conj_a, batch, K, J,
+                                                  e, planes, plane, ldp);
   return cudaGetLastError();
 }
 
