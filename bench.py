@@ -213,26 +213,37 @@ def kernel_roofline(stage: str, ms: float, work: dict, pk: dict) -> dict:
     return out
 
 
-def source_hash() -> str:
+# the sources that define each stage's main kernel and its launch (the
+# measured traffic of a capture stays valid while these are unchanged)
+KERNEL_SOURCES = {
+    "S1_collocate": ("tc_gemm.cu", "tc_gemm.cuh", "slices.cuh", "mbarrier.cuh", "thc_abi.cu"),
+    "S2_density": ("tc_gemm.cu", "tc_gemm.cuh", "slices.cuh", "mbarrier.cuh", "thc_abi.cu"),
+    "S3_kconv": ("kconv.cu", "mbarrier.cuh", "thc_internal.cuh", "thc_abi.cu"),
+    "S4a_apply_M": ("tc_gemm.cu", "tc_gemm.cuh", "slices.cuh", "mbarrier.cuh", "thc_abi.cu"),
+    "S4b_backproject": ("tc_gemm.cu", "tc_gemm.cuh", "slices.cuh", "mbarrier.cuh", "thc_abi.cu"),
+}
+
+
+def source_hash(stage: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2304_05505_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[stage]:
+        h.update(f.encode())
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def measured_traffic(stage: str):
     """DRAM bytes per launch from the committed ncu capture, if it was taken
-    on the current kernel sources; else None."""
+    on the current sources of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or stage not in KERNEL_SOURCES:
         return None
     try:
         t = json.load(open(path))
     except Exception:
         return None
-    if t.get("source_hash") != source_hash():
+    if t.get("source_hashes", {}).get(stage) != source_hash(stage):
         return None
     v = t.get("per_launch_bytes", {}).get(stage)
     return float(v) if v is not None else None
