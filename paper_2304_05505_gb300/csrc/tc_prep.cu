@@ -43,31 +43,49 @@ __global__ void rowexp_kernel(const CT* __restrict__ src, long sbs, int lds, int
 
 // Exponent of each column: e[b * cols + c] = max over r of src[b][r][c].
 // Block (b, column slab of 32) of 32 warps: warp w scans rows w, w + 32, ...
-// four at a time (lane = column), then the warps' maxima are combined.
+// four at a time (lane = column), then the warps' maxima are combined.  The
+// maxima are taken on the absolute values' bit patterns (non-negative floats
+// order as unsigned integers), exact and off the FP64 pipe.
+template <typename CT> struct AbsBits;
+template <> struct AbsBits<float2> {
+  typedef unsigned T;
+  __device__ static T of(float2 v) { return max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu); }
+  __device__ static double value(T t) { return (double)__uint_as_float(t); }
+};
+template <> struct AbsBits<double2> {
+  typedef unsigned long long T;
+  __device__ static T of(double2 v) {
+    const T m = 0x7fffffffffffffffull;
+    return max((T)__double_as_longlong(v.x) & m, (T)__double_as_longlong(v.y) & m);
+  }
+  __device__ static double value(T t) { return __longlong_as_double((long long)t); }
+};
+
 constexpr int CE_WARPS = 32;
 template <typename CT>
 __global__ void __launch_bounds__(CE_WARPS * 32) colexp_kernel(const CT* __restrict__ src, long sbs, int lds,
                                                                int batch, int rows, int cols, int* __restrict__ e) {
-  __shared__ double red[CE_WARPS][32];
+  typedef typename AbsBits<CT>::T T;
+  __shared__ T red[CE_WARPS][32];
   const int b = blockIdx.y;
   const int c = blockIdx.x * 32 + (threadIdx.x & 31);
   const int w = threadIdx.x >> 5;
-  double m = 0.0;
+  T m = 0;
   if (c < cols) {
     const CT* p = src + (long)b * sbs + c;
     int r = w;
     for (; r + 3 * CE_WARPS < rows; r += 4 * CE_WARPS) {
       const CT v0 = p[(long)r * lds], v1 = p[(long)(r + CE_WARPS) * lds];
       const CT v2 = p[(long)(r + 2 * CE_WARPS) * lds], v3 = p[(long)(r + 3 * CE_WARPS) * lds];
-      m = fmax(m, fmax(fmax(cmax(v0), cmax(v1)), fmax(cmax(v2), cmax(v3))));
+      m = max(m, max(max(AbsBits<CT>::of(v0), AbsBits<CT>::of(v1)), max(AbsBits<CT>::of(v2), AbsBits<CT>::of(v3))));
     }
-    for (; r < rows; r += CE_WARPS) m = fmax(m, cmax(p[(long)r * lds]));
+    for (; r < rows; r += CE_WARPS) m = max(m, AbsBits<CT>::of(p[(long)r * lds]));
   }
   red[w][threadIdx.x & 31] = m;
   __syncthreads();
   if (w == 0) {
-    for (int i = 1; i < CE_WARPS; i++) m = fmax(m, red[i][threadIdx.x]);
-    if (c < cols) e[(long)b * cols + c] = row_exponent(m);
+    for (int i = 1; i < CE_WARPS; i++) m = max(m, red[i][threadIdx.x]);
+    if (c < cols) e[(long)b * cols + c] = row_exponent(AbsBits<CT>::value(m));
   }
 }
 
