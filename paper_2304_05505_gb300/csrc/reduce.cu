@@ -54,8 +54,10 @@ __global__ void __launch_bounds__(RT) ex_partial_c(const float2* __restrict__ Ps
                                                     double* __restrict__ partial) {
   __shared__ double sh[RT / 32];
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  // unrolled so that the loads of several iterations are in flight together
+#pragma unroll 4
   for (long i = (long)blockIdx.x * RT + threadIdx.x; i < n; i += (long)gridDim.x * RT) {
-    float2 p = Psi[i], y = Y[i];
+    const float2 p = __ldcs(Psi + i), y = __ldcs(Y + i);
     float re = fmaf(p.x, y.x, p.y * y.y);
     float im = fmaf(p.x, y.y, -p.y * y.x);
     float s, e;
