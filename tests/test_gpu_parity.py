@@ -48,6 +48,8 @@ def gpu_build(torch, X, C, V, mesh, precision, keep=False):
         if keep:
             for i, nm in enumerate(["Psi", "D", "M", "Y"]):
                 out[nm] = eb.intermediate(i).cpu().numpy()
+            if precision == "mixed":
+                out["eM"] = eb.intermediate(4).cpu().numpy()
         return out
     finally:
         eb.close()
@@ -293,3 +295,6 @@ def test_non_hermitian_kernel_parity(torch_cuda, mesh, nisdf):
         assert_close(ref, got, "mixed")
         err = np.abs(got["M"] - ref["M"]).max() / np.abs(ref["M"]).max()
         assert err < 2e-6, err
+        # the row exponents of M from either convolution, exact (integers)
+        m = np.maximum(np.abs(got["M"].real), np.abs(got["M"].imag)).max(axis=2)
+        assert np.array_equal(got["eM"], np.where(m > 0, np.frexp(m)[1], 0).astype(np.float64))
