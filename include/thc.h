@@ -94,7 +94,10 @@ thc_status thc_set_collocation(thc_ctx* ctx, const double* X);
 /* V: device, [N_k][nisdf][nisdf] complex128, V[q] for q on the mesh index.
  * Prepares the DFT of V over the mesh, Vcheck[a] = (1/N_k) sum_q V[q] w^{+a.q}
  * (w = exp(2 pi i / n) per axis), in FP64, and keeps it (complex64 for
- * THC_MIXED).  Checked for NaN/Inf.  Synchronises the context's stream. */
+ * THC_MIXED).  Checked for NaN/Inf.  THC_MIXED also measures
+ * max |V[q] - V[q]^H| against max |V|; within 1e-12 the builds take the
+ * Hermitian form (thc_hermitian_kernel), else the general one.  Synchronises
+ * the context's stream. */
 thc_status thc_set_kernel(thc_ctx* ctx, const double* V);
 
 /* One build.  C: device [N_k][nbas][nocc] complex128 (read only).
