@@ -6,13 +6,21 @@
 //            = sum_a w^{+a.k} ( sum_{k'} w^{-a.k'} D^{k'}[P,Q] ) Vh^a[P,Q]
 //   Vh^a[P,Q] = (1/N_k) sum_q w^{+a.q} V^q[P,Q]           (prepare_kernel)
 //
-// with w = exp(2 pi i / n) per mesh axis.  Every (P,Q) element is independent:
-// one thread owns one element, keeps its N_k values in shared memory (column
-// layout [k][thread], conflict-free), runs the separable 3-D DFT axis by axis
-// with radix-2/3/4 butterflies or a direct DFT for other lengths, multiplies by
-// Vh and transforms back.  Loads and stores of D, Vh and M are coalesced
-// across the threads of a block (consecutive elements).  The stage is bound by
-// HBM: 3 N_k complex values move per element against ~6 N_k L flops.
+// with w = exp(2 pi i / n) per mesh axis.  Every (P,Q) element is
+// independent; the stage is bound by HBM (3 N_k complex values move per
+// element against ~6 N_k L flops).  Forms, fastest first:
+//   kconv_herm_kernel  Hermitian D^k and V^q (so M^k Hermitian), meshes 2^3,
+//                      3^3, 4^3, N_P even: TMA-fed tiles that reach the
+//                      diagonal, M mirrored through shared memory, row
+//                      exponents of M from per-tile keys
+//   kconv_pipe_kernel  the same meshes, any V: TMA-fed batches of consecutive
+//                      elements, row exponents of M folded in
+//   kconv_lanes_kernel the same meshes without TMA (N1 lanes per element,
+//                      first axis by shuffles)
+//   kconv_kernel       any mesh: one thread per element, its N_k values in
+//                      shared memory ([k][thread], conflict-free)
+// All run the separable 3-D DFT axis by axis with radix-2/3/4 butterflies or
+// a direct DFT for other lengths, multiply by Vh and transform back.
 //
 // FP32 form: a 2- or 4-point DFT has twiddles 1, -1, +-i and is exact up to the
 // additions; the only irrational twiddles (sqrt(3)/2 for lengths 3 and 6, the
