@@ -9,6 +9,7 @@ exchange, a symmetry, a literal Gamma-point formula, a scalar closed form).
 from __future__ import annotations
 
 import functools
+import itertools
 
 import numpy as np
 
@@ -185,3 +186,87 @@ def check_conv_single_term(mesh=(3, 4, 2)) -> float:
             for route in (O.kconv_direct, O.kconv_fft):
                 worst = max(worst, float(np.abs(route(D, V, mesh) - expect).max()))
     return worst
+
+
+# ---------------------------------------------------------------------------
+# the Coulomb kernel of the setup oracle, pinned to closed forms
+# ---------------------------------------------------------------------------
+
+# Energy per cell of a simple cubic lattice of unit point charges in a
+# neutralising uniform background is MADELUNG_SC / (2 L) (Nijboer and de
+# Wette's lattice constant, 2.8372974794806...).
+MADELUNG_SC = -2.8372974794806196
+
+
+def _grid_cart(lattice, grid):
+    axes = [np.arange(g) / g for g in grid]
+    f = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, 3)
+    return f @ np.asarray(lattice)
+
+
+def check_gaussian_self_energy(L: float, alpha: float = 1.0, g: int = 24) -> dict:
+    """Coulomb energy of a unit Gaussian charge (alpha/pi)^{3/2} exp(-alpha r^2)
+    repeated in a cubic box of side L, with the G = 0 term left out (a
+    neutralising background), from the oracle's ISDF kernel of that charge
+    taken as a single interpolation vector at Gamma: E = V^0[P, P] / 2.
+
+    Closed form (Ewald split with eta^2 = alpha / 2, whose reciprocal sum is
+    exactly this G sum): E = sqrt(alpha / (2 pi)) + MADELUNG_SC / (2 L)
+    + pi / (alpha L^3), up to a real-space tail below erfc(sqrt(alpha/2) L)."""
+    lattice = L * np.eye(3)
+    grid = (g, g, g)
+    r = _grid_cart(lattice, grid)
+    xi = np.zeros(len(r))
+    for n in itertools.product((-1, 0, 1), repeat=3):
+        d = r - np.array(n, dtype=float) * L
+        xi += (alpha / np.pi) ** 1.5 * np.exp(-alpha * np.einsum("ri,ri->r", d, d))
+    V = S.kernel_from_xi(lattice, grid, (1, 1, 1), xi[None, :], np.array([0]))
+    e = 0.5 * V[0, 0, 0].real
+    exact = np.sqrt(alpha / (2 * np.pi)) + MADELUNG_SC / (2 * L) + np.pi / (alpha * L ** 3)
+    return dict(rel=abs(e - exact) / abs(exact), e=e, exact=exact, imag=abs(V[0, 0, 0].imag))
+
+
+def check_plane_wave_kernel(lattice, grid, mesh, G0) -> float:
+    """A plane-wave interpolation vector xi(r) = exp(i G0.r) has the single
+    Fourier coefficient Omega at G0, so its kernel at q is the Coulomb energy
+    of the Bloch pair density exp(i (G0 + q).r) over the cell:
+        V^q[P, P] = (Omega / N_k) 4 pi / |G0 + q|^2     (0 where G0 + q = 0),
+    with q the shortest vector of its coset on the reciprocal lattice (the mean
+    over ties for a q on the zone boundary).  The shortest vector is found here
+    by brute force over the neighbouring cosets.  Returns the largest relative
+    deviation over the q of the mesh."""
+    lattice = np.asarray(lattice, dtype=float)
+    B = 2.0 * np.pi * np.linalg.inv(lattice).T
+    vol = abs(np.linalg.det(lattice))
+    nk = int(np.prod(mesh))
+    r = _grid_cart(lattice, grid)
+    G0 = np.asarray(G0, dtype=float)
+    xi = np.exp(1j * (r @ (G0 @ B)))
+    V = S.kernel_from_xi(lattice, grid, mesh, xi[None, :], np.array([0]))
+    worst = 0.0
+    for q in range(nk):
+        co = np.array(np.unravel_index(q, mesh), dtype=float) / np.array(mesh)
+        cands = [co + np.array(n, dtype=float) for n in itertools.product((-1, 0, 1), repeat=3)]
+        lens = np.array([np.linalg.norm(c @ B) for c in cands])
+        ties = [c for c, ln in zip(cands, lens) if ln <= lens.min() * (1 + 1e-12) + 1e-14]
+        vals = []
+        for c in ties:
+            K = (G0 + c) @ B
+            k2 = float(K @ K)
+            vals.append(0.0 if k2 < 1e-12 else 4.0 * np.pi / k2)
+        expect = vol / nk * float(np.mean(vals))
+        scale = max(abs(expect), vol / nk * 4.0 * np.pi / float(np.sum(B * B)))
+        worst = max(worst, abs(V[q, 0, 0] - expect) / scale)
+    return float(worst)
+
+
+def check_gset_symmetric(grid) -> float:
+    """The G set is the grid's FFT frequencies without the unpaired Nyquist
+    plane of an even size: every frequency whose negative is also one."""
+    got = {tuple(int(x) for x in t) for t in S.symmetric_gset(grid)}
+    axes = []
+    for g in grid:
+        f = set(int(x) for x in np.rint(np.fft.fftfreq(g) * g))
+        axes.append(sorted(x for x in f if -x in f))
+    want = set(itertools.product(*axes))
+    return float(len(got ^ want))

@@ -74,3 +74,61 @@ def test_mutant_is_caught(monkeypatch, name):
 
 def test_unmutated_passes():
     assert not _any_pin_fails()
+
+
+# ---------------------------------------------------------------------------
+# mutants of the setup oracle's Coulomb kernel and q representatives: both
+# sides of the full-grid identity share these, so they are caught by the
+# closed-form pins instead
+# ---------------------------------------------------------------------------
+
+from oracle import setup_oracle as S  # noqa: E402
+
+
+def _coulomb_2pi(K):
+    K2 = np.einsum("gi,gi->g", K, K)
+    out = np.zeros_like(K2)
+    nz = K2 > 1e-12
+    out[nz] = 2.0 * np.pi / K2[nz]
+    return out
+
+
+def _coulomb_first_power(K):
+    K2 = np.einsum("gi,gi->g", K, K)
+    out = np.zeros_like(K2)
+    nz = K2 > 1e-12
+    out[nz] = 4.0 * np.pi / np.sqrt(K2[nz])
+    return out
+
+
+def _representatives_unwrapped(qco, mesh):
+    return [np.array([(int(qco[a]) % mesh[a]) / mesh[a] for a in range(3)])]
+
+
+SETUP_MUTANTS = {
+    "coulomb_2pi": ("coulomb", _coulomb_2pi),
+    "coulomb_1_over_K": ("coulomb", _coulomb_first_power),
+    "q_not_minimum_image": ("representatives", _representatives_unwrapped),
+}
+
+
+def _coulomb_pins_fail() -> list:
+    fails = []
+    if pins.check_gaussian_self_energy(8.0)["rel"] > 1e-12:
+        fails.append("gaussian")
+    lattice = np.diag([6.95, 8.9, 6.45])
+    for mesh in [(2, 2, 2), (3, 3, 3)]:
+        if pins.check_plane_wave_kernel(lattice, (8, 8, 8), mesh, (1, 0, 0)) > 1e-13:
+            fails.append(f"plane_wave{mesh}")
+    return fails
+
+
+@pytest.mark.parametrize("name", sorted(SETUP_MUTANTS))
+def test_setup_mutant_is_caught(monkeypatch, name):
+    fn, mutant = SETUP_MUTANTS[name]
+    monkeypatch.setattr(S, fn, mutant)
+    assert _coulomb_pins_fail(), f"mutant {name} passed every Coulomb pin"
+
+
+def test_setup_unmutated_passes():
+    assert not _coulomb_pins_fail()

@@ -116,3 +116,32 @@ def test_random_inputs_symmetries():
     r = cells.random_problem((3, 2, 2), nbas=6, nocc=2, nisdf=7)
     assert pins.check_hermitian(r["X"], r["C"], r["V"], r["mesh"]) < 1e-12
     assert pins.check_time_reversal(r["X"], r["C"], r["V"], r["mesh"]) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# the Coulomb kernel, G set and q representatives of the setup oracle
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", [8.0, 9.0])
+def test_gaussian_self_energy_closed_form(L):
+    """The oracle's ISDF kernel of a repeated unit Gaussian charge gives its
+    Coulomb energy with the G = 0 term dropped: the Gaussian self-energy plus
+    the simple-cubic Madelung term and the background term (Ewald)."""
+    r = pins.check_gaussian_self_energy(L)
+    assert r["rel"] < 1e-12, r
+    assert r["imag"] < 1e-14
+
+
+@pytest.mark.parametrize("mesh", [(2, 2, 2), (3, 3, 3), (3, 2, 4)])
+@pytest.mark.parametrize("G0", [(0, 0, 0), (1, 0, 0), (0, -1, 2)])
+def test_plane_wave_kernel_closed_form(mesh, G0):
+    """A plane-wave interpolation vector gives 4 pi / |G0 + q|^2 (Omega / N_k)
+    at every q of the mesh, with q the shortest vector of its coset found by
+    brute force (orthorhombic cell; zone-boundary q averaged over its ties)."""
+    lattice = np.diag([6.95, 8.9, 6.45])
+    assert pins.check_plane_wave_kernel(lattice, (8, 8, 8), mesh, G0) < 1e-13
+
+
+@pytest.mark.parametrize("grid", [(8, 7, 6), (5, 5, 5), (16, 16, 16)])
+def test_gset_is_the_symmetric_fft_set(grid):
+    assert pins.check_gset_symmetric(grid) == 0.0
