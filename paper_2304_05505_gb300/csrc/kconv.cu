@@ -728,10 +728,14 @@ Twiddles make_twiddles(int n1, int n2, int n3) {
   return t;
 }
 
+// Threads per block of the one-element-per-thread forms: each thread keeps
+// its element's N_k values in shared memory, so blocks shrink (down to 8
+// threads: 8 x 512 complex128 values = 64 KB on an 8^3 mesh) to stay within
+// about 100 KB of dynamic shared memory.
 int pick_threads(int nk, size_t elem) {
   const size_t budget = 100 * 1024;
   int T = 256;
-  while (T > 32 && (size_t)T * nk * elem > budget) T /= 2;
+  while (T > 8 && (size_t)T * nk * elem > budget) T /= 2;
   return T;
 }
 

@@ -42,6 +42,14 @@ extern "C" thc_status thc_kconv_noalloc(const double* D, const double* V, double
   if (((uintptr_t)D | (uintptr_t)V | (uintptr_t)M) & 15u) return THC_ERR_ARG;
   if (n1 < 1 || n2 < 1 || n3 < 1 || n1 > 8 || n2 > 8 || n3 > 8 || npq < 1) return THC_ERR_ARG;
   const long nk = (long)n1 * n2 * n3;
+  // M must not overlap D or V: the convolution reads D while it writes M
+  const size_t bytes = (size_t)nk * (size_t)npq * sizeof(double2);
+  const char* m0 = (const char*)M;
+  for (const char* in : {(const char*)D, (const char*)V})
+    if (npq <= kScratchElems / nk && m0 < in + bytes && in < m0 + bytes) {
+      set_global_error("thc_kconv_noalloc: M overlaps D or V");
+      return THC_ERR_ARG;
+    }
   if (npq > kScratchElems / nk) {
     set_global_error("thc_kconv_noalloc: N_k * npq exceeds the static scratch of 2097152 complex "
                      "elements (32 MiB)");

@@ -240,13 +240,31 @@ def thc_sync(ctx) -> None:
 
 
 def thc_kconv_noalloc(D, V, M, mesh, npq: int, stream: int | None = None) -> None:
-    """k-mesh convolution without device allocation (see include/thc.h)."""
-    if stream is None:
-        import torch
-        stream = torch.cuda.current_stream().cuda_stream
-    _check(load().thc_kconv_noalloc(_dev_ptr(D, name="D"), _dev_ptr(V, name="V"), _dev_ptr(M, name="M"),
-                                    int(mesh[0]), int(mesh[1]), int(mesh[2]), int(npq), ctypes.c_void_p(stream)),
-           "thc_kconv_noalloc")
+    """k-mesh convolution without device allocation (see include/thc.h).
+
+    D, V and M are complex128 CUDA tensors of N_k * npq elements each, on one
+    device; the call runs on that device (its current stream unless `stream`
+    is given).  Sizes are checked here, before anything is queued."""
+    import torch
+    nk = int(mesh[0]) * int(mesh[1]) * int(mesh[2])
+    want = nk * int(npq)
+    for t, nm in ((D, "D"), (V, "V"), (M, "M")):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{nm}: expected a CUDA tensor")
+        if t.numel() != want:
+            raise ValueError(f"{nm}: {t.numel()} elements, the mesh and npq need {want}")
+    for t, nm in ((D, "D"), (V, "V"), (M, "M")):
+        if not t.is_cuda:
+            raise TypeError(f"{nm}: expected a CUDA tensor")
+    if not (D.device == V.device == M.device):
+        raise ValueError("D, V and M must be on one device")
+    with torch.cuda.device(D.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(D.device).cuda_stream
+        _check(load().thc_kconv_noalloc(_dev_ptr(D, name="D"), _dev_ptr(V, name="V"), _dev_ptr(M, name="M"),
+                                        int(mesh[0]), int(mesh[1]), int(mesh[2]), int(npq),
+                                        ctypes.c_void_p(stream)),
+               "thc_kconv_noalloc")
 
 
 def thc_select_points(U, npts: int, rel_tol: float = 1e-14, stream: int | None = None):

@@ -80,6 +80,7 @@ RANDOM_CASES = [
     ((2, 3, 1), 17, 17, 16),     # n = N
     ((4, 4, 4), 20, 3, 65),
     ((6, 1, 2), 10, 2, 33),      # 6-point DFT
+    ((8, 8, 8), 5, 2, 12),       # the largest mesh: 512 k-points per element in shared memory
 ]
 
 

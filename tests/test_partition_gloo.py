@@ -2,9 +2,9 @@
 
 The sharded design: every rank owns a block-cyclic share of the (P, Q) tiles
 of the point-space matrices.  It forms D and the k-convolution on its tiles
-only and adds M[P, Q] Psi[Q] into a partial Y.  An all-reduce sums Y; each
-rank then back-projects its slice of the P rows and an all-reduce sums KC and
-E_x.  The per-rank arithmetic is the FP64 oracle's (steps 1-5 of
+only and adds M[P, Q] Psi[Q] into a partial Y.  A reduce-scatter by P sums
+the partial Y and leaves each rank its own slice of the P rows; each rank
+back-projects that slice and an all-reduce sums KC and E_x.  The per-rank arithmetic is the FP64 oracle's (steps 1-5 of
 oracle/thc_oracle.py), so this checks the partition and the exchange steps,
 not the kernels.  The exchanges carry O(N_k N_P n) values against the
 O(N_k N_P^2) kernel each rank keeps."""
@@ -49,12 +49,16 @@ def _rank_main(rank, world, port, out_dir):
         M = O.kconv_direct(D, V[:, pr, qr], MESH)                             # step 3 on the tile
         for k in range(nk):
             Ypart[k][pr] += M[k] @ Psi[k][qr]                                 # step 4a, partial over Q
-    Y = torch.from_numpy(Ypart.copy())
-    dist.all_reduce(Y)                                # sum of the Q-partial products
-    Y = Y.numpy()
+    # reduce-scatter of Y by P: the Q-partial products are summed and each rank
+    # receives only its own slice of the P rows (P-major so the slices are contiguous)
+    assert npt % world == 0
     rows = slice(rank * npt // world, (rank + 1) * npt // world)
-    KC = torch.from_numpy(np.stack([X[k][:, rows].conj() @ Y[k][rows] for k in range(nk)]))
-    ex = torch.tensor([-np.sum(Psi[:, rows].conj() * Y[:, rows]).real / nk])
+    Yp = torch.from_numpy(np.ascontiguousarray(Ypart.transpose(1, 0, 2)))
+    Ymine = torch.zeros((npt // world, nk, Ypart.shape[2]), dtype=Yp.dtype)
+    dist.reduce_scatter_tensor(Ymine, Yp)
+    Yr = Ymine.numpy().transpose(1, 0, 2)            # [N_k][rows of this rank][n]
+    KC = torch.from_numpy(np.stack([X[k][:, rows].conj() @ Yr[k] for k in range(nk)]))
+    ex = torch.tensor([-np.sum(Psi[:, rows].conj() * Yr).real / nk])
     dist.all_reduce(KC)
     dist.all_reduce(ex)
     if rank == 0:

@@ -4,51 +4,72 @@ Some callers cannot allocate device memory when they call into the library:
 a host framework that has already reserved the GPU's memory in its own pool,
 or a caller that must not let cudaMalloc/cudaFree synchronise the device.
 thc_kconv_noalloc gives them the k-mesh convolution with its scratch in a
-static device array.  This file checks, through the C ABI, that two calls in a
-row give the same M as the library's own build (FP64 form), within the FP64
-tolerance of the other parity tests, and that sizes beyond the static scratch
-are refused.  It is named so that pytest collects it last.
+static device array.  These tests call it through the C ABI twice in a row,
+with a different mesh, size and kernel the second time (so a stale prepared
+kernel left in the shared scratch would show), and compare each result with
+the FP64 oracle's direct k' sum; they also check that sizes beyond the static
+scratch and outputs that overlap an input are refused.  The file is named so
+that pytest collects it last.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
-from paper_2304_05505_gb300 import cells
+from oracle import thc_oracle as O
 
-pytestmark = pytest.mark.gpu
+gpu = pytest.mark.gpu
 
 
-def test_noalloc_kconv_matches_build(cuda_required):
+def _case(mesh, npq, seed):
+    rng = np.random.default_rng(seed)
+    nk = int(np.prod(mesh))
+    D = rng.normal(size=(nk, npq)) + 1j * rng.normal(size=(nk, npq))
+    V = rng.normal(size=(nk, npq)) + 1j * rng.normal(size=(nk, npq))
+    return D, V, O.kconv_direct(D, V, mesh)
+
+
+@gpu
+def test_noalloc_kconv_two_calls_match_oracle(cuda_required):
     import torch
     from paper_2304_05505_gb300 import thc
-    mesh = (3, 2, 2)
-    r = cells.random_problem(mesh, nbas=20, nocc=4, nisdf=45, seed=12)
-    dims = dict(n1=3, n2=2, n3=2, nbas=20, nocc=4, nisdf=45)
-    eb = thc.ExchangeBuild(dims, "fp64")
-    eb.set_collocation(r["X"])
-    eb.set_kernel(r["V"])
-    eb.build(r["C"])
-    eb.sync()
-    D = eb.intermediate(1)                 # density of the build, [N_k][N_P][N_P]
-    M_ref = eb.intermediate(2)             # the build's own k-convolution
-    V = torch.from_numpy(r["V"]).cuda()
-    npq = 45 * 45
-    scale = float(M_ref.abs().max())
-    for _ in range(2):                     # two calls in a row share the static scratch
-        M = torch.full_like(M_ref, float("nan"))
-        thc.thc_kconv_noalloc(D, V, M, mesh, npq)
+    for mesh, npq, seed in (((3, 2, 2), 45 * 45, 12), ((2, 2, 2), 37 * 37, 13)):
+        D, V, M_ref = _case(mesh, npq, seed)
+        Dd = torch.from_numpy(D).cuda()
+        Vd = torch.from_numpy(V).cuda()
+        M = torch.full_like(Dd, float("nan"))
+        thc.thc_kconv_noalloc(Dd, Vd, M, mesh, npq)
         torch.cuda.synchronize()
-        err = float((M - M_ref).abs().max())
-        assert err <= 1e-12 * scale, err
-    eb.close()
+        err = float(np.abs(M.cpu().numpy() - M_ref).max())
+        assert err <= 1e-12 * float(np.abs(M_ref).max()), (mesh, err)
 
 
-def test_noalloc_kconv_rejects_oversize(cuda_required):
+@gpu
+def test_noalloc_kconv_rejects_oversize_and_overlap(cuda_required):
     import torch
     from paper_2304_05505_gb300 import thc
-    mesh = (4, 4, 4)
-    npq = (1 << 21) // 64 + 1              # one element per k beyond the 32 MiB scratch
-    D = torch.zeros(1, dtype=torch.complex128, device="cuda")
-    with pytest.raises(thc.ThcError) as e:
-        thc.thc_kconv_noalloc(D, D, torch.zeros(1, dtype=torch.complex128, device="cuda"), mesh, npq)
-    assert e.value.code == 1
-    assert b"static scratch" in thc.load().thc_last_error(None)
+    lib = thc.load()
+    buf = torch.zeros(2 * 64, dtype=torch.complex128, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    p = buf.data_ptr()
+    # one element per k beyond the 32 MiB scratch: refused before any device access
+    assert lib.thc_kconv_noalloc(p, p, p + 16 * 64, 4, 4, 4, (1 << 21) // 64 + 1, stream) == 1
+    assert b"static scratch" in lib.thc_last_error(None)
+    # M overlapping D
+    assert lib.thc_kconv_noalloc(p, p + 16 * 64, p, 4, 4, 4, 1, stream) == 1
+    assert b"overlaps" in lib.thc_last_error(None)
+
+
+def test_noalloc_wrapper_checks_sizes_before_the_call():
+    """The binding refuses tensors whose size does not match the mesh and npq
+    before it reaches the C call (no device needed)."""
+    import torch
+    from paper_2304_05505_gb300 import thc
+    a = torch.zeros(8 * 4, dtype=torch.complex128)
+    short = torch.zeros(8 * 4 - 1, dtype=torch.complex128)
+    with pytest.raises(ValueError):
+        thc.thc_kconv_noalloc(a, a, short, (2, 2, 2), 4)
+    with pytest.raises(ValueError):
+        thc.thc_kconv_noalloc(short, a, a, (2, 2, 2), 4)
+    with pytest.raises(TypeError):          # right sizes, but host tensors
+        thc.thc_kconv_noalloc(a, a, a, (2, 2, 2), 4)
