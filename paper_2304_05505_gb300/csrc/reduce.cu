@@ -94,6 +94,15 @@ __global__ void z2c_kernel(const double2* __restrict__ in, float2* __restrict__ 
     out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
+__global__ void z2c_rows_kernel(const double2* __restrict__ in, float2* __restrict__ out, long n, int cols,
+                                int ldo) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long r = i / cols;
+    const int c = (int)(i - r * cols);
+    out[r * ldo + c] = make_float2((float)in[i].x, (float)in[i].y);
+  }
+}
+
 __global__ void c2z_kernel(const float2* __restrict__ in, double2* __restrict__ out, long n) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     out[i] = make_double2((double)in[i].x, (double)in[i].y);
@@ -171,6 +180,12 @@ cudaError_t hermitian_fill_c2z(const float2* D, double2* out, int np, int nk, cu
 
 cudaError_t convert_z2c(const double2* in, float2* out, long n, cudaStream_t s) {
   z2c_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t convert_z2c_rows(const double2* in, float2* out, long rows, int cols, int ldo, cudaStream_t s) {
+  const long n = rows * cols;
+  z2c_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, out, n, cols, ldo);
   return cudaGetLastError();
 }
 

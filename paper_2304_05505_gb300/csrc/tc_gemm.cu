@@ -12,18 +12,27 @@
 // Exact accumulation (fixed-point slices).  The tensor core's FP32 accumulator
 // does not round to nearest, so summing floating-point products on it leaves
 // a one-sided error of about an ulp per step, which shows up as a bias in E_x.
-// Instead every operand row r is scaled by a power of two 2^-e_r so that its
-// entries lie in [-1, 1], and written as four slices of 8 bits:
-//   x = 2^(e_r - 7) (S0 + 2^-8 S1 + 2^-16 S2 + 2^-24 S3),  S_s integers in [-128, 128]
-// kept in bf16 planes P_s = 2^(-8 s) S_s (exact).  The product of two rows is
-// then 2^(e_a + e_b - 14) sum_{s,t} P_s^a P_t^b.  The leading class P_0 P_0 is a
-// sum of integers of at most 2^14 each; any partial sum of up to 1024 of them
-// is an integer below 2^24, which the FP32 accumulator holds exactly whatever
-// its rounding.  The nine classes with s + t = 1..3 go to a second
-// accumulator; their rounding is at least 2^-8 smaller.  Classes with
-// s + t >= 4 (below 2^-32 of the row scales) are dropped.  A GEMM whose
-// result is rounded to FP32 anyway may take three slices (24 bits) and the
-// six classes s + t <= 2.
+// Instead every operand row r is scaled by a power of two so that its entries
+// lie in [-128, 128] and cut into three fixed-point slices of 8, 11 and 11 bits:
+//   x = 2^(e_r - 7) (S0 + 2^-11 S1 + 2^-22 S2),  S0 in [-128, 128], S1, S2 in [-1024, 1024]
+// held in fp16 planes P0 = 2^8 S0, P1 = 2^-3 S1, P2 = 2^-14 S2 (all normal
+// fp16 numbers or zero, so exact).  Every product P_s P_t is exact in FP32, and
+// the product of two rows is 2^(e_a + e_b - 30) sum_{s,t} P_s^a P_t^b.  The
+// leading class P0 P0 is 2^16 times a sum of integers of at most 2^14 each; any
+// partial sum of up to 1024 of them is below 2^24 in those units, which the
+// FP32 accumulator holds exactly whatever its rounding.  The other kept
+// classes go to a second accumulator 2^-11 smaller or less:
+//   6 products: (0,0) | (0,2) (2,0) (1,1) (0,1) (1,0)       about 2^-27 of the row scales dropped
+//   8 products: the same and (1,2) (2,1)                      about 2^-30
+// against 10 products for four 8-bit bf16 slices at the same accuracy.  fp16
+// and bf16 operands run at the same kind::f16 rate.
+//
+// Operand A is either three planes written by a preparation kernel, or an
+// FP32 matrix that TMA brings into shared memory and converter warps cut into
+// the three planes inside the kernel (no planes of A through HBM):
+//   CV = 1  A stored [rows][K] (row-major complex): 128 x 32-float boxes, 128B swizzle
+//   CV = 2  A stored [K][rows] (A is the transpose of the stored matrix, as
+//           X^T in S1): 16 x 256-float boxes, the converters transpose
 //
 // Work units: a 128 x 128 output tile and a chunk of at most 1024 real K (so
 // the leading sum of a unit is exact), the chunks of one product of equal
@@ -32,25 +41,27 @@
 // buffer and tc_combine adds the chunks (split K); otherwise they write the
 // scaled result directly.
 //
-// Kernel structure (persistent: one CTA per SM loops over units, 384 threads):
-//   warp 0      TMA producer: NS A planes + NS B planes per 32-wide real-K
-//               block into a ring of 3 stages of 64 KB (NS = 4) or 4 of 48 KB
-//               (NS = 3), 64B swizzle, running ahead across units
+// Kernel structure (persistent: one CTA per SM loops over units):
+//   warp 0      TMA producer: A planes (or the FP32 A tile) and B planes per
+//               32-wide real-K block into a ring in shared memory, 64B
+//               swizzle, running ahead across units
 //   warp 1      allocates 512 TMEM columns = two accumulator sets (leading
-//               class, classes 1..3; 128 columns each) so that the epilogue of
-//               one unit overlaps the MMAs of the next; lane 0 issues
-//               tcgen05.mma (M = 128, N = 128, K = 16, bf16 x bf16 -> f32),
-//               10 (NS = 4) or 6 (NS = 3) per K step
-//   warps 2-3   idle
-//   warps 4-19  epilogue (4 per TMEM lane quadrant, 32 columns each): read
-//               both accumulators, scale and store (or write the partial
-//               sums), release the accumulator set.  Each warp turns its
-//               32-row x 16-column blocks around in a 2 KB shared tile so that
-//               every store instruction writes whole 64-byte row segments; the
-//               unit's row and column exponents are loaded before its
-//               accumulator is ready
+//               class, the other classes; 128 columns each) so that the
+//               epilogue of one unit overlaps the MMAs of the next; lane 0
+//               issues tcgen05.mma (M = 128, N = 128, K = 16, f16 x f16 -> f32),
+//               6 or 8 per K step
+//   CV:  warps 2-9 converters, warps 10-17 epilogue (8 warps, 64 columns each)
+//   else warps 2-3 idle, warps 4-19 epilogue (16 warps, 32 columns each)
+// The epilogue warps (4 per TMEM lane quadrant) read both accumulators with
+// tcgen05.ld, scale by exact powers of two and store (or write the partial
+// sums), then release the accumulator set.  Each warp turns its 32-row x
+// 16-column blocks around in a 2 KB shared tile so that every store
+// instruction writes whole 64-byte row segments; the unit's row and column
+// exponents are loaded before its accumulator is ready.
 // Every mbarrier wait is bounded (about 2 s of clock64); on expiry the thread
-// sets the error word, stops issuing work and the CTA releases TMEM and exits.
+// sets the error word and stops issuing work, the producer waits (bounded) for
+// its copies in flight, the MMA thread for its MMAs in flight, and the CTA
+// releases TMEM and exits.
 #include "thc_internal.cuh"
 #include "tc_gemm.cuh"
 #include "slices.cuh"
@@ -58,37 +69,28 @@
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
 namespace {
 
 constexpr int BM = 128, BN = 128, BKR = 32;
-constexpr int NPL = 4;                                       // slices per operand
+constexpr int NPL = 3;                                       // slices per operand
 constexpr uint32_t TILE_BYTES = BM * BKR * 2;                // 8 KB (one plane of A or B)
-constexpr int EPI_WARPS = 16;
 constexpr int MAX_CHUNK_KB = 32;                             // K blocks per exact chunk, at most (1024 real K)
 constexpr uint32_t TMEM_COLS = 512;
-
-// Operands in NS slices: 4 (10 products per real product) or 3 (6 products,
-// classes s + t <= 2; used where the output is rounded to FP32 anyway and K is
-// short).  The ring holds 3 stages of 64 KB or 4 of 48 KB.
-template <int NS> struct Ring {
-  static constexpr int STAGES = NS == 4 ? 3 : 4;
-  static constexpr uint32_t STAGE_BYTES = 2 * NS * TILE_BYTES;
-};
-constexpr uint32_t RING_BYTES = 3 * 2 * 4 * TILE_BYTES;     // 192 KB either way
-static_assert(Ring<4>::STAGES * Ring<4>::STAGE_BYTES == RING_BYTES, "ring size");
-static_assert(Ring<3>::STAGES * Ring<3>::STAGE_BYTES == RING_BYTES, "ring size");
+constexpr uint32_t RING_BYTES = 192 * 1024;
+constexpr uint32_t STAGE_BYTES = 2 * NPL * TILE_BYTES;       // A and B planes of one K block: 48 KB
 constexpr uint32_t EPI_TILE = 32 * 16;                       // floats per epilogue warp (32 rows x 16)
-constexpr size_t SMEM_BYTES = RING_BYTES + 1024 + 256 + EPI_WARPS * EPI_TILE * 4;
+constexpr int EPI_WARPS_MAX = 16;
+constexpr size_t SMEM_BYTES = RING_BYTES + 1024 + 256 + EPI_WARPS_MAX * EPI_TILE * 4;
+
 // Warp roles: 0 TMA, 1 MMA, then (CV) 8 converter warps, then the epilogue.
-// The converted-A form has the longer K per unit and takes 8 epilogue warps;
-// the others take 16.
-template <bool CV> struct Roles {
+// The converted-A forms take 8 epilogue warps, the others 16.
+template <int CV> struct Roles {
   static constexpr int CONV_WARPS = CV ? 8 : 0;                 // warps 2 .. 2 + CONV_WARPS - 1
-  static constexpr int EPI = CV ? 8 : EPI_WARPS;                // epilogue warps
+  static constexpr int EPI = CV ? 8 : 16;                       // epilogue warps
   static constexpr int EPI0 = CV ? 2 + CONV_WARPS : 4;          // first epilogue warp
   static constexpr int NT = (EPI0 + EPI) * 32;                  // threads
   static constexpr int COLS = 4 * BN / EPI;                     // columns of a unit per epilogue warp
@@ -105,13 +107,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-// kind::f16 instruction descriptor: D f32, A/B bf16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// kind::f16 instruction descriptor: D f32 (bits 4-5 = 1), A and B f16 (type
+// fields 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
@@ -165,21 +168,6 @@ __device__ __forceinline__ double pow2d(int e) {
   return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
 
-// The four fixed-point slices P_s = S_s 2^-8s of y = 2^(7 - e) x (|y| <= 255)
-// as FP32 values: the rounding of the remainder to a multiple of 2^-8s (to
-// nearest, ties to even, as rint) is an add and a subtract of
-// 1.5 * 2^(23 - 8s), exact for these magnitudes, and each remainder y - P_s is
-// exact.  Each P_s is an integer of at most 8 significant bits times 2^-8s,
-// exact in bf16, so its bf16 bits are the top half of its FP32 bits.
-__device__ __forceinline__ void slice4_planes(float y, float* p) {
-  const float magic[4] = {0x1.8p23f, 0x1.8p15f, 0x1.8p7f, 0x1.8p-1f};
-#pragma unroll
-  for (int s = 0; s < 4; s++) {
-    p[s] = __fsub_rn(__fadd_rn(y, magic[s]), magic[s]);
-    y = __fsub_rn(y, p[s]);
-  }
-}
-
 struct Geometry {
   int M, Nr, Kr, batch;
   int mt, nt, nchunk, nkb;   // tiles along M and N, K chunks, K blocks
@@ -202,53 +190,74 @@ __device__ __forceinline__ int row_exp(const int* e, long i) {
   return x < -1000 ? 0 : x;
 }
 
+// The three fp16 planes of 8 consecutive reals x[0..8) of one row (scale sc =
+// 2^(7 - e_row)), packed two reals per word: w[p][j] holds reals 2j, 2j + 1 of
+// plane p.
+__device__ __forceinline__ void slice8_f16(const float* x, float sc, uint32_t w[NPL][4]) {
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    float lo[NPL], hi[NPL];
+    slice3_planes(x[j] * sc, lo);
+    slice3_planes(x[j + 1] * sc, hi);
+#pragma unroll
+    for (int p = 0; p < NPL; p++) {
+      const __half2 h = __floats2half2_rn(lo[p], hi[p]);
+      w[p][j >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+  }
+}
+
 // OUT: 0 = FP32 result, 1 = FP64 result, 2 = partial sums (split K)
-// AR (A resident, short K in one chunk, three slices): the A tile of all K
-// (4 blocks x 3 planes, 96 KB) stays in shared memory while the CTA runs the
-// N tiles of one (batch, M tile) one after another; only B streams through a
-// 4-stage ring of 24 KB.  Each CTA takes a contiguous range of units so that
-// consecutive units share their A tile.
-// CV (A converted in shared memory): A is an FP32 (interleaved complex)
-// matrix.  TMA brings 128 x 32 FP32 tiles into a 3-stage staging ring
-// (128B swizzle); warps 2-3 cut each tile into the four bf16 slices with the
-// rows' exponents and write them in the 64B-swizzled K-major layout the MMA
-// reads, then fence the generic-proxy writes for the async proxy and arrive
-// on the stage's full barrier beside the TMA bytes of the B planes.  No slice
-// planes of A ever go through HBM.
-template <int OUT, int NS, bool AR, bool CV>
+// NP: 6 or 8 slice products per real product (see the header).
+// AR (A resident, short K in one chunk): the A tile of all K (4 blocks x 3
+// planes, 96 KB) stays in shared memory while the CTA runs the N tiles of one
+// (batch, M tile) one after another; only B streams through a 4-stage ring of
+// 24 KB.  Each CTA takes a contiguous range of units so that consecutive units
+// share their A tile.
+// CV (A converted in shared memory, 1 or 2): A is an FP32 (interleaved
+// complex) matrix.  TMA brings 16 KB FP32 tiles into a 3-stage staging ring;
+// converter warps cut each tile into the three fp16 slices with the rows'
+// exponents and write them in the 64B-swizzled K-major layout the MMA reads,
+// then fence the generic-proxy writes for the async proxy and arrive on the
+// stage's full barrier beside the TMA bytes of the B planes.
+template <int OUT, int NP, bool AR, int CV>
 __global__ void __launch_bounds__(Roles<CV>::NT, 1)
 tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restrict__ eA, long seA,
                const int* __restrict__ eB, long seB, void* out, long ldo, long sbo, int* __restrict__ ps0,
                float* __restrict__ pbc, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  static_assert(!AR || NS == 3, "A-resident mode uses three slices");
-  static_assert(!CV || (NS == 4 && !AR), "converted A uses four slices");
+  static_assert(NP == 6 || NP == 8, "slice products");
+  static_assert(!(AR && CV), "A is resident planes or converted, not both");
   constexpr int AKB = 4;                                           // K blocks the resident A tile holds
   constexpr int SA_STAGES = 3;                                     // FP32 staging ring of CV
   constexpr uint32_t SA_BYTES = BM * BKR * 4;                      // 16 KB
   constexpr int CONV_WARPS = Roles<CV>::CONV_WARPS;
   constexpr int EPI_W = Roles<CV>::EPI, EPI_W0 = Roles<CV>::EPI0, EPI_COLS = Roles<CV>::COLS;
-  constexpr int STAGES = AR ? 4 : CV ? 2 : Ring<NS>::STAGES;
   // what precedes the plane ring: the resident A tile, or the FP32 staging ring
-  constexpr uint32_t A_BYTES = AR ? AKB * NS * TILE_BYTES : CV ? SA_STAGES * SA_BYTES : 0;
-  constexpr uint32_t STAGE_BYTES = AR ? NS * TILE_BYTES : Ring<NS>::STAGE_BYTES;
-  static_assert(A_BYTES + STAGES * STAGE_BYTES <= RING_BYTES, "ring size");
+  constexpr uint32_t A_BYTES = AR ? AKB * NPL * TILE_BYTES : CV ? SA_STAGES * SA_BYTES : 0;
+  constexpr uint32_t SBYTES = AR ? NPL * TILE_BYTES : STAGE_BYTES;   // bytes of one ring stage
+  constexpr int STAGES = (RING_BYTES - A_BYTES) / SBYTES;
+  static_assert(STAGES >= 2 && STAGES <= 4, "ring stages");
   uint64_t* bars = (uint64_t*)(smem + RING_BYTES);
-  // bars: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2]
-  uint32_t* tmem_slot = (uint32_t*)(bars + 16);
-  float* epi_stage = (float*)(smem + RING_BYTES + 256);   // EPI_WARPS tiles of EPI_TILE floats
+  // barrier slots: full[4], empty[4], acc_full[2], acc_empty[2], resident A
+  // loaded / released, FP32 tile landed[3] / converted[3], MMAs drained, B
+  // planes landed[3] (CV: the full barrier then counts the converter warps)
+  uint32_t* tmem_slot = (uint32_t*)(bars + 24);
+  float* epi_stage = (float*)(smem + RING_BYTES + 256);   // EPI_W tiles of EPI_TILE floats
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = smem_u32(bars);
   auto FULL = [&](int s) { return bar0 + 8u * s; };
-  auto EMPTY = [&](int s) { return bar0 + 8u * (STAGES + s); };
-  auto AFULL = [&](int s) { return bar0 + 8u * (2 * STAGES + s); };
-  auto AEMPTY = [&](int s) { return bar0 + 8u * (2 * STAGES + 2 + s); };
-  const uint32_t AOP_FULL = bar0 + 8u * (2 * STAGES + 4);    // resident A tile loaded
-  const uint32_t AOP_EMPTY = bar0 + 8u * (2 * STAGES + 5);   // MMAs on the resident A tile done
-  auto SFULL = [&](int s) { return bar0 + 8u * (2 * STAGES + 6 + s); };    // CV: FP32 tile landed
-  auto SEMPTY = [&](int s) { return bar0 + 8u * (2 * STAGES + 9 + s); };   // CV: FP32 tile converted
-  static_assert(!CV || 2 * STAGES + 9 + SA_STAGES <= 16, "barrier slots");
+  auto EMPTY = [&](int s) { return bar0 + 8u * (4 + s); };
+  auto AFULL = [&](int s) { return bar0 + 8u * (8 + s); };
+  auto AEMPTY = [&](int s) { return bar0 + 8u * (10 + s); };
+  const uint32_t AOP_FULL = bar0 + 8u * 12;    // resident A tile loaded
+  const uint32_t AOP_EMPTY = bar0 + 8u * 13;   // MMAs on the resident A tile done
+  auto SFULL = [&](int s) { return bar0 + 8u * (14 + s); };    // CV: FP32 tile landed
+  auto SEMPTY = [&](int s) { return bar0 + 8u * (17 + s); };   // CV: FP32 tile converted
+  const uint32_t MMA_DONE = bar0 + 8u * 20;    // every MMA of the CTA complete
+  auto BFULL = [&](int s) { return bar0 + 8u * (21 + s); };    // CV: B planes landed
+  static_assert(!CV || STAGES <= 3, "barrier slots");
 
   __shared__ int abort_flag;
   if (threadIdx.x == 0) abort_flag = *(volatile int*)err;
@@ -259,8 +268,9 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
-      mbar_init(FULL(s), CV ? 1 + CONV_WARPS : 1);   // CV: B bytes + the converter warps
+      mbar_init(FULL(s), CV ? CONV_WARPS : 1);   // CV: the converter warps (B bytes on BFULL)
       mbar_init(EMPTY(s), 1);
+      if (CV) mbar_init(BFULL(s), 1);
     }
     if (CV) {
       for (int s = 0; s < SA_STAGES; s++) {
@@ -276,6 +286,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
       mbar_init(AOP_FULL, 1);
       mbar_init(AOP_EMPTY, 1);
     }
+    mbar_init(MMA_DONE, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -321,11 +332,11 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int s = 0; s < NS; s++) {
+      for (int s = 0; s < NPL; s++) {
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.a[s]) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.b[s]) : "memory");
       }
-      uint32_t it = 0, agen = 0;
+      uint32_t it = 0, agen = 0, nfull = 0, nsa = 0;   // K blocks; B (or A and B) and FP32 A copies issued
       long gprev = -1;
       bool ok = true;
       for (long u = u_begin; u < u_end && ok; u += u_step) {
@@ -336,10 +347,10 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
           if (grp != gprev) {
             // reload the resident A tile once the MMAs on the previous one are done
             if (agen > 0 && !mbar_wait(AOP_EMPTY, (agen - 1) & 1, err, 32)) { ok = false; break; }
-            mbar_expect_tx(AOP_FULL, g.nkb * NS * TILE_BYTES);
+            mbar_expect_tx(AOP_FULL, g.nkb * NPL * TILE_BYTES);
             for (int kb = 0; kb < g.nkb; kb++)
-              for (int p = 0; p < NS; p++)
-                tma_load_3d(sbase + (kb * NS + p) * TILE_BYTES, &maps.a[p], AOP_FULL, kb * BKR, mi * BM, b);
+              for (int p = 0; p < NPL; p++)
+                tma_load_3d(sbase + (kb * NPL + p) * TILE_BYTES, &maps.a[p], AOP_FULL, kb * BKR, mi * BM, b);
             gprev = grp;
             agen++;
           }
@@ -348,37 +359,59 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
         for (int kb = kc * g.ckb; kb < kb1; kb++, it++) {
           const int st = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
-          if constexpr (CV) {
+          if constexpr (CV != 0) {
             // the FP32 A tile into the staging ring, the B planes into the plane ring
             const int sa = it % SA_STAGES;
             if (!mbar_wait(SEMPTY(sa), ((it / SA_STAGES) & 1) ^ 1, err, 2)) { ok = false; break; }
             mbar_expect_tx(SFULL(sa), SA_BYTES);
-            tma_load_3d(sbase + sa * SA_BYTES, &maps.a[0], SFULL(sa), kb * BKR, mi * BM, b);
+            if constexpr (CV == 1)
+              tma_load_3d(sbase + sa * SA_BYTES, &maps.a[0], SFULL(sa), kb * BKR, mi * BM, b);
+            else   // [K][rows] source: 16 complex K values (rows of the box) x 128 complex rows
+              tma_load_3d(sbase + sa * SA_BYTES, &maps.a[0], SFULL(sa), mi * 2 * BM, kb * (BKR / 2), b);
+            nsa++;
             if (!mbar_wait(EMPTY(st), ph ^ 1, err, 2)) { ok = false; break; }
-            mbar_expect_tx(FULL(st), NS * TILE_BYTES);
-            const uint32_t dst = sbase + A_BYTES + st * STAGE_BYTES;
-            for (int p = 0; p < NS; p++)
-              tma_load_3d(dst + (NS + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
+            mbar_expect_tx(BFULL(st), NPL * TILE_BYTES);
+            const uint32_t dst = sbase + A_BYTES + st * SBYTES;
+            for (int p = 0; p < NPL; p++)
+              tma_load_3d(dst + (NPL + p) * TILE_BYTES, &maps.b[p], BFULL(st), kb * BKR, ni * BN, b);
+            nfull++;
             continue;
           }
           if (!mbar_wait(EMPTY(st), ph ^ 1, err, 2)) { ok = false; break; }
-          mbar_expect_tx(FULL(st), STAGE_BYTES);
-          const uint32_t dst = sbase + A_BYTES + st * STAGE_BYTES;
+          mbar_expect_tx(FULL(st), SBYTES);
+          const uint32_t dst = sbase + A_BYTES + st * SBYTES;
           if constexpr (AR) {
-            for (int p = 0; p < NS; p++)
+            for (int p = 0; p < NPL; p++)
               tma_load_3d(dst + p * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
           } else {
-            for (int p = 0; p < NS; p++)
+            for (int p = 0; p < NPL; p++)
               tma_load_3d(dst + p * TILE_BYTES, &maps.a[p], FULL(st), kb * BKR, mi * BM, b);
-            for (int p = 0; p < NS; p++)
-              tma_load_3d(dst + (NS + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
+            for (int p = 0; p < NPL; p++)
+              tma_load_3d(dst + (NPL + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
           }
+          nfull++;
+        }
+      }
+      if (!ok) {
+        // a wait gave up: let the copies already issued land before the CTA
+        // exits.  Each drained barrier completes on TMA bytes alone, and only
+        // the last ring's worth can be outstanding (a stage is reused only
+        // after its copy was consumed).  Every wait here is bounded.
+        const uint32_t n = nfull < (uint32_t)STAGES ? nfull : (uint32_t)STAGES;
+        for (uint32_t j = nfull - n; j < nfull; j++)
+          mbar_drain(CV ? BFULL(j % STAGES) : FULL(j % STAGES), (j / STAGES) & 1);
+        if constexpr (CV != 0) {
+          const uint32_t m = nsa < (uint32_t)SA_STAGES ? nsa : (uint32_t)SA_STAGES;
+          for (uint32_t j = nsa - m; j < nsa; j++) mbar_drain(SFULL(j % SA_STAGES), (j / SA_STAGES) & 1);
+        }
+        if constexpr (AR) {
+          if (agen > 0) mbar_drain(AOP_FULL, (agen - 1) & 1);
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(BM, BN);
+      const uint32_t idesc = idesc_f16(BM, BN);
       const uint64_t dbase = smem_desc(sbase);
       uint32_t it = 0, local = 0, agen = 0;
       long gprev = -1;
@@ -405,52 +438,54 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
           const int st = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
           if (!mbar_wait(FULL(st), ph, err, 8)) { ok = false; break; }
+          if (CV && !mbar_wait(BFULL(st), ph, err, 8)) { ok = false; break; }
           fence_after();
           // descriptors: one base per stage, planes and K steps are offsets of
           // (bytes >> 4) in the start-address field (no carry: smem < 256 KB)
-          const uint64_t aBase = AR ? dbase + (((uint32_t)kb * NS * TILE_BYTES) >> 4)
-                                    : dbase + ((A_BYTES + st * STAGE_BYTES) >> 4);
-          const uint64_t bBase = AR ? dbase + ((A_BYTES + st * STAGE_BYTES) >> 4)
-                                    : aBase + ((NS * TILE_BYTES) >> 4);
+          const uint64_t aBase = AR ? dbase + (((uint32_t)kb * NPL * TILE_BYTES) >> 4)
+                                    : dbase + ((A_BYTES + st * SBYTES) >> 4);
+          const uint64_t bBase = AR ? dbase + ((A_BYTES + st * SBYTES) >> 4)
+                                    : aBase + ((NPL * TILE_BYTES) >> 4);
           constexpr uint64_t PL = TILE_BYTES >> 4;
 #pragma unroll
           for (int kk = 0; kk < BKR / 16; kk++) {
             const uint64_t a = aBase + 2 * kk, b2 = bBase + 2 * kk;   // 32 B per K step
             const uint32_t acc = (kb == kb0 && kk == 0) ? 0u : 1u;
-            mma_bf16(accA, a, b2, idesc, acc);                          // exact leading class
-            // classes s + t = 3 (four slices only), 2, 1 (smallest first) into
-            // the second accumulator
-            if constexpr (NS == 4) {
-              mma_bf16(accBC, a, b2 + 3 * PL, idesc, acc);
-              mma_bf16(accBC, a + PL, b2 + 2 * PL, idesc, 1u);
-              mma_bf16(accBC, a + 2 * PL, b2 + PL, idesc, 1u);
-              mma_bf16(accBC, a + 3 * PL, b2, idesc, 1u);
-              mma_bf16(accBC, a, b2 + 2 * PL, idesc, 1u);
+            mma_f16(accA, a, b2, idesc, acc);                           // exact leading class (0,0)
+            // the other classes, smallest first, into the second accumulator
+            if constexpr (NP == 8) {
+              mma_f16(accBC, a + PL, b2 + 2 * PL, idesc, acc);          // (1,2)
+              mma_f16(accBC, a + 2 * PL, b2 + PL, idesc, 1u);           // (2,1)
+              mma_f16(accBC, a, b2 + 2 * PL, idesc, 1u);                // (0,2)
             } else {
-              mma_bf16(accBC, a, b2 + 2 * PL, idesc, acc);
+              mma_f16(accBC, a, b2 + 2 * PL, idesc, acc);               // (0,2)
             }
-            mma_bf16(accBC, a + PL, b2 + PL, idesc, 1u);
-            mma_bf16(accBC, a + 2 * PL, b2, idesc, 1u);
-            mma_bf16(accBC, a, b2 + PL, idesc, 1u);
-            mma_bf16(accBC, a + PL, b2, idesc, 1u);
+            mma_f16(accBC, a + 2 * PL, b2, idesc, 1u);                  // (2,0)
+            mma_f16(accBC, a + PL, b2 + PL, idesc, 1u);                 // (1,1)
+            mma_f16(accBC, a, b2 + PL, idesc, 1u);                      // (0,1)
+            mma_f16(accBC, a + PL, b2, idesc, 1u);                      // (1,0)
           }
           mma_commit(EMPTY(st));
         }
+        if (!ok) break;
         mma_commit(AFULL(set));
       }
+      // every MMA issued by this thread complete before TMEM is released
+      mma_commit(MMA_DONE);
+      mbar_drain(MMA_DONE, 0);
     }
-  } else if (CV && warp >= 2 && warp < 2 + CONV_WARPS) {
-    // converter warps: thread t converts half a row (16 reals) of each tile:
-    // row t / 2, plane chunks 2 (t & 1) and 2 (t & 1) + 1
-    const int t = (warp - 2) * 32 + lane;
-    const int r = t >> 1, hf = t & 1;
+  } else if (CV != 0 && warp >= 2 && warp < 2 + CONV_WARPS) {
+    // converter warps: warp w handles rows 32 (w & 3) .. + 31 (one per lane)
+    // and K half w >> 2 (16 reals = two 8-real chunks of each plane)
+    const int w = warp - 2;
+    const int r = 32 * (w & 3) + lane, hf = w >> 2;
     uint32_t it = 0;
     bool ok = true;
     for (long u = u_begin; u < u_end && ok; u += u_step) {
       int b, mi, ni, kc;
       decode(u, b, mi, ni, kc);
       const int row = mi * BM + r;
-      // 2^(7 - e): the row's scale, exact (e of a normal FP32 row maximum)
+      // 2^(7 - e): the row's scale, exact
       const float sc = pow2f(7 - (row < g.M ? row_exp(eA, (long)b * seA + row) : 0));
       const int kb1 = min(g.nkb, (kc + 1) * g.ckb);
       for (int kb = kc * g.ckb; kb < kb1; kb++, it++) {
@@ -458,28 +493,33 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
         if (!mbar_wait(SFULL(sa), (it / SA_STAGES) & 1, err, 128)) { ok = false; break; }
         if (!mbar_wait(EMPTY(st), ((it / STAGES) & 1) ^ 1, err, 256)) { ok = false; break; }
         const unsigned char* src = smem + sa * SA_BYTES;
-        unsigned char* dstp = smem + A_BYTES + st * STAGE_BYTES;
+        unsigned char* dstp = smem + A_BYTES + st * SBYTES;
 #pragma unroll
         for (int k2 = 0; k2 < 2; k2++) {
           const int pc = 2 * hf + k2;               // 8 reals = one 16-byte chunk of each plane
-          // FP32 row r, 128B swizzle: 16-byte chunk c at r * 128 + 16 (c ^ (r & 7))
-          const float4 f0 = *reinterpret_cast<const float4*>(src + r * 128 + 16 * ((2 * pc) ^ (r & 7)));
-          const float4 f1 = *reinterpret_cast<const float4*>(src + r * 128 + 16 * ((2 * pc + 1) ^ (r & 7)));
-          const float x[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-          uint32_t w[4][4];   // [plane][pair of reals]: the bf16 halves of two FP32 slices
+          float x[8];
+          if constexpr (CV == 1) {
+            // FP32 row r, 128B swizzle: 16-byte chunk c at r * 128 + 16 (c ^ (r & 7))
+            const float4 f0 = *reinterpret_cast<const float4*>(src + r * 128 + 16 * ((2 * pc) ^ (r & 7)));
+            const float4 f1 = *reinterpret_cast<const float4*>(src + r * 128 + 16 * ((2 * pc + 1) ^ (r & 7)));
+            x[0] = f0.x; x[1] = f0.y; x[2] = f0.z; x[3] = f0.w;
+            x[4] = f1.x; x[5] = f1.y; x[6] = f1.z; x[7] = f1.w;
+          } else {
+            // [16 K rows][256 floats]: the complex value (K j, row r) at (j * 256 + 2 r) floats
 #pragma unroll
-          for (int j = 0; j < 8; j += 2) {
-            float lo[4], hi[4];
-            slice4_planes(x[j] * sc, lo);
-            slice4_planes(x[j + 1] * sc, hi);
-#pragma unroll
-            for (int p = 0; p < 4; p++) w[p][j >> 1] = __byte_perm(__float_as_uint(lo[p]), __float_as_uint(hi[p]), 0x7632);
+            for (int j = 0; j < 4; j++) {
+              const float2 v = *reinterpret_cast<const float2*>(src + ((4 * pc + j) * 256 + 2 * r) * 4);
+              x[2 * j] = v.x;
+              x[2 * j + 1] = v.y;
+            }
           }
-          // bf16 row r of each plane, 64B swizzle: chunk pc at r * 64 + 16 (pc ^ ((r >> 1) & 3))
+          uint32_t wd[NPL][4];
+          slice8_f16(x, sc, wd);
+          // plane row r, 64B swizzle: chunk pc at r * 64 + 16 (pc ^ ((r >> 1) & 3))
           const uint32_t off = r * 64 + 16 * (pc ^ ((r >> 1) & 3));
 #pragma unroll
-          for (int p = 0; p < 4; p++)
-            *reinterpret_cast<uint4*>(dstp + p * TILE_BYTES + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+          for (int p = 0; p < NPL; p++)
+            *reinterpret_cast<uint4*>(dstp + p * TILE_BYTES + off) = make_uint4(wd[p][0], wd[p][1], wd[p][2], wd[p][3]);
         }
         // the planes were written by the generic proxy; the MMA reads them through the async proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -530,9 +570,10 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
 #pragma unroll
           for (int j = 0; j < 16; j += 2) {
             if (col0 + j >= g.Nr) break;
-            const double sc = pow2d(ea + ep[j >> 1] - 14);
-            const double x0 = ((double)__float2int_rn(va[j]) + (double)vb[j]) * sc;
-            const double x1 = ((double)__float2int_rn(va[j + 1]) + (double)vb[j + 1]) * sc;
+            const double sc = pow2d(ea + ep[j >> 1] - 30);
+            // va holds 2^16 times an exact integer below 2^24
+            const double x0 = ((double)va[j] + (double)vb[j]) * sc;
+            const double x1 = ((double)va[j + 1] + (double)vb[j + 1]) * sc;
             if (col0 + j + 1 < g.Nr && (ldo % 2) == 0) {
               *reinterpret_cast<double2*>(o + col0 + j) = make_double2(x0, x1);
             } else {
@@ -543,18 +584,22 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
         } else {
           // values of this lane's row into the staging tile
           if constexpr (OUT == 2) {
+            // the exact leading sum as an int32 (va / 2^16 is an integer below
+            // 2^24) and the remainder, both in units of 2^16
 #pragma unroll
             for (int j = 0; j < 16; j += 4)
               *reinterpret_cast<float4*>(stg + stage_off(lane, j >> 2)) =
-                  make_float4(__int_as_float(__float2int_rn(va[j])), __int_as_float(__float2int_rn(va[j + 1])),
-                              __int_as_float(__float2int_rn(va[j + 2])), __int_as_float(__float2int_rn(va[j + 3])));
+                  make_float4(__int_as_float(__float2int_rn(va[j] * 0x1p-16f)),
+                              __int_as_float(__float2int_rn(va[j + 1] * 0x1p-16f)),
+                              __int_as_float(__float2int_rn(va[j + 2] * 0x1p-16f)),
+                              __int_as_float(__float2int_rn(va[j + 3] * 0x1p-16f)));
           } else {
             float y[16];
 #pragma unroll
             for (int j = 0; j < 16; j += 4) {
-              const float s0 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, 8 * qq + (j >> 1)) - 14);
-              const float s1 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, 8 * qq + (j >> 1) + 1) - 14);
-              // va holds an exact integer below 2^24
+              const float s0 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, 8 * qq + (j >> 1)) - 30);
+              const float s1 = pow2f(ea + __shfl_sync(0xffffffffu, ebl, 8 * qq + (j >> 1) + 1) - 30);
+              // va is exact: one rounding in the add
               y[j] = (va[j] + vb[j]) * s0;
               y[j + 1] = (va[j + 1] + vb[j + 1]) * s0;
               y[j + 2] = (va[j + 2] + vb[j + 2]) * s1;
@@ -588,7 +633,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
 #pragma unroll
               for (int j = 0; j < 16; j += 4)
                 *reinterpret_cast<float4*>(stg + stage_off(lane, j >> 2)) =
-                    make_float4(vb[j], vb[j + 1], vb[j + 2], vb[j + 3]);
+                    make_float4(vb[j] * 0x1p-16f, vb[j + 1] * 0x1p-16f, vb[j + 2] * 0x1p-16f, vb[j + 3] * 0x1p-16f);
               __syncwarp();
             }
 #pragma unroll
@@ -716,7 +761,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-// A 3-D bf16 plane [batch][rows][ld] read as boxes of 32 (K) x 128 (rows).
+// A 3-D fp16 plane [batch][rows][ld] read as boxes of 32 (K) x 128 (rows).
 cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows, int cols, int ld) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
@@ -725,7 +770,7 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
   cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * rows};
   cuuint32_t box[3] = {BKR, 128, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides,
+  CUresult r = enc((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, (void*)base, dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -741,6 +786,22 @@ cudaError_t make_f32_map(void* map_out, const void* base, int batch, int rows, i
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t make_f32_map_t(void* map_out, const void* base, int batch, int kdim, int rows, int ld) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  if (((uintptr_t)base & 15) || (ld * 4) % 16) return cudaErrorInvalidValue;
+  // [batch][kdim][ld floats], 2 rows floats valid per K row; boxes of 128
+  // complex rows (256 floats) by 16 K rows
+  cuuint64_t dims[3] = {(cuuint64_t)(2 * rows), (cuuint64_t)kdim, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)ld * 4 * kdim};
+  cuuint32_t box[3] = {2 * BM, BKR / 2, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -798,8 +859,9 @@ long tc_partial_elems(int M, int Nr, int Kr, int batch) {
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
-                    cudaEvent_t gemm_done, int slices, bool a_f32, int herm) {
-  if (slices != 3 && slices != 4) return cudaErrorInvalidValue;
+                    cudaEvent_t gemm_done, int products, int a_conv, int herm) {
+  if (products != 6 && products != 8) return cudaErrorInvalidValue;
+  if (a_conv < 0 || a_conv > 2) return cudaErrorInvalidValue;
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   Maps maps;
   for (int p = 0; p < NPL; p++) {
@@ -819,7 +881,7 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   g.upb = 0;
   if (herm) {
     // a Hermitian FP32 product written whole: square, one chunk, FP32 interleaved output
-    if (Nr != 2 * M || g.nchunk != 1 || out_f64 || a_f32 || (ldo % 2) || (sbo % 2)) return cudaErrorInvalidValue;
+    if (Nr != 2 * M || g.nchunk != 1 || out_f64 || a_conv || (ldo % 2) || (sbo % 2)) return cudaErrorInvalidValue;
     for (int mi = 0; mi < g.mt; mi++) g.upb += g.nt - herm_n0(mi);
     g.units = (long)batch * g.upb;
   }
@@ -835,29 +897,29 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   }
   const unsigned grid = (unsigned)std::min<long>(g.units, nsm);
   cudaError_t e = cudaSuccess;
-#define LAUNCH4(OUTK, NSK, ARK, CVK)                                                                      \
+#define LAUNCH(OUTK, NPK, ARK, CVK)                                                                       \
   {                                                                                                       \
-    e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK, NSK, ARK, CVK>,                                         \
+    e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK, NPK, ARK, CVK>,                                         \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);               \
     if (e != cudaSuccess) return e;                                                                       \
-    tc_gemm_kernel<OUTK, NSK, ARK, CVK><<<grid, Roles<CVK>::NT, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, \
+    tc_gemm_kernel<OUTK, NPK, ARK, CVK><<<grid, Roles<CVK>::NT, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, \
                                                                            out, ldo, sbo, ps0, pbc, err); \
   }
-#define LAUNCH(OUTK, NSK, ARK) LAUNCH4(OUTK, NSK, ARK, false)
+#define BY_OUT(NPK, ARK, CVK) \
+  { if (split) LAUNCH(2, NPK, ARK, CVK) else if (out_f64) LAUNCH(1, NPK, ARK, CVK) else LAUNCH(0, NPK, ARK, CVK) }
   // A resident when all K fits the resident tile (one chunk of at most 4 K blocks)
-  const bool ar = slices == 3 && !split && g.nkb <= 4;
-  if (a_f32) {
-    if (slices != 4) return cudaErrorInvalidValue;
-    if (split) LAUNCH4(2, 4, false, true) else if (out_f64) LAUNCH4(1, 4, false, true) else LAUNCH4(0, 4, false, true)
-  } else if (slices == 4) {
-    if (split) LAUNCH(2, 4, false) else if (out_f64) LAUNCH(1, 4, false) else LAUNCH(0, 4, false)
+  const bool ar = !a_conv && !split && g.nkb <= 4 && products == 6;
+  if (a_conv == 1) {
+    if (products == 6) BY_OUT(6, false, 1) else BY_OUT(8, false, 1)
+  } else if (a_conv == 2) {
+    if (products == 6) BY_OUT(6, false, 2) else BY_OUT(8, false, 2)
   } else if (ar) {
-    if (out_f64) LAUNCH(1, 3, true) else LAUNCH(0, 3, true)
+    if (out_f64) LAUNCH(1, 6, true, 0) else LAUNCH(0, 6, true, 0)
   } else {
-    if (split) LAUNCH(2, 3, false) else if (out_f64) LAUNCH(1, 3, false) else LAUNCH(0, 3, false)
+    if (products == 6) BY_OUT(6, false, 0) else BY_OUT(8, false, 0)
   }
+#undef BY_OUT
 #undef LAUNCH
-#undef LAUNCH4
   e = cudaGetLastError();
   if (e == cudaSuccess && gemm_done) e = cudaEventRecord(gemm_done, s);
   if (e != cudaSuccess || !split) return e;

@@ -4,13 +4,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-// Four bf16 fixed-point slices of one GEMM operand, each a TMA tensor map
-// over [batch][rows][ld] (32-element K boxes, 128 rows, 64B swizzle).
+// Three fp16 fixed-point slices of one GEMM operand, each a TMA tensor map
+// over [batch][rows][ld] (32-element K boxes, 128 rows, 64B swizzle); an
+// operand converted inside the GEMM uses map[0] only (an FP32 map).
 struct TcOperand {
-  alignas(64) unsigned char map[4][128];
+  alignas(64) unsigned char map[3][128];
 };
 
-// Encode the map of one bf16 plane: `rows` x `cols` valid elements per batch,
+// Encode the map of one fp16 plane: `rows` x `cols` valid elements per batch,
 // leading dimension `ld` elements (ld * 2 bytes must be a multiple of 16).
 cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows, int cols, int ld);
 
@@ -19,27 +20,32 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
 // whose pair (2j, 2j + 1) shares the exponent eB[b * seB + j]; Kr real K.
 // FP32 output, or FP64 output when out_f64.  K is taken in the chunks
 // tc_chunk_blocks gives; with more than one chunk ps0 / pbc (tc_partial_elems
-// elements each) hold the exact chunk sums until they are combined.  `err` receives a nonzero code if a device wait
-// gave up.
-// gemm_done (may be null) is recorded on `s` right after the GEMM kernel,
-// before any combine kernel, so that the GEMM alone can be timed.  slices: 4
-// (all four planes, 10 slice products) or 3 (the first three planes, the 6
-// products s + t <= 2: about 2^-24 of the row scales).  a_f32: A.map[0] is an
-// FP32 map (make_f32_map) of the interleaved complex A, cut into its four
-// slices inside the kernel with the row exponents eA.  herm (1 or 2): the
-// product is Hermitian (B built from conj(A), Nr = 2 M, one K chunk, FP32
-// output): only the tiles that reach the diagonal are computed, and each
-// writes its values on or above the diagonal, and with herm = 1 also their
-// conjugates at the mirrored positions (herm = 2 leaves the part below the
-// diagonal unwritten).
+// elements each) hold the exact chunk sums until they are combined.  `err`
+// receives a nonzero code if a device wait gave up.  gemm_done (may be null)
+// is recorded on `s` right after the GEMM kernel, before any combine kernel,
+// so that the GEMM alone can be timed.  products: 6 or 8 slice products per
+// real product (about 2^-27 or 2^-30 of the row scales dropped).  a_conv: 0 =
+// A is three planes; 1 = A.map[0] is an FP32 map (make_f32_map) of the
+// interleaved complex A [rows][K], cut into its slices inside the kernel with
+// the row exponents eA; 2 = A.map[0] is an FP32 map (make_f32_map_t) of the
+// stored transpose [K][rows] of A.  herm (1 or 2): the product is Hermitian
+// (B built from conj(A), Nr = 2 M, one K chunk, FP32 output): only the tiles
+// that reach the diagonal are computed, and each writes its values on or
+// above the diagonal, and with herm = 1 also their conjugates at the mirrored
+// positions (herm = 2 leaves the part below the diagonal unwritten).
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
-                    cudaEvent_t gemm_done = nullptr, int slices = 4, bool a_f32 = false, int herm = 0);
+                    cudaEvent_t gemm_done = nullptr, int products = 8, int a_conv = 0, int herm = 0);
 
 // Map of an FP32 matrix [batch][rows][ld floats] (cols valid) in 32-float K
 // boxes of 128 rows with 128B swizzle (ld * 4 bytes a multiple of 16).
 cudaError_t make_f32_map(void* map_out, const void* base, int batch, int rows, int cols, int ld);
+
+// Map of the FP32 matrix [batch][kdim][ld floats] whose first 2 rows floats
+// of each K row are valid, read as the transpose: boxes of 16 K rows by 128
+// complex rows (256 floats), no swizzle (ld * 4 bytes a multiple of 16).
+cudaError_t make_f32_map_t(void* map_out, const void* base, int batch, int kdim, int rows, int ld);
 
 // Map of a 2-D FP32 array [outer][inner] (rows stride_bytes apart, a multiple
 // of 16) read as boxes of box0 (inner, box0 * 4 bytes a multiple of 16) by
@@ -74,25 +80,16 @@ cudaError_t col_exponents_z(const double2* src, long sbs, int lds, int batch, in
 cudaError_t col_exponents_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, int* e,
                             cudaStream_t s);
 
-// Fixed-point slices of src[b][r][c] into planes[p][b][r][2c + d] (plane p at
-// planes + p * plane elements, leading dimension ldp) with row exponents e[b][r].
-cudaError_t slice_rows_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
-                         uint16_t* planes, long plane, int ldp, cudaStream_t s);
-cudaError_t slice_rows_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
-                         uint16_t* planes, long plane, int ldp, cudaStream_t s);
-// Slices of the contiguous rows src[row][0..np) (rows = batch x rows per
-// batch) with each row's exact exponent, found by the same kernel; writes the
-// exponents to e[row].
+// The three fp16 slices of the contiguous rows src[row][0..np) (rows = batch
+// x rows per batch) with each row's exact exponent, found by the same kernel;
+// writes the exponents to e[row].
 cudaError_t slice_rows_exact(const float2* src, int np, long rows, int* e, uint16_t* planes, long plane, int ldp,
                              cudaStream_t s);
 // Exponents alone of the contiguous rows src[row][0..np): one warp per row,
 // 16-byte loads when np is even.
 cudaError_t row_exponents_rows(const float2* src, int np, long rows, int* e, cudaStream_t s);
-// Transposed: planes[p][b][c][2r + d] of src[b][r][c] with column exponents e[b][c].
-cudaError_t slice_cols_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
-                         uint16_t* planes, long plane, int ldp, cudaStream_t s);
 
-// Embedded B operand planes of a complex B(k, j) (K x J per batch):
+// Embedded B operand planes (three fp16 slices) of a complex B(k, j) (K x J per batch):
 //   planes[p][b][2j + c][2k + d] = slice_p(E_cd(B(k, j)))  with row exponent e[b][j]
 // E = [[Br, -Bi], [Bi, Br]] (conj_a = 0) or [[Br, Bi], [Bi, -Br]] (conj_a = 1).
 // B(k, j) = src[b * sbs + k * ldk + j * ldj], conjugated if conj_src; the
@@ -101,6 +98,3 @@ cudaError_t embed_b(const void* src, bool src_f64, long sbs, long ldk, long ldj,
                     int batch, int K, int J, const int* e, uint16_t* planes, long plane, int ldp,
                     cudaStream_t s);
 
-// out[b][r][c] = 2^(e[b][r] - 7) (P0 + P1 + P2 + P3) at [b][r][2c + d], for tests.
-cudaError_t combine_planes(const uint16_t* planes, long plane, const int* e, int batch, int rows, int cols,
-                           int ldp, double2* out, cudaStream_t s);

@@ -1,19 +1,17 @@
-// Operand preparation of the tensor-core GEMMs (tc_gemm.cu): fixed-point
-// slicing of complex matrices into four bf16 planes, and the real embedding
-// of the thin B operand.
+// Operand preparation of the tensor-core GEMMs (tc_gemm.cu): row and column
+// exponents, fixed-point slicing of complex rows into three fp16 planes, and
+// the real embedding of the thin B operand.
 //
 // A row r with exponent e_r (max |re|, |im| over the row < 2^e_r) is written
-// as x = 2^(e_r - 7) (P0 + P1 + P2 + P3) with P_s = 2^(-8 s) S_s and S_s the
-// integers
-//   y0 = 2^(7 - e_r) x,  S0 = rint(y0),  y_{s+1} = 2^8 (y_s - S_s),  S_{s+1} = rint(y_{s+1})
-// each in [-128, 128].  Every step is exact in the working precision (FP64 for
-// the static collocation X, FP32 for per-build operands), so the planes carry
-// the first 32 bits of x relative to its row scale.
+// as x = 2^(e_r - 7) (S0 + 2^-11 S1 + 2^-22 S2) with the integers
+//   y = 2^(7 - e_r) x,  S0 = rint(y),  S1 = rint(2^11 (y - S0)),  S2 = rint(2^22 (y - S0) - 2^11 S1)
+// held in fp16 planes P0 = 2^8 S0, P1 = 2^-3 S1, P2 = 2^-14 S2 (slices.cuh).
+// Every step is exact in FP32, so the planes carry the first 30 bits of x
+// relative to its row scale.
 #include "thc_internal.cuh"
 #include "tc_gemm.cuh"
 #include "slices.cuh"
 
-#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <type_traits>
@@ -89,50 +87,6 @@ __global__ void __launch_bounds__(CE_WARPS * 32) colexp_kernel(const CT* __restr
   }
 }
 
-// planes[p][b][r][2c + d] of src[b][r][c] with row exponents e[b][r].
-template <typename CT, typename R>
-__global__ void slice_rows_kernel(const CT* __restrict__ src, long sbs, int lds, int batch, int rows, int cols,
-                                  const int* __restrict__ e, uint16_t* planes, long plane, int ldp) {
-  const long total = (long)batch * rows * cols;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % cols);
-    const long br = i / cols;
-    const int r = (int)(br % rows);
-    const int b = (int)(br / rows);
-    const CT v = src[(long)b * sbs + (long)r * lds + c];
-    const int ex = e[br];
-    uint16_t sr[4], si[4];
-    slice4((R)v.x, ex, sr);
-    slice4((R)v.y, ex, si);
-    store4(planes, plane, br * ldp + 2L * c, sr, si);
-  }
-}
-
-// planes[p][b][c][2r + d] of src[b][r][c] (the transpose), column exponents
-// e[b][c]; 32 x 32 tiles through shared memory.
-__global__ void slice_cols_kernel(const double2* __restrict__ src, long sbs, int lds, int rows, int cols,
-                                  const int* __restrict__ e, uint16_t* planes, long plane, int ldp) {
-  __shared__ double2 t[32][33];
-  const int b = blockIdx.z;
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int r = r0 + y, c = c0 + threadIdx.x;
-    t[y][threadIdx.x] = (r < rows && c < cols) ? src[(long)b * sbs + (long)r * lds + c] : make_double2(0, 0);
-  }
-  __syncthreads();
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int c = c0 + y, r = r0 + threadIdx.x;
-    if (c < cols && r < rows) {
-      const double2 v = t[threadIdx.x][y];
-      const int ex = e[(long)b * cols + c];
-      uint16_t sr[4], si[4];
-      slice4(v.x, ex, sr);
-      slice4(v.y, ex, si);
-      store4(planes, plane, ((long)b * cols + c) * ldp + 2L * r, sr, si);
-    }
-  }
-}
-
 // Embedded B planes of B(k, j) = src[b*sbs + k*ldk + j*ldj] (conjugated if
 // conj_src), row exponents e[b][j]:
 //   planes[p][b][2j + c][2k + d] = slice_p(E_cd(B(k, j)))
@@ -152,24 +106,24 @@ __global__ void embed_kernel(const CT* __restrict__ src, long sbs, long ldk, lon
     const R bi = conj_src ? -(R)v.y : (R)v.y;
     const int ex = e[bj];
     const long row0 = ((long)b * 2 * J + 2L * j) * ldp + 2L * k;
-    uint16_t s_br[4], s_bi[4], s_nbr[4], s_nbi[4];
-    slice4(br, ex, s_br);
-    slice4(bi, ex, s_bi);
-    negate4(s_br, s_nbr);
-    negate4(s_bi, s_nbi);
+    uint16_t s_br[3], s_bi[3], s_nbr[3], s_nbi[3];
+    slice3(br, ex, s_br);
+    slice3(bi, ex, s_bi);
+    negate3(s_br, s_nbr);
+    negate3(s_bi, s_nbi);
     if (!conj_a) {
-      store4(planes, plane, row0, s_br, s_nbi);
-      store4(planes, plane, row0 + ldp, s_bi, s_br);
+      store3(planes, plane, row0, s_br, s_nbi);
+      store3(planes, plane, row0 + ldp, s_bi, s_br);
     } else {
-      store4(planes, plane, row0, s_br, s_bi);
-      store4(planes, plane, row0 + ldp, s_bi, s_nbr);
+      store3(planes, plane, row0, s_br, s_bi);
+      store3(planes, plane, row0 + ldp, s_bi, s_nbr);
     }
   }
 }
 
 // Slices of the contiguous rows src[row][0..np) with the exact row exponent,
 // one warp per row: the warp reduces max(|re|, |im|) over its row, then
-// writes the four planes.  V = 2: two consecutive complex values per lane
+// writes the three planes.  V = 2: two consecutive complex values per lane
 // access (16-byte loads, np even).  R > 0: the row stays in registers (R
 // accesses per lane, np / V <= 32 R; used for short rows); R = 0: the row is
 // read twice, the second time mostly from cache (long rows: holding a row of
@@ -194,15 +148,15 @@ __global__ void slice_rowmax_kernel(const float2* __restrict__ src, int np, long
     } else {
       v[0] = w;
     }
-    uint16_t sl[V][2][4];
+    uint16_t sl[V][2][3];
 #pragma unroll
     for (int j = 0; j < V; j++) {
-      slice4(v[j].x, ex, sl[j][0]);
-      slice4(v[j].y, ex, sl[j][1]);
+      slice3(v[j].x, ex, sl[j][0]);
+      slice3(v[j].y, ex, sl[j][1]);
     }
     const long off = row * ldp + 2L * c * V;
 #pragma unroll
-    for (int p = 0; p < 4; p++) {
+    for (int p = 0; p < 3; p++) {
       if constexpr (V == 2) {
         *reinterpret_cast<uint2*>(planes + p * plane + off) =
             make_uint2((uint32_t)sl[0][0][p] | ((uint32_t)sl[0][1][p] << 16),
@@ -281,27 +235,6 @@ cudaError_t col_exponents_c(const float2* src, long sbs, int lds, int batch, int
   return cudaGetLastError();
 }
 
-cudaError_t slice_rows_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
-                         uint16_t* planes, long plane, int ldp, cudaStream_t s) {
-  slice_rows_kernel<double2, double><<<grid1((long)batch * rows * cols), 256, 0, s>>>(
-      src, sbs, lds, batch, rows, cols, e, planes, plane, ldp);
-  return cudaGetLastError();
-}
-
-cudaError_t slice_rows_c(const float2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
-                         uint16_t* planes, long plane, int ldp, cudaStream_t s) {
-  slice_rows_kernel<float2, float><<<grid1((long)batch * rows * cols), 256, 0, s>>>(
-      src, sbs, lds, batch, rows, cols, e, planes, plane, ldp);
-  return cudaGetLastError();
-}
-
-cudaError_t slice_cols_z(const double2* src, long sbs, int lds, int batch, int rows, int cols, const int* e,
-                         uint16_t* planes, long plane, int ldp, cudaStream_t s) {
-  dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch);
-  slice_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(src, sbs, lds, rows, cols, e, planes, plane, ldp);
-  return cudaGetLastError();
-}
-
 cudaError_t slice_rows_exact(const float2* src, int np, long rows, int* e, uint16_t* planes, long plane, int ldp,
                              cudaStream_t s) {
   const long nb = std::min<long>((rows + 3) / 4, 152L * 128);   // 4 warps (rows) per block
@@ -342,27 +275,5 @@ cudaError_t embed_b(const void* src, bool src_f64, long sbs, long ldk, long ldj,
   else
     embed_kernel<float2, float><<<grid, blk, 0, s>>>((const float2*)src, sbs, ldk, ldj, conj_src, conj_a, batch, K, J,
                                                   e, planes, plane, ldp);
-  return cudaGetLastError();
-}
-
-__global__ void combine_kernel(const uint16_t* planes, long plane, const int* e, int batch, int rows, int cols,
-                               int ldp, double2* out) {
-  const long total = (long)batch * rows * cols;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % cols);
-    const long br = i / cols;
-    const long off = br * ldp + 2L * c;
-    double re = 0.0, im = 0.0;
-    for (int p = 0; p < 4; p++) {
-      re += (double)__bfloat162float(__ushort_as_bfloat16(planes[p * plane + off]));
-      im += (double)__bfloat162float(__ushort_as_bfloat16(planes[p * plane + off + 1]));
-    }
-    out[i] = make_double2(ldexp(re, e[br] - 7), ldexp(im, e[br] - 7));
-  }
-}
-
-cudaError_t combine_planes(const uint16_t* planes, long plane, const int* e, int batch, int rows, int cols,
-                           int ldp, double2* out, cudaStream_t s) {
-  combine_kernel<<<grid1((long)batch * rows * cols), 256, 0, s>>>(planes, plane, e, batch, rows, cols, ldp, out);
   return cudaGetLastError();
 }

@@ -35,9 +35,11 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 struct Sizes {
   long nk, x, v, psi, kc;
   size_t el;  // bytes of a workspace complex element
-  // tensor-core planes (elements of one plane)
-  int ldXT, ldM, ldPs;
-  long plXn, plXT, plPs, plBc, plBd, plBy, plM;
+  // tensor-core operands: FP32 X with even leading dimension, planes (elements of one plane)
+  int ldX;
+  long x32;
+  int ldC, ldM, ldPs;
+  long plPs, plBc, plBd, plBy, plM;
   long nexp;  // exponents: eXn + eXT + ePsi + eC + eY + eM
   long npart; // split-K partial elements (max over the tensor-core GEMMs)
   long hkey;  // key words of the Hermitian convolution (0 where it does not apply)
@@ -53,13 +55,13 @@ Sizes sizes_of(const thc_dims* d, int precision) {
   s.psi = s.nk * d->nisdf * d->nocc;
   s.kc = s.nk * d->nbas * d->nocc;
   s.el = precision == THC_FP64 ? sizeof(double2) : sizeof(float2);
-  s.ldXT = pad8(2 * d->nbas);
+  s.ldX = d->nisdf + (d->nisdf & 1);
+  s.x32 = s.nk * d->nbas * (long)s.ldX;
+  s.ldC = pad8(2 * d->nbas);
   s.ldM = pad8(2 * d->nisdf);
   s.ldPs = pad8(2 * d->nocc);
-  s.plXn = s.nk * d->nbas * s.ldM;
-  s.plXT = s.nk * d->nisdf * s.ldXT;
   s.plPs = s.nk * d->nisdf * s.ldPs;
-  s.plBc = s.nk * 2 * d->nocc * s.ldXT;
+  s.plBc = s.nk * 2 * d->nocc * s.ldC;
   s.plBd = s.nk * 2L * d->nisdf * s.ldPs;
   s.plBy = s.nk * 2 * d->nocc * (long)s.ldM;
   s.plM = (d->nisdf % 2) ? s.nk * d->nisdf * (long)s.ldM : 0;   // M's slices only for odd N_P
@@ -94,7 +96,8 @@ size_t memory_bytes(const thc_dims* d, int precision) {
   b += 2 * s.psi * s.el;         // Psi, Y
   b += 2 * s.v * s.el;           // D, M
   if (precision == THC_MIXED) {
-    b += 4 * 2 * (s.plXn + s.plXT + s.plPs + s.plBc + s.plBd + s.plBy + s.plM);   // bf16 slices
+    b += s.x32 * sizeof(float2);                                             // X in FP32
+    b += 3 * 2 * (s.plPs + s.plBc + s.plBd + s.plBy + s.plM);               // fp16 slices
     b += sizeof(int) * s.nexp + 64;                                         // exponents, error word
     b += (sizeof(int) + sizeof(float)) * s.npart;                           // split-K partial sums
     b += sizeof(uint32_t) * s.hkey;                                          // Hermitian convolution keys
@@ -108,7 +111,7 @@ size_t memory_bytes(const thc_dims* d, int precision) {
 
 void free_all(thc_ctx* c) {
   void* ptrs[] = {c->X64, c->Vh64, c->X32, c->Vh32, c->Psi, c->D, c->M, c->Y,
-                  c->Cdev, c->KCdev, c->exdev, c->partial, c->flag, c->Xn_pl, c->XT_pl,
+                  c->Cdev, c->KCdev, c->exdev, c->partial, c->flag,
                   c->PsiA_pl, c->Bc_pl, c->Bd_pl, c->By_pl, c->ex_pl, c->tc_err, c->part_s0,
                   c->part_bc, c->M_pl, c->hkeys};
   for (void* p : ptrs)
@@ -189,13 +192,12 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
   } else {
     W((void**)&c->Vh32, s.v * s.el);
     W(&c->M, s.v * s.el);
-    if (s.plM) W((void**)&c->M_pl, 4 * 2 * s.plM);
-    W((void**)&c->Xn_pl, 4 * 2 * s.plXn);
-    W((void**)&c->XT_pl, 4 * 2 * s.plXT);
-    W((void**)&c->PsiA_pl, 4 * 2 * s.plPs);
-    W((void**)&c->Bc_pl, 4 * 2 * s.plBc);
-    W((void**)&c->Bd_pl, 4 * 2 * s.plBd);
-    W((void**)&c->By_pl, 4 * 2 * s.plBy);
+    W((void**)&c->X32, s.x32 * sizeof(float2));
+    if (s.plM) W((void**)&c->M_pl, 3 * 2 * s.plM);
+    W((void**)&c->PsiA_pl, 3 * 2 * s.plPs);
+    W((void**)&c->Bc_pl, 3 * 2 * s.plBc);
+    W((void**)&c->Bd_pl, 3 * 2 * s.plBd);
+    W((void**)&c->By_pl, 3 * 2 * s.plBy);
     W((void**)&c->ex_pl, sizeof(int) * s.nexp);
     W((void**)&c->tc_err, 64);
     if (s.npart > 0) {
@@ -227,8 +229,8 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
     }
   }
   if (precision == THC_MIXED) {
-    c->ldXT = s.ldXT; c->ldM = s.ldM; c->ldPs = s.ldPs;
-    c->plXn = s.plXn; c->plXT = s.plXT; c->plPs = s.plPs;
+    c->ldX = s.ldX; c->ldC = s.ldC; c->ldM = s.ldM; c->ldPs = s.ldPs;
+    c->plPs = s.plPs;
     c->plBc = s.plBc; c->plBd = s.plBd; c->plBy = s.plBy; c->plM = s.plM;
     const int nk = (int)s.nk, N = d->nbas, n = d->nocc, P = d->nisdf;
     c->eXn = c->ex_pl;
@@ -239,15 +241,16 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
     c->eM = c->eY + (long)nk * n;
     struct MapReq { TcOperand* op; uint16_t* base; long pl; int rows, cols, ld; };
     MapReq reqs[] = {
-        {&c->opXT, c->XT_pl, s.plXT, P, 2 * N, s.ldXT},
         {&c->opPs, c->PsiA_pl, s.plPs, P, 2 * n, s.ldPs},
-        {&c->opXn, c->Xn_pl, s.plXn, N, 2 * P, s.ldM},
-        {&c->opBc, c->Bc_pl, s.plBc, 2 * n, 2 * N, s.ldXT},
+        {&c->opBc, c->Bc_pl, s.plBc, 2 * n, 2 * N, s.ldC},
         {&c->opBd, c->Bd_pl, s.plBd, 2 * P, 2 * n, s.ldPs},
         {&c->opBy, c->By_pl, s.plBy, 2 * n, 2 * P, s.ldM},
     };
+    // X in FP32: A of S1 read as the transpose [mu][P] -> rows P, and A of S4b (rows mu)
+    e = make_f32_map_t(c->opXT.map[0], c->X32, nk, N, P, 2 * s.ldX);
+    if (e == cudaSuccess) e = make_f32_map(c->opXn.map[0], c->X32, nk, N, 2 * P, 2 * s.ldX);
     for (auto& r : reqs)
-      for (int p = 0; p < 4; p++) {
+      for (int p = 0; p < 3 && e == cudaSuccess; p++) {
         e = make_plane_map(r.op->map[p], r.base + p * r.pl, nk, r.rows, r.cols, r.ld);
         if (e != cudaSuccess) {
           g_create_error = std::string("cuTensorMapEncodeTiled: ") + cudaGetErrorString(e);
@@ -257,7 +260,7 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
         }
       }
     if (s.plM)
-      for (int p = 0; p < 4 && e == cudaSuccess; p++)
+      for (int p = 0; p < 3 && e == cudaSuccess; p++)
         e = make_plane_map(c->opM.map[p], c->M_pl + p * s.plM, nk, P, 2 * P, s.ldM);
     else
       e = make_f32_map(c->opMf.map[0], c->M, nk, P, 2 * P, 2 * P);
@@ -313,14 +316,13 @@ thc_status thc_set_collocation(thc_ctx* c, const double* X) {
   } else if (c->precision == THC_MIXED_SIMT) {
     CKC(c, convert_z2c(x, c->X32, n, c->stream));
   } else {
-    // X (rows mu, A of S4b) and X^T (rows P, A of S1) as fixed-point slices
-    const long sb = (long)c->nbas * c->nisdf;
-    CKC(c, row_exponents_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->eXn, c->stream));
-    CKC(c, col_exponents_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->eXT, c->stream));
-    CKC(c, slice_rows_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->eXn, c->Xn_pl, c->plXn, c->ldM,
-                        c->stream));
-    CKC(c, slice_cols_z(x, sb, c->nisdf, c->nk, c->nbas, c->nisdf, c->eXT, c->XT_pl, c->plXT, c->ldXT,
-                        c->stream));
+    // X in FP32 (rows padded to an even length), and the exponents that slice
+    // it inside the GEMMs: per basis function (rows of A in S4b) and per point
+    // (rows of A = X^T in S1), taken on the FP32 values
+    CKC(c, convert_z2c_rows(x, c->X32, (long)c->nk * c->nbas, c->nisdf, c->ldX, c->stream));
+    const long sb = (long)c->nbas * c->ldX;
+    CKC(c, row_exponents_c(c->X32, sb, c->ldX, c->nk, c->nbas, c->nisdf, c->eXn, c->stream));
+    CKC(c, col_exponents_c(c->X32, sb, c->ldX, c->nk, c->nbas, c->nisdf, c->eXT, c->stream));
   }
   CKC(c, cudaStreamSynchronize(c->stream));
   c->have_x = true;
@@ -440,6 +442,12 @@ static thc_status build_mixed(thc_ctx* c, const double2* C, double2* KC, double*
   return THC_OK;
 }
 
+// Slice products of the tensor-core GEMMs S1, S2, S4a and S4b (6 or 8, see
+// tc_gemm.cu).  Measured at 4x4x4 k, N_P = 1200 against the FP64 oracle: the
+// back-projections S4a and S4b, whose outputs carry the final precision, take
+// 8; S1 (rounded to FP32 Psi) and S2 (FP32 D) take 6.
+constexpr int kProducts[4] = {6, 6, 8, 8};
+
 static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex) {
   const int nk = c->nk, N = c->nbas, n = c->nocc, P = c->nisdf;
   const long PP = (long)P * P, Pn = (long)P * n, Nn = (long)N * n;
@@ -451,24 +459,24 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, mark(c, 0, s, false));
   // S1  Psi = X^T C on tensor cores: B = embedded C, one exponent per orbital
   CKC(c, col_exponents_z(C, Nn, n, nk, N, n, c->eC, s));
-  CKC(c, embed_b(C, true, Nn, n, 1, false, false, nk, N, n, c->eC, c->Bc_pl, c->plBc, c->ldXT, s));
+  CKC(c, embed_b(C, true, Nn, n, 1, false, false, nk, N, n, c->eC, c->Bc_pl, c->plBc, c->ldC, s));
   CKC(c, record_core(c, 0, 0, s));
+  // A = X^T, read from FP32 X [mu][P] and sliced (transposed) inside the GEMM
   CKC(c, tc_gemm(c->opXT, c->opBc, P, 2 * n, 2 * N, nk, c->eXT, P, c->eC, n, Psi, false, 2 * n, 2 * Pn,
-                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 0, 1)));
+                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 0, 1), kProducts[0], 2));
   CKC(c, mark(c, 1, s, false));
   // S2  D = Psi Psi^H on tensor cores: A = Psi and B = embedded Psi^H share the
   // row exponents of Psi
   CKC(c, slice_rows_exact(Psi, n, (long)nk * P, c->ePsi, c->PsiA_pl, c->plPs, c->ldPs, s));
   CKC(c, embed_b(Psi, false, Pn, 1, n, true, false, nk, n, P, c->ePsi, c->Bd_pl, c->plBd, c->ldPs, s));
   CKC(c, record_core(c, 1, 0, s));
-  // D is rounded to FP32 on output and K = 2 n is short: three slices; D is
-  // Hermitian, so only the tiles that reach the diagonal are multiplied
+  // D is Hermitian, so only the tiles that reach the diagonal are multiplied
   // (Hermitian V: M^k is Hermitian too, and S3 reads D on and above the
   // diagonal only, so S2 leaves the part below it unwritten)
   const bool a_f32 = c->plM == 0;
   const bool herm = c->herm_v && c->hkeys && a_f32;
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
-                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 1, 1), 3, false, herm ? 2 : 1));
+                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 1, 1), kProducts[1], 0, herm ? 2 : 1));
   c->d_upper = herm;
   CKC(c, mark(c, 2, s, false));
   // S3  M = IDFT(DFT(D) o Vh) in FP32
@@ -501,14 +509,15 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, embed_b(Psi, false, Pn, n, 1, false, false, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
   CKC(c, record_core(c, 3, 0, s));
   CKC(c, tc_gemm(a_f32 ? c->opMf : c->opM, c->opBy, P, 2 * n, 2 * P, nk, c->eM, P, c->eY, n, Y, false, 2 * n,
-                 2 * Pn, c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 3, 1), 4, a_f32));
+                 2 * Pn, c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 3, 1), kProducts[2], a_f32 ? 1 : 0));
   CKC(c, mark(c, 4, s, false));
-  // S4b KC = conj(X) Y on tensor cores: B = embedded Y (conj-A form)
+  // S4b KC = conj(X) Y on tensor cores: A = X (FP32, sliced inside the GEMM),
+  // B = embedded Y (conj-A form)
   CKC(c, col_exponents_c(Y, Pn, n, nk, P, n, c->eY, s));
   CKC(c, embed_b(Y, false, Pn, n, 1, false, true, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
   CKC(c, record_core(c, 4, 0, s));
   CKC(c, tc_gemm(c->opXn, c->opBy, N, 2 * n, 2 * P, nk, c->eXn, N, c->eY, n, KC, true, 2 * n, 2 * Nn,
-                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 4, 1)));
+                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 4, 1), kProducts[3], 1));
   CKC(c, mark(c, 5, s, false));
   CKC(c, record_core(c, 5, 0, s));
   CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));

@@ -50,8 +50,10 @@ struct thc_ctx {
   double2* X64;     // [nk][nbas][nisdf]
   double2* Vh64;    // [nk][nisdf][nisdf] prepared kernel (FP64 mode)
   // mixed state
-  float2* X32;      // [nk][nbas][nisdf]
+  float2* X32;      // [nk][nbas][ldX] (THC_MIXED_SIMT: ldX = nisdf; THC_MIXED: nisdf rounded up to
+                    // even, so that the FP32 rows are 16-byte strided for TMA)
   float2* Vh32;     // [nk][nisdf][nisdf]
+  int ldX;
   // workspace (element type follows the precision)
   void* Psi;        // [nk][nisdf][nocc]
   void* D;          // [nk][nisdf][nisdf]
@@ -63,26 +65,26 @@ struct thc_ctx {
   double* partial;  // reduction scratch
   int* flag;        // device flag word (finite checks)
   int n_partial;
-  // tensor-core operands (THC_MIXED): four bf16 fixed-point planes each,
+  // tensor-core operands (THC_MIXED): three fp16 fixed-point planes each,
   // plane p at base + p * plane elements, rows padded to 8 elements, and one
-  // power-of-two exponent per row
-  uint16_t* Xn_pl;    // [nk][nbas][ldM]     X, A of S4b          exponents eXn [nk][nbas]
-  uint16_t* XT_pl;    // [nk][nisdf][ldXT]   X^T, A of S1         eXT [nk][nisdf]
+  // power-of-two exponent per row.  X is A of S1 (as its transpose) and of
+  // S4b, read in FP32 from X32 and sliced inside the GEMM (exponents eXT per
+  // point, eXn per basis function).
   uint16_t* PsiA_pl;  // [nk][nisdf][ldPs]   Psi, A of S2         ePsi [nk][nisdf]
-  uint16_t* Bc_pl;    // [nk][2 nocc][ldXT]  embedded C, B of S1  eC [nk][nocc]
+  uint16_t* Bc_pl;    // [nk][2 nocc][ldC]   embedded C, B of S1  eC [nk][nocc]
   uint16_t* Bd_pl;    // [nk][2 nisdf][ldPs] embedded Psi^H, B of S2 (ePsi)
   uint16_t* By_pl;    // [nk][2 nocc][ldM]   embedded Psi, B of S4a, then embedded Y, B of S4b
                       //                     (column exponents of Psi, then of Y, in eY [nk][nocc])
                       // M (FP32 workspace) is A of S4a, sliced inside the GEMM   eM [nk][nisdf]
   uint16_t* M_pl;     // [nk][nisdf][ldM] M's slices, only for odd nisdf (FP32 rows of 8 nisdf
                       // bytes are not 16-byte strided, which the FP32 tensor map needs)
-  int* ex_pl;         // eXn | eXT | ePsi | eC | eY
+  int* ex_pl;         // eXn | eXT | ePsi | eC | eY | eM
   int* part_s0;       // split-K partial sums of the tensor-core GEMMs (exact leading class)
   float* part_bc;     // and their FP32 remainders
   int *eXn, *eXT, *ePsi, *eC, *eY, *eM;
-  long plXn, plXT, plPs, plBc, plBd, plBy, plM;
-  int ldXT, ldM, ldPs;
-  TcOperand opXT, opPs, opXn, opBc, opBd, opBy;
+  long plPs, plBc, plBd, plBy, plM;
+  int ldC, ldM, ldPs;
+  TcOperand opXT, opPs, opXn, opBc, opBd, opBy;   // opXT, opXn: FP32 maps of X32
   TcOperand opMf;     // map[0]: FP32 map of M (A of S4a, converted in the GEMM), even nisdf
   TcOperand opM;      // M's slices, odd nisdf
   int* tc_err;        // device word: nonzero after a device wait gave up
@@ -174,6 +176,8 @@ void set_global_error(const std::string& msg);
 
 // conversions and checks
 cudaError_t convert_z2c(const double2* in, float2* out, long n, cudaStream_t s);
+// out[r][c] (leading dimension ldo) = in[r][c] (contiguous rows of cols) in FP32.
+cudaError_t convert_z2c_rows(const double2* in, float2* out, long rows, int cols, int ldo, cudaStream_t s);
 cudaError_t convert_c2z(const float2* in, double2* out, long n, cudaStream_t s);
 cudaError_t check_finite_z(const double2* in, long n, int* flag, cudaStream_t s);
 
