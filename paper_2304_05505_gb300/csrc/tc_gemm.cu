@@ -80,11 +80,17 @@ constexpr int NPL = 3;                                       // slices per opera
 constexpr uint32_t TILE_BYTES = BM * BKR * 2;                // 8 KB (one plane of A or B)
 constexpr int MAX_CHUNK_KB = 32;                             // K blocks per exact chunk, at most (1024 real K)
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t RING_BYTES = 192 * 1024;
 constexpr uint32_t STAGE_BYTES = 2 * NPL * TILE_BYTES;       // A and B planes of one K block: 48 KB
 constexpr uint32_t EPI_TILE = 32 * 16;                       // floats per epilogue warp (32 rows x 16)
-constexpr int EPI_WARPS_MAX = 16;
-constexpr size_t SMEM_BYTES = RING_BYTES + 1024 + 256 + EPI_WARPS_MAX * EPI_TILE * 4;
+// Shared memory: the operand rings, 256 B of barriers, then the epilogue
+// warps' staging tiles.  Plane-fed forms: a 192 KB ring and 16 epilogue
+// warps; converted forms: 208 KB of rings (see the kernel) and 8 epilogue
+// warps.  Both come to the same total.
+template <int CV> struct Smem {
+  static constexpr uint32_t RING = CV ? 208 * 1024 : 192 * 1024;
+  static constexpr size_t BYTES = RING + 1024 + 256 + (CV ? 8 : 16) * EPI_TILE * 4;
+};
+static_assert(Smem<1>::BYTES <= 232448 && Smem<0>::BYTES <= 232448, "227 KB of shared memory per block");
 
 // Warp roles: 0 TMA, 1 MMA, then (CV) 8 converter warps, then the epilogue.
 // The converted-A forms take 8 epilogue warps, the others 16.
@@ -230,20 +236,29 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
   static_assert(NP == 6 || NP == 8, "slice products");
   static_assert(!(AR && CV), "A is resident planes or converted, not both");
   constexpr int AKB = 4;                                           // K blocks the resident A tile holds
-  constexpr int SA_STAGES = 3;                                     // FP32 staging ring of CV
-  constexpr uint32_t SA_BYTES = BM * BKR * 4;                      // 16 KB
   constexpr int CONV_WARPS = Roles<CV>::CONV_WARPS;
   constexpr int EPI_W = Roles<CV>::EPI, EPI_W0 = Roles<CV>::EPI0, EPI_COLS = Roles<CV>::COLS;
+  constexpr uint32_t RING_BYTES = Smem<CV>::RING;
+  // Converted forms: three decoupled rings so that the DRAM stream of A runs
+  // well ahead of the MMAs: FP32 A tiles (SA_STAGES x 16 KB, from DRAM), B
+  // planes (B_STAGES x 24 KB, TMA only) and the converted A planes (STAGES x
+  // 24 KB, written by the converter warps).
+  constexpr int SA_STAGES = 4, B_STAGES = 4;
+  constexpr uint32_t SA_BYTES = BM * BKR * 4;                      // 16 KB
+  constexpr uint32_t PL_BYTES = NPL * TILE_BYTES;                  // 24 KB: three planes of one operand
+  constexpr uint32_t B_OFF = SA_STAGES * SA_BYTES + 2 * PL_BYTES;  // CV: the B ring after the A plane ring
   // what precedes the plane ring: the resident A tile, or the FP32 staging ring
   constexpr uint32_t A_BYTES = AR ? AKB * NPL * TILE_BYTES : CV ? SA_STAGES * SA_BYTES : 0;
-  constexpr uint32_t SBYTES = AR ? NPL * TILE_BYTES : STAGE_BYTES;   // bytes of one ring stage
-  constexpr int STAGES = (RING_BYTES - A_BYTES) / SBYTES;
+  constexpr uint32_t SBYTES = (AR || CV) ? PL_BYTES : STAGE_BYTES;  // bytes of one plane-ring stage
+  constexpr int STAGES = CV ? 2 : (RING_BYTES - A_BYTES) / SBYTES;
   static_assert(STAGES >= 2 && STAGES <= 4, "ring stages");
+  static_assert(!CV || B_OFF + B_STAGES * PL_BYTES <= RING_BYTES, "ring size");
   uint64_t* bars = (uint64_t*)(smem + RING_BYTES);
   // barrier slots: full[4], empty[4], acc_full[2], acc_empty[2], resident A
-  // loaded / released, FP32 tile landed[3] / converted[3], MMAs drained, B
-  // planes landed[3] (CV: the full barrier then counts the converter warps)
-  uint32_t* tmem_slot = (uint32_t*)(bars + 24);
+  // loaded / released, FP32 tile landed / converted [SA_STAGES each], B planes
+  // landed / consumed [B_STAGES each], MMAs drained.  CV: full / empty are the
+  // converted A planes.
+  uint32_t* tmem_slot = (uint32_t*)(bars + 31);
   float* epi_stage = (float*)(smem + RING_BYTES + 256);   // EPI_W tiles of EPI_TILE floats
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = smem_u32(bars);
@@ -253,11 +268,12 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
   auto AEMPTY = [&](int s) { return bar0 + 8u * (10 + s); };
   const uint32_t AOP_FULL = bar0 + 8u * 12;    // resident A tile loaded
   const uint32_t AOP_EMPTY = bar0 + 8u * 13;   // MMAs on the resident A tile done
-  auto SFULL = [&](int s) { return bar0 + 8u * (14 + s); };    // CV: FP32 tile landed
-  auto SEMPTY = [&](int s) { return bar0 + 8u * (17 + s); };   // CV: FP32 tile converted
-  const uint32_t MMA_DONE = bar0 + 8u * 20;    // every MMA of the CTA complete
-  auto BFULL = [&](int s) { return bar0 + 8u * (21 + s); };    // CV: B planes landed
-  static_assert(!CV || STAGES <= 3, "barrier slots");
+  auto SFULL = [&](int s) { return bar0 + 8u * (14 + s); };                            // CV: FP32 tile landed
+  auto SEMPTY = [&](int s) { return bar0 + 8u * (14 + SA_STAGES + s); };               // CV: FP32 tile converted
+  auto BFULL = [&](int s) { return bar0 + 8u * (14 + 2 * SA_STAGES + s); };            // CV: B planes landed
+  auto BEMPTY = [&](int s) { return bar0 + 8u * (14 + 2 * SA_STAGES + B_STAGES + s); };  // CV: B planes consumed
+  const uint32_t MMA_DONE = bar0 + 8u * 30;    // every MMA of the CTA complete
+  static_assert(2 * SA_STAGES + 2 * B_STAGES <= 16, "barrier slots 14 .. 29");
 
   __shared__ int abort_flag;
   if (threadIdx.x == 0) abort_flag = *(volatile int*)err;
@@ -268,14 +284,17 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
-      mbar_init(FULL(s), CV ? CONV_WARPS : 1);   // CV: the converter warps (B bytes on BFULL)
+      mbar_init(FULL(s), CV ? CONV_WARPS : 1);   // CV: the converter warps
       mbar_init(EMPTY(s), 1);
-      if (CV) mbar_init(BFULL(s), 1);
     }
     if (CV) {
       for (int s = 0; s < SA_STAGES; s++) {
         mbar_init(SFULL(s), 1);
         mbar_init(SEMPTY(s), CONV_WARPS);
+      }
+      for (int s = 0; s < B_STAGES; s++) {
+        mbar_init(BFULL(s), 1);
+        mbar_init(BEMPTY(s), 1);
       }
     }
     for (int s = 0; s < 2; s++) {
@@ -369,11 +388,12 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
             else   // [K][rows] source: 16 complex K values (rows of the box) x 128 complex rows
               tma_load_3d(sbase + sa * SA_BYTES, &maps.a[0], SFULL(sa), mi * 2 * BM, kb * (BKR / 2), b);
             nsa++;
-            if (!mbar_wait(EMPTY(st), ph ^ 1, err, 2)) { ok = false; break; }
-            mbar_expect_tx(BFULL(st), NPL * TILE_BYTES);
-            const uint32_t dst = sbase + A_BYTES + st * SBYTES;
+            const int sb = it % B_STAGES;
+            if (!mbar_wait(BEMPTY(sb), ((it / B_STAGES) & 1) ^ 1, err, 2)) { ok = false; break; }
+            mbar_expect_tx(BFULL(sb), PL_BYTES);
             for (int p = 0; p < NPL; p++)
-              tma_load_3d(dst + (NPL + p) * TILE_BYTES, &maps.b[p], BFULL(st), kb * BKR, ni * BN, b);
+              tma_load_3d(sbase + B_OFF + sb * PL_BYTES + p * TILE_BYTES, &maps.b[p], BFULL(sb), kb * BKR,
+                          ni * BN, b);
             nfull++;
             continue;
           }
@@ -397,9 +417,9 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
         // exits.  Each drained barrier completes on TMA bytes alone, and only
         // the last ring's worth can be outstanding (a stage is reused only
         // after its copy was consumed).  Every wait here is bounded.
-        const uint32_t n = nfull < (uint32_t)STAGES ? nfull : (uint32_t)STAGES;
-        for (uint32_t j = nfull - n; j < nfull; j++)
-          mbar_drain(CV ? BFULL(j % STAGES) : FULL(j % STAGES), (j / STAGES) & 1);
+        constexpr uint32_t RS = CV ? B_STAGES : STAGES;
+        const uint32_t n = nfull < RS ? nfull : RS;
+        for (uint32_t j = nfull - n; j < nfull; j++) mbar_drain(CV ? BFULL(j % RS) : FULL(j % RS), (j / RS) & 1);
         if constexpr (CV != 0) {
           const uint32_t m = nsa < (uint32_t)SA_STAGES ? nsa : (uint32_t)SA_STAGES;
           for (uint32_t j = nsa - m; j < nsa; j++) mbar_drain(SFULL(j % SA_STAGES), (j / SA_STAGES) & 1);
@@ -437,15 +457,17 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
         for (int kb = kb0; kb < kb1; kb++, it++) {
           const int st = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
+          const int sb = it % B_STAGES;
           if (!mbar_wait(FULL(st), ph, err, 8)) { ok = false; break; }
-          if (CV && !mbar_wait(BFULL(st), ph, err, 8)) { ok = false; break; }
+          if (CV && !mbar_wait(BFULL(sb), (it / B_STAGES) & 1, err, 8)) { ok = false; break; }
           fence_after();
           // descriptors: one base per stage, planes and K steps are offsets of
           // (bytes >> 4) in the start-address field (no carry: smem < 256 KB)
           const uint64_t aBase = AR ? dbase + (((uint32_t)kb * NPL * TILE_BYTES) >> 4)
                                     : dbase + ((A_BYTES + st * SBYTES) >> 4);
           const uint64_t bBase = AR ? dbase + ((A_BYTES + st * SBYTES) >> 4)
-                                    : aBase + ((NPL * TILE_BYTES) >> 4);
+                                 : CV ? dbase + ((B_OFF + sb * PL_BYTES) >> 4)
+                                      : aBase + ((NPL * TILE_BYTES) >> 4);
           constexpr uint64_t PL = TILE_BYTES >> 4;
 #pragma unroll
           for (int kk = 0; kk < BKR / 16; kk++) {
@@ -466,6 +488,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
             mma_f16(accBC, a + PL, b2, idesc, 1u);                      // (1,0)
           }
           mma_commit(EMPTY(st));
+          if (CV) mma_commit(BEMPTY(sb));
         }
         if (!ok) break;
         mma_commit(AFULL(set));
@@ -900,9 +923,9 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
 #define LAUNCH(OUTK, NPK, ARK, CVK)                                                                       \
   {                                                                                                       \
     e = cudaFuncSetAttribute(tc_gemm_kernel<OUTK, NPK, ARK, CVK>,                                         \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);               \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<CVK>::BYTES);               \
     if (e != cudaSuccess) return e;                                                                       \
-    tc_gemm_kernel<OUTK, NPK, ARK, CVK><<<grid, Roles<CVK>::NT, SMEM_BYTES, s>>>(maps, g, eA, seA, eB, seB, \
+    tc_gemm_kernel<OUTK, NPK, ARK, CVK><<<grid, Roles<CVK>::NT, Smem<CVK>::BYTES, s>>>(maps, g, eA, seA, eB, seB, \
                                                                            out, ldo, sbo, ps0, pbc, err); \
   }
 #define BY_OUT(NPK, ARK, CVK) \
