@@ -60,11 +60,12 @@ typedef enum {
 
 typedef enum {
   THC_FP64 = 0,            /* every step in FP64 on CUDA cores */
-  THC_MIXED = 1,           /* S1, S2, S4b on tensor cores (tcgen05): each operand
-                              row scaled by a power of two and cut into four 8-bit
-                              fixed-point slices held in bf16, the leading products
-                              summed exactly; S3 in FP32; S4a on CUDA cores with
-                              compensated FP32 sums; E_x summed in FP64 */
+  THC_MIXED = 1,           /* S1, S2, S4a, S4b on tensor cores (tcgen05): each
+                              operand row scaled by a power of two and cut into
+                              three fixed-point slices of 8, 11 and 11 bits held
+                              as fp16, the leading products summed exactly, 6 or 8
+                              slice products per product; S3 in FP32; E_x summed
+                              in FP64 */
   THC_MIXED_SIMT = 2       /* the same precision on CUDA cores: FP32 operands,
                               float-float compensated sums in S1, S4a, S4b */
 } thc_precision;
@@ -149,6 +150,25 @@ thc_status thc_profile_kernels(const thc_ctx* ctx, float core_ms[6]);
  * wait of a tensor-core kernel gave up since the last thc_sync (its outputs
  * are then invalid; the context stays usable), else THC_OK. */
 thc_status thc_sync(thc_ctx* ctx);
+
+/* Test hooks for failure detection (no GPU fault is involved in either).
+ *
+ * thc_debug_set_wait_limit: the limit, in SM clock cycles, of the bounded
+ * device-side waits of the context's kernels (THC_MIXED; THC_ERR_UNSUPPORTED
+ * for the forms without such waits).  cycles <= 0 restores the default (about
+ * 2 s).  A limit of a few hundred cycles makes the waits of the next build
+ * give up before their data arrives: each kernel then lets its copies and
+ * MMAs in flight finish (with the default limit), stops, and thc_sync returns
+ * THC_ERR_TIMEOUT; after the default is restored the context builds
+ * correctly again.  Synchronises the context's stream.
+ *
+ * thc_debug_fail_alloc: the allocation with index nth (0-based, in the order
+ * thc_create makes them) of the next thc_create on the calling thread fails
+ * as if the device were out of memory, without calling the allocator; that
+ * thc_create then returns THC_ERR_OOM having freed everything it allocated.
+ * nth < 0 disables the hook. */
+thc_status thc_debug_set_wait_limit(thc_ctx* ctx, long long cycles);
+thc_status thc_debug_fail_alloc(int nth);
 
 /* Number of kernel launches one thc_build makes. */
 thc_status thc_launches_per_build(const thc_ctx* ctx, int* launches);

@@ -1,7 +1,9 @@
 // Shared-memory mbarrier helpers of the TMA-fed kernels (inline PTX,
-// sm_90 and later).  Every wait is bounded: about 2 s of clock64, after which
-// the waiting thread sets its code in an error word the host reads, so that a
-// lost transfer ends the kernel with an error status instead of a hang.
+// sm_90 and later).  Every wait is bounded: about 2 s of clock64 (or the
+// shorter limit stored beside the error word), after which the waiting thread
+// sets its code in an error word the host reads, so that a lost transfer ends
+// the kernel with an error status instead of a hang.  The drain after a
+// failed wait always takes the full limit.
 #pragma once
 
 #include <stdint.h>
@@ -9,6 +11,14 @@
 namespace {
 
 constexpr long long WAIT_LIMIT = 4000000000LL;   // clock64 cycles (~2 s)
+
+// The limit of the waits that report to the error word `err`: the 64-bit
+// value at err + 2 (bytes 8-15 of the word's 64-byte block) when positive (a
+// test sets a short one to make waits run out), else WAIT_LIMIT.
+__device__ __forceinline__ long long wait_limit(const int* err) {
+  const long long v = *reinterpret_cast<const volatile long long*>(err + 2);
+  return v > 0 ? v : WAIT_LIMIT;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -32,6 +42,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // CTA has set the error word.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
   const long long t0 = clock64();
+  long long limit = WAIT_LIMIT;
   for (uint32_t it = 0;; it++) {
     uint32_t done;
     asm volatile(
@@ -41,8 +52,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
+    if (it == 0) limit = wait_limit(err);   // read only when the first test fails
     if ((it & 255) == 255 && *(volatile int*)err != 0) return false;
-    if (clock64() - t0 > WAIT_LIMIT) {
+    if (clock64() - t0 > limit) {
       atomicOr(err, code);
       return false;
     }
@@ -56,6 +68,7 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, in
   int ok = 1;
   if ((threadIdx.x & 31) == 0) {
     const long long t0 = clock64();
+    long long limit = WAIT_LIMIT;
     uint32_t ns = 8;
     for (uint32_t it = 0;; it++) {
       uint32_t done;
@@ -66,8 +79,9 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, in
           : "r"(bar), "r"(parity)
           : "memory");
       if (done) break;
+      if (it == 0) limit = wait_limit(err);
       if ((it & 15) == 15 && *(volatile int*)err != 0) { ok = 0; break; }
-      if (clock64() - t0 > WAIT_LIMIT) {
+      if (clock64() - t0 > limit) {
         atomicOr(err, code);
         ok = 0;
         break;

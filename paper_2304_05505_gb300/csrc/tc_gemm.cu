@@ -412,11 +412,13 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
           nfull++;
         }
       }
-      if (!ok) {
-        // a wait gave up: let the copies already issued land before the CTA
-        // exits.  Each drained barrier completes on TMA bytes alone, and only
-        // the last ring's worth can be outstanding (a stage is reused only
-        // after its copy was consumed).  Every wait here is bounded.
+      {
+        // let the copies already issued land before the CTA exits (another
+        // role may have given up a wait, leaving them unconsumed).  Each
+        // drained barrier completes on TMA bytes alone, and only the last
+        // ring's worth can be outstanding (a stage is reused only after its
+        // copy was consumed); on the normal path every phase tested here has
+        // completed already.  Every wait here is bounded.
         constexpr uint32_t RS = CV ? B_STAGES : STAGES;
         const uint32_t n = nfull < RS ? nfull : RS;
         for (uint32_t j = nfull - n; j < nfull; j++) mbar_drain(CV ? BFULL(j % RS) : FULL(j % RS), (j / RS) & 1);

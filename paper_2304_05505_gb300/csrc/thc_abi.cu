@@ -20,6 +20,7 @@
 namespace {
 
 thread_local std::string g_create_error;
+thread_local int g_fail_alloc = -1;   // test hook: index of the next thc_create allocation to fail
 
 #define CKC(ctx, call)                                                       \
   do {                                                                       \
@@ -214,9 +215,11 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
   W((void**)&c->exdev, 2 * sizeof(double));
   W((void**)&c->partial, 2 * kPartials * sizeof(double));
   W((void**)&c->flag, 64);
+  const int fail_at = g_fail_alloc;
+  g_fail_alloc = -1;
   for (int i = 0; i < nw; i++) {
     Want& w = want[i];
-    e = cudaMalloc(w.p, w.bytes);
+    e = i == fail_at ? cudaErrorMemoryAllocation : cudaMalloc(w.p, w.bytes);
     if (e == cudaSuccess) e = cudaMemset(*w.p, 0, w.bytes);   // plane padding stays zero
     if (e != cudaSuccess) {
       if (*w.p) cudaFree(*w.p);
@@ -557,6 +560,20 @@ thc_status thc_build_host(thc_ctx* c, const double* C_host, double* KC_host, dou
   CKC(c, cudaMemcpyAsync(KC_host, c->KCdev, kcb, cudaMemcpyDeviceToHost, c->stream));
   CKC(c, cudaMemcpyAsync(ex_host, c->exdev, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return thc_sync(c);
+}
+
+thc_status thc_debug_set_wait_limit(thc_ctx* c, long long cycles) {
+  if (!c) return THC_ERR_ARG;
+  if (!c->tc_err) return THC_ERR_UNSUPPORTED;   // only the tensor-core form has device-side waits
+  const long long v = cycles > 0 ? cycles : 0;
+  CKC(c, cudaMemcpyAsync(reinterpret_cast<char*>(c->tc_err) + 8, &v, sizeof v, cudaMemcpyHostToDevice, c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return THC_OK;
+}
+
+thc_status thc_debug_fail_alloc(int nth) {
+  g_fail_alloc = nth >= 0 ? nth : -1;
+  return THC_OK;
 }
 
 thc_status thc_sync(thc_ctx* c) {

@@ -30,7 +30,8 @@ EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_ker
            "thc_launches_per_build", "thc_hermitian_kernel", "thc_destroy", "thc_status_string", "thc_last_error",
            "thc_profile_begin", "thc_profile_end", "thc_sync", "thc_kconv_noalloc",
            "thc_select_points", "thc_fit_kernel", "thc_profile_kernels", "thc_mlp_features", "thc_mlp_score",
-           "thc_mlp_workspace_bytes", "thc_mlp_train_step", "thc_mlp_candidates", "thc_select_points_among"]
+           "thc_mlp_workspace_bytes", "thc_mlp_train_step", "thc_mlp_candidates", "thc_select_points_among",
+           "thc_debug_set_wait_limit", "thc_debug_fail_alloc"]
 
 MLP_NPARAM = 8641
 
@@ -74,6 +75,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_profile_kernels.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.thc_destroy.argtypes = [vp]
     lib.thc_sync.argtypes = [vp]
+    lib.thc_debug_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    lib.thc_debug_fail_alloc.argtypes = [ip]
     lib.thc_kconv_noalloc.argtypes = [dp, dp, dp, ip, ip, ip, ctypes.c_long, vp]
     lib.thc_select_points.argtypes = [dp, ip, ip, ip, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), dp, vp]
@@ -237,6 +240,16 @@ def thc_launches_per_build(ctx) -> int:
 
 def thc_sync(ctx) -> None:
     _check(load().thc_sync(ctx), "thc_sync", ctx)
+
+
+def thc_debug_set_wait_limit(ctx, cycles: int) -> None:
+    """Test hook: the limit of the context's bounded device waits (see include/thc.h)."""
+    _check(load().thc_debug_set_wait_limit(ctx, int(cycles)), "thc_debug_set_wait_limit", ctx)
+
+
+def thc_debug_fail_alloc(nth: int) -> None:
+    """Test hook: make allocation nth of the next thc_create fail (see include/thc.h)."""
+    _check(load().thc_debug_fail_alloc(int(nth)), "thc_debug_fail_alloc")
 
 
 def thc_kconv_noalloc(D, V, M, mesh, npq: int, stream: int | None = None) -> None:

@@ -58,8 +58,10 @@ def test_memory_bytes_arithmetic():
 
     def pad8(x):
         return (x + 7) // 8 * 8
-    planes = nk * (N * pad8(2 * P) + P * pad8(2 * N) + P * pad8(2 * n)
-                   + 2 * n * pad8(2 * N) + 2 * P * pad8(2 * n) + 2 * n * pad8(2 * P))
+    # fp16 planes of Psi (A of S2), embedded C, Psi^H and Psi / Y (B operands);
+    # X itself is kept once in FP32 with rows padded to an even length
+    planes = nk * (P * pad8(2 * n) + 2 * n * pad8(2 * N) + 2 * P * pad8(2 * n) + 2 * n * pad8(2 * P))
+    x32 = 8 * nk * N * (P + P % 2)
     exps = nk * (N + 3 * P + 2 * n)
     def chunks(rows, kr):
         # split-K chunks: the fewest of at most 32 K blocks of 32 reals, one
@@ -76,12 +78,12 @@ def test_memory_bytes_arithmetic():
     # row and column keys of the Hermitian convolution: tiles of 8 rows by
     # 32 / n1 columns, n1 slots of ceil(N2 N3 / 2) words per row
     hkey = (-(-P // 8) + -(-P // 8)) * P * 4 * 8 + -(-P // 8) + 1   # + the tile table
-    tc = 8 * (nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + 4 * 2 * planes \
+    tc = 8 * (nk * P * P + 2 * nk * P * n + 2 * nk * P * P) + x32 + 3 * 2 * planes \
         + 4 * exps + 64 + 8 * part + 4 * hkey + common
     assert thc.thc_memory_bytes(d, thc.THC_MIXED) == tc
     # odd N_P: M's slices are kept in HBM as well (FP32 rows not 16-byte strided)
     d1 = dict(d, nisdf=P + 1)
-    extra = 4 * 2 * nk * (P + 1) * pad8(2 * (P + 1))
+    extra = 3 * 2 * nk * (P + 1) * pad8(2 * (P + 1))
     # (and the Hermitian convolution, which needs 16-byte strided FP32 rows too, has no keys)
     assert thc.thc_memory_bytes(d1, thc.THC_MIXED) - extra > thc.thc_memory_bytes(d, thc.THC_MIXED) - 4 * hkey
 
