@@ -30,19 +30,28 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "THC-oo-K exchange builds/s, mixed vs FP64 on one GB300 at <=1e-6 Ha; % roofline"
-WORKLOAD = ("benzene-shaped orthorhombic cell 13.9x17.8x12.9 bohr, 48 centres, N=432, n_occ=60, "
-            "4x4x4 k (N_k=64), N_ISDF=1200, 40^3 grid (config C2)")
-CONFIG = "C2"
+WORKLOADS = {
+    "C2": ("benzene-shaped orthorhombic cell 13.9x17.8x12.9 bohr, 48 centres, N=432, n_occ=60, "
+           "4x4x4 k (N_k=64), N_ISDF=1200, 40^3 grid (config C2)"),
+    "C3": ("2x1x1 supercell of the benzene-shaped cell, 27.8x17.8x12.9 bohr, 96 centres, N=864, n_occ=120, "
+           "6x6x6 k (N_k=216), N_ISDF=2400, 80x40x40 grid (config C3)"),
+}
 SAMPLE_FRACTION = 8      # the CPU oracle sample is 1/8 of a build
-# bf16 slice products per real product of each tensor-core GEMM
-SLICE_PRODUCTS = {"S1_collocate": 10, "S2_density": 6, "S4a_apply_M": 10, "S4b_backproject": 10}
-# the main kernel of each stage of the tensor-core build
-KERNEL_NAMES = {"S1_collocate": "tc_gemm_kernel<0, 4, 0, 0> (S1)",
-                "S2_density": "tc_gemm_kernel<0, 3, 1, 0> (S2, Hermitian tiles)",
-                "S3_kconv": "kconv_herm_kernel<4, 4, 4> (S3, Hermitian tiles)",
-                "S4a_apply_M": "tc_gemm_kernel<2, 4, 0, 1> (S4a, split-K, M sliced in the GEMM)",
-                "S4b_backproject": "tc_gemm_kernel<2, 4, 0, 0> (S4b, split-K)",
-                "S5_energy": "ex_partial_c + ex_final (S5)"}
+# fp16 slice products per real product of each tensor-core GEMM (the
+# library's plan: S1 and S2 rounded to FP32 take 6, the back-projections 8)
+SLICE_PRODUCTS = {"S1_collocate": 6, "S2_density": 6, "S4a_apply_M": 8, "S4b_backproject": 8}
+
+
+def kernel_names(hermitian: bool) -> dict:
+    """The main kernel of each stage of the tensor-core build."""
+    return {"S1_collocate": "tc_gemm_kernel<0, 6, 0, 2> (S1, X^T read from FP32 X and sliced in the GEMM)",
+            "S2_density": ("tc_gemm_kernel<0, 6, 1, 0> (S2, A resident, Hermitian tiles)" if hermitian else
+                           "tc_gemm_kernel<0, 6, 1, 0> (S2, A resident, Hermitian tiles mirrored)"),
+            "S3_kconv": ("kconv_herm_kernel<4, 4, 4> (S3, Hermitian tiles)" if hermitian else
+                         "kconv_tile_kernel (S3, TMA-fed shared-memory DFTs)"),
+            "S4a_apply_M": "tc_gemm_kernel<2, 8, 0, 1> (S4a, split-K, M sliced in the GEMM)",
+            "S4b_backproject": "tc_gemm_kernel<2, 8, 0, 1> (S4b, split-K, X sliced in the GEMM)",
+            "S5_energy": "ex_partial_c + ex_final (S5)"}
 
 
 def parse():
@@ -54,6 +63,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-samples", type=int, default=4)
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error and CPU baseline")
+    ap.add_argument("--config", default="C2", choices=sorted(WORKLOADS),
+                    help="C2 (default: the headline workload) or C3, the 6x6x6-k supercell at scale, "
+                         "timed once for the record (its inputs take minutes to make)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="time the mixed build alone (no host-buffer, CUDA-core, FP64 or oracle arms): "
                          "the small process a profiler capture runs")
@@ -313,18 +325,58 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     from paper_2304_05505_gb300 import cells
-    p = cells.make_problem(CONFIG)
+    p = make_inputs(args.config)
     steps = args.steps
     warm = args.warmup
     cb = time_oracle(p, steps, warm)
     line = {"metric": METRIC, "value": cb["value"], "unit": "builds/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "ms_per_step": cb["step_s"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (oracle/thc_oracle.py)"},
+            "config": {"workload": WORKLOADS[args.config], "impl": "FP64 CPU oracle (oracle/thc_oracle.py)"},
             "impl": "reference",
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": cb["value"], "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_simt(args, thc, d, p, C, KC, ex, dev, stream, world, e0, e1):
+    """The mixed precision on CUDA cores: ms per build, stage ms, KC, E_x."""
+    import torch
+    es = thc.ExchangeBuild(d, "mixed_simt", device=dev, stream=stream)
+    es.set_collocation(p.X)
+    es.set_kernel(p.V)
+    for _ in range(2):
+        es.build(C, KC, ex)
+    torch.cuda.synchronize()
+    nsimt = max(3, min(args.steps, 10))
+    thc.thc_profile_begin(es.ctx, nsimt)
+    e0.record(stream)
+    for _ in range(nsimt):
+        es.build(C, KC, ex)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_simt = max_over_ranks(world, e0.elapsed_time(e1)) / nsimt
+    st_simt, _ = thc.thc_profile_end(es.ctx)
+    KC_simt = KC.cpu().numpy()
+    ex_simt = ex.cpu().numpy().copy()
+    es.close()
+    del es
+    torch.cuda.empty_cache()
+
+    return ms_simt, st_simt, KC_simt, ex_simt
+
+
+def make_inputs(config: str):
+    """The seeded synthetic cell of `config`; the largest one makes its
+    matrix products through torch on the GPU (input generation only)."""
+    from paper_2304_05505_gb300 import cells
+    if config == "C3":
+        cells.set_accelerator("cuda")
+        try:
+            return cells.make_problem(config)
+        finally:
+            cells.set_accelerator(None)
+    return cells.make_problem(config)
 
 
 def run_ours(args, world, rank, local):
@@ -337,7 +389,7 @@ def run_ours(args, world, rank, local):
         raise RuntimeError("libthc.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
     thc.load()
     dev = torch.device("cuda", torch.cuda.current_device())
-    p = cells.make_problem(CONFIG)
+    p = make_inputs(args.config)
     d = p.dims
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
@@ -408,27 +460,10 @@ def run_ours(args, world, rank, local):
     del eb
     torch.cuda.empty_cache()
 
-    # --- the same precision on CUDA cores (comparison) -----------------------
-    es = thc.ExchangeBuild(d, "mixed_simt", device=dev, stream=stream)
-    es.set_collocation(p.X)
-    es.set_kernel(p.V)
-    for _ in range(2):
-        es.build(C, KC, ex)
-    torch.cuda.synchronize()
-    nsimt = max(3, min(args.steps, 10))
-    thc.thc_profile_begin(es.ctx, nsimt)
-    e0.record(stream)
-    for _ in range(nsimt):
-        es.build(C, KC, ex)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_simt = max_over_ranks(world, e0.elapsed_time(e1)) / nsimt
-    st_simt, _ = thc.thc_profile_end(es.ctx)
-    KC_simt = KC.cpu().numpy()
-    ex_simt = ex.cpu().numpy().copy()
-    es.close()
-    del es
-    torch.cuda.empty_cache()
+    # --- the same precision on CUDA cores (comparison; the headline cell only) --
+    ms_simt, st_simt, KC_simt, ex_simt = None, [0.0] * 6, None, None
+    if args.config == "C2":
+        ms_simt, st_simt, KC_simt, ex_simt = run_simt(args, thc, d, p, C, KC, ex, dev, stream, world, e0, e1)
 
     # --- FP64 GPU build -----------------------------------------------------
     e64 = thc.ExchangeBuild(d, "fp64", device=dev, stream=stream)
@@ -457,18 +492,20 @@ def run_ours(args, world, rank, local):
     kernels = {nm: ms for nm, ms in zip(names, kernel_ms)}
     dominant = max(kernels, key=kernels.get)
     roof = kernel_roofline(dominant, kernels[dominant], work, pk)
-    roof["name"] = KERNEL_NAMES[dominant]
+    roof["name"] = kernel_names(hermitian)[dominant]
     per_kernel = {nm: kernel_roofline(nm, kernels[nm], work, pk) for nm in names}
 
 
     line = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16-slices/f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD,
-                       "precision": "mixed: S1/S4a/S4b tcgen05 bf16 GEMMs on 4-slice fixed-point operands, S2 on "
-                                    "3 slices (exact leading sums, FP32 remainders), S3 FP32, E_x FP64 sum",
+            "config": {"workload": WORKLOADS[args.config],
+                       "precision": "mixed: S1/S2/S4a/S4b tcgen05 GEMMs on 3-slice fixed-point fp16 operands "
+                                    "(8+11+11 bits; 6, 6, 8, 8 slice products; exact leading sums, FP32 "
+                                    "remainders), X and M sliced inside the GEMMs, S3 FP32, E_x FP64 sum",
+                       "kernel_source": "model kernel V^q (Gaussian-smeared point deltas), density-sampled points",
                        "hermitian_form": hermitian,
-                       "l2": "inputs larger than L2 (prepared kernel 737 MB, X 265 MB complex64)",
+                       "l2": "inputs larger than L2 (prepared kernel complex64 > 700 MB, X FP32 > 260 MB)",
                        "parallelism": f"{world} independent builds (one per GPU)"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "stages_ms": stages, "kernels_ms": kernels,
@@ -478,22 +515,27 @@ def run_ours(args, world, rank, local):
                                 for k, v in per_kernel.items()},
             "fp64_gpu": {"value": world / (ms64 * 1e-3), "unit": "builds/s", "ms_per_step": ms64,
                          "stages_ms": {nm: ms for nm, ms in zip(names, st64)}},
-            "mixed_cuda_cores": {"value": world / (ms_simt * 1e-3), "unit": "builds/s", "ms_per_step": ms_simt,
-                                 "stages_ms": {nm: ms for nm, ms in zip(names, st_simt)}},
             "Ex_mixed": float(ex_mixed[0]), "Ex_fp64_gpu": float(ex_64[0])}
+    if ms_simt is not None:
+        line["mixed_cuda_cores"] = {"value": world / (ms_simt * 1e-3), "unit": "builds/s", "ms_per_step": ms_simt,
+                                    "stages_ms": {nm: ms for nm, ms in zip(names, st_simt)}}
     if not args.no_oracle:
         from oracle import thc_oracle as O
         t0 = time.perf_counter()
-        ref = O.build(p.X, p.C, p.V, p.cell.mesh, route="fft")
+        if args.config == "C2":
+            ref = O.build(p.X, p.C, p.V, p.cell.mesh, route="fft")
+        else:   # D and M of the largest cell do not fit in host memory whole
+            ref = O.build_rowblocks(p.X, p.C, p.V, p.cell.mesh)
         t_full = time.perf_counter() - t0
         line["accuracy_vs_oracle"] = {
             "mixed": {"max_abs_dKC": float(np.abs(KC_mixed - ref["KC"]).max()),
                       "abs_dEx": abs(float(ex_mixed[0]) - ref["Ex"])},
             "fp64_gpu": {"max_abs_dKC": float(np.abs(KC_64 - ref["KC"]).max()),
                          "abs_dEx": abs(float(ex_64[0]) - ref["Ex"])},
-            "mixed_cuda_cores": {"max_abs_dKC": float(np.abs(KC_simt - ref["KC"]).max()),
-                                 "abs_dEx": abs(float(ex_simt[0]) - ref["Ex"])},
             "Ex_oracle": ref["Ex"], "oracle_full_build_s": t_full}
+        if KC_simt is not None:
+            line["accuracy_vs_oracle"]["mixed_cuda_cores"] = {
+                "max_abs_dKC": float(np.abs(KC_simt - ref["KC"]).max()), "abs_dEx": abs(float(ex_simt[0]) - ref["Ex"])}
         cb = time_oracle(p, args.cpu_samples, 1)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)

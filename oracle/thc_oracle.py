@@ -73,6 +73,16 @@ def density(Psi: np.ndarray) -> np.ndarray:
     return np.stack([Psi[k] @ Psi[k].conj().T for k in range(nk)])
 
 
+def density_rows(Psi: np.ndarray, rows) -> np.ndarray:
+    """Step 2 for the rows P in ``rows`` only: D^k[P, Q] for all k and Q.
+
+    Every (P, Q) element of steps 2 and 3 is independent of the others, so
+    the build on the largest cells runs them a block of rows at a time
+    (D and M for all rows do not fit in memory at once)."""
+    nk = Psi.shape[0]
+    return np.stack([Psi[k][rows] @ Psi[k].conj().T for k in range(nk)])
+
+
 def kconv_direct(D: np.ndarray, V: np.ndarray, mesh) -> np.ndarray:
     """Step 3, defining form: M^k = sum_{k'} D^{k'} o V^{q(k, k')}, q = k' - k.
 
@@ -142,6 +152,22 @@ def build(X, C, V, mesh, route: str = "direct", keep: bool = False) -> dict:
     if keep:
         out.update(Psi=Psi, D=D, M=M, Y=Y)
     return out
+
+
+def build_rowblocks(X, C, V, mesh, block: int = 200) -> dict:
+    """The same build with steps 2-4a run on blocks of ``block`` rows P (the
+    FFT route of step 3 on each block), for cells whose D and M do not fit in
+    memory whole.  Steps 1, 4b and 5 are those of ``build``."""
+    Psi = collocate(X, C)
+    npt = Psi.shape[1]
+    Y = np.zeros_like(Psi)
+    for r0 in range(0, npt, block):
+        rows = slice(r0, min(npt, r0 + block))
+        M = kconv_fft(density_rows(Psi, rows), V[:, rows, :], mesh)
+        Y[:, rows, :] = apply_M(M, Psi)
+    KC = backproject(X, Y)
+    ex = exchange_energy(Psi, Y)
+    return dict(KC=KC, Ex=float(ex.real), Ex_imag=float(ex.imag))
 
 
 def exchange_matrix(X: np.ndarray, M: np.ndarray) -> np.ndarray:

@@ -47,6 +47,31 @@ import numpy as np
 IMAGE_CUTOFF = 20.0
 GAUSS_DROP = 36.8
 
+# Optional torch device for the large complex matrix products of input
+# generation (the quadrature matrices S, T, V of the model Hamiltonian and the
+# Gram products of the model kernel), in FP64 as on the CPU.  None: numpy.
+# Only these products move; the inputs stay numpy arrays that the library and
+# the oracle both consume.
+_ACCEL = None
+
+
+def set_accelerator(device) -> None:
+    """Route the generator's large matrix products through torch on `device`
+    (e.g. "cuda"), or back to numpy with None.  Used to make the largest
+    synthetic cell in reasonable time; results agree with numpy to rounding."""
+    global _ACCEL
+    _ACCEL = device
+
+
+def _mm_h(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """a @ b^H (complex, FP64)."""
+    if _ACCEL is None:
+        return a @ b.conj().T
+    import torch
+    ta = torch.from_numpy(np.ascontiguousarray(a)).to(_ACCEL)
+    tb = torch.from_numpy(np.ascontiguousarray(b)).to(_ACCEL)
+    return (ta @ tb.conj().T).cpu().numpy()
+
 
 @dataclasses.dataclass
 class Cell:
@@ -366,12 +391,12 @@ def occupied_coefficients(cell: Cell) -> np.ndarray:
         if done[k]:
             continue
         phi = bloch_collocation(cell, pts, kf[k:k + 1], terms)[0]  # (N, ng)
-        S = (vol / ng) * (phi.conj() @ phi.T)
+        S = (vol / ng) * _mm_h(phi, phi).conj()
         u = phi * np.exp(-1j * (pts @ kc[k]))[None, :]
         uh = np.fft.fftn(u.reshape((-1,) + qshape), axes=(1, 2, 3)).reshape(cell.nbas, -1) / ng
         kin = 0.5 * np.einsum("gi,gi->g", G + kc[k], G + kc[k])
-        T = vol * ((uh.conj() * kin[None, :]) @ uh.T)
-        Vw = (vol / ng) * ((phi.conj() * wpot[None, :]) @ phi.T)
+        T = vol * _mm_h(uh * kin[None, :], uh).conj()
+        Vw = (vol / ng) * _mm_h(phi * wpot[None, :], phi).conj()
         H = T + Vw
         H = 0.5 * (H + H.conj().T)
         S = 0.5 * (S + S.conj().T)
@@ -499,7 +524,7 @@ def model_kernel(cell: Cell, points: np.ndarray, weights: np.ndarray | None = No
         K2 = np.einsum("gi,gi->g", K, K)
         w = pref * 4 * np.pi / K2 * np.exp(-K2 / (2 * smear))
         A = np.exp(-1j * (points @ K.T)) * np.sqrt(w)[None, :] * weights[:, None]
-        Vq = A @ A.conj().T
+        Vq = _mm_h(A, A)
         Vq = 0.5 * (Vq + Vq.conj().T)
         if mk[q] == q:
             V[q] = Vq.real

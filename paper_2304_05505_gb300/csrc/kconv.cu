@@ -105,6 +105,27 @@ __device__ __forceinline__ void line_dft(typename cplx<R>::type* x, int step, co
     x[2 * step] = csub(a0, b0);
     x[step] = cadd(a1, ib1);
     x[3 * step] = csub(a1, ib1);
+  } else if constexpr (L == 6) {
+    // prime-factor (Good-Thomas) 6 = 2 x 3, no twiddles between the factors:
+    // inputs n = (3 n1 + 2 n2) mod 6, outputs m = (3 m1 + 4 m2) mod 6,
+    // X[m] = sum_{n1} (-1)^{n1 m1} sum_{n2} x[n] w3^{n2 m2}
+    CT y0[3], y1[3];
+    auto dft3v = [&](CT a, CT b, CT c, CT* y) {
+      const CT t = cadd(b, c), d = csub(b, c);
+      const CT m = CT{a.x - (R)0.5 * t.x, a.y - (R)0.5 * t.y};
+      const CT sd = Tw<R>::mul_s3(d, sign);
+      y[0] = cadd(a, t);
+      y[1] = cadd(m, sd);
+      y[2] = csub(m, sd);
+    };
+    dft3v(v[0], v[2], v[4], y0);
+    dft3v(v[3], v[5], v[1], y1);
+    x[0] = cadd(y0[0], y1[0]);
+    x[3 * step] = csub(y0[0], y1[0]);
+    x[4 * step] = cadd(y0[1], y1[1]);
+    x[step] = csub(y0[1], y1[1]);
+    x[2 * step] = cadd(y0[2], y1[2]);
+    x[5 * step] = csub(y0[2], y1[2]);
   } else {
 #pragma unroll
     for (int m = 0; m < L; m++) {
@@ -425,6 +446,132 @@ __global__ void __launch_bounds__(256, 2) kconv_pipe_kernel(const __grid_constan
     }
   }
   if (rowkey && el == 0 && live) flush();
+  // the copy of the batch whose wait gave up may still be in flight
+  if (!good && threadIdx.x == 0) mbar_drain(bar, fail_parity);
+}
+
+// TMA-fed shared-memory form for the other meshes (N_k <= 256, N_P^2 even):
+// a batch is TILE_EPB = 32 consecutive (P, Q) elements of all N_k planes; one
+// 2-D box of D and one of Vh ([N_k][32] complex) land in shared memory, and
+// the 3-D DFT runs in place there, axis by axis: warp w takes the lines w,
+// w + 8, ... of an axis and lane l the element l of each, so every access of
+// a warp is 256 contiguous bytes.  Two blocks per SM (for N_k <= 216) each
+// keep one batch in flight.  M leaves from shared memory in 256-byte rows, and
+// the row keys of M (as rowkey of kconv_pipe_kernel) are reduced per k plane
+// by the warp and kept per block while consecutive batches stay in one row.
+constexpr int TILE_EPB = 32;
+
+template <typename R>
+__device__ __forceinline__ void smem_line(float2* x, int L, int step, const Twiddles& tw, int ax, int sign) {
+  switch (L) {
+    case 2: line_dft<float, 2>(x, step, tw, ax, sign); break;
+    case 3: line_dft<float, 3>(x, step, tw, ax, sign); break;
+    case 4: line_dft<float, 4>(x, step, tw, ax, sign); break;
+    case 5: line_dft<float, 5>(x, step, tw, ax, sign); break;
+    case 6: line_dft<float, 6>(x, step, tw, ax, sign); break;
+    case 7: line_dft<float, 7>(x, step, tw, ax, sign); break;
+    default: line_dft<float, 8>(x, step, tw, ax, sign); break;
+  }
+}
+
+// The DFT of all elements of the box along every mesh axis (sign -1 forward,
+// +1 inverse); the box is [k][TILE_EPB] with k = (i1 n2 + i2) n3 + i3.
+__device__ __forceinline__ void tile_dft3(float2* box, const Twiddles& tw, int sign, int warp, int lane) {
+  const int n1 = tw.n[0], n2 = tw.n[1], n3 = tw.n[2];
+  const int nk = n1 * n2 * n3;
+#pragma unroll 1
+  for (int ax = 0; ax < 3; ax++) {
+    const int L = tw.n[ax];
+    if (L > 1) {
+      const int nl = nk / L;                         // lines along this axis
+      for (int l = warp; l < nl; l += 8) {
+        int base, st;
+        if (ax == 0) { base = l; st = n2 * n3; }                                  // l = i2 n3 + i3
+        else if (ax == 1) { base = (l / n3) * n2 * n3 + (l % n3); st = n3; }       // l = i1 n3 + i3
+        else { base = l * n3; st = 1; }                                           // l = i1 n2 + i2
+        smem_line<float>(box + base * TILE_EPB + lane, L, st * TILE_EPB, tw, ax, sign);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) kconv_tile_kernel(const __grid_constant__ CUtensorMap mapD,
+                                                      const __grid_constant__ CUtensorMap mapV,
+                                                      float2* __restrict__ M, long npq, long nbatch, Twiddles tw,
+                                                      unsigned* __restrict__ rowkey, int np, int* err) {
+  const int nk = tw.n[0] * tw.n[1] * tw.n[2];
+  const uint32_t box_bytes = (uint32_t)nk * TILE_EPB * sizeof(float2);
+  extern __shared__ __align__(128) unsigned char kt_smem[];   // [D box][Vh box][row maxima][mbarrier]
+  float2* sD = reinterpret_cast<float2*>(kt_smem);
+  const float2* sV = reinterpret_cast<const float2*>(kt_smem + box_bytes);
+  unsigned* rmax = reinterpret_cast<unsigned*>(kt_smem + 2 * box_bytes);
+  const uint32_t bar = smem_u32(kt_smem + 2 * box_bytes + ((nk * 4 + 15) & ~15));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long b0 = nbatch * blockIdx.x / gridDim.x, b1 = nbatch * (blockIdx.x + 1) / gridDim.x;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) rmax[k] = 0u;
+  __syncthreads();
+  auto issue = [&](long bt) {
+    mbar_expect_tx(bar, 2 * box_bytes);
+    tma_load_2d(smem_u32(sD), &mapD, bar, (int)(2 * bt * TILE_EPB), 0);
+    tma_load_2d(smem_u32(sV), &mapV, bar, (int)(2 * bt * TILE_EPB), 0);
+  };
+  if (threadIdx.x == 0 && b0 < b1) issue(b0);
+  long cur_row = -1;                     // the row whose maxima rmax holds (block-uniform)
+  bool good = true;
+  uint32_t fail_parity = 0;
+  for (long bt = b0; bt < b1; bt++) {
+    fail_parity = (uint32_t)((bt - b0) & 1);
+    good = mbar_wait_warp(bar, fail_parity, err, 4096);
+    good = __syncthreads_and(good);
+    if (!good) break;
+    tile_dft3(sD, tw, -1, warp, lane);
+    for (int k = warp; k < nk; k += 8) sD[k * TILE_EPB + lane] = cmul(sD[k * TILE_EPB + lane], sV[k * TILE_EPB + lane]);
+    __syncthreads();
+    tile_dft3(sD, tw, +1, warp, lane);
+    // M out, and the row keys: warp w owns the k planes w, w + 8, ... of rmax
+    const long e0 = bt * TILE_EPB, e = e0 + lane;
+    const long rfirst = e0 / np, rlast = (min(e0 + TILE_EPB, npq) - 1) / np;
+    if (rowkey && rfirst != cur_row && cur_row >= 0) {
+      for (int k = warp; k < nk; k += 8)
+        if (lane == 0 && rmax[k]) atomicMax(rowkey + (long)k * np + cur_row, rmax[k]);
+      for (int k = warp; k < nk; k += 8)
+        if (lane == 0) rmax[k] = 0u;
+    }
+    for (int k = warp; k < nk; k += 8) {
+      const float2 v = sD[k * TILE_EPB + lane];
+      unsigned key = 0u;
+      if (e < npq) {
+        M[(long)k * npq + e] = v;
+        key = abs_bits(v) >> 16;
+      }
+      if (rowkey) {
+        if (rfirst == rlast) {
+          key = __reduce_max_sync(0xffffffffu, key);
+          if (lane == 0) rmax[k] = max(rmax[k], key);
+        } else {
+          // a batch across a row boundary: each row's part straight to memory
+          const bool first = e / np == rfirst;
+          const unsigned ka = __reduce_max_sync(0xffffffffu, first ? key : 0u);
+          const unsigned kb = __reduce_max_sync(0xffffffffu, first ? 0u : key);
+          if (lane == 0) {
+            if (ka) atomicMax(rowkey + (long)k * np + rfirst, ka);
+            if (kb) atomicMax(rowkey + (long)k * np + rlast, kb);
+          }
+        }
+      }
+    }
+    if (rfirst == rlast) cur_row = rfirst;
+    __syncthreads();                      // the boxes are free again
+    if (threadIdx.x == 0 && bt + 1 < b1) issue(bt + 1);
+  }
+  if (rowkey && cur_row >= 0)
+    for (int k = warp; k < nk; k += 8)
+      if (lane == 0 && rmax[k]) atomicMax(rowkey + (long)k * np + cur_row, rmax[k]);
   // the copy of the batch whose wait gave up may still be in flight
   if (!good && threadIdx.x == 0) mbar_drain(bar, fail_parity);
 }
@@ -867,13 +1014,60 @@ cudaError_t kconv_c_herm(const float2* D, const float2* Vh, float2* M, int np, i
   return kconv_herm_launch<2, 2, 2>(D, Vh, M, np, keys, e, err, conv_done, s);
 }
 
+// Shared memory of kconv_tile_kernel for N_k k-planes: two boxes, the row
+// maxima and the barrier.
+size_t tile_smem(int nk) { return 2 * (size_t)nk * TILE_EPB * sizeof(float2) + ((nk * 4 + 15) & ~15) + 16; }
+
+cudaError_t kconv_tile_launch(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
+                              unsigned* rowkey, int* err, cudaStream_t s) {
+  const int nk = n1 * n2 * n3;
+  const long npq = (long)np * np;
+  alignas(64) unsigned char mD[128], mV[128];
+  cudaError_t e = make_f32_map_2d(mD, D, 2 * npq, nk, 8 * npq, 2 * TILE_EPB, nk);
+  if (e == cudaSuccess) e = make_f32_map_2d(mV, Vh, 2 * npq, nk, 8 * npq, 2 * TILE_EPB, nk);
+  if (e != cudaSuccess) return e;
+  CUtensorMap mapD, mapV;
+  memcpy(&mapD, mD, sizeof mapD);
+  memcpy(&mapV, mV, sizeof mapV);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
+  }
+  const size_t sm = tile_smem(nk);
+  e = cudaFuncSetAttribute(kconv_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long nbatch = (npq + TILE_EPB - 1) / TILE_EPB;
+  const int per_sm = sm <= 113 * 1024 ? 2 : 1;
+  const unsigned grid = (unsigned)std::min<long>(nbatch, (long)per_sm * nsm);
+  kconv_tile_kernel<<<grid, 256, sm, s>>>(mapD, mapV, M, npq, nbatch, make_twiddles(n1, n2, n3), rowkey, np, err);
+  return cudaGetLastError();
+}
+
 cudaError_t kconv_c_rowexp(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3, int* e,
                            bool* done, int* err, cudaEvent_t started, cudaEvent_t conv_done, cudaStream_t s) {
   *done = false;
   const long npq = (long)np * np;
-  const bool pipe = n1 == n2 && n2 == n3 && n1 >= 2 && n1 <= 4 && np >= 1 && npq % 2 == 0 && npq < (1L << 29) &&
-                    ((uintptr_t)D & 15) == 0 && ((uintptr_t)Vh & 15) == 0 && err;
+  const bool aligned = np >= 1 && npq % 2 == 0 && npq < (1L << 29) && ((uintptr_t)D & 15) == 0 &&
+                       ((uintptr_t)Vh & 15) == 0 && err;
+  const bool pipe = aligned && n1 == n2 && n2 == n3 && n1 >= 2 && n1 <= 4;
+  // the shared-memory form: up to 256 k-planes (one TMA box along k)
+  const bool tile = aligned && !pipe && n1 * n2 * n3 <= 256 && n1 * n2 * n3 > 1;
   cudaError_t r = cudaSuccess;
+  if (tile) {
+    const long rows = (long)n1 * n2 * n3 * np;
+    unsigned* key = reinterpret_cast<unsigned*>(e);
+    r = cudaMemsetAsync(key, 0, rows * sizeof(unsigned), s);
+    if (r == cudaSuccess && started) r = cudaEventRecord(started, s);
+    if (r == cudaSuccess) r = kconv_tile_launch(D, Vh, M, np, n1, n2, n3, key, err, s);
+    if (r == cudaSuccess && conv_done) r = cudaEventRecord(conv_done, s);
+    if (r != cudaSuccess) return r;
+    rowkey_to_exponents<<<(unsigned)std::min<long>((rows + 255) / 256, 152L * 8), 256, 0, s>>>(key, rows);
+    r = cudaGetLastError();
+    *done = r == cudaSuccess;
+    return r;
+  }
   if (!pipe) {
     if (started) r = cudaEventRecord(started, s);
     if (r == cudaSuccess) r = kconv_c(D, Vh, M, npq, n1, n2, n3, s);

@@ -81,6 +81,8 @@ RANDOM_CASES = [
     ((4, 4, 4), 20, 3, 65),
     ((6, 1, 2), 10, 2, 33),      # 6-point DFT
     ((8, 8, 8), 5, 2, 12),       # the largest mesh: 512 k-points per element in shared memory
+    ((6, 6, 6), 12, 3, 40),      # 6-point DFTs; TMA-fed shared-memory convolution, batches across rows
+    ((5, 3, 2), 10, 2, 32),      # mixed radices in the shared-memory convolution, one row per batch
 ]
 
 
@@ -249,6 +251,7 @@ def test_profile_stage_times(torch_cuda, precision):
     ((2, 2, 2), 6),
     ((4, 4, 4), 65),       # odd N_P: the slices of M go through HBM
     ((3, 2, 4), 60),       # a mesh without the lane-split convolution
+    ((6, 6, 6), 40),       # the shared-memory convolution, batches across rows
 ])
 def test_row_exponents_of_M(torch_cuda, mesh, nisdf):
     """The row exponents S4a slices M with, from the TMA-fed convolution

@@ -145,3 +145,13 @@ def test_plane_wave_kernel_closed_form(mesh, G0):
 @pytest.mark.parametrize("grid", [(8, 7, 6), (5, 5, 5), (16, 16, 16)])
 def test_gset_is_the_symmetric_fft_set(grid):
     assert pins.check_gset_symmetric(grid) == 0.0
+
+
+def test_rowblock_build_equals_build():
+    """Running steps 2-4a a block of rows at a time (for cells too large to
+    hold D and M) gives the build itself: the (P, Q) elements are independent."""
+    r = cells.random_problem((3, 2, 2), nbas=9, nocc=3, nisdf=37, seed=4)
+    a = O.build(r["X"], r["C"], r["V"], r["mesh"], route="direct")
+    b = O.build_rowblocks(r["X"], r["C"], r["V"], r["mesh"], block=8)
+    assert np.abs(a["KC"] - b["KC"]).max() <= 1e-13 * np.abs(a["KC"]).max()
+    assert abs(a["Ex"] - b["Ex"]) <= 1e-13 * abs(a["Ex"])
