@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--config", default="C2", choices=sorted(WORKLOADS),
                     help="C2 (default: the headline workload) or C3, the 6x6x6-k supercell at scale, "
                          "timed once for the record (its inputs take minutes to make)")
+    ap.add_argument("--no-rebuild", action="store_true",
+                    help="skip timing the per-iteration kernel rebuild (C2 only)")
+    ap.add_argument("--rebuild-fp64", action="store_true",
+                    help="also time the all-FP64 kernel rebuild (about a minute at C2)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="time the mixed build alone (no host-buffer, CUDA-core, FP64 or oracle arms): "
                          "the small process a profiler capture runs")
@@ -185,9 +189,11 @@ def stage_work(d: dict, hermitian: bool = False) -> dict:
     N, n, P = d["nbas"], d["nocc"], d["nisdf"]
     c64 = 8
     half = P * (P + 1) / 2 if hermitian else P * P
+    # S2 multiplies only the tiles that reach the diagonal in both forms (the
+    # other form writes the mirror image too)
     return {
         "S1_collocate": dict(flops=8.0 * nk * P * n * N, bytes=c64 * nk * (N * P + P * n) + 16 * nk * N * n),
-        "S2_density": dict(flops=8.0 * nk * half * n, bytes=c64 * nk * (P * n + half)),
+        "S2_density": dict(flops=8.0 * nk * P * (P + 1) / 2 * n, bytes=c64 * nk * (P * n + half)),
         "S3_kconv": dict(flops=None, bytes=c64 * nk * (2.0 * half + P * P)),
         "S4a_apply_M": dict(flops=8.0 * nk * P * P * n, bytes=c64 * nk * (P * P + 2 * P * n)),
         "S4b_backproject": dict(flops=8.0 * nk * N * n * P, bytes=c64 * nk * (N * P + P * n) + 16 * nk * N * n),
@@ -366,6 +372,42 @@ def run_simt(args, thc, d, p, C, KC, ex, dev, stream, world, e0, e1):
     return ms_simt, st_simt, KC_simt, ex_simt
 
 
+def time_rebuild(p, thc, args) -> dict:
+    """The per-iteration kernel rebuild of THC-oo-K at the bench's cell (the
+    fit of the interpolation vectors to the current orbitals, their FFT and
+    the contraction over G; Algorithm 2's first three steps): device ms per
+    step, with the points of the FP64 full-grid pivoted Cholesky (chosen once
+    before the SCF loop, as Algorithm 2 chooses its points)."""
+    import torch
+    from paper_2304_05505_gb300 import cells
+    cell = p.cell
+    cells.set_accelerator("cuda")
+    try:
+        U = cells.grid_orbitals(cell, p.C)
+    finally:
+        cells.set_accelerator(None)
+    Ud = torch.from_numpy(U).cuda()
+    del U
+    t0 = time.perf_counter()
+    pts, _ = thc.thc_select_points(Ud, cell.nisdf)
+    t_sel = time.perf_counter() - t0
+    names = ["metric_B_R_S", "cholesky", "solve", "fft", "contraction"]
+    thc.thc_rebuild_kernel(Ud, cell.grid, cell.lattice, cell.mesh, pts, "mixed")   # warm-up
+    runs = [thc.thc_rebuild_kernel(Ud, cell.grid, cell.lattice, cell.mesh, pts, "mixed")[1] for _ in range(3)]
+    mean = [sum(r[i] for r in runs) / len(runs) for i in range(5)]
+    out = {"unit": "ms per rebuild (device time of its steps)", "grid": list(cell.grid), "n_grid": int(np.prod(cell.grid)),
+           "points": f"{cell.nisdf} from the FP64 full-grid pivoted Cholesky ({t_sel:.2f} s, once)",
+           "mixed": {"ms": sum(mean), "steps_ms": dict(zip(names, mean)),
+                     "form": "metric, Cholesky, solve and FFT in FP64; contraction on tcgen05 (FP32 operands, "
+                             "3 fp16 slices, 8 products, exact K chunks)"}}
+    if args.rebuild_fp64:
+        ms = thc.thc_rebuild_kernel(Ud, cell.grid, cell.lattice, cell.mesh, pts, "fp64")[1]
+        out["fp64"] = {"ms": sum(ms), "steps_ms": dict(zip(names, ms))}
+    del Ud
+    torch.cuda.empty_cache()
+    return out
+
+
 def make_inputs(config: str):
     """The seeded synthetic cell of `config`; the largest one makes its
     matrix products through torch on the GPU (input generation only)."""
@@ -483,6 +525,10 @@ def run_ours(args, world, rank, local):
     ex_64 = ex.cpu().numpy().copy()
     e64.close()
 
+    rebuild = None
+    if args.config == "C2" and not args.no_rebuild:
+        rebuild = time_rebuild(p, thc, args)
+
     if rank != 0:
         return
     pk = peaks()
@@ -516,6 +562,8 @@ def run_ours(args, world, rank, local):
             "fp64_gpu": {"value": world / (ms64 * 1e-3), "unit": "builds/s", "ms_per_step": ms64,
                          "stages_ms": {nm: ms for nm, ms in zip(names, st64)}},
             "Ex_mixed": float(ex_mixed[0]), "Ex_fp64_gpu": float(ex_64[0])}
+    if rebuild is not None:
+        line["kernel_rebuild"] = rebuild
     if ms_simt is not None:
         line["mixed_cuda_cores"] = {"value": world / (ms_simt * 1e-3), "unit": "builds/s", "ms_per_step": ms_simt,
                                     "stages_ms": {nm: ms for nm, ms in zip(names, st_simt)}}

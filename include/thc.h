@@ -228,6 +228,27 @@ thc_status thc_fit_kernel(const double* U, int nfunc, const int* grid_host, cons
                           const int* mesh_host, const int* points_host, int npts, double* V_out,
                           double* xi_out, void* stream);
 
+/* The per-iteration kernel rebuild of THC-oo-K (Algorithm 2: the fit of the
+ * interpolation vectors to the current orbitals, their FFT, and M^q as a sum
+ * over G; Sec. 2.2).  Computes what thc_fit_kernel computes, with the same
+ * arguments, conventions and errors (no xi output), and times its steps.
+ * precision THC_FP64: every step in FP64 (the result equals thc_fit_kernel's
+ * bit for bit).  THC_MIXED: the fit's metric, its Cholesky factor, the solve
+ * and the FFT stay FP64; the contraction
+ *   V^q[P,Q] = sum_G Xq[P][G] conj(Xq[Q][G]),  Xq = xh sqrt(v(G+q)) e^{-i q.r_P} (scaled),
+ * which dominates the rebuild (N_k N_P^2 N_G complex multiply-adds), runs on
+ * the tcgen05 tensor cores: Xq rounded to FP32 and cut into three fp16
+ * slices inside the GEMM, 8 slice products, the leading products summed
+ * exactly in chunks of at most 1024 real K and the chunks combined in FP64
+ * (relative error of V about 1e-7 of its largest entries, from the FP32
+ * rounding of Xq).  step_ms_host (host, 5 floats, may be NULL) receives the
+ * device time of each step in ms: metric (B, R = |B|^2, S), Cholesky, solve,
+ * FFT, contraction.  Allocates its own scratch and waits for `stream`;
+ * THC_ERR_TIMEOUT if a device wait of the tensor-core contraction gave up. */
+thc_status thc_rebuild_kernel(const double* U, int nfunc, const int* grid_host, const double* lattice_host,
+                              const int* mesh_host, const int* points_host, int npts, int precision, double* V_out,
+                              float* step_ms_host, void* stream);
+
 /* Learned interpolation-point proposal (setup, outside the timed build).  The
  * paper has no learned part (its points come from a QR decomposition with
  * column pivoting, Sec. 2.1, or from k-means on the density, Sec. 4); these

@@ -412,6 +412,29 @@ def occupied_coefficients(cell: Cell) -> np.ndarray:
     return C
 
 
+def grid_orbitals(cell: Cell, C: np.ndarray, stride: int = 1) -> np.ndarray:
+    """The input of the setup calls (interpolation-point selection and the
+    ISDF kernel fit): the occupied orbitals' cell-periodic parts on the grid
+    sub-sampled by ``stride``, U[f][r] = u^k_i(r) = exp(-i k.r) sum_mu
+    X^k_mu(r) C^k_mu,i for f = (k, i), shape (N_k n_occ, N_g) c128.
+
+    These are grid values for the setup stage; the build itself collocates
+    the orbitals at the interpolation points (its step 1), which this module
+    never does."""
+    pts = grid_points(cell, stride)
+    kf = kmesh_frac(cell.mesh)
+    kc = kf @ cell.recip
+    terms = collocation_terms(cell, pts)
+    nk, n = C.shape[0], C.shape[2]
+    U = np.zeros((nk, n, pts.shape[0]), dtype=np.complex128)
+    for k in range(nk):
+        Xk = bloch_collocation(cell, pts, kf[k:k + 1], terms)[0]          # (N, ng)
+        # C^T X: the conjugate of (conj(C)^T ...)^H products, as a @ b^H
+        psi = _mm_h(np.ascontiguousarray(C[k].T), np.ascontiguousarray(Xk.T.conj()))
+        U[k] = psi * np.exp(-1j * (pts @ kc[k]))[None, :]
+    return U.reshape(nk * n, -1)
+
+
 # ----------------------------------------------------------------------------
 # interpolation points and the model kernel
 # ----------------------------------------------------------------------------

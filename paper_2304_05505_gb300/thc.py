@@ -31,7 +31,7 @@ EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_ker
            "thc_profile_begin", "thc_profile_end", "thc_sync", "thc_kconv_noalloc",
            "thc_select_points", "thc_fit_kernel", "thc_profile_kernels", "thc_mlp_features", "thc_mlp_score",
            "thc_mlp_workspace_bytes", "thc_mlp_train_step", "thc_mlp_candidates", "thc_select_points_among",
-           "thc_debug_set_wait_limit", "thc_debug_fail_alloc"]
+           "thc_debug_set_wait_limit", "thc_debug_fail_alloc", "thc_rebuild_kernel"]
 
 MLP_NPARAM = 8641
 
@@ -80,6 +80,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_kconv_noalloc.argtypes = [dp, dp, dp, ip, ip, ip, ctypes.c_long, vp]
     lib.thc_select_points.argtypes = [dp, ip, ip, ip, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), dp, vp]
+    lib.thc_rebuild_kernel.argtypes = [dp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, ip, dp,
+                                       ctypes.POINTER(ctypes.c_float), vp]
     lib.thc_fit_kernel.argtypes = [dp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, dp, dp, vp]
     fp = ctypes.POINTER(ctypes.c_float)
@@ -320,6 +323,30 @@ def thc_fit_kernel(U, grid, lattice, mesh, points, want_xi: bool = False, stream
                                  xi.data_ptr() if xi is not None else None, ctypes.c_void_p(stream)),
            "thc_fit_kernel")
     return (V, xi) if want_xi else V
+
+
+def thc_rebuild_kernel(U, grid, lattice, mesh, points, precision="mixed", stream: int | None = None):
+    """The per-iteration kernel rebuild (see include/thc.h): V [N_k][npts][npts]
+    complex128 (CUDA tensor) and the device ms of its five steps (metric,
+    Cholesky, solve, FFT, contraction)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    nfunc, ng = U.shape
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    m = (ctypes.c_int * 3)(*[int(x) for x in mesh])
+    lat = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(lattice, dtype=np.float64).ravel()])
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int32))
+    npts = int(pts.size)
+    nk = int(np.prod([int(x) for x in mesh]))
+    V = torch.empty((nk, npts, npts), dtype=torch.complex128, device=U.device)
+    ms = (ctypes.c_float * 5)()
+    _check(load().thc_rebuild_kernel(_dev_ptr(U, name="U"), int(nfunc), g, lat, m,
+                                     pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), npts,
+                                     int(PRECISIONS.get(precision, precision)), V.data_ptr(), ms,
+                                     ctypes.c_void_p(stream)),
+           "thc_rebuild_kernel")
+    return V, [float(x) for x in ms]
 
 
 def _f32_dev(t, n=None, name="tensor") -> int:

@@ -86,3 +86,40 @@ def test_bad_points_rejected(thc_mod):
     extra = [i for i in range(512) if i not in set(P.tolist())][:3]
     with pytest.raises(thc_mod.ThcError):
         thc_mod.thc_fit_kernel(Ud, c.grid, c.lattice, c.mesh, list(P) + extra)
+
+
+@pytest.mark.parametrize("mesh,grid,npts", [((2, 2, 2), (16, 16, 16), 48), ((3, 3, 3), (8, 8, 8), 40)])
+def test_rebuild_fp64_is_the_fit(thc_mod, mesh, grid, npts):
+    """The FP64 rebuild is thc_fit_kernel, bit for bit, and reports its step times."""
+    import torch
+    c, U = toy_u(mesh, grid)
+    P = S.pivoted_cholesky(U, npts)["points"]
+    Ud = torch.from_numpy(U).cuda()
+    V0 = thc_mod.thc_fit_kernel(Ud, c.grid, c.lattice, c.mesh, P)
+    V1, ms = thc_mod.thc_rebuild_kernel(Ud, c.grid, c.lattice, c.mesh, P, "fp64")
+    assert torch.equal(V0, V1)
+    assert len(ms) == 5 and all(t >= 0 for t in ms) and sum(ms) > 0
+
+
+@pytest.mark.parametrize("mesh,grid,npts", [((2, 2, 2), (16, 16, 16), 48), ((3, 3, 3), (8, 8, 8), 40),
+                                            ((4, 4, 4), (12, 12, 12), 64)])
+def test_rebuild_mixed_matches_oracle(thc_mod, mesh, grid, npts):
+    """The kernel contraction on tensor cores against the oracle's FP64 fit:
+    within 1e-6 of the largest entry (the vectors are rounded to FP32,
+    6e-8 relative, before the exact-chunked slice products), and the FP64
+    build with it within 1e-6 relative of the build with the oracle's kernel
+    in E_x and KC."""
+    import torch
+    from oracle import thc_oracle as O
+    c, U = toy_u(mesh, grid)
+    P = S.pivoted_cholesky(U, npts)["points"]
+    ref = S.fit_kernel(c.lattice, c.grid, c.mesh, U, P)
+    V, ms = thc_mod.thc_rebuild_kernel(torch.from_numpy(U).cuda(), c.grid, c.lattice, c.mesh, P, "mixed")
+    V = V.cpu().numpy()
+    assert np.abs(V - ref).max() <= 1e-6 * np.abs(ref).max()
+    X = cells.bloch_collocation(c, cells.points_from_indices(c, P), cells.kmesh_frac(c.mesh))
+    C = cells.occupied_coefficients(c)
+    a = O.build(X, C, ref, c.mesh)
+    b = O.build(X, C, V, c.mesh)
+    assert abs(a["Ex"] - b["Ex"]) <= 1e-6 * abs(a["Ex"])
+    assert np.abs(a["KC"] - b["KC"]).max() <= 1e-6 * np.abs(a["KC"]).max()

@@ -1,0 +1,86 @@
+"""The target configuration on an ISDF-fitted kernel (4x4x4 k, N_P = 1200,
+n = 60, N = 432, 40^3 grid).
+
+The other full-size tests use the model kernel of the seeded generator.  Here
+the kernel is the one the method feeds the build:
+* the interpolation points are the FP64 full-grid pivoted Cholesky of the
+  occupied pair products (thc_select_points on the orbitals on all 64,000
+  grid points; Sec. 2.1, in the pivoted-Cholesky reading of the QRCP
+  selection);
+* V^q is the least-squares fit of those products and its Coulomb kernel
+  (thc_rebuild_kernel, Sec. 2.2 and the first three steps of Algorithm 2),
+  in FP64 and with the contraction on tensor cores.
+The mixed build with the FP64-fitted V must meet the target (max|dKC| <= 1e-7,
+|dE_x| <= 1e-6 Ha per cell) against the oracle with the same V, and the
+tensor-core kernel must agree with the FP64 one (1e-6 of its largest entry;
+the oracle builds with the two within 1e-6 relative in E_x)."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import thc_oracle as O
+from paper_2304_05505_gb300 import cells
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def fitted(cuda_required):
+    import os
+
+    import torch
+    from paper_2304_05505_gb300 import build_lib, thc
+    if not os.path.exists(thc.LIB_PATH):
+        build_lib.build()
+    t0 = time.perf_counter()
+    cell = cells.make_cell("C2")
+    cells.set_accelerator("cuda")
+    try:
+        C = cells.occupied_coefficients(cell)
+        U = cells.grid_orbitals(cell, C)
+    finally:
+        cells.set_accelerator(None)
+    t1 = time.perf_counter()
+    Ud = torch.from_numpy(U).cuda()
+    del U
+    pts, _ = thc.thc_select_points(Ud, cell.nisdf)
+    t2 = time.perf_counter()
+    V64, ms64 = thc.thc_rebuild_kernel(Ud, cell.grid, cell.lattice, cell.mesh, pts, "fp64")
+    Vtc, mstc = thc.thc_rebuild_kernel(Ud, cell.grid, cell.lattice, cell.mesh, pts, "mixed")
+    del Ud
+    X = cells.bloch_collocation(cell, cells.points_from_indices(cell, pts), cells.kmesh_frac(cell.mesh))
+    print(f"fitted C2: inputs {t1 - t0:.0f} s, points {t2 - t1:.1f} s, rebuild FP64 {sum(ms64):.0f} ms "
+          f"{[round(x, 1) for x in ms64]}, tensor cores {sum(mstc):.0f} ms {[round(x, 1) for x in mstc]}")
+    return cell, X, C, V64.cpu().numpy(), Vtc.cpu().numpy()
+
+
+def test_fitted_kernel_mixed_build_target(fitted):
+    from paper_2304_05505_gb300 import thc
+    cell, X, C, V64, _ = fitted
+    ref = O.build(X, C, V64, cell.mesh, route="fft")
+    dims = dict(n1=4, n2=4, n3=4, nbas=cell.nbas, nocc=cell.nocc, nisdf=cell.nisdf)
+    eb = thc.ExchangeBuild(dims, "mixed")
+    try:
+        eb.set_collocation(X)
+        eb.set_kernel(V64)
+        KC, ex = eb.build(C)
+        eb.sync()
+        dkc = float(np.abs(KC.cpu().numpy() - ref["KC"]).max())
+        dex = abs(float(ex[0]) - ref["Ex"])
+        print(f"fitted C2 mixed: max|dKC| = {dkc:.3e}, |dE_x| = {dex:.3e}, E_x = {ref['Ex']:.9f}, "
+              f"Hermitian form {thc.thc_hermitian_kernel(eb.ctx)}")
+    finally:
+        eb.close()
+    assert dkc <= 1e-7, dkc
+    assert dex <= 1e-6, dex
+
+
+def test_tensor_core_rebuild_matches_fp64(fitted):
+    cell, X, C, V64, Vtc = fitted
+    dv = float(np.abs(Vtc - V64).max()) / float(np.abs(V64).max())
+    a = O.build(X, C, V64, cell.mesh, route="fft")
+    b = O.build(X, C, Vtc, cell.mesh, route="fft")
+    print(f"fitted C2 rebuild: max|dV|/max|V| = {dv:.3e}, dE_x = {abs(a['Ex'] - b['Ex']):.3e}")
+    assert dv <= 1e-6, dv
+    assert abs(a["Ex"] - b["Ex"]) <= 1e-6 * abs(a["Ex"])
