@@ -408,6 +408,39 @@ def time_rebuild(p, thc, args) -> dict:
     return out
 
 
+def time_aok(d, p, thc, dev, stream) -> dict:
+    """The THC-AO-K form of the build (Algorithm 1's K step: the full AO
+    exchange matrix K^k = conj(X^k) M^k X^{kT}) on the same inputs: mixed
+    builds/s, and one FP64 build."""
+    import torch
+    out = {"unit": "builds/s", "output": "K^k [N_k][N][N] complex128 and E_x"}
+    for prec, nb in (("mixed", 10), ("fp64", 1)):
+        eb = thc.ExchangeBuild(d, prec, device=dev, stream=stream)
+        eb.set_collocation(p.X)
+        eb.set_kernel(p.V)
+        C = torch.from_numpy(p.C).to(dev)
+        K, ex = eb.build_K(C)
+        torch.cuda.synchronize()
+        thc.thc_profile_begin(eb.ctx, nb)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(nb):
+            eb.build_K(C, K, ex)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        eb.sync()
+        st, _ = thc.thc_profile_end(eb.ctx)
+        ms = e0.elapsed_time(e1) / nb
+        out[prec] = {"value": 1e3 / ms, "ms_per_step": ms,
+                     "stages_ms": dict(zip(["S1", "S2", "S3", "Z=M X^T", "K=conj(X) Z", "E_x"], st)),
+                     "Ex": float(ex[0])}
+        eb.close()
+        del eb, K, C
+        torch.cuda.empty_cache()
+    return out
+
+
 def make_inputs(config: str):
     """The seeded synthetic cell of `config`; the largest one makes its
     matrix products through torch on the GPU (input generation only)."""
@@ -528,6 +561,7 @@ def run_ours(args, world, rank, local):
     rebuild = None
     if args.config == "C2" and not args.no_rebuild:
         rebuild = time_rebuild(p, thc, args)
+    aok = time_aok(d, p, thc, dev, stream) if args.config == "C2" else None
 
     if rank != 0:
         return
@@ -564,6 +598,8 @@ def run_ours(args, world, rank, local):
             "Ex_mixed": float(ex_mixed[0]), "Ex_fp64_gpu": float(ex_64[0])}
     if rebuild is not None:
         line["kernel_rebuild"] = rebuild
+    if aok is not None:
+        line["thc_ao_k"] = aok
     if ms_simt is not None:
         line["mixed_cuda_cores"] = {"value": world / (ms_simt * 1e-3), "unit": "builds/s", "ms_per_step": ms_simt,
                                     "stages_ms": {nm: ms for nm, ms in zip(names, st_simt)}}

@@ -114,6 +114,26 @@ thc_status thc_build(thc_ctx* ctx, const double* C, double* KC, double* ex);
  * ex_host: 2 doubles as in thc_build. */
 thc_status thc_build_host(thc_ctx* ctx, const double* C_host, double* KC_host, double* ex_host);
 
+/* The THC-AO-K form of the build (Algorithm 1 of the paper: its convolution
+ * step forms X^k_PQ, and its K step the full AO exchange matrix):
+ *   S1-S3 as thc_build, then K^k[mu,nu] = sum_PQ conj(X^k[mu,P]) M^k[P,Q] X^k[nu,Q]
+ * (K^k = conj(X^k) M^k X^{kT}) and E_x = -(1/N_k) sum_k sum_PQ conj(D^k[P,Q]) M^k[P,Q]
+ * (the energy of thc_build).  For THC-AO-K the points and V^q are those of
+ * the fit of all basis-function products (thc_fit_kernel with U the
+ * cell-periodic parts of the basis functions instead of the occupied
+ * orbitals); the build takes any V.  C: device [N_k][nbas][nocc] complex128;
+ * K: device [N_k][nbas][nbas] complex128 (written, must not overlap C); ex:
+ * device, 2 doubles as in thc_build.  THC_FP64: every step in FP64 (the two
+ * products on CUDA cores).  THC_MIXED: Z = M X^T and K = conj(X) Z on the
+ * tensor cores (three fp16 slices, 8 slice products, exact leading sums; the
+ * planes of X^T are made once per thc_set_collocation).  THC_MIXED_SIMT:
+ * THC_ERR_UNSUPPORTED.  The first call on a context allocates the form's
+ * extra workspace (THC_ERR_OOM if the device cannot hold it; the context
+ * stays usable).  Asynchronous on the context's stream.  thc_profile_* and
+ * thc_stage_times report its stages in the slots S1, S2, S3, then Z, K and
+ * the energy in place of S4a, S4b and S5. */
+thc_status thc_build_K(thc_ctx* ctx, const double* C, double* K, double* ex);
+
 /* Intermediates of the last build, copied to device buffers the caller owns
  * (for tests).  which: 0 = Psi [N_k][nisdf][nocc], 1 = D [N_k][nisdf][nisdf],
  * 2 = M [N_k][nisdf][nisdf], 3 = Y = M Psi [N_k][nisdf][nocc].  Written as

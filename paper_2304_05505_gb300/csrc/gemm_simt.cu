@@ -4,8 +4,8 @@
 //   C[b](m, n) = sum_k A[b](m, k) B[b](k, n)
 //
 // A is read as A[m*lda + k] (A_MK), A[k*lda + m] (A_KM, a transpose) or
-// conj(A[m*lda + k]) (A_MK_CONJ); B as B[k*ldb + n] (B_KN) or
-// conj(B[n*ldb + k]) (B_NK_CONJ).  Tiles of 64 x 64 outputs, 16-deep k slabs
+// conj(A[m*lda + k]) (A_MK_CONJ); B as B[k*ldb + n] (B_KN),
+// conj(B[n*ldb + k]) (B_NK_CONJ) or B[n*ldb + k] (B_NK, FP64 form).  Tiles of 64 x 64 outputs, 16-deep k slabs
 // staged in shared memory.  FP64: 256 threads with 4 x 4 outputs each.  FP32:
 // 512 threads with 2 x 4 outputs each and double-buffered slabs.
 //
@@ -106,7 +106,10 @@ gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int lda, long sA,
       CT v = CT{zr, zr};
       if (gn < N && gk < K) {
         if (LB == B_KN) v = to_c(B[(long)gk * ldb + gn], zr);
-        else { v = to_c(B[(long)gn * ldb + gk], zr); v.y = -v.y; }
+        else {
+          v = to_c(B[(long)gn * ldb + gk], zr);
+          if (LB == B_NK_CONJ) v.y = -v.y;
+        }
       }
       Bs[kk][nn] = v;
     }
@@ -308,7 +311,7 @@ cudaError_t launch(int la, int lb, int M, int N, int K, const TA* A, int lda, lo
                                                                   B, ldb, sB, C, ldc, sC); \
     return cudaGetLastError();                                                          \
   }
-  L(A_MK, B_KN) L(A_KM, B_KN) L(A_MK_CONJ, B_KN) L(A_MK, B_NK_CONJ)
+  L(A_MK, B_KN) L(A_KM, B_KN) L(A_MK_CONJ, B_KN) L(A_MK, B_NK_CONJ) L(A_MK, B_NK)
 #undef L
   return cudaErrorInvalidValue;
 }

@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 namespace {
 
@@ -114,7 +115,8 @@ void free_all(thc_ctx* c) {
   void* ptrs[] = {c->X64, c->Vh64, c->X32, c->Vh32, c->Psi, c->D, c->M, c->Y,
                   c->Cdev, c->KCdev, c->exdev, c->partial, c->flag,
                   c->PsiA_pl, c->Bc_pl, c->Bd_pl, c->By_pl, c->ex_pl, c->tc_err, c->part_s0,
-                  c->part_bc, c->M_pl, c->hkeys};
+                  c->part_bc, c->M_pl, c->hkeys, c->Zao, c->Wao, c->BxT_pl, c->Bz_pl, c->eZ, c->ps0_ao,
+                  c->pbc_ao};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 7; i++)
@@ -329,6 +331,7 @@ thc_status thc_set_collocation(thc_ctx* c, const double* X) {
   }
   CKC(c, cudaStreamSynchronize(c->stream));
   c->have_x = true;
+  c->bxt_valid = false;   // the THC-AO-K planes of X^T follow the collocation
   return THC_OK;
 }
 
@@ -390,7 +393,9 @@ static cudaError_t mark(thc_ctx* c, int i, cudaStream_t s, bool simple) {
   return e;
 }
 
-static thc_status build_fp64(thc_ctx* c, const double2* C, double2* KC, double* ex) {
+// Kao (THC-AO-K): after S3, K^k = conj(X^k) M^k X^{kT} into Kao instead of S4a,
+// S4b, and E_x = -(1/N_k) sum_k sum_PQ conj(D^k_PQ) M^k_PQ (the same energy).
+static thc_status build_fp64(thc_ctx* c, const double2* C, double2* KC, double* ex, double2* Kao = nullptr) {
   const int nk = c->nk, N = c->nbas, n = c->nocc, P = c->nisdf;
   const long PP = (long)P * P;
   double2* Psi = (double2*)c->Psi;
@@ -407,6 +412,15 @@ static thc_status build_fp64(thc_ctx* c, const double2* C, double2* KC, double* 
   CKC(c, mark(c, 2, s, true));
   CKC(c, kconv_z(D, c->Vh64, M, PP, c->n1, c->n2, c->n3, s));
   CKC(c, mark(c, 3, s, true));
+  if (Kao) {
+    CKC(c, gemm_z(A_MK_CONJ, B_KN, N, P, P, c->X64, P, (long)N * P, M, P, PP, c->Wao, P, (long)N * P, nk, s));
+    CKC(c, mark(c, 4, s, true));
+    CKC(c, gemm_z(A_MK, B_NK, N, N, P, c->Wao, P, (long)N * P, c->X64, P, (long)N * P, Kao, N, (long)N * N, nk, s));
+    CKC(c, mark(c, 5, s, true));
+    CKC(c, ex_reduce_z(D, M, (long)nk * PP, nk, c->partial, c->n_partial, ex, s));
+    CKC(c, mark(c, 6, s, true));
+    return THC_OK;
+  }
   CKC(c, gemm_z(A_MK, B_KN, P, n, P, M, P, PP, Psi, n, (long)P * n, Y, n, (long)P * n, nk, s));
   CKC(c, mark(c, 4, s, true));
   CKC(c, gemm_z(A_MK_CONJ, B_KN, N, n, P, c->X64, P, (long)N * P, Y, n, (long)P * n, KC, n,
@@ -451,7 +465,7 @@ static thc_status build_mixed(thc_ctx* c, const double2* C, double2* KC, double*
 // 8; S1 (rounded to FP32 Psi) and S2 (FP32 D) take 6.
 constexpr int kProducts[4] = {6, 6, 8, 8};
 
-static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex) {
+static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex, double2* Kao = nullptr) {
   const int nk = c->nk, N = c->nbas, n = c->nocc, P = c->nisdf;
   const long PP = (long)P * P, Pn = (long)P * n, Nn = (long)N * n;
   float2* Psi = (float2*)c->Psi;
@@ -478,9 +492,11 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   // diagonal only, so S2 leaves the part below it unwritten)
   const bool a_f32 = c->plM == 0;
   const bool herm = c->herm_v && c->hkeys && a_f32;
+  // (THC-AO-K reads all of D for its energy, so D is written whole there)
+  const bool upper = herm && !Kao;
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
-                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 1, 1), kProducts[1], 0, herm ? 2 : 1));
-  c->d_upper = herm;
+                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 1, 1), kProducts[1], 0, upper ? 2 : 1));
+  c->d_upper = upper;
   CKC(c, mark(c, 2, s, false));
   // S3  M = IDFT(DFT(D) o Vh) in FP32
   // (2^3, 3^3 and 4^3 meshes: the convolution also finds the exact row
@@ -499,6 +515,35 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
     CKC(c, record_core(c, 2, 1, s));
   }
   CKC(c, mark(c, 3, s, false));
+  if (Kao) {
+    // THC-AO-K: Z = M X^T (A = M as in S4a; B = the embedded X^T, made once
+    // per collocation), then K = conj(X) Z (A = X as in S4b; B = embedded Z)
+    if (a_f32) {
+      if (!have_eM) CKC(c, row_exponents_rows(M, P, (long)nk * P, c->eM, s));
+    } else {
+      CKC(c, slice_rows_exact(M, P, (long)nk * P, c->eM, c->M_pl, c->plM, c->ldM, s));
+    }
+    if (!c->bxt_valid) {
+      CKC(c, embed_b(c->X32, false, (long)N * c->ldX, 1, c->ldX, false, false, nk, P, N, c->eXn, c->BxT_pl, c->plAO,
+                     c->ldAO, s));
+      c->bxt_valid = true;
+    }
+    CKC(c, record_core(c, 3, 0, s));
+    CKC(c, tc_gemm(a_f32 ? c->opMf : c->opM, c->opBxT, P, 2 * N, 2 * P, nk, c->eM, P, c->eXn, N, c->Zao, false,
+                   2 * N, 2L * P * N, c->ps0_ao, c->pbc_ao, c->tc_err, s, core_event(c, 3, 1), 8, a_f32 ? 1 : 0));
+    CKC(c, mark(c, 4, s, false));
+    CKC(c, col_exponents_c(c->Zao, (long)P * N, N, nk, P, N, c->eZ, s));
+    CKC(c, embed_b(c->Zao, false, (long)P * N, N, 1, false, true, nk, P, N, c->eZ, c->Bz_pl, c->plAO, c->ldAO, s));
+    CKC(c, record_core(c, 4, 0, s));
+    CKC(c, tc_gemm(c->opXn, c->opBz, N, 2 * N, 2 * P, nk, c->eXn, N, c->eZ, N, Kao, true, 2 * N, 2L * N * N,
+                   c->ps0_ao, c->pbc_ao, c->tc_err, s, core_event(c, 4, 1), 8, 1));
+    CKC(c, mark(c, 5, s, false));
+    CKC(c, record_core(c, 5, 0, s));
+    CKC(c, ex_reduce_c(D, M, (long)nk * PP, nk, c->partial, c->n_partial, ex, s));
+    CKC(c, record_core(c, 5, 1, s));
+    CKC(c, mark(c, 6, s, false));
+    return THC_OK;
+  }
   // S4a Y = M Psi on tensor cores: A = M in FP32, cut into its slices inside
   // the GEMM with the exact row exponents of M; B = embedded Psi with one
   // exponent per orbital
@@ -546,6 +591,77 @@ thc_status thc_build(thc_ctx* c, const double* C, double* KC, double* ex) {
     if (c->prof_max > 0 && c->prof_n < c->prof_max) {
       c->prof_n++;
     }
+  }
+  return st;
+}
+
+// The THC-AO-K workspace, made by the first thc_build_K of a context.
+static thc_status ao_prepare(thc_ctx* c) {
+  if (c->ao_ready) return THC_OK;
+  const int nk = c->nk, N = c->nbas, P = c->nisdf;
+  struct Want { void** p; size_t bytes; };
+  std::vector<Want> want;
+  if (c->precision == THC_FP64) {
+    want.push_back({(void**)&c->Wao, sizeof(double2) * (size_t)nk * N * P});
+  } else {
+    c->ldAO = pad8(2 * P);
+    c->plAO = (long)nk * 2 * N * c->ldAO;
+    const long npart = std::max(tc_partial_elems(P, 2 * N, 2 * P, nk), tc_partial_elems(N, 2 * N, 2 * P, nk));
+    want.push_back({(void**)&c->Zao, sizeof(float2) * (size_t)nk * P * N});
+    want.push_back({(void**)&c->BxT_pl, 3 * 2 * (size_t)c->plAO});
+    want.push_back({(void**)&c->Bz_pl, 3 * 2 * (size_t)c->plAO});
+    want.push_back({(void**)&c->eZ, sizeof(int) * (size_t)nk * N});
+    if (npart > 0) {
+      want.push_back({(void**)&c->ps0_ao, sizeof(int) * (size_t)npart});
+      want.push_back({(void**)&c->pbc_ao, sizeof(float) * (size_t)npart});
+    }
+  }
+  for (auto& w : want) {
+    cudaError_t e = cudaMalloc(w.p, w.bytes);
+    if (e == cudaSuccess) e = cudaMemset(*w.p, 0, w.bytes);   // plane padding stays zero
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      for (auto& x : want)
+        if (*x.p) {
+          cudaFree(*x.p);
+          *x.p = nullptr;
+        }
+      c->last_error = std::string("thc_build_K workspace: ") + cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? THC_ERR_OOM : THC_ERR_CUDA;
+    }
+  }
+  if (c->precision == THC_MIXED) {
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < 3 && e == cudaSuccess; p++) {
+      e = make_plane_map(c->opBxT.map[p], c->BxT_pl + p * c->plAO, nk, 2 * N, 2 * P, c->ldAO);
+      if (e == cudaSuccess) e = make_plane_map(c->opBz.map[p], c->Bz_pl + p * c->plAO, nk, 2 * N, 2 * P, c->ldAO);
+    }
+    if (e != cudaSuccess) {
+      c->last_error = std::string("thc_build_K maps: ") + cudaGetErrorString(e);
+      return THC_ERR_CUDA;
+    }
+  }
+  c->ao_ready = true;
+  return THC_OK;
+}
+
+thc_status thc_build_K(thc_ctx* c, const double* C, double* K, double* ex) {
+  if (!c || !C || !K || !ex) return THC_ERR_ARG;
+  if (!aligned16(C) || !aligned16(K) || ((uintptr_t)ex & 7u)) return THC_ERR_ARG;
+  if (c->precision == THC_MIXED_SIMT) return THC_ERR_UNSUPPORTED;
+  const size_t cb = (size_t)c->nk * c->nbas * c->nocc * sizeof(double2);
+  const size_t kb = (size_t)c->nk * c->nbas * c->nbas * sizeof(double2);
+  const char* a = (const char*)C;
+  const char* b = (const char*)K;
+  if (a < b + kb && b < a + cb) return THC_ERR_ARG;   // K overlaps C
+  if (!c->have_x || !c->have_v) return THC_ERR_STATE;
+  thc_status st = ao_prepare(c);
+  if (st != THC_OK) return st;
+  if (c->precision == THC_FP64) st = build_fp64(c, (const double2*)C, nullptr, ex, (double2*)K);
+  else st = build_tc(c, (const double2*)C, nullptr, ex, (double2*)K);
+  if (st == THC_OK) {
+    c->built = true;
+    if (c->prof_max > 0 && c->prof_n < c->prof_max) c->prof_n++;
   }
   return st;
 }

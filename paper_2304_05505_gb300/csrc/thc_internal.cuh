@@ -87,6 +87,21 @@ struct thc_ctx {
   TcOperand opXT, opPs, opXn, opBc, opBd, opBy;   // opXT, opXn: FP32 maps of X32
   TcOperand opMf;     // map[0]: FP32 map of M (A of S4a, converted in the GEMM), even nisdf
   TcOperand opM;      // M's slices, odd nisdf
+  // THC-AO-K (thc_build_K), allocated by its first call: Z = M X^T and, for
+  // the tensor-core form, the embedded planes of X^T (static) and of Z, the
+  // column exponents of Z and split-K partials of the two products; for the
+  // FP64 form W = conj(X) M
+  bool ao_ready, bxt_valid;
+  float2* Zao;        // [nk][nisdf][nbas]
+  double2* Wao;       // [nk][nbas][nisdf] (FP64)
+  uint16_t* BxT_pl;   // [nk][2 nbas][ldAO]  embedded X^T, B of Z = M X^T (exponents eXn)
+  uint16_t* Bz_pl;    // [nk][2 nbas][ldAO]  embedded Z, B of K = conj(X) Z (exponents eZ)
+  int* eZ;            // [nk][nbas]
+  int* ps0_ao;
+  float* pbc_ao;
+  long plAO;
+  int ldAO;
+  TcOperand opBxT, opBz;
   int* tc_err;        // device word: nonzero after a device wait gave up
   uint32_t* hkeys;    // row and column keys of the Hermitian convolution (when its form applies)
   bool herm_v;        // every V^q Hermitian (to 1e-12 of max |V|): S2 writes D's upper part, S3 mirrors M
@@ -106,7 +121,7 @@ struct thc_ctx {
 
 // GEMM operand layouts.  A(m, k) and B(k, n) for C(m, n) = sum_k A B.
 enum GemmA { A_MK = 0, A_KM = 1, A_MK_CONJ = 2 };   // A[m*lda+k], A[k*lda+m], conj(A[m*lda+k])
-enum GemmB { B_KN = 0, B_NK_CONJ = 1 };             // B[k*ldb+n], conj(B[n*ldb+k])
+enum GemmB { B_KN = 0, B_NK_CONJ = 1, B_NK = 2 };  // B[k*ldb+n], conj(B[n*ldb+k]), B[n*ldb+k]
 
 // FP64 complex batched GEMM on CUDA cores.
 cudaError_t gemm_z(int la, int lb, int M, int N, int K, const double2* A, int lda, long sA,

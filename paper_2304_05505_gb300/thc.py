@@ -31,7 +31,7 @@ EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_ker
            "thc_profile_begin", "thc_profile_end", "thc_sync", "thc_kconv_noalloc",
            "thc_select_points", "thc_fit_kernel", "thc_profile_kernels", "thc_mlp_features", "thc_mlp_score",
            "thc_mlp_workspace_bytes", "thc_mlp_train_step", "thc_mlp_candidates", "thc_select_points_among",
-           "thc_debug_set_wait_limit", "thc_debug_fail_alloc", "thc_rebuild_kernel"]
+           "thc_debug_set_wait_limit", "thc_debug_fail_alloc", "thc_rebuild_kernel", "thc_build_K"]
 
 MLP_NPARAM = 8641
 
@@ -66,6 +66,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_set_kernel.argtypes = [vp, dp]
     lib.thc_build.argtypes = [vp, dp, dp, dp]
     lib.thc_build_host.argtypes = [vp, dp, dp, dp]
+    lib.thc_build_K.argtypes = [vp, dp, dp, dp]
     lib.thc_get_intermediate.argtypes = [vp, ip, dp]
     lib.thc_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.thc_launches_per_build.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
@@ -184,6 +185,15 @@ def _host_ptr(a, dtype, name) -> int:
             raise ValueError(f"{name}: must be contiguous")
         return a.ctypes.data
     raise TypeError(f"{name}: expected a host tensor or numpy array")
+
+
+def thc_build_K(ctx, C, K, ex) -> None:
+    """THC-AO-K build (see include/thc.h): K [N_k][nbas][nbas] complex128."""
+    import torch
+    if not (isinstance(ex, torch.Tensor) and ex.is_cuda and ex.dtype == torch.float64 and ex.numel() >= 2):
+        raise TypeError("ex: expected a CUDA float64 tensor with 2 elements")
+    _check(load().thc_build_K(ctx, _dev_ptr(C, name="C"), _dev_ptr(K, name="K"), ex.data_ptr()),
+           "thc_build_K", ctx)
 
 
 def thc_build_host(ctx, C_host, KC_host, ex_host) -> None:
@@ -491,6 +501,18 @@ class ExchangeBuild:
             ex = t.empty(2, dtype=t.float64, device=self.device)
         thc_build(self.ctx, C, KC, ex)
         return KC, ex
+
+    def build_K(self, C, K=None, ex=None):
+        """THC-AO-K: the full AO exchange matrix K^k = conj(X^k) M^k X^{kT} and E_x."""
+        t = self.torch
+        C = self._to_dev(C)
+        d = self.dims
+        if K is None:
+            K = t.empty((self.nk, d["nbas"], d["nbas"]), dtype=t.complex128, device=self.device)
+        if ex is None:
+            ex = t.empty(2, dtype=t.float64, device=self.device)
+        thc_build_K(self.ctx, C, K, ex)
+        return K, ex
 
     def sync(self):
         thc_sync(self.ctx)
