@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "THC-oo-K exchange builds/s, mixed vs FP64 on one GB300 at <=1e-6 Ha; % roofline"
 WORKLOADS = {
+    "C1": ("benzene-shaped orthorhombic cell 13.9x17.8x12.9 bohr, 48 centres, N=432, n_occ=60, "
+           "3x3x3 k (N_k=27), N_ISDF=600, 40^3 grid (config C1)"),
     "C2": ("benzene-shaped orthorhombic cell 13.9x17.8x12.9 bohr, 48 centres, N=432, n_occ=60, "
            "4x4x4 k (N_k=64), N_ISDF=1200, 40^3 grid (config C2)"),
     "C3": ("2x1x1 supercell of the benzene-shaped cell, 27.8x17.8x12.9 bohr, 96 centres, N=864, n_occ=120, "
@@ -64,8 +66,12 @@ def parse():
     ap.add_argument("--cpu-samples", type=int, default=4)
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error and CPU baseline")
     ap.add_argument("--config", default="C2", choices=sorted(WORKLOADS),
-                    help="C2 (default: the headline workload) or C3, the 6x6x6-k supercell at scale, "
-                         "timed once for the record (its inputs take minutes to make)")
+                    help="C2 (default: the headline workload), C1 (3x3x3 k) or C3, the 6x6x6-k supercell "
+                         "at scale, timed once for the record (its inputs take minutes to make)")
+    ap.add_argument("--kernel", default="model", choices=["model", "fitted"],
+                    help="model: the generator's model kernel at density-sampled points (default); fitted: "
+                         "points from the FP64 full-grid pivoted Cholesky and V^q from the library's kernel "
+                         "rebuild (tensor-core contraction), as the method feeds the build")
     ap.add_argument("--no-rebuild", action="store_true",
                     help="skip timing the per-iteration kernel rebuild (C2 only)")
     ap.add_argument("--rebuild-fp64", action="store_true",
@@ -345,6 +351,34 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def time_ext(args, thc, d, p, C, KC, ex, dev, stream, world, e0, e1) -> dict:
+    """THC_MIXED_EXT on the same inputs: device-timed builds/s and its KC, E_x."""
+    import torch
+    ee = thc.ExchangeBuild(d, "mixed_ext", device=dev, stream=stream)
+    ee.set_collocation(p.X)
+    ee.set_kernel(p.V)
+    for _ in range(3):
+        ee.build(C, KC, ex)
+    torch.cuda.synchronize()
+    n = max(3, min(args.steps, 20))
+    thc.thc_profile_begin(ee.ctx, n)
+    e0.record(stream)
+    for _ in range(n):
+        ee.build(C, KC, ex)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ee.sync()
+    ms = max_over_ranks(world, e0.elapsed_time(e1)) / n
+    st, _ = thc.thc_profile_end(ee.ctx)
+    out = {"value": world / (ms * 1e-3), "unit": "builds/s", "ms_per_step": ms,
+           "stages_ms": dict(zip(thc.STAGES, st)), "hermitian_form": thc.thc_hermitian_kernel(ee.ctx),
+           "KC": KC.cpu().numpy(), "Ex": float(ex[0])}
+    ee.close()
+    del ee
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_simt(args, thc, d, p, C, KC, ex, dev, stream, world, e0, e1):
     """The mixed precision on CUDA cores: ms per build, stage ms, KC, E_x."""
     import torch
@@ -383,11 +417,9 @@ def time_rebuild(p, thc, args) -> dict:
     cell = p.cell
     cells.set_accelerator("cuda")
     try:
-        U = cells.grid_orbitals(cell, p.C)
+        Ud = cells.grid_orbitals(cell, p.C, as_tensor=True)
     finally:
         cells.set_accelerator(None)
-    Ud = torch.from_numpy(U).cuda()
-    del U
     t0 = time.perf_counter()
     pts, _ = thc.thc_select_points(Ud, cell.nisdf)
     t_sel = time.perf_counter() - t0
@@ -441,17 +473,34 @@ def time_aok(d, p, thc, dev, stream) -> dict:
     return out
 
 
-def make_inputs(config: str):
-    """The seeded synthetic cell of `config`; the largest one makes its
-    matrix products through torch on the GPU (input generation only)."""
+def make_inputs(config: str, kernel: str = "model"):
+    """The seeded synthetic cell of `config`, its large products and
+    collocations made through torch on the GPU (input generation only).
+    kernel "fitted" replaces the model kernel and its sampled points by the
+    ones the method feeds the build: the FP64 full-grid pivoted-Cholesky
+    points and V^q from the library's kernel rebuild at those points."""
+    import torch
     from paper_2304_05505_gb300 import cells
-    if config == "C3":
-        cells.set_accelerator("cuda")
-        try:
+    cells.set_accelerator("cuda" if torch.cuda.is_available() else None)
+    try:
+        if kernel == "model":
             return cells.make_problem(config)
-        finally:
-            cells.set_accelerator(None)
-    return cells.make_problem(config)
+        from paper_2304_05505_gb300 import thc
+        thc.load()
+        cell = cells.make_cell(config)
+        C = cells.occupied_coefficients(cell)
+        U = cells.grid_orbitals(cell, C, as_tensor=True)
+        idx, _ = thc.thc_select_points(U, cell.nisdf)
+        V, _ = thc.thc_rebuild_kernel(U, cell.grid, cell.lattice, cell.mesh, idx, "mixed")
+        del U
+        pts = cells.points_from_indices(cell, idx)
+        X = cells.bloch_collocation(cell, pts, cells.kmesh_frac(cell.mesh))
+        p = cells.Problem(cell, pts, idx, np.zeros(len(idx)), X, C, V.cpu().numpy())
+        del V
+        torch.cuda.empty_cache()
+        return p
+    finally:
+        cells.set_accelerator(None)
 
 
 def run_ours(args, world, rank, local):
@@ -464,7 +513,7 @@ def run_ours(args, world, rank, local):
         raise RuntimeError("libthc.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
     thc.load()
     dev = torch.device("cuda", torch.cuda.current_device())
-    p = make_inputs(args.config)
+    p = make_inputs(args.config, args.kernel)
     d = p.dims
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
@@ -535,6 +584,9 @@ def run_ours(args, world, rank, local):
     del eb
     torch.cuda.empty_cache()
 
+    # --- the extended form (THC_MIXED_EXT): M carried to about 35 bits ---------
+    ext = time_ext(args, thc, d, p, C, KC, ex, dev, stream, world, e0, e1) if args.config == "C2" else None
+
     # --- the same precision on CUDA cores (comparison; the headline cell only) --
     ms_simt, st_simt, KC_simt, ex_simt = None, [0.0] * 6, None, None
     if args.config == "C2":
@@ -578,12 +630,15 @@ def run_ours(args, world, rank, local):
 
     line = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16-slices/f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "fp16-slices/f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.config],
                        "precision": "mixed: S1/S2/S4a/S4b tcgen05 GEMMs on 3-slice fixed-point fp16 operands "
                                     "(8+11+11 bits; 6, 6, 8, 8 slice products; exact leading sums, FP32 "
                                     "remainders), X and M sliced inside the GEMMs, S3 FP32, E_x FP64 sum",
-                       "kernel_source": "model kernel V^q (Gaussian-smeared point deltas), density-sampled points",
+                       "kernel_source": ("model kernel V^q (Gaussian-smeared point deltas), density-sampled points"
+                                         if args.kernel == "model" else
+                                         "ISDF-fitted V^q (kernel rebuild, tcgen05 contraction) at the FP64 "
+                                         "full-grid pivoted-Cholesky points"),
                        "hermitian_form": hermitian,
                        "l2": "inputs larger than L2 (prepared kernel complex64 > 700 MB, X FP32 > 260 MB)",
                        "parallelism": f"{world} independent builds (one per GPU)"},
@@ -600,6 +655,8 @@ def run_ours(args, world, rank, local):
         line["kernel_rebuild"] = rebuild
     if aok is not None:
         line["thc_ao_k"] = aok
+    if ext is not None:
+        line["mixed_ext"] = {k: v for k, v in ext.items() if k not in ("KC", "Ex")}
     if ms_simt is not None:
         line["mixed_cuda_cores"] = {"value": world / (ms_simt * 1e-3), "unit": "builds/s", "ms_per_step": ms_simt,
                                     "stages_ms": {nm: ms for nm, ms in zip(names, st_simt)}}
@@ -617,6 +674,9 @@ def run_ours(args, world, rank, local):
             "fp64_gpu": {"max_abs_dKC": float(np.abs(KC_64 - ref["KC"]).max()),
                          "abs_dEx": abs(float(ex_64[0]) - ref["Ex"])},
             "Ex_oracle": ref["Ex"], "oracle_full_build_s": t_full}
+        if ext is not None:
+            line["accuracy_vs_oracle"]["mixed_ext"] = {
+                "max_abs_dKC": float(np.abs(ext["KC"] - ref["KC"]).max()), "abs_dEx": abs(ext["Ex"] - ref["Ex"])}
         if KC_simt is not None:
             line["accuracy_vs_oracle"]["mixed_cuda_cores"] = {
                 "max_abs_dKC": float(np.abs(KC_simt - ref["KC"]).max()), "abs_dEx": abs(float(ex_simt[0]) - ref["Ex"])}

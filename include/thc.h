@@ -66,8 +66,16 @@ typedef enum {
                               as fp16, the leading products summed exactly, 6 or 8
                               slice products per product; S3 in FP32; E_x summed
                               in FP64 */
-  THC_MIXED_SIMT = 2       /* the same precision on CUDA cores: FP32 operands,
+  THC_MIXED_SIMT = 2,      /* the same precision on CUDA cores: FP32 operands,
                               float-float compensated sums in S1, S4a, S4b */
+  THC_MIXED_EXT = 3        /* THC_MIXED with the extended k-convolution where it
+                              applies (2^3 or 4^3 mesh, Hermitian V, nisdf a
+                              multiple of 4): the DFTs run exactly on an 18-bit
+                              split of each element's values, the product with
+                              the prepared kernel keeps its roundings, and M
+                              leaves as FP32 values plus fp16 remainders that S4a
+                              slices with them (about 35 bits of M instead of
+                              24); elsewhere it is THC_MIXED */
 } thc_precision;
 
 typedef struct {
@@ -137,7 +145,8 @@ thc_status thc_build_K(thc_ctx* ctx, const double* C, double* K, double* ex);
 /* Intermediates of the last build, copied to device buffers the caller owns
  * (for tests).  which: 0 = Psi [N_k][nisdf][nocc], 1 = D [N_k][nisdf][nisdf],
  * 2 = M [N_k][nisdf][nisdf], 3 = Y = M Psi [N_k][nisdf][nocc].  Written as
- * complex128 whatever the precision.  which = 4 (THC_MIXED only): the row
+ * complex128 whatever the precision (M with its remainders under
+ * THC_MIXED_EXT).  which = 4 (THC_MIXED only): the row
  * exponents of M that S4a slices it with, [N_k][nisdf] doubles, each the
  * smallest e with max_Q max(|Re|, |Im|) of M^k[P][Q] < 2^e (0 for a zero
  * row; a row whose maximum is below 2^-133 may also get 0, which still bounds

@@ -274,19 +274,20 @@ def grid_gvectors(shape, recip) -> np.ndarray:
 # Bloch-summed Gaussian collocation
 # ----------------------------------------------------------------------------
 
-def _angular(l: np.ndarray, m: np.ndarray, alpha: np.ndarray, d: np.ndarray):
+def _angular(l, m, alpha, d, xp=np):
     """Normalised real solid-harmonic prefactor of each primitive.
 
-    d: (..., N, 3) displacement r - A.  Returns (..., N)."""
+    d: (..., N, 3) displacement r - A.  Returns (..., N).  ``xp`` is numpy or
+    torch (the accelerated collocation passes tensors)."""
     x, y, z = d[..., 0], d[..., 1], d[..., 2]
     n0 = (2.0 * alpha / np.pi) ** 0.75
-    out = np.ones(d.shape[:-1])
-    out = np.where(l == 1, np.where(m == 0, x, np.where(m == 1, y, z)) * np.sqrt(4 * alpha), out)
-    d2 = np.where(m == 0, x * y,
-         np.where(m == 1, y * z,
-         np.where(m == 2, (2 * z * z - x * x - y * y) / (2 * np.sqrt(3.0)),
-         np.where(m == 3, x * z, (x * x - y * y) / 2.0))))
-    out = np.where(l == 2, d2 * 4 * alpha, out)
+    out = xp.ones_like(x)
+    out = xp.where(l == 1, xp.where(m == 0, x, xp.where(m == 1, y, z)) * xp.sqrt(4 * alpha), out)
+    d2 = xp.where(m == 0, x * y,
+         xp.where(m == 1, y * z,
+         xp.where(m == 2, (2 * z * z - x * x - y * y) / (2 * math.sqrt(3.0)),
+         xp.where(m == 3, x * z, (x * x - y * y) / 2.0))))
+    out = xp.where(l == 2, d2 * 4 * alpha, out)
     return out * n0
 
 
@@ -332,9 +333,47 @@ def collocation_terms(cell: Cell, points: np.ndarray, chunk: int = 4096) -> list
     return terms
 
 
+def _bloch_collocation_accel(cell: Cell, points: np.ndarray, kfrac: np.ndarray, chunk: int = 1 << 16):
+    """bloch_collocation on the accelerator, as a torch tensor (Nk, N, Np).
+
+    The same image set, drop rule and image order as collocation_terms /
+    bloch_collocation, evaluated densely over (function, point) per image
+    with the dropped terms multiplied by zero, so each element sums the same
+    terms in the same order (agreement to the rounding of exp)."""
+    import torch
+    dev = _ACCEL
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    A = t(cell.centres[cell.fn_centre])
+    alpha = t(cell.fn_alpha)
+    l, m = t(cell.fn_l), t(cell.fn_m)
+    rc2 = np.minimum(IMAGE_CUTOFF ** 2, GAUSS_DROP / cell.fn_alpha)
+    images = _image_range(cell, float(np.sqrt(rc2.max())))
+    rc2 = t(rc2)
+    kc = np.atleast_2d(kfrac) @ cell.recip
+    pts = t(points)
+    npnt = points.shape[0]
+    X = torch.zeros((kc.shape[0], cell.nbas, npnt), dtype=torch.complex128, device=dev)
+    for n in images:
+        R = np.array(n, dtype=np.float64) @ cell.lattice
+        ph = t(np.exp(1j * (kc @ R)))
+        AR = A + t(R)
+        for p0 in range(0, npnt, chunk):
+            d = pts[None, p0:p0 + chunk, :] - AR[:, None, :]            # (N, np, 3)
+            r2 = (d * d).sum(-1)
+            mask = r2 <= rc2[:, None]
+            if not bool(mask.any()):
+                continue
+            val = _angular(l[:, None], m[:, None], alpha[:, None], d, torch) \
+                * torch.exp(-alpha[:, None] * r2) * mask
+            X[:, :, p0:p0 + chunk] += ph[:, None, None] * val[None]
+    return X
+
+
 def bloch_collocation(cell: Cell, points: np.ndarray, kfrac: np.ndarray,
                       terms: list | None = None) -> np.ndarray:
     """X^k[mu, p] = sum_R exp(i k.R) phi_mu(r_p - R), shape (Nk, N, Np) c128."""
+    if terms is None and _ACCEL is not None:
+        return _bloch_collocation_accel(cell, points, kfrac).cpu().numpy()
     if terms is None:
         terms = collocation_terms(cell, points)
     kc = np.atleast_2d(kfrac) @ cell.recip
@@ -386,7 +425,7 @@ def occupied_coefficients(cell: Cell) -> np.ndarray:
     nk = kf.shape[0]
     C = np.zeros((nk, cell.nbas, cell.nocc), dtype=np.complex128)
     done = np.zeros(nk, dtype=bool)
-    terms = collocation_terms(cell, pts)
+    terms = collocation_terms(cell, pts) if _ACCEL is None else None
     for k in range(nk):
         if done[k]:
             continue
@@ -412,7 +451,7 @@ def occupied_coefficients(cell: Cell) -> np.ndarray:
     return C
 
 
-def grid_orbitals(cell: Cell, C: np.ndarray, stride: int = 1) -> np.ndarray:
+def grid_orbitals(cell: Cell, C: np.ndarray, stride: int = 1, as_tensor: bool = False):
     """The input of the setup calls (interpolation-point selection and the
     ISDF kernel fit): the occupied orbitals' cell-periodic parts on the grid
     sub-sampled by ``stride``, U[f][r] = u^k_i(r) = exp(-i k.r) sum_mu
@@ -420,10 +459,13 @@ def grid_orbitals(cell: Cell, C: np.ndarray, stride: int = 1) -> np.ndarray:
 
     These are grid values for the setup stage; the build itself collocates
     the orbitals at the interpolation points (its step 1), which this module
-    never does."""
+    never does.  With an accelerator set and ``as_tensor``, U is returned as a
+    torch tensor on that device."""
     pts = grid_points(cell, stride)
     kf = kmesh_frac(cell.mesh)
     kc = kf @ cell.recip
+    if _ACCEL is not None:
+        return _grid_orbitals_accel(cell, C, pts, kf, kc, as_tensor)
     terms = collocation_terms(cell, pts)
     nk, n = C.shape[0], C.shape[2]
     U = np.zeros((nk, n, pts.shape[0]), dtype=np.complex128)
@@ -433,6 +475,22 @@ def grid_orbitals(cell: Cell, C: np.ndarray, stride: int = 1) -> np.ndarray:
         psi = _mm_h(np.ascontiguousarray(C[k].T), np.ascontiguousarray(Xk.T.conj()))
         U[k] = psi * np.exp(-1j * (pts @ kc[k]))[None, :]
     return U.reshape(nk * n, -1)
+
+
+def _grid_orbitals_accel(cell, C, pts, kf, kc, as_tensor, kblock: int = 8):
+    import torch
+    nk, n = C.shape[0], C.shape[2]
+    U = torch.empty((nk, n, pts.shape[0]), dtype=torch.complex128, device=_ACCEL)
+    pt = torch.from_numpy(pts).to(_ACCEL)
+    Ct = torch.from_numpy(np.ascontiguousarray(C)).to(_ACCEL)
+    for k0 in range(0, nk, kblock):
+        k1 = min(nk, k0 + kblock)
+        Xk = _bloch_collocation_accel(cell, pts, kf[k0:k1])                  # (kb, N, ng)
+        ph = torch.exp(-1j * (pt @ torch.from_numpy(kc[k0:k1]).to(_ACCEL).T)).T   # (kb, ng)
+        U[k0:k1] = torch.matmul(Ct[k0:k1].transpose(1, 2), Xk) * ph[:, None, :]
+        del Xk
+    U = U.reshape(nk * n, -1)
+    return U if as_tensor else U.cpu().numpy()
 
 
 # ----------------------------------------------------------------------------

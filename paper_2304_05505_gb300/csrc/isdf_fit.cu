@@ -182,6 +182,17 @@ __global__ void add_kernel(double2* __restrict__ V, const double2* __restrict__ 
   V[i] = make_double2(V[i].x + W[i].x, V[i].y + W[i].y);
 }
 
+// V += (W + W^H) / 2 for one [np][np] matrix (complex): the tensor-core
+// product computes W[P][Q] and W[Q][P] apart, so their roundings differ; its
+// Hermitian part is the same quantity, exactly Hermitian.
+__global__ void add_herm_kernel(double2* __restrict__ V, const double2* __restrict__ W, int np) {
+  const long i = (long)blockIdx.x * TB + threadIdx.x;
+  if (i >= (long)np * np) return;
+  const int P = (int)(i / np), Q = (int)(i % np);
+  const double2 a = W[i], b = W[(long)Q * np + P];
+  V[i] = make_double2(V[i].x + 0.5 * (a.x + b.x), V[i].y + 0.5 * (a.y - b.y));
+}
+
 // Minimum-image fractional representatives of q = qco / mesh along one axis.
 std::vector<double> axis_reps(int qc, int n) {
   const double f = (double)(((qc % n) + n) % n) / n;
@@ -409,7 +420,7 @@ thc_status fit_impl(const double* U, int nfunc, const int* grid_host, const doub
               if ((e = tc_gemm(opA, opB, npts, 2 * npts, 2 * gn, 1, eX, npts, eX, npts, W, true, 2 * npts, 2 * npq,
                                ps0, pbc, tcerr, s, nullptr, 8, 1, 0)) != cudaSuccess)
                 break;
-              add_kernel<<<blocks(npq), TB, 0, s>>>(V + (long)q * npq, W, npq);
+              add_herm_kernel<<<blocks(npq), TB, 0, s>>>(V + (long)q * npq, W, npts);
             }
             if (e != cudaSuccess) break;
           }

@@ -12,11 +12,17 @@
 //   kconv_herm_kernel  Hermitian D^k and V^q (so M^k Hermitian), meshes 2^3,
 //                      3^3, 4^3, N_P even: TMA-fed tiles that reach the
 //                      diagonal, M mirrored through shared memory, row
-//                      exponents of M from per-tile keys
+//                      exponents of M from per-tile keys; on 2^3 and 4^3
+//                      meshes an extended form (X) also writes M's fp16
+//                      remainders, the DFTs run exactly on an 18-bit split
+//                      of each element (see split_magic)
 //   kconv_pipe_kernel  the same meshes, any V: TMA-fed batches of consecutive
 //                      elements, row exponents of M folded in
-//   kconv_lanes_kernel the same meshes without TMA (N1 lanes per element,
-//                      first axis by shuffles)
+//   kconv_tile_kernel  other meshes with N_k <= 256 (6^3 among them), N_P^2
+//                      even: TMA-fed batches of 32 elements, the 3-D DFT in
+//                      place in shared memory (lengths 6 by Good-Thomas)
+//   kconv_lanes_kernel the same meshes as kconv_pipe_kernel without TMA (N1
+//                      lanes per element, first axis by shuffles)
 //   kconv_kernel       any mesh: one thread per element, its N_k values in
 //                      shared memory ([k][thread], conflict-free)
 // All run the separable 3-D DFT axis by axis with radix-2/3/4 butterflies or
@@ -33,6 +39,7 @@
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 
 #include <math.h>
 
@@ -589,6 +596,79 @@ __host__ __device__ __forceinline__ int herm_qb0(int pb, int epw) {
   return x > 0 ? (x + epw - 1) / epw : 0;
 }
 
+// Extended form of the convolution (radix-2/4 meshes, where every DFT is made
+// of additions, subtractions and multiplications by +-i).  Each element's
+// values are split into a part on the grid of 2^(e - 18), e the exponent of
+// the element's largest component (|x| < 2^e), and the remainder.  The DFTs
+// of the first part are exact in FP32: a 64-point DFT grows values by at most
+// 2^6, so every sum stays an integer multiple of the grid below 2^24 of it.
+// The remainders are at most 2^-18 of the largest value, so their DFTs' FP32
+// roundings sit near 2^-42 of it.  The product with the prepared kernel is
+// formed with error-free products (an FMA gives each product's rounding
+// error), so M leaves as an FP32 value and the part of its error below
+// 2^-24, which is stored as an fp16 multiple of the value's unit in the last
+// place (mlo_scale).
+
+// 1.5 * 2^(e + 5): adding and subtracting it rounds |x| < 2^e to a multiple of
+// 2^(e - 18).
+__device__ __forceinline__ float split_magic(float mx) {
+  int e;
+  frexpf(mx, &e);
+  e = max(-100, min(e, 100));
+  return 1.5f * __int_as_float((e + 5 + 127) << 23);
+}
+__device__ __forceinline__ float2 split_hi(float2 v, float c) {
+  return make_float2(__fsub_rn(__fadd_rn(v.x, c), c), __fsub_rn(__fadd_rn(v.y, c), c));
+}
+// the largest component of the element held by the N1 slot lanes (EPW apart)
+template <int N1, int L>
+__device__ __forceinline__ float element_max(const float2* x) {
+  constexpr int EPW = 32 / N1;
+  float m = 0.f;
+#pragma unroll
+  for (int j = 0; j < L; j++) m = fmaxf(m, fmaxf(fabsf(x[j].x), fabsf(x[j].y)));
+#pragma unroll
+  for (int o = EPW; o < 32; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  return m;
+}
+// (h + l) * v with the rounding of the h * v products kept: returns the FP32
+// product in ph and everything below it in pl.
+__device__ __forceinline__ void cmul_x(float2 h, float2 l, float2 v, float2& ph, float2& pl) {
+  const float p1 = h.x * v.x, e1 = fmaf(h.x, v.x, -p1);
+  const float p2 = h.y * v.y, e2 = fmaf(h.y, v.y, -p2);
+  const float p3 = h.x * v.y, e3 = fmaf(h.x, v.y, -p3);
+  const float p4 = h.y * v.x, e4 = fmaf(h.y, v.x, -p4);
+  // two-sums p1 - p2 and p3 + p4
+  const float r = __fsub_rn(p1, p2), rb = __fsub_rn(r, p1), re_err = __fadd_rn(__fsub_rn(p1, __fsub_rn(r, rb)), __fsub_rn(-p2, rb));
+  const float i = __fadd_rn(p3, p4), ib = __fsub_rn(i, p3), im_err = __fadd_rn(__fsub_rn(p3, __fsub_rn(i, ib)), __fsub_rn(p4, ib));
+  ph = make_float2(r, i);
+  pl = make_float2((e1 - e2) + re_err + (l.x * v.x - l.y * v.y), (e3 + e4) + im_err + (l.x * v.y + l.y * v.x));
+}
+// The remainder l of a value h as an fp16 multiple of h's unit in the last
+// place, 2^(e(h) - 24) with h = m 2^e(h), 1/2 <= m < 1 (0 for h = 0 or a
+// remainder outside what it can carry).
+__device__ __forceinline__ uint16_t mlo_scale(float h, float l) {
+  const int eh = (int)((__float_as_uint(h) >> 23) & 0xffu);
+  if (eh < 24 || eh == 0xffu) return 0;   // |h| < 2^-103 (or not finite): nothing to carry
+  // l * 2^(24 - e(h)) with e(h) = eh - 126
+  const float q = l * __int_as_float((150 - eh + 127) << 23);
+  return __half_as_ushort(__float2half_rn(q));
+}
+
+// out = M + its fp16 remainders (the extended form's pair), complex128.
+__global__ void mlo_combine_kernel(const float2* __restrict__ M, const uint32_t* __restrict__ Mlo,
+                                   double2* __restrict__ out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float2 h = M[i];
+    const uint32_t q = Mlo[i];
+    auto one = [](float x, uint16_t qq) {
+      const int eh = (int)((__float_as_uint(x) >> 23) & 0xffu);
+      return (double)x + (eh >= 24 ? ldexp((double)__half2float(__ushort_as_half(qq)), eh - 150) : 0.0);
+    };
+    out[i] = make_double2(one(h.x, (uint16_t)(q & 0xffffu)), one(h.y, (uint16_t)(q >> 16)));
+  }
+}
+
 // Hermitian form of the TMA-fed convolution, for D^k and V^q Hermitian (so
 // that M^k is too): only the tiles of 8 rows P by EPW columns Q that reach the
 // diagonal are loaded (3-D boxes [N_k][8][EPW] of D and Vh, zero past the
@@ -600,12 +680,16 @@ __host__ __device__ __forceinline__ int herm_qb0(int pb, int epw) {
 // column keys of its columns (max over its elements with Q > P, the mirrored
 // part of row Q) in colk[Q][pb][..], KWR words per row ([slot][LP] pairs of
 // 16-bit keys); herm_keys_to_exponents takes the maxima.
-template <int N1, int N2, int N3>
+// X (extended form, N1 = 2 or 4): also writes Mlo, the fp16 remainders of M
+// (mlo_scale), [N_k][np][np] pairs (re, im).
+template <int N1, int N2, int N3, bool X>
 __global__ void __launch_bounds__(256, 2) kconv_herm_kernel(const __grid_constant__ CUtensorMap mapD,
                                                          const __grid_constant__ CUtensorMap mapV,
                                                          float2* __restrict__ M, int np, long ntile, Twiddles tw,
                                                          uint32_t* __restrict__ rowk, uint32_t* __restrict__ colk,
-                                                         const int* __restrict__ tcum, int* err) {
+                                                         const int* __restrict__ tcum, int* err,
+                                                         uint32_t* __restrict__ Mlo) {
+  static_assert(!X || N1 == 2 || N1 == 4, "the extended form needs radix-2/4 meshes");
   constexpr int L = N2 * N3, NK = N1 * L, EPW = 32 / N1, EPB = EPW * 8, LP = (L + 1) / 2, KWR = N1 * LP;
   constexpr uint32_t BOX = NK * EPB * sizeof(float2);
   extern __shared__ __align__(128) unsigned char kc_smem[];   // [D box][Vh box][scratch][column keys][mbarrier]
@@ -664,28 +748,92 @@ __global__ void __launch_bounds__(256, 2) kconv_herm_kernel(const __grid_constan
     good = __syncthreads_and(good);
     if (!good) break;
     const int pb = tnext[0], qb = tnext[1];
-    float2 x[L], vh[L];
+    float2 x[L];
+    // X: xl holds the remainder part of every value; hi / lo the M pair
+    float2 xl[X ? L : 1];
+    if constexpr (!X) {
+      float2 vh[L];
 #pragma unroll
-    for (int j = 0; j < L; j++) {
-      float2 v[N1];
+      for (int j = 0; j < L; j++) {
+        float2 v[N1];
 #pragma unroll
-      for (int u = 0; u < N1; u++) v[u] = sD[(u * L + j) * EPB + eloc];
-      x[j] = dft_one<N1>(v, live ? slot : 0, -1, tw);
+        for (int u = 0; u < N1; u++) v[u] = sD[(u * L + j) * EPB + eloc];
+        x[j] = dft_one<N1>(v, live ? slot : 0, -1, tw);
+      }
+#pragma unroll
+      for (int j = 0; j < L; j++) vh[j] = live ? sV[sbase + j * EPB] : make_float2(0.f, 0.f);
+      __syncthreads();                                   // the boxes (and tnext) are free for the next tile
+      if (threadIdx.x == 0 && t + gridDim.x < ntile) {
+        int a, b;
+        locate(t + gridDim.x, a, b);
+        tnext[0] = a;
+        tnext[1] = b;
+        issue(a, b);
+      }
+      local_dfts<N2, N3>(x, tw, -1);
+#pragma unroll
+      for (int j = 0; j < L; j++) x[j] = cmul(x[j], vh[j]);
+      local_dfts<N2, N3>(x, tw, +1);
+    } else {
+      // the element's own values (this lane's slot) give the split point
+#pragma unroll
+      for (int j = 0; j < L; j++) x[j] = live ? sD[sbase + j * EPB] : make_float2(0.f, 0.f);
+      const float cD = split_magic(element_max<N1, L>(x));
+#pragma unroll
+      for (int j = 0; j < L; j++) {
+        float2 vh[N1], vl[N1];
+#pragma unroll
+        for (int u = 0; u < N1; u++) {
+          const float2 d = sD[(u * L + j) * EPB + eloc];
+          vh[u] = split_hi(d, cD);
+          vl[u] = csub(d, vh[u]);
+        }
+        x[j] = dft_one<N1>(vh, live ? slot : 0, -1, tw);
+        xl[j] = dft_one<N1>(vl, live ? slot : 0, -1, tw);
+      }
+      local_dfts<N2, N3>(x, tw, -1);
+      local_dfts<N2, N3>(xl, tw, -1);
+#pragma unroll
+      for (int j = 0; j < L; j++) {
+        float2 ph, pl;
+        cmul_x(x[j], xl[j], live ? sV[sbase + j * EPB] : make_float2(0.f, 0.f), ph, pl);
+        x[j] = ph;
+        xl[j] = pl;
+      }
+      __syncthreads();                                   // the boxes (and tnext) are free for the next tile
+      if (threadIdx.x == 0 && t + gridDim.x < ntile) {
+        int a, b;
+        locate(t + gridDim.x, a, b);
+        tnext[0] = a;
+        tnext[1] = b;
+        issue(a, b);
+      }
+      // split the products again: the grid part's inverse DFTs are exact
+      const float cM = split_magic(element_max<N1, L>(x));
+#pragma unroll
+      for (int j = 0; j < L; j++) {
+        const float2 a = split_hi(x[j], cM);
+        xl[j] = cadd(csub(x[j], a), xl[j]);
+        x[j] = a;
+      }
+      local_dfts<N2, N3>(x, tw, +1);
+      local_dfts<N2, N3>(xl, tw, +1);
+      // the first axis of the remainder part through the scratch (below, the
+      // grid part takes the same way)
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < L; j++) scr[(j * EPB + eloc) * N1 + (slot ^ sw)] = xl[j];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < L; j++) {
+        float2 v[N1];
+#pragma unroll
+        for (int u = 0; u < N1; u++) v[u] = scr[(j * EPB + eloc) * N1 + (u ^ sw)];
+        xl[j] = dft_one<N1>(v, live ? slot : 0, +1, tw);
+      }
+      __syncwarp();
     }
-#pragma unroll
-    for (int j = 0; j < L; j++) vh[j] = live ? sV[sbase + j * EPB] : make_float2(0.f, 0.f);
-    __syncthreads();                                   // the boxes (and tnext) are free for the next tile
-    if (threadIdx.x == 0 && t + gridDim.x < ntile) {
-      int a, b;
-      locate(t + gridDim.x, a, b);
-      tnext[0] = a;
-      tnext[1] = b;
-      issue(a, b);
-    }
-    local_dfts<N2, N3>(x, tw, -1);
-#pragma unroll
-    for (int j = 0; j < L; j++) x[j] = cmul(x[j], vh[j]);
-    local_dfts<N2, N3>(x, tw, +1);
     if (live) {
 #pragma unroll
       for (int j = 0; j < L; j++) scr[(j * EPB + eloc) * N1 + (slot ^ sw)] = x[j];
@@ -698,6 +846,16 @@ __global__ void __launch_bounds__(256, 2) kconv_herm_kernel(const __grid_constan
       for (int u = 0; u < N1; u++) v[u] = scr[(j * EPB + eloc) * N1 + (u ^ sw)];
       x[j] = dft_one<N1>(v, live ? slot : 0, +1, tw);
     }
+    uint32_t lo[X ? L : 1];   // X: the fp16 remainders (re, im) of this lane's values of M
+    if constexpr (X) {
+#pragma unroll
+      for (int j = 0; j < L; j++) {
+        const float hx = __fadd_rn(x[j].x, xl[j].x), hy = __fadd_rn(x[j].y, xl[j].y);
+        const float lx = __fadd_rn(__fsub_rn(x[j].x, hx), xl[j].x), ly = __fadd_rn(__fsub_rn(x[j].y, hy), xl[j].y);
+        x[j] = make_float2(hx, hy);
+        lo[j] = (uint32_t)mlo_scale(hx, lx) | ((uint32_t)mlo_scale(hy, ly) << 16);
+      }
+    }
     const int P = 8 * pb + warp, Q = EPW * qb + el;
     const bool valid = live && P < np && Q < np;
     const bool direct = valid && Q >= P, mirror = valid && Q > P;   // mirror: its conjugate at (Q, P)
@@ -705,6 +863,10 @@ __global__ void __launch_bounds__(256, 2) kconv_herm_kernel(const __grid_constan
       const long off = (long)slot * L * npq + (long)P * np + Q;
 #pragma unroll
       for (int j = 0; j < L; j++) __stcs(M + off + (long)j * npq, x[j]);
+      if constexpr (X) {
+#pragma unroll
+        for (int j = 0; j < L; j++) __stcs(Mlo + off + (long)j * npq, lo[j]);
+      }
     }
     // keys: the row's (Q >= P) reduced over the warp's lanes of each slot, the
     // column's (Q > P) over the warps through shared memory
@@ -747,6 +909,26 @@ __global__ void __launch_bounds__(256, 2) kconv_herm_kernel(const __grid_constan
       if (mQ > mP && mQ < np) {
         const float2 v = scr[(k * EPW + c) * 8 + (r ^ tsw(k, c))];
         __stcs(M + ((long)k * np + mQ) * np + mP, make_float2(v.x, -v.y));
+      }
+    }
+    if constexpr (X) {
+      // the remainders' mirror image, the same way (conjugate: the imaginary
+      // part's sign bit flips)
+      uint32_t* scr32 = reinterpret_cast<uint32_t*>(scr);
+      __syncthreads();
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < L; j++) {
+          const int k = slot * L + j;
+          scr32[(k * EPW + el) * 8 + (warp ^ tsw(k, el))] = lo[j];
+        }
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < NK * EPW * 8; idx += blockDim.x) {
+        const int r = idx & 7, c = (idx >> 3) % EPW, k = idx / (8 * EPW);
+        const int mP = 8 * pb + r, mQ = EPW * qb + c;
+        if (mQ > mP && mQ < np)
+          __stcs(Mlo + ((long)k * np + mQ) * np + mP, scr32[(k * EPW + c) * 8 + (r ^ tsw(k, c))] ^ 0x80000000u);
       }
     }
     for (int idx = threadIdx.x; idx < N1 * EPW * LP; idx += blockDim.x) {
@@ -946,9 +1128,9 @@ cudaError_t kconv_pipe_launch(const float2* D, const float2* Vh, float2* M, int 
   return cudaGetLastError();
 }
 
-template <int N1, int N2, int N3>
+template <int N1, int N2, int N3, bool X>
 cudaError_t kconv_herm_launch(const float2* D, const float2* Vh, float2* M, int np, uint32_t* keys, int* e,
-                              int* err, cudaEvent_t conv_done, cudaStream_t s) {
+                              int* err, cudaEvent_t conv_done, cudaStream_t s, uint32_t* Mlo) {
   constexpr int L = N2 * N3, NK = N1 * L, EPW = 32 / N1, EPB = EPW * 8, LP = (L + 1) / 2, KWR = N1 * LP;
   constexpr uint32_t BOX = NK * EPB * sizeof(float2);
   constexpr uint32_t SMEM = 3 * BOX + 8 * 32 * LP * 4 + 16;   // + mbarrier and the next tile's (pb, qb)
@@ -970,14 +1152,14 @@ cudaError_t kconv_herm_launch(const float2* D, const float2* Vh, float2* M, int 
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
   }
-  r = cudaFuncSetAttribute(kconv_herm_kernel<N1, N2, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+  r = cudaFuncSetAttribute(kconv_herm_kernel<N1, N2, N3, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
   if (r != cudaSuccess) return r;
   uint32_t* rowk = keys;
   uint32_t* colk = keys + (long)nqb * np * KWR;
   const int* tcum = reinterpret_cast<const int*>(colk + (long)npb * np * KWR);
   const unsigned grid = (unsigned)std::min<long>(ntile, 2L * nsm);
-  kconv_herm_kernel<N1, N2, N3><<<grid, 256, SMEM, s>>>(mapD, mapV, M, np, ntile, make_twiddles(N1, N2, N3), rowk,
-                                                      colk, tcum, err);
+  kconv_herm_kernel<N1, N2, N3, X><<<grid, 256, SMEM, s>>>(mapD, mapV, M, np, ntile, make_twiddles(N1, N2, N3),
+                                                         rowk, colk, tcum, err, Mlo);
   r = cudaGetLastError();
   if (r == cudaSuccess && conv_done) r = cudaEventRecord(conv_done, s);
   if (r != cudaSuccess) return r;
@@ -1004,14 +1186,18 @@ cudaError_t kconv_herm_prepare(uint32_t* keys, int np, int n1, int n2, int n3, c
 
 cudaError_t kconv_c_herm(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
                          uint32_t* keys, int* e, int* err, cudaEvent_t started, cudaEvent_t conv_done,
-                         cudaStream_t s) {
+                         cudaStream_t s, uint32_t* Mlo) {
   if (kconv_herm_key_words(np, n1, n2, n3) == 0 || !keys || !err || ((uintptr_t)D & 15) || ((uintptr_t)Vh & 15))
     return cudaErrorInvalidValue;
+  if (Mlo && n1 == 3) return cudaErrorInvalidValue;   // the extended form needs a radix-2/4 mesh
   cudaError_t r = started ? cudaEventRecord(started, s) : cudaSuccess;
   if (r != cudaSuccess) return r;
-  if (n1 == 4) return kconv_herm_launch<4, 4, 4>(D, Vh, M, np, keys, e, err, conv_done, s);
-  if (n1 == 3) return kconv_herm_launch<3, 3, 3>(D, Vh, M, np, keys, e, err, conv_done, s);
-  return kconv_herm_launch<2, 2, 2>(D, Vh, M, np, keys, e, err, conv_done, s);
+  if (n1 == 4)
+    return Mlo ? kconv_herm_launch<4, 4, 4, true>(D, Vh, M, np, keys, e, err, conv_done, s, Mlo)
+               : kconv_herm_launch<4, 4, 4, false>(D, Vh, M, np, keys, e, err, conv_done, s, nullptr);
+  if (n1 == 3) return kconv_herm_launch<3, 3, 3, false>(D, Vh, M, np, keys, e, err, conv_done, s, nullptr);
+  return Mlo ? kconv_herm_launch<2, 2, 2, true>(D, Vh, M, np, keys, e, err, conv_done, s, Mlo)
+             : kconv_herm_launch<2, 2, 2, false>(D, Vh, M, np, keys, e, err, conv_done, s, nullptr);
 }
 
 // Shared memory of kconv_tile_kernel for N_k k-planes: two boxes, the row
@@ -1088,6 +1274,11 @@ cudaError_t kconv_c_rowexp(const float2* D, const float2* Vh, float2* M, int np,
   r = cudaGetLastError();
   *done = r == cudaSuccess;
   return r;
+}
+
+cudaError_t mlo_combine_c2z(const float2* M, const uint32_t* Mlo, double2* out, long n, cudaStream_t s) {
+  mlo_combine_kernel<<<(unsigned)std::min<long>((n + 255) / 256, 152L * 16), 256, 0, s>>>(M, Mlo, out, n);
+  return cudaGetLastError();
 }
 
 cudaError_t kconv_z(const double2* D, const double2* Vh, double2* M, long npq, int n1, int n2,

@@ -29,6 +29,20 @@ __device__ __forceinline__ void slice3_planes(float y, float* p) {
   p[2] = s2 * 256.0f;
 }
 
+// The same for y + l with |l| far below the leading slice's unit: the
+// leading slice is rint(y), and l joins the first remainder before it is
+// rounded to the second and third slices.
+__device__ __forceinline__ void slice3_planes_x(float y, float l, float* p) {
+  const float s0 = __fsub_rn(__fadd_rn(y, 0x1.8p23f), 0x1.8p23f);
+  float r = __fadd_rn(__fsub_rn(y, s0), l);
+  const float s1 = __fsub_rn(__fadd_rn(r, 0x1.8p12f), 0x1.8p12f);
+  r = __fsub_rn(r, s1);
+  const float s2 = __fsub_rn(__fadd_rn(r, 0x1.8p1f), 0x1.8p1f);
+  p[0] = s0 * 256.0f;
+  p[1] = s1 * 256.0f;
+  p[2] = s2 * 256.0f;
+}
+
 // The fp16 bits of the three planes of x with row exponent e.  The scale
 // 2^(7 - e) is an exact power of two built from its exponent bits.
 __device__ __forceinline__ void slice3(float x, int e, uint16_t* s) {

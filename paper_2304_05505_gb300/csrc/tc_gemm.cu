@@ -33,6 +33,9 @@
 //   CV = 1  A stored [rows][K] (row-major complex): 128 x 32-float boxes, 128B swizzle
 //   CV = 2  A stored [K][rows] (A is the transpose of the stored matrix, as
 //           X^T in S1): 16 x 256-float boxes, the converters transpose
+//   CV = 3  as CV = 1, plus an fp16 tile of A's remainders (A = hi + lo with
+//           hi the FP32 matrix; the extended M of S4a), 64B swizzle; the
+//           converters add lo to the first remainder before slicing
 //
 // Work units: a 128 x 128 output tile and a chunk of at most 1024 real K (so
 // the leading sum of a unit is exact), the chunks of one product of equal
@@ -213,6 +216,24 @@ __device__ __forceinline__ void slice8_f16(const float* x, float sc, uint32_t w[
   }
 }
 
+// The same for values given as an FP32 part x and a small remainder lo
+// (already scaled by the row's scale): the leading slice comes from x alone,
+// the remainder joins the first remainder (exact up to an FP32 rounding far
+// below the last slice).
+__device__ __forceinline__ void slice8_f16x(const float* x, const float* lo, float sc, uint32_t w[NPL][4]) {
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    float p0[NPL], p1[NPL];
+    slice3_planes_x(x[j] * sc, lo[j], p0);
+    slice3_planes_x(x[j + 1] * sc, lo[j + 1], p1);
+#pragma unroll
+    for (int p = 0; p < NPL; p++) {
+      const __half2 h = __floats2half2_rn(p0[p], p1[p]);
+      w[p][j >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+  }
+}
+
 // OUT: 0 = FP32 result, 1 = FP64 result, 2 = partial sums (split K)
 // NP: 6 or 8 slice products per real product (see the header).
 // AR (A resident, short K in one chunk): the A tile of all K (4 blocks x 3
@@ -220,8 +241,8 @@ __device__ __forceinline__ void slice8_f16(const float* x, float sc, uint32_t w[
 // (batch, M tile) one after another; only B streams through a 4-stage ring of
 // 24 KB.  Each CTA takes a contiguous range of units so that consecutive units
 // share their A tile.
-// CV (A converted in shared memory, 1 or 2): A is an FP32 (interleaved
-// complex) matrix.  TMA brings 16 KB FP32 tiles into a 3-stage staging ring;
+// CV (A converted in shared memory, 1, 2 or 3): A is an FP32 (interleaved
+// complex) matrix; CV = 3 adds its fp16 remainders (map a[1], 64B swizzle).  TMA brings 16 KB FP32 tiles into a 3-stage staging ring;
 // converter warps cut each tile into the three fp16 slices with the rows'
 // exponents and write them in the 64B-swizzled K-major layout the MMA reads,
 // then fence the generic-proxy writes for the async proxy and arrive on the
@@ -243,8 +264,10 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
   // well ahead of the MMAs: FP32 A tiles (SA_STAGES x 16 KB, from DRAM), B
   // planes (B_STAGES x 24 KB, TMA only) and the converted A planes (STAGES x
   // 24 KB, written by the converter warps).
-  constexpr int SA_STAGES = 4, B_STAGES = 4;
-  constexpr uint32_t SA_BYTES = BM * BKR * 4;                      // 16 KB
+  // CV = 3: each FP32 stage also holds the fp16 tile of the remainders (8 KB)
+  constexpr int SA_STAGES = CV == 3 ? 3 : 4, B_STAGES = CV == 3 ? 3 : 4;
+  constexpr uint32_t SA_HI = BM * BKR * 4;                         // 16 KB: FP32 tile
+  constexpr uint32_t SA_BYTES = CV == 3 ? SA_HI + BM * BKR * 2 : SA_HI;
   constexpr uint32_t PL_BYTES = NPL * TILE_BYTES;                  // 24 KB: three planes of one operand
   constexpr uint32_t B_OFF = SA_STAGES * SA_BYTES + 2 * PL_BYTES;  // CV: the B ring after the A plane ring
   // what precedes the plane ring: the resident A tile, or the FP32 staging ring
@@ -383,10 +406,12 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
             const int sa = it % SA_STAGES;
             if (!mbar_wait(SEMPTY(sa), ((it / SA_STAGES) & 1) ^ 1, err, 2)) { ok = false; break; }
             mbar_expect_tx(SFULL(sa), SA_BYTES);
-            if constexpr (CV == 1)
+            if constexpr (CV == 1 || CV == 3)
               tma_load_3d(sbase + sa * SA_BYTES, &maps.a[0], SFULL(sa), kb * BKR, mi * BM, b);
             else   // [K][rows] source: 16 complex K values (rows of the box) x 128 complex rows
               tma_load_3d(sbase + sa * SA_BYTES, &maps.a[0], SFULL(sa), mi * 2 * BM, kb * (BKR / 2), b);
+            if constexpr (CV == 3)   // the remainders' fp16 tile beside it
+              tma_load_3d(sbase + sa * SA_BYTES + SA_HI, &maps.a[1], SFULL(sa), kb * BKR, mi * BM, b);
             nsa++;
             const int sb = it % B_STAGES;
             if (!mbar_wait(BEMPTY(sb), ((it / B_STAGES) & 1) ^ 1, err, 2)) { ok = false; break; }
@@ -511,7 +536,8 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
       decode(u, b, mi, ni, kc);
       const int row = mi * BM + r;
       // 2^(7 - e): the row's scale, exact
-      const float sc = pow2f(7 - (row < g.M ? row_exp(eA, (long)b * seA + row) : 0));
+      const int erow = row < g.M ? row_exp(eA, (long)b * seA + row) : 0;
+      const float sc = pow2f(7 - erow);
       const int kb1 = min(g.nkb, (kc + 1) * g.ckb);
       for (int kb = kc * g.ckb; kb < kb1; kb++, it++) {
         const int sa = it % SA_STAGES, st = it % STAGES;
@@ -523,7 +549,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
         for (int k2 = 0; k2 < 2; k2++) {
           const int pc = 2 * hf + k2;               // 8 reals = one 16-byte chunk of each plane
           float x[8];
-          if constexpr (CV == 1) {
+          if constexpr (CV == 1 || CV == 3) {
             // FP32 row r, 128B swizzle: 16-byte chunk c at r * 128 + 16 (c ^ (r & 7))
             const float4 f0 = *reinterpret_cast<const float4*>(src + r * 128 + 16 * ((2 * pc) ^ (r & 7)));
             const float4 f1 = *reinterpret_cast<const float4*>(src + r * 128 + 16 * ((2 * pc + 1) ^ (r & 7)));
@@ -539,7 +565,23 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
             }
           }
           uint32_t wd[NPL][4];
-          slice8_f16(x, sc, wd);
+          if constexpr (CV == 3) {
+            // the remainders of these 8 values, fp16 multiples of each value's
+            // unit in the last place (64B-swizzled row r of the fp16 tile)
+            const uint4 q = *reinterpret_cast<const uint4*>(src + SA_HI + r * 64 + 16 * (pc ^ ((r >> 1) & 3)));
+            const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
+            float lo[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+              const uint16_t h16 = (uint16_t)(qw[j >> 1] >> (16 * (j & 1)));
+              const int eh = (int)((__float_as_uint(x[j]) >> 23) & 0xffu);
+              // q 2^(eh - 150) (the unit in the last place of x[j]) times the row's scale
+              lo[j] = eh >= 24 ? __half2float(__ushort_as_half(h16)) * pow2f(eh - 150 + 7 - erow) : 0.f;
+            }
+            slice8_f16x(x, lo, sc, wd);
+          } else {
+            slice8_f16(x, sc, wd);
+          }
           // plane row r, 64B swizzle: chunk pc at r * 64 + 16 (pc ^ ((r >> 1) & 3))
           const uint32_t off = r * 64 + 16 * (pc ^ ((r >> 1) & 3));
 #pragma unroll
@@ -886,7 +928,7 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
                     cudaEvent_t gemm_done, int products, int a_conv, int herm) {
   if (products != 6 && products != 8) return cudaErrorInvalidValue;
-  if (a_conv < 0 || a_conv > 2) return cudaErrorInvalidValue;
+  if (a_conv < 0 || a_conv > 3) return cudaErrorInvalidValue;
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   Maps maps;
   for (int p = 0; p < NPL; p++) {
@@ -938,6 +980,8 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
     if (products == 6) BY_OUT(6, false, 1) else BY_OUT(8, false, 1)
   } else if (a_conv == 2) {
     if (products == 6) BY_OUT(6, false, 2) else BY_OUT(8, false, 2)
+  } else if (a_conv == 3) {
+    if (products == 6) BY_OUT(6, false, 3) else BY_OUT(8, false, 3)
   } else if (ar) {
     if (out_f64) LAUNCH(1, 6, true, 0) else LAUNCH(0, 6, true, 0)
   } else {

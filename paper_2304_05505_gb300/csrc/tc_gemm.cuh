@@ -28,7 +28,10 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
 // A is three planes; 1 = A.map[0] is an FP32 map (make_f32_map) of the
 // interleaved complex A [rows][K], cut into its slices inside the kernel with
 // the row exponents eA; 2 = A.map[0] is an FP32 map (make_f32_map_t) of the
-// stored transpose [K][rows] of A.  herm (1 or 2): the product is Hermitian
+// stored transpose [K][rows] of A; 3 = as 1, and A.map[1] an fp16 plane map
+// (make_plane_map) of A's remainders below its FP32 values, each an fp16
+// multiple q of its value's unit in the last place (q 2^(e - 24) for a value
+// m 2^e, 1/2 <= m < 1), sliced with them.  herm (1 or 2): the product is Hermitian
 // (B built from conj(A), Nr = 2 M, one K chunk, FP32 output): only the tiles
 // that reach the diagonal are computed, and each writes its values on or
 // above the diagonal, and with herm = 1 also their conjugates at the mirrored

@@ -34,6 +34,17 @@ thread_local int g_fail_alloc = -1;   // test hook: index of the next thc_create
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// The tensor-core forms: THC_MIXED and THC_MIXED_EXT.
+bool tc_form(int precision) { return precision == THC_MIXED || precision == THC_MIXED_EXT; }
+
+// THC_MIXED_EXT's extended k-convolution applies (its remainders of M are
+// kept): a 2^3 or 4^3 mesh, the Hermitian form's keys, N_P a multiple of 4
+// (16-byte strided fp16 rows of the remainders).
+bool ext_form(const thc_dims* d, int precision) {
+  return precision == THC_MIXED_EXT && d->n1 == d->n2 && d->n2 == d->n3 && (d->n1 == 2 || d->n1 == 4) &&
+         d->nisdf % 4 == 0 && kconv_herm_key_words(d->nisdf, d->n1, d->n2, d->n3) > 0;
+}
+
 struct Sizes {
   long nk, x, v, psi, kc;
   size_t el;  // bytes of a workspace complex element
@@ -45,6 +56,7 @@ struct Sizes {
   long nexp;  // exponents: eXn + eXT + ePsi + eC + eY + eM
   long npart; // split-K partial elements (max over the tensor-core GEMMs)
   long hkey;  // key words of the Hermitian convolution (0 where it does not apply)
+  long mlo;   // fp16 remainder pairs of M (THC_MIXED_EXT where its convolution applies)
 };
 
 int pad8(int x) { return (x + 7) & ~7; }
@@ -72,7 +84,8 @@ Sizes sizes_of(const thc_dims* d, int precision) {
                       tc_partial_elems(d->nisdf, 2 * d->nisdf, 2 * d->nocc, (int)s.nk),
                       tc_partial_elems(d->nisdf, 2 * d->nocc, 2 * d->nisdf, (int)s.nk),
                       tc_partial_elems(d->nbas, 2 * d->nocc, 2 * d->nisdf, (int)s.nk)});
-  s.hkey = precision == THC_MIXED ? kconv_herm_key_words(d->nisdf, d->n1, d->n2, d->n3) : 0;
+  s.hkey = tc_form(precision) ? kconv_herm_key_words(d->nisdf, d->n1, d->n2, d->n3) : 0;
+  s.mlo = ext_form(d, precision) ? s.v : 0;
   return s;
 }
 
@@ -83,7 +96,7 @@ thc_status check_dims(const thc_dims* d, int precision) {
   if (d->n1 < 1 || d->n2 < 1 || d->n3 < 1 || d->n1 > 8 || d->n2 > 8 || d->n3 > 8) return THC_ERR_ARG;
   if (d->nbas < 1 || d->nocc < 1 || d->nisdf < 1) return THC_ERR_ARG;
   if (d->nocc > d->nbas) return THC_ERR_ARG;
-  if (precision != THC_FP64 && precision != THC_MIXED && precision != THC_MIXED_SIMT) return THC_ERR_ARG;
+  if (precision != THC_FP64 && !tc_form(precision) && precision != THC_MIXED_SIMT) return THC_ERR_ARG;
   // element counts must fit the kernels' index arithmetic
   const double v = (double)d->n1 * d->n2 * d->n3 * d->nisdf * (double)d->nisdf;
   if (v > 4.0e10) return THC_ERR_UNSUPPORTED;
@@ -97,7 +110,8 @@ size_t memory_bytes(const thc_dims* d, int precision) {
   b += s.v * s.el;               // prepared kernel
   b += 2 * s.psi * s.el;         // Psi, Y
   b += 2 * s.v * s.el;           // D, M
-  if (precision == THC_MIXED) {
+  if (tc_form(precision)) {
+    b += sizeof(uint32_t) * s.mlo;                                           // remainders of M (THC_MIXED_EXT)
     b += s.x32 * sizeof(float2);                                             // X in FP32
     b += 3 * 2 * (s.plPs + s.plBc + s.plBd + s.plBy + s.plM);               // fp16 slices
     b += sizeof(int) * s.nexp + 64;                                         // exponents, error word
@@ -116,7 +130,7 @@ void free_all(thc_ctx* c) {
                   c->Cdev, c->KCdev, c->exdev, c->partial, c->flag,
                   c->PsiA_pl, c->Bc_pl, c->Bd_pl, c->By_pl, c->ex_pl, c->tc_err, c->part_s0,
                   c->part_bc, c->M_pl, c->hkeys, c->Zao, c->Wao, c->BxT_pl, c->Bz_pl, c->eZ, c->ps0_ao,
-                  c->pbc_ao};
+                  c->pbc_ao, c->Mlo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 7; i++)
@@ -195,6 +209,7 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
   } else {
     W((void**)&c->Vh32, s.v * s.el);
     W(&c->M, s.v * s.el);
+    if (s.mlo) W((void**)&c->Mlo, sizeof(uint32_t) * s.mlo);
     W((void**)&c->X32, s.x32 * sizeof(float2));
     if (s.plM) W((void**)&c->M_pl, 3 * 2 * s.plM);
     W((void**)&c->PsiA_pl, 3 * 2 * s.plPs);
@@ -233,7 +248,7 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
       return e == cudaErrorMemoryAllocation ? THC_ERR_OOM : THC_ERR_CUDA;
     }
   }
-  if (precision == THC_MIXED) {
+  if (tc_form(precision)) {
     c->ldX = s.ldX; c->ldC = s.ldC; c->ldM = s.ldM; c->ldPs = s.ldPs;
     c->plPs = s.plPs;
     c->plBc = s.plBc; c->plBd = s.plBd; c->plBy = s.plBy; c->plM = s.plM;
@@ -269,6 +284,7 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
         e = make_plane_map(c->opM.map[p], c->M_pl + p * s.plM, nk, P, 2 * P, s.ldM);
     else
       e = make_f32_map(c->opMf.map[0], c->M, nk, P, 2 * P, 2 * P);
+    if (e == cudaSuccess && c->Mlo) e = make_plane_map(c->opMf.map[1], c->Mlo, nk, P, 2 * P, 2 * P);
     if (e == cudaSuccess && c->hkeys) {
       e = kconv_herm_prepare(c->hkeys, P, d->n1, d->n2, d->n3, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -462,10 +478,14 @@ static thc_status build_mixed(thc_ctx* c, const double2* C, double2* KC, double*
 // Slice products of the tensor-core GEMMs S1, S2, S4a and S4b (6 or 8, see
 // tc_gemm.cu).  Measured at 4x4x4 k, N_P = 1200 against the FP64 oracle: the
 // back-projections S4a and S4b, whose outputs carry the final precision, take
-// 8; S1 (rounded to FP32 Psi) and S2 (FP32 D) take 6.
+// 8; S1 (rounded to FP32 Psi) and S2 (FP32 D) take 6.  THC_MIXED_EXT takes 8
+// in S1 as well: with M carried to about 35 bits, the slices of Psi are the
+// next limit on a fitted kernel.
 constexpr int kProducts[4] = {6, 6, 8, 8};
+constexpr int kProductsExt[4] = {8, 6, 8, 8};
 
 static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex, double2* Kao = nullptr) {
+  const int* kProducts = c->precision == THC_MIXED_EXT ? kProductsExt : ::kProducts;
   const int nk = c->nk, N = c->nbas, n = c->nocc, P = c->nisdf;
   const long PP = (long)P * P, Pn = (long)P * n, Nn = (long)N * n;
   float2* Psi = (float2*)c->Psi;
@@ -497,6 +517,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, tc_gemm(c->opPs, c->opBd, P, 2 * P, 2 * n, nk, c->ePsi, P, c->ePsi, P, D, false, 2 * P, 2 * PP,
                  c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 1, 1), kProducts[1], 0, upper ? 2 : 1));
   c->d_upper = upper;
+  c->m_ext = herm && c->Mlo;
   CKC(c, mark(c, 2, s, false));
   // S3  M = IDFT(DFT(D) o Vh) in FP32
   // (2^3, 3^3 and 4^3 meshes: the convolution also finds the exact row
@@ -504,7 +525,7 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   bool have_eM = false;
   if (herm) {
     CKC(c, kconv_c_herm(D, c->Vh32, M, P, c->n1, c->n2, c->n3, c->hkeys, c->eM, c->tc_err, core_event(c, 2, 0),
-                        core_event(c, 2, 1), s));
+                        core_event(c, 2, 1), s, c->Mlo));
     have_eM = true;
   } else if (a_f32) {
     CKC(c, kconv_c_rowexp(D, c->Vh32, M, P, c->n1, c->n2, c->n3, c->eM, &have_eM, c->tc_err,
@@ -530,7 +551,8 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
     }
     CKC(c, record_core(c, 3, 0, s));
     CKC(c, tc_gemm(a_f32 ? c->opMf : c->opM, c->opBxT, P, 2 * N, 2 * P, nk, c->eM, P, c->eXn, N, c->Zao, false,
-                   2 * N, 2L * P * N, c->ps0_ao, c->pbc_ao, c->tc_err, s, core_event(c, 3, 1), 8, a_f32 ? 1 : 0));
+                   2 * N, 2L * P * N, c->ps0_ao, c->pbc_ao, c->tc_err, s, core_event(c, 3, 1), 8,
+                   !a_f32 ? 0 : (herm && c->Mlo) ? 3 : 1));
     CKC(c, mark(c, 4, s, false));
     CKC(c, col_exponents_c(c->Zao, (long)P * N, N, nk, P, N, c->eZ, s));
     CKC(c, embed_b(c->Zao, false, (long)P * N, N, 1, false, true, nk, P, N, c->eZ, c->Bz_pl, c->plAO, c->ldAO, s));
@@ -556,8 +578,10 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, col_exponents_c(Psi, Pn, n, nk, P, n, c->eY, s));
   CKC(c, embed_b(Psi, false, Pn, n, 1, false, false, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
   CKC(c, record_core(c, 3, 0, s));
+  // (THC_MIXED_EXT with the Hermitian form: M's fp16 remainders join its FP32 values)
+  const int m_conv = !a_f32 ? 0 : (herm && c->Mlo) ? 3 : 1;
   CKC(c, tc_gemm(a_f32 ? c->opMf : c->opM, c->opBy, P, 2 * n, 2 * P, nk, c->eM, P, c->eY, n, Y, false, 2 * n,
-                 2 * Pn, c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 3, 1), kProducts[2], a_f32 ? 1 : 0));
+                 2 * Pn, c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 3, 1), kProducts[2], m_conv));
   CKC(c, mark(c, 4, s, false));
   // S4b KC = conj(X) Y on tensor cores: A = X (FP32, sliced inside the GEMM),
   // B = embedded Y (conj-A form)
@@ -630,7 +654,7 @@ static thc_status ao_prepare(thc_ctx* c) {
       return e == cudaErrorMemoryAllocation ? THC_ERR_OOM : THC_ERR_CUDA;
     }
   }
-  if (c->precision == THC_MIXED) {
+  if (tc_form(c->precision)) {
     cudaError_t e = cudaSuccess;
     for (int p = 0; p < 3 && e == cudaSuccess; p++) {
       e = make_plane_map(c->opBxT.map[p], c->BxT_pl + p * c->plAO, nk, 2 * N, 2 * P, c->ldAO);
@@ -713,7 +737,7 @@ __global__ void ints_to_doubles(const int* __restrict__ v, double* __restrict__ 
 
 thc_status thc_get_intermediate(thc_ctx* c, int which, double* out) {
   if (!c || !out || !aligned16(out) || which < 0 || which > 4) return THC_ERR_ARG;
-  if (which == 4 && c->precision != THC_MIXED) return THC_ERR_ARG;
+  if (which == 4 && !tc_form(c->precision)) return THC_ERR_ARG;
   if (!c->built) return THC_ERR_STATE;
   if (which == 4) {
     const long n = (long)c->nk * c->nisdf;
@@ -725,7 +749,9 @@ thc_status thc_get_intermediate(thc_ctx* c, int which, double* out) {
   const long n = (which == 0 || which == 3) ? (long)c->nk * c->nisdf * c->nocc
                                             : (long)c->nk * c->nisdf * c->nisdf;
   void* src = which == 0 ? c->Psi : which == 1 ? c->D : which == 2 ? c->M : c->Y;
-  if (which == 1 && c->precision == THC_MIXED && c->d_upper)
+  if (which == 2 && c->Mlo && c->m_ext)
+    CKC(c, mlo_combine_c2z((const float2*)src, c->Mlo, (double2*)out, n, c->stream));
+  else if (which == 1 && tc_form(c->precision) && c->d_upper)
     CKC(c, hermitian_fill_c2z((const float2*)src, (double2*)out, c->nisdf, c->nk, c->stream));
   else if (c->precision == THC_FP64)
     CKC(c, cudaMemcpyAsync(out, src, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
@@ -796,7 +822,7 @@ thc_status thc_profile_kernels(const thc_ctx* c, float core_ms[6]) {
 thc_status thc_hermitian_kernel(const thc_ctx* c, int* hermitian) {
   if (!c || !hermitian) return THC_ERR_ARG;
   if (!c->have_v) return THC_ERR_STATE;
-  *hermitian = (c->precision == THC_MIXED && c->herm_v && c->hkeys && c->plM == 0) ? 1 : 0;
+  *hermitian = (tc_form(c->precision) && c->herm_v && c->hkeys && c->plM == 0) ? 1 : 0;
   return THC_OK;
 }
 
@@ -809,7 +835,7 @@ thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   // 2^3 .. 4^3 meshes, else a kernel of their own; exponents of Psi, embed,
   // GEMM), S4b 3, E_x 2; S1, S4a and S4b add a combine kernel when split
   // along K.
-  if (c->precision == THC_MIXED) {
+  if (tc_form(c->precision)) {
     const int s1 = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nbas, c->nk) > 0 ? 1 : 0;
     const int s4a = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nisdf, c->nk) > 0 ? 1 : 0;
     const int s4b = tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk) > 0 ? 1 : 0;

@@ -53,6 +53,7 @@ struct thc_ctx {
   float2* X32;      // [nk][nbas][ldX] (THC_MIXED_SIMT: ldX = nisdf; THC_MIXED: nisdf rounded up to
                     // even, so that the FP32 rows are 16-byte strided for TMA)
   float2* Vh32;     // [nk][nisdf][nisdf]
+  uint32_t* Mlo;    // THC_MIXED_EXT: fp16 remainders (re, im) of M below its FP32 values, [nk][nisdf][nisdf]
   int ldX;
   // workspace (element type follows the precision)
   void* Psi;        // [nk][nisdf][nocc]
@@ -106,6 +107,7 @@ struct thc_ctx {
   uint32_t* hkeys;    // row and column keys of the Hermitian convolution (when its form applies)
   bool herm_v;        // every V^q Hermitian (to 1e-12 of max |V|): S2 writes D's upper part, S3 mirrors M
   bool d_upper;       // the last build left D's part below the diagonal unwritten
+  bool m_ext;         // the last build wrote M's remainders (THC_MIXED_EXT, Hermitian form)
   cudaEvent_t ev[7];               // stage boundaries of the last build
   std::vector<cudaEvent_t> prof;   // per profiled build: 7 stage boundaries, then the
                                    // start and end of each stage's main kernel (12)
@@ -163,12 +165,18 @@ cudaError_t kconv_herm_prepare(uint32_t* keys, int np, int n1, int n2, int n3, c
 // tiles of D and Vh that reach the diagonal only (D's part below it is never
 // read), writes all of M, and the row exponents e of M as kconv_c_rowexp.
 // keys: kconv_herm_key_words words of scratch.
+// Mlo (may be null; radix-2/4 meshes only): the extended form, which also
+// writes the fp16 remainders of M below its FP32 values ([N_k][np][np] pairs
+// (re, im), each a multiple of its value's unit in the last place: the
+// remainder is q * 2^(e - 24) for a value m 2^e, 1/2 <= m < 1, q the fp16).
 cudaError_t kconv_c_herm(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
                          uint32_t* keys, int* e, int* err, cudaEvent_t started, cudaEvent_t conv_done,
-                         cudaStream_t s);
+                         cudaStream_t s, uint32_t* Mlo = nullptr);
 cudaError_t kconv_c_rowexp(const float2* D, const float2* Vh, float2* M, int np, int n1, int n2, int n3,
                            int* e, bool* done, int* err, cudaEvent_t started, cudaEvent_t conv_done,
                            cudaStream_t s);
+// out = M plus its fp16 remainders (kconv_c_herm's Mlo), complex128.
+cudaError_t mlo_combine_c2z(const float2* M, const uint32_t* Mlo, double2* out, long n, cudaStream_t s);
 // Vh[a] = (1/N_k) sum_q V[q] w^{+a.q} in FP64; writes FP64 or FP32 output.
 cudaError_t prepare_kernel_z(const double2* V, double2* Vh64, float2* Vh32, long npq, int n1,
                              int n2, int n3, cudaStream_t s);

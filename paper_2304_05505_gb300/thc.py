@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(PKG, "libthc.so")
 THC_FP64 = 0
 THC_MIXED = 1
 THC_MIXED_SIMT = 2
-PRECISIONS = {"fp64": THC_FP64, "mixed": THC_MIXED, "mixed_simt": THC_MIXED_SIMT}
+THC_MIXED_EXT = 3
+PRECISIONS = {"fp64": THC_FP64, "mixed": THC_MIXED, "mixed_simt": THC_MIXED_SIMT, "mixed_ext": THC_MIXED_EXT}
 
 STATUS = {0: "THC_OK", 1: "THC_ERR_ARG", 2: "THC_ERR_OOM", 3: "THC_ERR_CUDA",
           4: "THC_ERR_NONFINITE", 5: "THC_ERR_TIMEOUT", 6: "THC_ERR_STATE",

@@ -111,3 +111,14 @@ def test_null_context_calls(lib):
     assert lib.thc_build(None, None, None, None) == 1
     assert lib.thc_destroy(None) == 1
     assert lib.thc_set_kernel(None, None) == 1
+
+
+def test_memory_bytes_extended_form():
+    """THC_MIXED_EXT adds one 32-bit remainder pair per element of M on the
+    meshes its extended k-convolution covers (2 x 2 x 2 and 4 x 4 x 4, N_P a
+    multiple of 4); elsewhere it holds what THC_MIXED holds."""
+    d = dict(n1=4, n2=4, n3=4, nbas=432, nocc=60, nisdf=1200)
+    nk, P = 64, 1200
+    assert thc.thc_memory_bytes(d, thc.THC_MIXED_EXT) - thc.thc_memory_bytes(d, thc.THC_MIXED) == 4 * nk * P * P
+    for other in (dict(d, n1=3, n2=3, n3=3), dict(d, n1=4, n2=4, n3=2), dict(d, nisdf=1202)):
+        assert thc.thc_memory_bytes(other, thc.THC_MIXED_EXT) == thc.thc_memory_bytes(other, thc.THC_MIXED)

@@ -10,15 +10,18 @@ the kernel is the one the method feeds the build:
 * V^q is the least-squares fit of those products and its Coulomb kernel
   (thc_rebuild_kernel, Sec. 2.2 and the first three steps of Algorithm 2),
   in FP64 and with the contraction on tensor cores.
-Tolerances.  E_x must meet the target, |dE_x| <= 1e-6 Ha per cell.  KC is held
-to the general mixed-precision bound, max|dKC| <= 1e-6 max|KC|: on this
-kernel the build measures max|dKC| = 3.6e-7 (max|KC| = 0.74), above the
-target's 1e-7.  The loss is in the FP32 k-convolution: the fitted M^k makes
-Y = M Psi cancel (sum |M| |Psi| is about 6 |Y|), so the FP32 rounding of M
-alone gives 1e-7 in KC and the FP32 DFT arithmetic about 3.5e-7, while FP32
-D, Psi and V^q each stay below 2e-8.  The tensor-core kernel must agree with
-the FP64 one (1e-6 of its largest entry; the oracle builds with the two
-within 1e-6 relative in E_x)."""
+Tolerances.  Both mixed forms meet the target in E_x, |dE_x| <= 1e-6 Ha per
+cell (the extended form, THC_MIXED_EXT, within 1e-7), and are held to the
+general mixed-precision bound in KC, max|dKC| <= 1e-6 max|KC| (max|KC| =
+0.74 here).  The target's max|dKC| <= 1e-7 is not met on this kernel: THC_MIXED
+measures 3.6e-7 and THC_MIXED_EXT 1.7e-7.  The fitted M^k makes Y = M Psi
+cancel (sum |M| |Psi| is about 6 |Y|):
+* in THC_MIXED the FP32 k-convolution dominates (the FP32 rounding of M alone
+  gives 1e-7 in KC, the FP32 DFT arithmetic about 3.5e-7);
+* the extended convolution carries M to about 1e-11, and what remains comes
+  from the FP32 Psi, D and Y, each near 5e-8 in KC after the amplification.
+The tensor-core kernel must agree with the FP64 one (1e-6 of its largest
+entry; the oracle builds with the two within 1e-6 relative in E_x)."""
 import time
 
 import numpy as np
@@ -60,31 +63,43 @@ def fitted(cuda_required):
     return cell, X, C, V64.cpu().numpy(), Vtc.cpu().numpy()
 
 
-def test_fitted_kernel_mixed_build_target(fitted):
+@pytest.fixture(scope="module")
+def fitted_ref(fitted):
+    cell, X, C, V64, _ = fitted
+    return O.build(X, C, V64, cell.mesh, route="fft")
+
+
+def _fitted_build(fitted, precision):
     from paper_2304_05505_gb300 import thc
     cell, X, C, V64, _ = fitted
-    ref = O.build(X, C, V64, cell.mesh, route="fft")
     dims = dict(n1=4, n2=4, n3=4, nbas=cell.nbas, nocc=cell.nocc, nisdf=cell.nisdf)
-    eb = thc.ExchangeBuild(dims, "mixed")
+    eb = thc.ExchangeBuild(dims, precision)
     try:
         eb.set_collocation(X)
         eb.set_kernel(V64)
         KC, ex = eb.build(C)
         eb.sync()
-        dkc = float(np.abs(KC.cpu().numpy() - ref["KC"]).max())
-        dex = abs(float(ex[0]) - ref["Ex"])
-        print(f"fitted C2 mixed: max|dKC| = {dkc:.3e}, |dE_x| = {dex:.3e}, E_x = {ref['Ex']:.9f}, "
-              f"Hermitian form {thc.thc_hermitian_kernel(eb.ctx)}")
+        return KC.cpu().numpy(), float(ex[0]), thc.thc_hermitian_kernel(eb.ctx)
     finally:
         eb.close()
-    assert dkc <= 1e-6 * float(np.abs(ref["KC"]).max()), dkc
-    assert dex <= 1e-6, dex
 
 
-def test_tensor_core_rebuild_matches_fp64(fitted):
+@pytest.mark.parametrize("precision", ["mixed_ext", "mixed"])
+def test_fitted_kernel_mixed_build(fitted, fitted_ref, precision):
+    kc, ex, herm = _fitted_build(fitted, precision)
+    dkc = float(np.abs(kc - fitted_ref["KC"]).max())
+    dex = abs(ex - fitted_ref["Ex"])
+    print(f"fitted C2 {precision}: max|dKC| = {dkc:.3e}, |dE_x| = {dex:.3e}, E_x = {fitted_ref['Ex']:.9f}, "
+          f"Hermitian form {herm}")
+    assert herm                          # the fitted kernel is exactly Hermitian per q
+    assert dkc <= 1e-6 * float(np.abs(fitted_ref["KC"]).max()), dkc
+    assert dex <= (1e-7 if precision == "mixed_ext" else 1e-6), dex
+
+
+def test_tensor_core_rebuild_matches_fp64(fitted, fitted_ref):
     cell, X, C, V64, Vtc = fitted
     dv = float(np.abs(Vtc - V64).max()) / float(np.abs(V64).max())
-    a = O.build(X, C, V64, cell.mesh, route="fft")
+    a = fitted_ref
     b = O.build(X, C, Vtc, cell.mesh, route="fft")
     print(f"fitted C2 rebuild: max|dV|/max|V| = {dv:.3e}, dE_x = {abs(a['Ex'] - b['Ex']):.3e}")
     assert dv <= 1e-6, dv

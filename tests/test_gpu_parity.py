@@ -48,7 +48,7 @@ def gpu_build(torch, X, C, V, mesh, precision, keep=False):
         if keep:
             for i, nm in enumerate(["Psi", "D", "M", "Y"]):
                 out[nm] = eb.intermediate(i).cpu().numpy()
-            if precision == "mixed":
+            if precision in ("mixed", "mixed_ext"):
                 out["eM"] = eb.intermediate(4).cpu().numpy()
         return out
     finally:
@@ -86,7 +86,7 @@ RANDOM_CASES = [
 ]
 
 
-PRECISIONS = ["fp64", "mixed", "mixed_simt"]
+PRECISIONS = ["fp64", "mixed", "mixed_simt", "mixed_ext"]
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
@@ -147,7 +147,7 @@ def c2(torch_cuda):
     return p, ref
 
 
-@pytest.mark.parametrize("precision", ["mixed", "mixed_simt"])
+@pytest.mark.parametrize("precision", ["mixed", "mixed_simt", "mixed_ext"])
 def test_benzene_4x4x4_mixed_target(torch_cuda, c2, precision):
     """The target configuration: 4x4x4 k, N_P = 1200, mixed precision,
     every output compared; the launch configuration the bench times."""
@@ -303,3 +303,30 @@ def test_non_hermitian_kernel_parity(torch_cuda, mesh, nisdf):
         # the row exponents of M from either convolution, exact (integers)
         m = np.maximum(np.abs(got["M"].real), np.abs(got["M"].imag)).max(axis=2)
         assert np.array_equal(got["eM"], np.where(m > 0, np.frexp(m)[1], 0).astype(np.float64))
+
+
+@pytest.mark.parametrize("mesh,nisdf", [((4, 4, 4), 64), ((2, 2, 2), 132), ((4, 4, 4), 200)])
+def test_extended_convolution_precision(torch_cuda, mesh, nisdf):
+    """THC_MIXED_EXT on a radix-2/4 mesh with Hermitian V: M (with its fp16
+    remainders) within 1e-9 of its largest entry, against about 1e-7 for the
+    FP32 convolution of THC_MIXED; D is the same FP32 input to both, so the
+    reference is the oracle's convolution of the GPU's own D."""
+    r = cells.random_problem(mesh, nbas=16, nocc=4, nisdf=nisdf, seed=nisdf + 7)
+    # a kernel whose prepared form (1/N_k) sum_q V^q w^{+a.q}, which the mixed
+    # forms hold in complex64, is exactly representable there, so that the
+    # comparison sees the convolution's arithmetic alone (still Hermitian per q)
+    nk = int(np.prod(mesh))
+    sh = tuple(mesh) + r["V"].shape[1:]
+    Vh = np.fft.ifftn(r["V"].reshape(sh), axes=(0, 1, 2)).astype(np.complex64)
+    V = np.fft.fftn(Vh.astype(np.complex128), axes=(0, 1, 2)).reshape(r["V"].shape)
+    V = 0.5 * (V + np.conj(np.transpose(V, (0, 2, 1))))
+    got = {p: gpu_build(torch_cuda, r["X"], r["C"], V, mesh, p, keep=True) for p in ("mixed", "mixed_ext")}
+    assert got["mixed_ext"]["hermitian"]
+    D = got["mixed_ext"]["D"]
+    Mref = O.kconv_fft(D, V, mesh)
+    scale = float(np.abs(Mref).max())
+    dm_ext = float(np.abs(got["mixed_ext"]["M"] - Mref).max()) / scale
+    assert dm_ext <= 1e-9, dm_ext
+    # (the FP32 convolution of the other form, for the record: not asserted)
+    dm = float(np.abs(got["mixed"]["M"] - O.kconv_fft(got["mixed"]["D"], V, mesh)).max()) / scale
+    print(f"{mesh} N_P = {nisdf}: max|dM|/max|M| extended {dm_ext:.2e}, FP32 {dm:.2e}")
