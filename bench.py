@@ -207,15 +207,34 @@ def stage_work(d: dict, hermitian: bool = False) -> dict:
     }
 
 
+def fp64_roofline(d: dict, stages_ms: dict, fp64_tflops: float, pk: dict) -> dict:
+    """The FP64 build against its own peaks: its four GEMMs (full D in S2) run
+    on the FP64 pipe of the CUDA cores, reported against the measured FP64
+    FMA rate; its k-convolution (complex128 D, Vh and M) against the copy
+    bandwidth."""
+    nk = d["n1"] * d["n2"] * d["n3"]
+    N, n, P = d["nbas"], d["nocc"], d["nisdf"]
+    flops = {"S1_collocate": 8.0 * nk * P * n * N, "S2_density": 8.0 * nk * P * P * n,
+             "S4a_apply_M": 8.0 * nk * P * P * n, "S4b_backproject": 8.0 * nk * N * n * P}
+    out = {"fp64_peak_tflops": fp64_tflops, "peak_source": "measured FP64 FMA rate (thc_measure_fp64_rate)"}
+    for st, f in flops.items():
+        a = f / (stages_ms[st] * 1e-3) / 1e12
+        out[st] = {"bound": "fp64", "achieved_tflops": a, "frac": a / fp64_tflops}
+    b = 16.0 * nk * 3 * P * P
+    a = b / (stages_ms["S3_kconv"] * 1e-3) / 1e9
+    out["S3_kconv"] = {"bound": "hbm", "achieved_gbs": a, "frac": a / pk["hbm_gbs"]}
+    return out
+
+
 def kernel_roofline(stage: str, ms: float, work: dict, pk: dict) -> dict:
     """Roofline of one stage's main kernel (or the stage) at `ms` per build.
 
     The bound is whichever lower limit is larger: algorithmic bytes over the
     measured copy bandwidth, or algorithmic flops over the sustained bf16
-    tensor peak (the kernels run inside a multi-millisecond build).  The
-    tensor-core GEMMs issue several bf16 slice products per real product (10
-    for four-slice operands, 6 for S2's three-slice operands), so their
-    issued tensor fraction is also given."""
+    tensor peak (the kernels run inside a multi-millisecond build; fp16 runs
+    at the bf16 rate).  The tensor-core GEMMs issue 6 or 8 fp16 slice
+    products per real product (SLICE_PRODUCTS), so their issued tensor
+    fraction is also given."""
     w = work[stage]
     sec = ms * 1e-3
     t_hbm = w["bytes"] / (pk["hbm_gbs"] * 1e9)
@@ -609,6 +628,7 @@ def run_ours(args, world, rank, local):
     KC_64 = KC.cpu().numpy()
     ex_64 = ex.cpu().numpy().copy()
     e64.close()
+    fp64_rate = thc.thc_measure_fp64_rate(stream.cuda_stream)
 
     rebuild = None
     if args.config == "C2" and not args.no_rebuild:
@@ -649,7 +669,8 @@ def run_ours(args, world, rank, local):
                                                           if "issued_tensor_frac" in v else {})}
                                 for k, v in per_kernel.items()},
             "fp64_gpu": {"value": world / (ms64 * 1e-3), "unit": "builds/s", "ms_per_step": ms64,
-                         "stages_ms": {nm: ms for nm, ms in zip(names, st64)}},
+                         "stages_ms": {nm: ms for nm, ms in zip(names, st64)},
+                         "roofline": fp64_roofline(d, dict(zip(names, st64)), fp64_rate, pk)},
             "Ex_mixed": float(ex_mixed[0]), "Ex_fp64_gpu": float(ex_64[0])}
     if rebuild is not None:
         line["kernel_rebuild"] = rebuild

@@ -199,6 +199,13 @@ thc_status thc_sync(thc_ctx* ctx);
 thc_status thc_debug_set_wait_limit(thc_ctx* ctx, long long cycles);
 thc_status thc_debug_fail_alloc(int nth);
 
+/* The FP64 fused multiply-add rate of the current device, measured: a kernel
+ * of independent FMA chains on every SM, timed with CUDA events on `stream`
+ * (a cudaStream_t) after one warm-up launch.  *tflops_host = FP64 TFLOP/s
+ * (2 flops per FMA).  The FP64 build's stages are reported against it.
+ * Synchronises the stream; changes no device setting. */
+thc_status thc_measure_fp64_rate(void* stream, double* tflops_host);
+
 /* Number of kernel launches one thc_build makes. */
 thc_status thc_launches_per_build(const thc_ctx* ctx, int* launches);
 

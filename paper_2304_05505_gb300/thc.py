@@ -32,7 +32,8 @@ EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_ker
            "thc_profile_begin", "thc_profile_end", "thc_sync", "thc_kconv_noalloc",
            "thc_select_points", "thc_fit_kernel", "thc_profile_kernels", "thc_mlp_features", "thc_mlp_score",
            "thc_mlp_workspace_bytes", "thc_mlp_train_step", "thc_mlp_candidates", "thc_select_points_among",
-           "thc_debug_set_wait_limit", "thc_debug_fail_alloc", "thc_rebuild_kernel", "thc_build_K"]
+           "thc_debug_set_wait_limit", "thc_debug_fail_alloc", "thc_rebuild_kernel", "thc_build_K",
+           "thc_measure_fp64_rate"]
 
 MLP_NPARAM = 8641
 
@@ -79,6 +80,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_sync.argtypes = [vp]
     lib.thc_debug_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.thc_debug_fail_alloc.argtypes = [ip]
+    lib.thc_measure_fp64_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.thc_kconv_noalloc.argtypes = [dp, dp, dp, ip, ip, ip, ctypes.c_long, vp]
     lib.thc_select_points.argtypes = [dp, ip, ip, ip, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), dp, vp]
@@ -244,6 +246,13 @@ def thc_hermitian_kernel(ctx) -> bool:
     n = ctypes.c_int(0)
     _check(load().thc_hermitian_kernel(ctx, ctypes.byref(n)), "thc_hermitian_kernel", ctx)
     return bool(n.value)
+
+
+def thc_measure_fp64_rate(stream=None) -> float:
+    """The device's measured FP64 FMA rate in TFLOP/s (see include/thc.h)."""
+    r = ctypes.c_double(0.0)
+    _check(load().thc_measure_fp64_rate(ctypes.c_void_p(_stream(stream)), ctypes.byref(r)), "thc_measure_fp64_rate")
+    return r.value
 
 
 def thc_launches_per_build(ctx) -> int:

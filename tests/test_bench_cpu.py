@@ -74,3 +74,15 @@ def test_source_hash_covers_the_kernel_files():
         assert len(bench.source_hash(st)) == 16
     assert bench.source_hash("S1_collocate") == bench.source_hash("S4a_apply_M")   # the same GEMM sources
     assert bench.source_hash("S1_collocate") != bench.source_hash("S3_kconv")
+
+
+def test_fp64_roofline_arithmetic():
+    # the FP64 build computes all of D; its GEMMs are reported against the
+    # FP64 rate, its convolution (complex128) against the copy bandwidth
+    pk = dict(hbm_gbs=6000.0)
+    st = {"S1_collocate": 10.0, "S2_density": 40.0, "S3_kconv": 5.0, "S4a_apply_M": 40.0, "S4b_backproject": 10.0}
+    r = bench.fp64_roofline(C2, st, 1.25, pk)
+    nk, N, n, P = 64, 432, 60, 1200
+    assert r["S2_density"]["achieved_tflops"] == pytest.approx(8 * nk * P * P * n / 40e-3 / 1e12)
+    assert r["S1_collocate"]["frac"] == pytest.approx(8 * nk * P * n * N / 10e-3 / 1e12 / 1.25)
+    assert r["S3_kconv"]["achieved_gbs"] == pytest.approx(16 * nk * 3 * P * P / 5e-3 / 1e9)

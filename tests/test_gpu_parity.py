@@ -83,6 +83,7 @@ RANDOM_CASES = [
     ((8, 8, 8), 5, 2, 12),       # the largest mesh: 512 k-points per element in shared memory
     ((6, 6, 6), 12, 3, 40),      # 6-point DFTs; TMA-fed shared-memory convolution, batches across rows
     ((5, 3, 2), 10, 2, 32),      # mixed radices in the shared-memory convolution, one row per batch
+    ((3, 3, 3), 650, 20, 740),   # 162 output tiles in S1, S4a and S4b, ragged M tiles, two K chunks
 ]
 
 
