@@ -7,10 +7,13 @@
 // as the QR decomposition with column pivoting of Sec. 2.1 in exact
 // arithmetic.  A is never formed: each step builds one column from U.
 //
-// Per step j (host loop, two kernels):
+// Per step j (host loop):
 //   argmax  p = argmax_r d[r] (lowest r among equal values), d[p], sum_r d[r]
+//           (block partials, then one block)
 //   column  a = |B(:, p)|^2, l = (a - sum_{t<j} L[t][:] L[t][p]) / sqrt(d[p]),
-//           L[j][:] = l, d = max(d - l^2, 0), d[p] = 0
+//           L[j][:] = l, d = max(d - l^2, 0), d[p] = 0; a block takes 32
+//           candidates (one per lane, coalesced) and its 8 warps split the
+//           sums over f and over t, added in a fixed order
 // The loop stops after npts pivots or when sum d <= rel_tol * trace(A).
 #include "thc_internal.cuh"
 
@@ -103,23 +106,37 @@ __global__ void __launch_bounds__(PT) argmax_final(const double* pv, const int* 
   }
 }
 
-__global__ void column_kernel(const double2* __restrict__ U, int nfunc, int ncand, int j,
-                              const int* __restrict__ sel, const double* __restrict__ selv,
-                              double* __restrict__ L, double* __restrict__ d) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncand) return;
+constexpr int CW = 8;   // warps of a column block
+
+__global__ void __launch_bounds__(32 * CW) column_kernel(const double2* __restrict__ U, int nfunc, int ncand, int j,
+                                                         const int* __restrict__ sel,
+                                                         const double* __restrict__ selv, double* __restrict__ L,
+                                                         double* __restrict__ d) {
+  __shared__ double sr[CW][32], si[CW][32], sl[CW][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
   const int p = sel[0];
-  const double dp = selv[0];
-  double br = 0.0, bi = 0.0;   // B(c, p) = sum_f conj(U[f][c]) U[f][p]
-  for (int f = 0; f < nfunc; f++) {
-    const double2 u = U[(long)f * ncand + c];
-    const double2 w = U[(long)f * ncand + p];
-    br += u.x * w.x + u.y * w.y;
-    bi += u.x * w.y - u.y * w.x;
+  double br = 0.0, bi = 0.0, ll = 0.0;   // B(c, p) = sum_f conj(U[f][c]) U[f][p]; sum_t L[t][c] L[t][p]
+  if (c < ncand) {
+    for (int f = w; f < nfunc; f += CW) {
+      const double2 u = U[(long)f * ncand + c];
+      const double2 v = U[(long)f * ncand + p];
+      br += u.x * v.x + u.y * v.y;
+      bi += u.x * v.y - u.y * v.x;
+    }
+    for (int t = w; t < j; t += CW) ll += L[(long)t * ncand + c] * L[(long)t * ncand + p];
   }
-  double a = br * br + bi * bi;
-  for (int t = 0; t < j; t++) a -= L[(long)t * ncand + c] * L[(long)t * ncand + p];
-  const double l = a / sqrt(dp);
+  sr[w][lane] = br;
+  si[w][lane] = bi;
+  sl[w][lane] = ll;
+  __syncthreads();
+  if (w != 0 || c >= ncand) return;
+  for (int k = 1; k < CW; k++) {
+    br += sr[k][lane];
+    bi += si[k][lane];
+    ll += sl[k][lane];
+  }
+  const double l = (br * br + bi * bi - ll) / sqrt(selv[0]);
   L[(long)j * ncand + c] = l;
   d[c] = (c == p) ? 0.0 : fmax(d[c] - l * l, 0.0);
 }
@@ -166,7 +183,7 @@ extern "C" thc_status thc_select_points(const double* U, int nfunc, int ncand, i
       if (j == 0) tr0 = trace;
       if (!(trace > rel_tol * tr0) || !(host[0] > 0.0)) break;   // rank reached
       points_host[j] = *(int*)(host + 2);
-      column_kernel<<<g, PT, 0, s>>>(u, nfunc, ncand, j, sel, selv, L, d);
+      column_kernel<<<(unsigned)((ncand + 31) / 32), 32 * CW, 0, s>>>(u, nfunc, ncand, j, sel, selv, L, d);
       if ((e = cudaGetLastError()) != cudaSuccess) break;
       count = j + 1;
     }
