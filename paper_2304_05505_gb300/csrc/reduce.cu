@@ -131,6 +131,11 @@ cudaError_t ex_reduce_z(const double2* Psi, const double2* Y, long n, int nk, do
   return cudaGetLastError();
 }
 
+cudaError_t ex_finalize(const double* partial, int npartial, int nk, double* ex, cudaStream_t s) {
+  ex_final<<<1, RT, 0, s>>>(partial, npartial, nk, ex);
+  return cudaGetLastError();
+}
+
 cudaError_t ex_reduce_c(const float2* Psi, const float2* Y, long n, int nk, double* partial,
                         int npartial, double* ex, cudaStream_t s) {
   ex_partial_c<<<npartial, RT, 0, s>>>(Psi, Y, n, partial);

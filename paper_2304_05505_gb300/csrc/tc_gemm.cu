@@ -143,19 +143,27 @@ __device__ __forceinline__ void fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
-// 16 consecutive fp32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 16 consecutive fp32 columns of this thread's TMEM lane, at each of two
+// TMEM addresses, both loads in flight before one wait.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float* va, float* vb) {
+  uint32_t r[32];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-      "%13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      "%13, %14, %15}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%33];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta), "r"(tb)
+      : "memory");
 #pragma unroll
-  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; i++) {
+    va[i] = __uint_as_float(r[i]);
+    vb[i] = __uint_as_float(r[16 + i]);
+  }
 }
 
 // Float offset of 16-byte chunk c (0..3) of row r in a 32 x 16 staging tile;
@@ -623,8 +631,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
 #pragma unroll 1
       for (int qq = 0; qq < EPI_COLS / 16; qq++) {
         float va[16], vb[16];
-        tmem_ld16(accA + EPI_COLS * h + 16 * qq, va);
-        tmem_ld16(accBC + EPI_COLS * h + 16 * qq, vb);
+        tmem_ld16x2(accA + EPI_COLS * h + 16 * qq, accBC + EPI_COLS * h + 16 * qq, va, vb);
         const int col0 = cbase + 16 * qq;             // even: complex pairs stay together
         if (col0 >= g.Nr) continue;                   // the whole block is padding (warp-uniform)
         if constexpr (OUT == 1) {
@@ -747,15 +754,30 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
   }
 }
 
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
 // Adds the K chunks of a split-K product: out = 2^(e_a + e_b - 14) (sum s0 + sum bc).
 // V = 4: four consecutive columns per thread (16-byte partial loads; Nr, ldo
-// and sbo multiples of 4), V = 1 otherwise.
-template <bool OUT_F64, int V>
-__global__ void tc_combine_kernel(const int* __restrict__ ps0, const float* __restrict__ pbc, int nchunk,
-                                  int batch, int M, int Nr, const int* __restrict__ eA, long seA,
-                                  const int* __restrict__ eB, long seB, void* out, long ldo, long sbo) {
+// and sbo multiples of 4), V = 1 otherwise.  DOT (FP32 output, V = 4, out
+// contiguous): also the block's partial sums of sum conj(w) out over its
+// elements for the interleaved complex w laid out as out (the exchange
+// energy's <Psi, Y> when out = Y and w = Psi): each product formed in FP32,
+// a thread's products summed in a float-float pair, then FP64 across the
+// block; dot[2 b], dot[2 b + 1] = real and imaginary part of block b's sum.
+template <bool OUT_F64, int V, bool DOT>
+__global__ void __launch_bounds__(256) tc_combine_kernel(const int* __restrict__ ps0, const float* __restrict__ pbc,
+                                                         int nchunk, int batch, int M, int Nr,
+                                                         const int* __restrict__ eA, long seA,
+                                                         const int* __restrict__ eB, long seB, void* out, long ldo,
+                                                         long sbo, const float* __restrict__ w, double* dot) {
+  static_assert(!DOT || (!OUT_F64 && V == 4), "the dot product of an FP32 result, four columns per thread");
   const long total = (long)batch * M * Nr;
   const long nv = total / V;
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
   for (long iv = (long)blockIdx.x * blockDim.x + threadIdx.x; iv < nv; iv += (long)gridDim.x * blockDim.x) {
     const long i = iv * V;
     const int col = (int)(i % Nr);
@@ -809,6 +831,38 @@ __global__ void tc_combine_kernel(const int* __restrict__ ps0, const float* __re
       }
       if constexpr (V == 4) *reinterpret_cast<float4*>((float*)out + o) = make_float4(x[0], x[1], x[2], x[3]);
       else ((float*)out)[o] = x[0];
+      if constexpr (DOT) {
+        const float4 p = __ldcs(reinterpret_cast<const float4*>(w + o));
+        const float re0 = fmaf(p.x, x[0], p.y * x[1]), im0 = fmaf(p.x, x[1], -p.y * x[0]);
+        const float re1 = fmaf(p.z, x[2], p.w * x[3]), im1 = fmaf(p.z, x[3], -p.w * x[2]);
+        float sv, ev;
+        two_sum_f(rh, re0, sv, ev); rh = sv; rl += ev;
+        two_sum_f(ih, im0, sv, ev); ih = sv; il += ev;
+        two_sum_f(rh, re1, sv, ev); rh = sv; rl += ev;
+        two_sum_f(ih, im1, sv, ev); ih = sv; il += ev;
+      }
+    }
+  }
+  if constexpr (DOT) {
+    __shared__ double sh[2][8];
+    double re = (double)rh + (double)rl, im = (double)ih + (double)il;
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_down_sync(0xffffffffu, re, o);
+      im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sh[0][threadIdx.x >> 5] = re;
+      sh[1][threadIdx.x >> 5] = im;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tr = 0.0, ti = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+        tr += sh[0][i];
+        ti += sh[1][i];
+      }
+      dot[2 * blockIdx.x] = tr;
+      dot[2 * blockIdx.x + 1] = ti;
     }
   }
 }
@@ -926,7 +980,9 @@ long tc_partial_elems(int M, int Nr, int Kr, int batch) {
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
-                    cudaEvent_t gemm_done, int products, int a_conv, int herm) {
+                    cudaEvent_t gemm_done, int products, int a_conv, int herm, const float* dot_with,
+                    double* dot_partial, int dot_max, int* dot_blocks) {
+  if (dot_blocks) *dot_blocks = 0;
   if (products != 6 && products != 8) return cudaErrorInvalidValue;
   if (a_conv < 0 || a_conv > 3) return cudaErrorInvalidValue;
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
@@ -994,13 +1050,22 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   if (e != cudaSuccess || !split) return e;
   const long total = (long)batch * M * Nr;
   const bool v4 = Nr % 4 == 0 && ldo % 4 == 0 && sbo % 4 == 0 && ((uintptr_t)out & 31) == 0;
-  const unsigned cg = (unsigned)std::min<long>((total / (v4 ? 4 : 1) + 255) / 256, 152L * 16);
-#define COMBINE(F64, V) \
-  tc_combine_kernel<F64, V><<<cg, 256, 0, s>>>(ps0, pbc, g.nchunk, batch, M, Nr, eA, seA, eB, seB, out, ldo, sbo)
+  unsigned cg = (unsigned)std::min<long>((total / (v4 ? 4 : 1) + 255) / 256, 152L * 16);
+  // the dot product rides along when the result is a contiguous FP32 array
+  // and w has its layout (16-byte aligned)
+  const bool dot = dot_with && dot_partial && dot_blocks && dot_max > 0 && !out_f64 && v4 && ldo == Nr &&
+                   sbo == (long)M * Nr && ((uintptr_t)dot_with & 15) == 0;
+  if (dot) cg = std::min<unsigned>(cg, (unsigned)dot_max);
+#define COMBINE(F64, V, D)                                                                                 \
+  tc_combine_kernel<F64, V, D><<<cg, 256, 0, s>>>(ps0, pbc, g.nchunk, batch, M, Nr, eA, seA, eB, seB, out, ldo, \
+                                                  sbo, dot_with, dot_partial)
   if (out_f64) {
-    if (v4) COMBINE(true, 4); else COMBINE(true, 1);
+    if (v4) COMBINE(true, 4, false); else COMBINE(true, 1, false);
+  } else if (dot) {
+    COMBINE(false, 4, true);
+    *dot_blocks = (int)cg;
   } else {
-    if (v4) COMBINE(false, 4); else COMBINE(false, 1);
+    if (v4) COMBINE(false, 4, false); else COMBINE(false, 1, false);
   }
 #undef COMBINE
   return cudaGetLastError();

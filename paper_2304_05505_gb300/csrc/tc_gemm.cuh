@@ -36,10 +36,17 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
 // that reach the diagonal are computed, and each writes its values on or
 // above the diagonal, and with herm = 1 also their conjugates at the mirrored
 // positions (herm = 2 leaves the part below the diagonal unwritten).
+// dot_with (optional): when the product is split along K and its FP32 result
+// is contiguous ([batch][M][Nr], ldo = Nr), the combine kernel also writes
+// block partial sums of sum conj(w) out for w = dot_with of the same layout
+// (2 doubles per block, at most dot_max blocks, into dot_partial) and sets
+// *dot_blocks to their count; otherwise *dot_blocks = 0 and nothing is summed.
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
-                    cudaEvent_t gemm_done = nullptr, int products = 8, int a_conv = 0, int herm = 0);
+                    cudaEvent_t gemm_done = nullptr, int products = 8, int a_conv = 0, int herm = 0,
+                    const float* dot_with = nullptr, double* dot_partial = nullptr, int dot_max = 0,
+                    int* dot_blocks = nullptr);
 
 // Map of an FP32 matrix [batch][rows][ld floats] (cols valid) in 32-float K
 // boxes of 128 rows with 128B swizzle (ld * 4 bytes a multiple of 16).
@@ -85,9 +92,11 @@ cudaError_t col_exponents_c(const float2* src, long sbs, int lds, int batch, int
 
 // The three fp16 slices of the contiguous rows src[row][0..np) (rows = batch
 // x rows per batch) with each row's exact exponent, found by the same kernel;
-// writes the exponents to e[row].
+// writes the exponents to e[row].  bplanes (optional, same ldp): also the
+// embedded B operand of src^H that embed_b writes for (src, conj_src,
+// conj_a = 0) with these exponents (rows 2 row, 2 row + 1).
 cudaError_t slice_rows_exact(const float2* src, int np, long rows, int* e, uint16_t* planes, long plane, int ldp,
-                             cudaStream_t s);
+                             cudaStream_t s, uint16_t* bplanes = nullptr, long bplane = 0);
 // Exponents alone of the contiguous rows src[row][0..np): one warp per row,
 // 16-byte loads when np is even.
 cudaError_t row_exponents_rows(const float2* src, int np, long rows, int* e, cudaStream_t s);

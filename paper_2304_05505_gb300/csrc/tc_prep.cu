@@ -128,9 +128,14 @@ __global__ void embed_kernel(const CT* __restrict__ src, long sbs, long ldk, lon
 // accesses per lane, np / V <= 32 R; used for short rows); R = 0: the row is
 // read twice, the second time mostly from cache (long rows: holding a row of
 // 1200 complex values in registers costs more residency than the re-read).
-template <int V, int R, bool PLANES = true>
+// EMB: also the embedded B operand of src^H (embed_b with conj_src, conj_a = 0,
+// the row exponents of src): rows 2 row and 2 row + 1 of bplanes hold the
+// slices of (re, im) and of (-im, re) of each value, the first the same words
+// as the row's own planes.
+template <int V, int R, bool PLANES = true, bool EMB = false>
 __global__ void slice_rowmax_kernel(const float2* __restrict__ src, int np, long rows, int* __restrict__ e,
-                                    uint16_t* planes, long plane, int ldp) {
+                                    uint16_t* planes, long plane, int ldp, uint16_t* bplanes = nullptr,
+                                    long bplane = 0) {
   typedef typename std::conditional<V == 2, float4, float2>::type VT;
   const long w0 = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long nw = ((long)gridDim.x * blockDim.x) >> 5;
@@ -155,14 +160,27 @@ __global__ void slice_rowmax_kernel(const float2* __restrict__ src, int np, long
       slice3(v[j].y, ex, sl[j][1]);
     }
     const long off = row * ldp + 2L * c * V;
+    const long bo = 2 * row * ldp + 2L * c * V;
 #pragma unroll
     for (int p = 0; p < 3; p++) {
       if constexpr (V == 2) {
-        *reinterpret_cast<uint2*>(planes + p * plane + off) =
-            make_uint2((uint32_t)sl[0][0][p] | ((uint32_t)sl[0][1][p] << 16),
-                       (uint32_t)sl[1][0][p] | ((uint32_t)sl[1][1][p] << 16));
+        const uint2 wv = make_uint2((uint32_t)sl[0][0][p] | ((uint32_t)sl[0][1][p] << 16),
+                                    (uint32_t)sl[1][0][p] | ((uint32_t)sl[1][1][p] << 16));
+        *reinterpret_cast<uint2*>(planes + p * plane + off) = wv;
+        if constexpr (EMB) {
+          *reinterpret_cast<uint2*>(bplanes + p * bplane + bo) = wv;
+          *reinterpret_cast<uint2*>(bplanes + p * bplane + bo + ldp) =
+              make_uint2(((uint32_t)sl[0][1][p] ^ 0x8000u) | ((uint32_t)sl[0][0][p] << 16),
+                         ((uint32_t)sl[1][1][p] ^ 0x8000u) | ((uint32_t)sl[1][0][p] << 16));
+        }
       } else {
-        *reinterpret_cast<uint32_t*>(planes + p * plane + off) = (uint32_t)sl[0][0][p] | ((uint32_t)sl[0][1][p] << 16);
+        const uint32_t wv = (uint32_t)sl[0][0][p] | ((uint32_t)sl[0][1][p] << 16);
+        *reinterpret_cast<uint32_t*>(planes + p * plane + off) = wv;
+        if constexpr (EMB) {
+          *reinterpret_cast<uint32_t*>(bplanes + p * bplane + bo) = wv;
+          *reinterpret_cast<uint32_t*>(bplanes + p * bplane + bo + ldp) =
+              ((uint32_t)sl[0][1][p] ^ 0x8000u) | ((uint32_t)sl[0][0][p] << 16);
+        }
       }
     }
   };
@@ -236,17 +254,21 @@ cudaError_t col_exponents_c(const float2* src, long sbs, int lds, int batch, int
 }
 
 cudaError_t slice_rows_exact(const float2* src, int np, long rows, int* e, uint16_t* planes, long plane, int ldp,
-                             cudaStream_t s) {
+                             cudaStream_t s, uint16_t* bplanes, long bplane) {
   const long nb = std::min<long>((rows + 3) / 4, 152L * 128);   // 4 warps (rows) per block
   // 16-byte loads and 8-byte plane stores need even rows and 8-byte aligned plane rows
   const bool v2 = np % 2 == 0 && ldp % 4 == 0 && ((uintptr_t)src & 15) == 0;
   const int per = v2 ? np / 2 : np;   // lane accesses of a row
-#define SR(V_, R_) slice_rowmax_kernel<V_, R_><<<(unsigned)nb, 128, 0, s>>>(src, np, rows, e, planes, plane, ldp)
+#define SR(V_, R_, E_)                                                                                    \
+  slice_rowmax_kernel<V_, R_, true, E_><<<(unsigned)nb, 128, 0, s>>>(src, np, rows, e, planes, plane, ldp, \
+                                                                     bplanes, bplane)
+#define SR2(V_, R_) { if (bplanes) SR(V_, R_, true); else SR(V_, R_, false); }
   if (v2) {
-    if (per <= 32) SR(2, 1); else if (per <= 128) SR(2, 4); else SR(2, 0);
+    if (per <= 32) SR2(2, 1) else if (per <= 128) SR2(2, 4) else SR2(2, 0)
   } else {
-    if (per <= 32) SR(1, 1); else if (per <= 128) SR(1, 4); else SR(1, 0);
+    if (per <= 32) SR2(1, 1) else if (per <= 128) SR2(1, 4) else SR2(1, 0)
   }
+#undef SR2
 #undef SR
   return cudaGetLastError();
 }

@@ -504,8 +504,8 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, mark(c, 1, s, false));
   // S2  D = Psi Psi^H on tensor cores: A = Psi and B = embedded Psi^H share the
   // row exponents of Psi
-  CKC(c, slice_rows_exact(Psi, n, (long)nk * P, c->ePsi, c->PsiA_pl, c->plPs, c->ldPs, s));
-  CKC(c, embed_b(Psi, false, Pn, 1, n, true, false, nk, n, P, c->ePsi, c->Bd_pl, c->plBd, c->ldPs, s));
+  // (one kernel: the slices of Psi with its row exponents, and the embedded Psi^H)
+  CKC(c, slice_rows_exact(Psi, n, (long)nk * P, c->ePsi, c->PsiA_pl, c->plPs, c->ldPs, s, c->Bd_pl, c->plBd));
   CKC(c, record_core(c, 1, 0, s));
   // D is Hermitian, so only the tiles that reach the diagonal are multiplied
   // (Hermitian V: M^k is Hermitian too, and S3 reads D on and above the
@@ -580,8 +580,11 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, record_core(c, 3, 0, s));
   // (THC_MIXED_EXT with the Hermitian form: M's fp16 remainders join its FP32 values)
   const int m_conv = !a_f32 ? 0 : (herm && c->Mlo) ? 3 : 1;
+  // (the split-K combine that writes Y also forms the block sums of <Psi, Y> for S5)
+  int ex_blocks = 0;
   CKC(c, tc_gemm(a_f32 ? c->opMf : c->opM, c->opBy, P, 2 * n, 2 * P, nk, c->eM, P, c->eY, n, Y, false, 2 * n,
-                 2 * Pn, c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 3, 1), kProducts[2], m_conv));
+                 2 * Pn, c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 3, 1), kProducts[2], m_conv, 0,
+                 (const float*)Psi, c->partial, c->n_partial, &ex_blocks));
   CKC(c, mark(c, 4, s, false));
   // S4b KC = conj(X) Y on tensor cores: A = X (FP32, sliced inside the GEMM),
   // B = embedded Y (conj-A form)
@@ -592,7 +595,10 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
                  c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 4, 1), kProducts[3], 1));
   CKC(c, mark(c, 5, s, false));
   CKC(c, record_core(c, 5, 0, s));
-  CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
+  if (ex_blocks > 0)
+    CKC(c, ex_finalize(c->partial, ex_blocks, nk, ex, s));
+  else
+    CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
   CKC(c, record_core(c, 5, 1, s));
   CKC(c, mark(c, 6, s, false));
   return THC_OK;
@@ -829,17 +835,18 @@ thc_status thc_hermitian_kernel(const thc_ctx* c, int* hermitian) {
 thc_status thc_launches_per_build(const thc_ctx* c, int* launches) {
   if (!c || !launches) return THC_ERR_ARG;
   // FP64 and CUDA-core forms: S1, S2, S3, S4a, S4b, E_x partial, E_x final.
-  // Tensor-core form: S1 3 (exponents, embed, GEMM), S2 3 (slices with their
-  // row exponents, embed, GEMM), S3 + S4a 5 (the convolution, the row
+  // Tensor-core form: S1 3 (exponents, embed, GEMM), S2 2 (slices with their
+  // row exponents and the embedded Psi^H, GEMM), S3 + S4a 5 (the convolution, the row
   // exponents of M: in the convolution plus a conversion kernel on the
   // 2^3 .. 4^3 meshes, else a kernel of their own; exponents of Psi, embed,
   // GEMM), S4b 3, E_x 2; S1, S4a and S4b add a combine kernel when split
-  // along K.
+  // along K, and S4a's combine then forms the partial sums of E_x (E_x 1)
+  // when its result rows are 16-byte strided (n_occ even).
   if (tc_form(c->precision)) {
     const int s1 = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nbas, c->nk) > 0 ? 1 : 0;
     const int s4a = tc_partial_elems(c->nisdf, 2 * c->nocc, 2 * c->nisdf, c->nk) > 0 ? 1 : 0;
     const int s4b = tc_partial_elems(c->nbas, 2 * c->nocc, 2 * c->nisdf, c->nk) > 0 ? 1 : 0;
-    *launches = 3 + s1 + 3 + 1 + 4 + s4a + 3 + s4b + 2;
+    *launches = 3 + s1 + 2 + 1 + 4 + s4a + 3 + s4b + (s4a && c->nocc % 2 == 0 ? 1 : 2);
   } else {
     *launches = 7;
   }

@@ -191,6 +191,10 @@ cudaError_t hermitian_fill_c2z(const float2* D, double2* out, int np, int nk, cu
 // E_x = -(1/nk) sum conj(Psi) Y, FP64 accumulation, deterministic two-pass.
 cudaError_t ex_reduce_z(const double2* Psi, const double2* Y, long n, int nk, double* partial,
                         int npartial, double* ex, cudaStream_t s);
+// E_x from block partial sums of <Psi, Y> already written (2 doubles each,
+// real and imaginary part), added in a fixed order: ex[0] = -re / nk,
+// ex[1] = -im / nk.
+cudaError_t ex_finalize(const double* partial, int npartial, int nk, double* ex, cudaStream_t s);
 cudaError_t ex_reduce_c(const float2* Psi, const float2* Y, long n, int nk, double* partial,
                         int npartial, double* ex, cudaStream_t s);
 

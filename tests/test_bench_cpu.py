@@ -86,3 +86,11 @@ def test_fp64_roofline_arithmetic():
     assert r["S2_density"]["achieved_tflops"] == pytest.approx(8 * nk * P * P * n / 40e-3 / 1e12)
     assert r["S1_collocate"]["frac"] == pytest.approx(8 * nk * P * n * N / 10e-3 / 1e12 / 1.25)
     assert r["S3_kconv"]["achieved_gbs"] == pytest.approx(16 * nk * 3 * P * P / 5e-3 / 1e9)
+
+
+def test_s4a_split_rule():
+    # S4a's K is 2 N_P reals: split (and, n_occ even, carrying S5's partial sums) above 1024
+    assert bench.s4a_split(C2)
+    assert not bench.s4a_split(dict(C2, nisdf=512))
+    assert bench.s4a_split(dict(C2, nisdf=513))
+    assert not bench.s4a_split(dict(C2, nocc=61))      # odd n_occ: the combine kernel, S5 whole
