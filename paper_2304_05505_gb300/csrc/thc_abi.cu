@@ -309,9 +309,17 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
   return THC_OK;
 }
 
+// Drops the captured build (the inputs or the kernel form changed).
+static void drop_graph(thc_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->g_C = c->g_KC = c->g_ex = nullptr;
+}
+
 thc_status thc_destroy(thc_ctx* c) {
   if (!c) return THC_ERR_ARG;
   cudaStreamSynchronize(c->stream);
+  drop_graph(c);
   free_all(c);
   delete c;
   return THC_OK;
@@ -332,6 +340,7 @@ thc_status thc_set_collocation(thc_ctx* c, const double* X) {
   const double2* x = (const double2*)X;
   thc_status st = finite_check(c, x, n);
   if (st != THC_OK) return st;
+  drop_graph(c);
   if (c->precision == THC_FP64) {
     CKC(c, cudaMemcpyAsync(c->X64, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
   } else if (c->precision == THC_MIXED_SIMT) {
@@ -357,6 +366,7 @@ thc_status thc_set_kernel(thc_ctx* c, const double* V) {
   const double2* v = (const double2*)V;
   thc_status st = finite_check(c, v, npq * c->nk);
   if (st != THC_OK) return st;
+  drop_graph(c);
   CKC(c, prepare_kernel_z(v, c->Vh64, c->Vh32, npq, c->n1, c->n2, c->n3, c->stream));
   c->herm_v = false;
   if (c->hkeys) {
@@ -604,6 +614,34 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   return THC_OK;
 }
 
+// The tensor-core build as one CUDA graph launch: its 16-odd kernels (and the
+// stage-boundary events) are captured from the stream once per (C, KC, ex)
+// triple and replayed.  If the capture fails the build runs directly.
+static thc_status build_tc_graph(thc_ctx* c, const double2* C, double2* KC, double* ex) {
+  if (!c->gexec || c->g_C != C || c->g_KC != KC || c->g_ex != ex) {
+    drop_graph(c);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      return build_tc(c, C, KC, ex);
+    }
+    const thc_status st = build_tc(c, C, KC, ex);
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    cudaGraphExec_t x = nullptr;
+    if (st == THC_OK && e == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
+      c->gexec = x;
+      c->g_C = C;
+      c->g_KC = KC;
+      c->g_ex = ex;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();   // a failed capture leaves no sticky error: run the build directly
+    if (!c->gexec) return build_tc(c, C, KC, ex);
+  }
+  CKC(c, cudaGraphLaunch(c->gexec, c->stream));
+  return THC_OK;
+}
+
 thc_status thc_build(thc_ctx* c, const double* C, double* KC, double* ex) {
   if (!c || !C || !KC || !ex) return THC_ERR_ARG;
   if (!aligned16(C) || !aligned16(KC) || ((uintptr_t)ex & 7u)) return THC_ERR_ARG;
@@ -615,7 +653,8 @@ thc_status thc_build(thc_ctx* c, const double* C, double* KC, double* ex) {
   thc_status st;
   if (c->precision == THC_FP64) st = build_fp64(c, (const double2*)C, (double2*)KC, ex);
   else if (c->precision == THC_MIXED_SIMT) st = build_mixed(c, (const double2*)C, (double2*)KC, ex);
-  else st = build_tc(c, (const double2*)C, (double2*)KC, ex);
+  else if (profiling(c)) st = build_tc(c, (const double2*)C, (double2*)KC, ex);
+  else st = build_tc_graph(c, (const double2*)C, (double2*)KC, ex);
   if (st == THC_OK) {
     c->built = true;
     if (c->prof_max > 0 && c->prof_n < c->prof_max) {

@@ -46,6 +46,10 @@ struct thc_ctx {
   int device;
   cudaStream_t stream;
   bool have_x, have_v, built;
+  // the tensor-core build replayed as a CUDA graph while not profiled: its
+  // executable graph and the caller buffers it was captured with
+  cudaGraphExec_t gexec;
+  const void *g_C, *g_KC, *g_ex;
   // FP64 state
   double2* X64;     // [nk][nbas][nisdf]
   double2* Vh64;    // [nk][nisdf][nisdf] prepared kernel (FP64 mode)
