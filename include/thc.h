@@ -113,7 +113,12 @@ thc_status thc_set_kernel(thc_ctx* ctx, const double* V);
  * KC: device [N_k][nbas][nocc] complex128 (written; must not alias C).
  * ex: device, 2 doubles: ex[0] = E_x (Hartree per cell), ex[1] = the
  * imaginary part of the S5 sum (a residual, zero for Hermitian V).
- * Asynchronous on the context's stream. */
+ * Asynchronous on the context's stream.  In the tensor-core forms a build
+ * that is not being profiled runs as one CUDA graph launch: its kernels are
+ * captured from the stream on the first build with these (C, KC, ex)
+ * pointers and replayed on later ones (the contents of C may change between
+ * builds; new pointers, thc_set_collocation or thc_set_kernel capture anew;
+ * a capture the driver refuses falls back to launching the kernels). */
 thc_status thc_build(thc_ctx* ctx, const double* C, double* KC, double* ex);
 
 /* The same build from and to host memory: copies C_host in, runs the build,
@@ -170,7 +175,8 @@ thc_status thc_profile_end(thc_ctx* ctx, float mean_ms[6], int* nbuilds);
 /* Mean device time (ms) of each stage's main kernel over the builds of the
  * last completed profile: the GEMM of S1, S2, S4a and S4b (without operand
  * preparation or the combine of split-K partials), the convolution of S3, the
- * two reduction kernels of S5.  In the FP64 and CUDA-core forms each stage is
+ * reduction of S5 (its final sum when S4a's split-K combine formed the partial
+ * sums, else both of its kernels).  In the FP64 and CUDA-core forms each stage is
  * one kernel and this equals the stage time.  THC_ERR_STATE before a profile
  * has completed. */
 thc_status thc_profile_kernels(const thc_ctx* ctx, float core_ms[6]);
