@@ -234,7 +234,7 @@ def fp64_roofline(d: dict, stages_ms: dict, fp64_tflops: float, pk: dict) -> dic
     return out
 
 
-def kernel_roofline(stage: str, ms: float, work: dict, pk: dict) -> dict:
+def kernel_roofline(stage: str, ms: float, work: dict, pk: dict, config: str = "C2") -> dict:
     """Roofline of one stage's main kernel (or the stage) at `ms` per build.
 
     The bound is whichever lower limit is larger: algorithmic bytes over the
@@ -247,7 +247,7 @@ def kernel_roofline(stage: str, ms: float, work: dict, pk: dict) -> dict:
     sec = ms * 1e-3
     t_hbm = w["bytes"] / (pk["hbm_gbs"] * 1e9)
     t_ten = (w["flops"] / (pk["bf16_tflops_sustained"] * 1e12)) if w["flops"] else 0.0
-    out = {"kernel": stage, "ms": ms, "algorithmic_bytes": w["bytes"], "traffic": measured_traffic(stage)}
+    out = {"kernel": stage, "ms": ms, "algorithmic_bytes": w["bytes"], "traffic": measured_traffic(stage, config)}
     if t_ten > t_hbm:
         achieved = w["flops"] / sec / 1e12
         peak = pk["bf16_tflops_sustained"]
@@ -287,9 +287,9 @@ def source_hash(stage: str) -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(stage: str):
+def measured_traffic(stage: str, config: str = "C2"):
     """DRAM bytes per launch from the committed ncu capture, if it was taken
-    on the current sources of that kernel; else None."""
+    on this workload and on the current sources of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path) or stage not in KERNEL_SOURCES:
         return None
@@ -297,7 +297,7 @@ def measured_traffic(stage: str):
         t = json.load(open(path))
     except Exception:
         return None
-    if t.get("source_hashes", {}).get(stage) != source_hash(stage):
+    if t.get("config", "C2") != config or t.get("source_hashes", {}).get(stage) != source_hash(stage):
         return None
     v = t.get("per_launch_bytes", {}).get(stage)
     return float(v) if v is not None else None
@@ -662,10 +662,10 @@ def run_ours(args, world, rank, local):
     stages = {nm: ms for nm, ms in zip(names, stage_ms)}
     kernels = {nm: ms for nm, ms in zip(names, kernel_ms)}
     dominant = max(kernels, key=kernels.get)
-    roof = kernel_roofline(dominant, kernels[dominant], work, pk)
+    roof = kernel_roofline(dominant, kernels[dominant], work, pk, args.config)
     roof["name"] = kernel_names(hermitian)[dominant]
     # (S5 fused into S4a's combine moves only its partial sums: no roofline of its own)
-    per_kernel = {nm: kernel_roofline(nm, kernels[nm], work, pk) for nm in names
+    per_kernel = {nm: kernel_roofline(nm, kernels[nm], work, pk, args.config) for nm in names
                   if not (nm == "S5_energy" and s4a_split(d))}
 
 

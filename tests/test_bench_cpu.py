@@ -63,6 +63,8 @@ def test_measured_traffic_follows_the_sources(monkeypatch, tmp_path):
     assert bench.measured_traffic("S3_kconv") is None
     assert bench.measured_traffic("S4a_apply_M") == 1000 + stages.index("S4a_apply_M")
     assert bench.measured_traffic("S5_energy") is None          # no capture for S5
+    # a capture counts only for the workload it was taken on
+    assert bench.measured_traffic("S4a_apply_M", "C3") is None
 
 
 def test_source_hash_covers_the_kernel_files():
