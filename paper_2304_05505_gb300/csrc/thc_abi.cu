@@ -137,6 +137,8 @@ void free_all(thc_ctx* c) {
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   for (cudaEvent_t e : c->prof) cudaEventDestroy(e);
   c->prof.clear();
+  if (c->tc_err_host) cudaFreeHost(c->tc_err_host);
+  c->tc_err_host = nullptr;
 }
 
 constexpr int kStages = 6;
@@ -295,6 +297,12 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
       delete c;
       return e == cudaErrorNotSupported ? THC_ERR_UNSUPPORTED : THC_ERR_CUDA;
     }
+  }
+  if (c->tc_err && (e = cudaMallocHost(&c->tc_err_host, sizeof(int))) != cudaSuccess) {
+    g_create_error = std::string("cudaMallocHost: ") + cudaGetErrorString(e);
+    free_all(c);
+    delete c;
+    return THC_ERR_OOM;
   }
   for (int i = 0; i < 7; i++) {
     e = cudaEventCreate(&c->ev[i]);
@@ -763,10 +771,11 @@ thc_status thc_debug_fail_alloc(int nth) {
 
 thc_status thc_sync(thc_ctx* c) {
   if (!c) return THC_ERR_ARG;
+  // the error word comes back with the stream's last work: one wait
+  if (c->tc_err) CKC(c, cudaMemcpyAsync(c->tc_err_host, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CKC(c, cudaStreamSynchronize(c->stream));
   if (!c->tc_err) return THC_OK;
-  int h = 0;
-  CKC(c, cudaMemcpy(&h, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  const int h = *c->tc_err_host;
   if (h) {
     CKC(c, cudaMemset(c->tc_err, 0, sizeof(int)));
     c->last_error = "device wait timed out, code " + std::to_string(h);

@@ -108,6 +108,7 @@ struct thc_ctx {
   int ldAO;
   TcOperand opBxT, opBz;
   int* tc_err;        // device word: nonzero after a device wait gave up
+  int* tc_err_host;   // pinned host copy of it, read by thc_sync
   uint32_t* hkeys;    // row and column keys of the Hermitian convolution (when its form applies)
   bool herm_v;        // every V^q Hermitian (to 1e-12 of max |V|): S2 writes D's upper part, S3 mirrors M
   bool d_upper;       // the last build left D's part below the diagonal unwritten
