@@ -192,6 +192,7 @@ struct Geometry {
   long units;
   int herm;                  // Hermitian product: tiles reaching the diagonal only (1: mirrored, 2: upper part)
   long upb;                  // units per batch entry when herm
+  int b0;                    // batch offset of the operands' tensor maps (a sub-batch of a product)
 };
 
 // First n tile of m tile mi that reaches the diagonal of a Hermitian product
@@ -392,6 +393,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
       for (long u = u_begin; u < u_end && ok; u += u_step) {
         int b, mi, ni, kc;
         decode(u, b, mi, ni, kc);
+        const int bz = b + g.b0;   // the batch coordinate in the operands' tensor maps
         if constexpr (AR) {
           const long grp = (long)b * g.mt + mi;
           if (grp != gprev) {
@@ -400,7 +402,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
             mbar_expect_tx(AOP_FULL, g.nkb * NPL * TILE_BYTES);
             for (int kb = 0; kb < g.nkb; kb++)
               for (int p = 0; p < NPL; p++)
-                tma_load_3d(sbase + (kb * NPL + p) * TILE_BYTES, &maps.a[p], AOP_FULL, kb * BKR, mi * BM, b);
+                tma_load_3d(sbase + (kb * NPL + p) * TILE_BYTES, &maps.a[p], AOP_FULL, kb * BKR, mi * BM, bz);
             gprev = grp;
             agen++;
           }
@@ -415,18 +417,18 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
             if (!mbar_wait(SEMPTY(sa), ((it / SA_STAGES) & 1) ^ 1, err, 2)) { ok = false; break; }
             mbar_expect_tx(SFULL(sa), SA_BYTES);
             if constexpr (CV == 1 || CV == 3)
-              tma_load_3d(sbase + sa * SA_BYTES, &maps.a[0], SFULL(sa), kb * BKR, mi * BM, b);
+              tma_load_3d(sbase + sa * SA_BYTES, &maps.a[0], SFULL(sa), kb * BKR, mi * BM, bz);
             else   // [K][rows] source: 16 complex K values (rows of the box) x 128 complex rows
-              tma_load_3d(sbase + sa * SA_BYTES, &maps.a[0], SFULL(sa), mi * 2 * BM, kb * (BKR / 2), b);
+              tma_load_3d(sbase + sa * SA_BYTES, &maps.a[0], SFULL(sa), mi * 2 * BM, kb * (BKR / 2), bz);
             if constexpr (CV == 3)   // the remainders' fp16 tile beside it
-              tma_load_3d(sbase + sa * SA_BYTES + SA_HI, &maps.a[1], SFULL(sa), kb * BKR, mi * BM, b);
+              tma_load_3d(sbase + sa * SA_BYTES + SA_HI, &maps.a[1], SFULL(sa), kb * BKR, mi * BM, bz);
             nsa++;
             const int sb = it % B_STAGES;
             if (!mbar_wait(BEMPTY(sb), ((it / B_STAGES) & 1) ^ 1, err, 2)) { ok = false; break; }
             mbar_expect_tx(BFULL(sb), PL_BYTES);
             for (int p = 0; p < NPL; p++)
               tma_load_3d(sbase + B_OFF + sb * PL_BYTES + p * TILE_BYTES, &maps.b[p], BFULL(sb), kb * BKR,
-                          ni * BN, b);
+                          ni * BN, bz);
             nfull++;
             continue;
           }
@@ -435,12 +437,12 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, Geometry g, const int* __restr
           const uint32_t dst = sbase + A_BYTES + st * SBYTES;
           if constexpr (AR) {
             for (int p = 0; p < NPL; p++)
-              tma_load_3d(dst + p * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
+              tma_load_3d(dst + p * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, bz);
           } else {
             for (int p = 0; p < NPL; p++)
-              tma_load_3d(dst + p * TILE_BYTES, &maps.a[p], FULL(st), kb * BKR, mi * BM, b);
+              tma_load_3d(dst + p * TILE_BYTES, &maps.a[p], FULL(st), kb * BKR, mi * BM, bz);
             for (int p = 0; p < NPL; p++)
-              tma_load_3d(dst + (NPL + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, b);
+              tma_load_3d(dst + (NPL + p) * TILE_BYTES, &maps.b[p], FULL(st), kb * BKR, ni * BN, bz);
           }
           nfull++;
         }
@@ -981,8 +983,9 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
                     cudaEvent_t gemm_done, int products, int a_conv, int herm, const float* dot_with,
-                    double* dot_partial, int dot_max, int* dot_blocks) {
+                    double* dot_partial, int dot_max, int* dot_blocks, int b0, int ckb) {
   if (dot_blocks) *dot_blocks = 0;
+  if (b0 < 0) return cudaErrorInvalidValue;
   if (products != 6 && products != 8) return cudaErrorInvalidValue;
   if (a_conv < 0 || a_conv > 3) return cudaErrorInvalidValue;
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
@@ -996,12 +999,13 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int K
   g.mt = (M + BM - 1) / BM;
   g.nt = (Nr + BN - 1) / BN;
   g.nkb = (Kr + BKR - 1) / BKR;
-  g.ckb = tc_chunk_blocks(M, Nr, Kr, batch);
+  g.ckb = ckb > 0 ? std::min(ckb, MAX_CHUNK_KB) : tc_chunk_blocks(M, Nr, Kr, batch);
   g.nchunk = (g.nkb + g.ckb - 1) / g.ckb;
   g.units = (long)batch * g.mt * g.nt * g.nchunk;
   if (herm < 0 || herm > 2) return cudaErrorInvalidValue;
   g.herm = herm;
   g.upb = 0;
+  g.b0 = b0;
   if (herm) {
     // a Hermitian FP32 product written whole: square, one chunk, FP32 interleaved output
     if (Nr != 2 * M || g.nchunk != 1 || out_f64 || a_conv || (ldo % 2) || (sbo % 2)) return cudaErrorInvalidValue;

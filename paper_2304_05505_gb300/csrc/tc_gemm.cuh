@@ -41,12 +41,17 @@ cudaError_t make_plane_map(void* map_out, const void* base, int batch, int rows,
 // block partial sums of sum conj(w) out for w = dot_with of the same layout
 // (2 doubles per block, at most dot_max blocks, into dot_partial) and sets
 // *dot_blocks to their count; otherwise *dot_blocks = 0 and nothing is summed.
+// b0: the product is entries b0 .. b0 + batch - 1 of the batches the operand
+// maps cover (eA, eB, out and the partial buffers are then the sub-batch's own:
+// the caller offsets them).  ckb > 0: K blocks per chunk instead of
+// tc_chunk_blocks' choice for this shape (a sub-batch then sums in the whole
+// product's order; at most 32).
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int Nr, int Kr, int batch,
                     const int* eA, long seA, const int* eB, long seB, void* out, bool out_f64, long ldo,
                     long sbo, int* ps0, float* pbc, int* err, cudaStream_t s,
                     cudaEvent_t gemm_done = nullptr, int products = 8, int a_conv = 0, int herm = 0,
                     const float* dot_with = nullptr, double* dot_partial = nullptr, int dot_max = 0,
-                    int* dot_blocks = nullptr);
+                    int* dot_blocks = nullptr, int b0 = 0, int ckb = 0);
 
 // Map of an FP32 matrix [batch][rows][ld floats] (cols valid) in 32-float K
 // boxes of 128 rows with 128B swizzle (ld * 4 bytes a multiple of 16).

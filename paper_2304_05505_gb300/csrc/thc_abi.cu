@@ -139,6 +139,10 @@ void free_all(thc_ctx* c) {
   c->prof.clear();
   if (c->tc_err_host) cudaFreeHost(c->tc_err_host);
   c->tc_err_host = nullptr;
+  for (cudaEvent_t& e : c->cev)
+    if (e) cudaEventDestroy(e), e = nullptr;
+  if (c->cstream) cudaStreamDestroy(c->cstream);
+  c->cstream = nullptr;
 }
 
 constexpr int kStages = 6;
@@ -298,6 +302,14 @@ thc_status thc_create(thc_ctx** out, const thc_dims* d, int precision, void* str
       return e == cudaErrorNotSupported ? THC_ERR_UNSUPPORTED : THC_ERR_CUDA;
     }
   }
+  e = cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking);
+  for (int i = 0; i < 6 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&c->cev[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("copy stream: ") + cudaGetErrorString(e);
+    free_all(c);
+    delete c;
+    return THC_ERR_CUDA;
+  }
   if (c->tc_err && (e = cudaMallocHost(&c->tc_err_host, sizeof(int))) != cudaSuccess) {
     g_create_error = std::string("cudaMallocHost: ") + cudaGetErrorString(e);
     free_all(c);
@@ -322,6 +334,9 @@ static void drop_graph(thc_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   c->gexec = nullptr;
   c->g_C = c->g_KC = c->g_ex = nullptr;
+  if (c->gexec_h) cudaGraphExecDestroy(c->gexec_h);
+  c->gexec_h = nullptr;
+  c->gh_C = c->gh_KC = nullptr;
 }
 
 thc_status thc_destroy(thc_ctx* c) {
@@ -502,7 +517,15 @@ static thc_status build_mixed(thc_ctx* c, const double2* C, double2* KC, double*
 constexpr int kProducts[4] = {6, 6, 8, 8};
 constexpr int kProductsExt[4] = {8, 6, 8, 8};
 
-static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex, double2* Kao = nullptr) {
+// Host buffers of a host-buffer build that moves C in and KC out in halves on
+// the context's copy stream, beside S1 and S4b, which then run per half.
+struct HostIO {
+  const double2* C;
+  double2* KC;
+};
+
+static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex, double2* Kao = nullptr,
+                           const HostIO* io = nullptr) {
   const int* kProducts = c->precision == THC_MIXED_EXT ? kProductsExt : ::kProducts;
   const int nk = c->nk, N = c->nbas, n = c->nocc, P = c->nisdf;
   const long PP = (long)P * P, Pn = (long)P * n, Nn = (long)N * n;
@@ -512,13 +535,35 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   float2* Y = (float2*)c->Y;
   cudaStream_t s = c->stream;
   CKC(c, mark(c, 0, s, false));
-  // S1  Psi = X^T C on tensor cores: B = embedded C, one exponent per orbital
-  CKC(c, col_exponents_z(C, Nn, n, nk, N, n, c->eC, s));
-  CKC(c, embed_b(C, true, Nn, n, 1, false, false, nk, N, n, c->eC, c->Bc_pl, c->plBc, c->ldC, s));
-  CKC(c, record_core(c, 0, 0, s));
-  // A = X^T, read from FP32 X [mu][P] and sliced (transposed) inside the GEMM
-  CKC(c, tc_gemm(c->opXT, c->opBc, P, 2 * n, 2 * N, nk, c->eXT, P, c->eC, n, Psi, false, 2 * n, 2 * Pn,
-                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 0, 1), kProducts[0], 2));
+  // host-buffer build: the copy stream brings C in two halves of the k
+  // points, and S1 starts on the first while the second is in flight (the
+  // halves keep the whole product's K chunks, so the results are the same bits)
+  const int nh = io ? 2 : 1;
+  auto kb = [&](int h) { return nk * h / nh; };
+  cudaStream_t cs = c->cstream;
+  if (io) {
+    CKC(c, cudaEventRecord(c->cev[0], s));
+    CKC(c, cudaStreamWaitEvent(cs, c->cev[0], 0));
+    for (int h = 0; h < nh; h++) {
+      CKC(c, cudaMemcpyAsync((double2*)C + kb(h) * Nn, io->C + kb(h) * Nn, sizeof(double2) * Nn * (kb(h + 1) - kb(h)),
+                             cudaMemcpyHostToDevice, cs));
+      CKC(c, cudaEventRecord(c->cev[1 + h], cs));
+    }
+  }
+  for (int h = 0; h < nh; h++) {
+    const int b0 = kb(h), nb = kb(h + 1) - kb(h);
+    if (io) CKC(c, cudaStreamWaitEvent(s, c->cev[1 + h], 0));
+    // S1  Psi = X^T C on tensor cores: B = embedded C, one exponent per orbital
+    CKC(c, col_exponents_z(C + b0 * Nn, Nn, n, nb, N, n, c->eC + b0 * n, s));
+    CKC(c, embed_b(C + b0 * Nn, true, Nn, n, 1, false, false, nb, N, n, c->eC + b0 * n,
+                   c->Bc_pl + (long)b0 * 2 * n * c->ldC, c->plBc, c->ldC, s));
+    if (h == 0) CKC(c, record_core(c, 0, 0, s));
+    // A = X^T, read from FP32 X [mu][P] and sliced (transposed) inside the GEMM
+    CKC(c, tc_gemm(c->opXT, c->opBc, P, 2 * n, 2 * N, nb, c->eXT + (long)b0 * P, P, c->eC + b0 * n, n,
+                   Psi + b0 * Pn, false, 2 * n, 2 * Pn, c->part_s0, c->part_bc, c->tc_err, s,
+                   h == nh - 1 ? core_event(c, 0, 1) : nullptr, kProducts[0], 2, 0, nullptr, nullptr, 0, nullptr,
+                   b0, tc_chunk_blocks(P, 2 * n, 2 * N, nk)));
+  }
   CKC(c, mark(c, 1, s, false));
   // S2  D = Psi Psi^H on tensor cores: A = Psi and B = embedded Psi^H share the
   // row exponents of Psi
@@ -609,8 +654,20 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
   CKC(c, col_exponents_c(Y, Pn, n, nk, P, n, c->eY, s));
   CKC(c, embed_b(Y, false, Pn, n, 1, false, true, nk, P, n, c->eY, c->By_pl, c->plBy, c->ldM, s));
   CKC(c, record_core(c, 4, 0, s));
-  CKC(c, tc_gemm(c->opXn, c->opBy, N, 2 * n, 2 * P, nk, c->eXn, N, c->eY, n, KC, true, 2 * n, 2 * Nn,
-                 c->part_s0, c->part_bc, c->tc_err, s, core_event(c, 4, 1), kProducts[3], 1));
+  // (host-buffer build: per half of the k points, its KC going out on the
+  // copy stream while the next half is computed)
+  for (int h = 0; h < nh; h++) {
+    const int b0 = kb(h), nb = kb(h + 1) - kb(h);
+    CKC(c, tc_gemm(c->opXn, c->opBy, N, 2 * n, 2 * P, nb, c->eXn + (long)b0 * N, N, c->eY + b0 * n, n,
+                   KC + b0 * Nn, true, 2 * n, 2 * Nn, c->part_s0, c->part_bc, c->tc_err, s,
+                   h == nh - 1 ? core_event(c, 4, 1) : nullptr, kProducts[3], 1, 0, nullptr, nullptr, 0, nullptr,
+                   b0, tc_chunk_blocks(N, 2 * n, 2 * P, nk)));
+    if (io) {
+      CKC(c, cudaEventRecord(c->cev[3 + h], s));
+      CKC(c, cudaStreamWaitEvent(cs, c->cev[3 + h], 0));
+      CKC(c, cudaMemcpyAsync(io->KC + b0 * Nn, KC + b0 * Nn, sizeof(double2) * Nn * nb, cudaMemcpyDeviceToHost, cs));
+    }
+  }
   CKC(c, mark(c, 5, s, false));
   CKC(c, record_core(c, 5, 0, s));
   if (ex_blocks > 0)
@@ -619,6 +676,10 @@ static thc_status build_tc(thc_ctx* c, const double2* C, double2* KC, double* ex
     CKC(c, ex_reduce_c(Psi, Y, (long)nk * P * n, nk, c->partial, c->n_partial, ex, s));
   CKC(c, record_core(c, 5, 1, s));
   CKC(c, mark(c, 6, s, false));
+  if (io) {   // the copies out joined to the context's stream
+    CKC(c, cudaEventRecord(c->cev[5], cs));
+    CKC(c, cudaStreamWaitEvent(s, c->cev[5], 0));
+  }
   return THC_OK;
 }
 
@@ -743,9 +804,47 @@ thc_status thc_build_K(thc_ctx* c, const double* C, double* K, double* ex) {
   return st;
 }
 
+// The host-buffer tensor-core build with its copies overlapped (build_tc with
+// HostIO), as one CUDA graph launch captured per pair of host buffers; if the
+// capture is refused (pageable host memory, for one) it runs directly.
+static thc_status build_host_overlapped(thc_ctx* c, const double2* C_host, double2* KC_host) {
+  const HostIO io{C_host, KC_host};
+  const double2* C = (const double2*)c->Cdev;
+  double2* KC = (double2*)c->KCdev;
+  if (!c->gexec_h || c->gh_C != C_host || c->gh_KC != KC_host) {
+    if (c->gexec_h) cudaGraphExecDestroy(c->gexec_h);
+    c->gexec_h = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      return build_tc(c, C, KC, c->exdev, nullptr, &io);
+    }
+    const thc_status st = build_tc(c, C, KC, c->exdev, nullptr, &io);
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    cudaGraphExec_t x = nullptr;
+    if (st == THC_OK && e == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
+      c->gexec_h = x;
+      c->gh_C = C_host;
+      c->gh_KC = KC_host;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (!c->gexec_h) return build_tc(c, C, KC, c->exdev, nullptr, &io);
+  }
+  CKC(c, cudaGraphLaunch(c->gexec_h, c->stream));
+  return THC_OK;
+}
+
 thc_status thc_build_host(thc_ctx* c, const double* C_host, double* KC_host, double* ex_host) {
   if (!c || !C_host || !KC_host || !ex_host) return THC_ERR_ARG;
   if (!c->have_x || !c->have_v) return THC_ERR_STATE;
+  if (tc_form(c->precision) && !profiling(c) && c->nk >= 2) {
+    const thc_status st = build_host_overlapped(c, (const double2*)C_host, (double2*)KC_host);
+    if (st != THC_OK) return st;
+    c->built = true;
+    CKC(c, cudaMemcpyAsync(ex_host, c->exdev, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return thc_sync(c);
+  }
   const size_t kcb = (size_t)c->nk * c->nbas * c->nocc * sizeof(double2);
   CKC(c, cudaMemcpyAsync(c->Cdev, C_host, kcb, cudaMemcpyHostToDevice, c->stream));
   thc_status st = thc_build(c, (const double*)c->Cdev, (double*)c->KCdev, c->exdev);

@@ -50,6 +50,13 @@ struct thc_ctx {
   // executable graph and the caller buffers it was captured with
   cudaGraphExec_t gexec;
   const void *g_C, *g_KC, *g_ex;
+  // thc_build_host: a copy stream that moves C in and KC out in halves beside
+  // the build (events: fork, the two halves in, the two halves out, join),
+  // and the captured host-buffer build with its host buffers
+  cudaStream_t cstream;
+  cudaEvent_t cev[6];
+  cudaGraphExec_t gexec_h;
+  const void *gh_C, *gh_KC;
   // FP64 state
   double2* X64;     // [nk][nbas][nisdf]
   double2* Vh64;    // [nk][nisdf][nisdf] prepared kernel (FP64 mode)
