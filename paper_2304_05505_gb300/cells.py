@@ -410,6 +410,13 @@ def occupied_coefficients(cell: Cell) -> np.ndarray:
     Quadrature on the grid sub-sampled by ``quad_stride``.  For each +-k pair
     only one k is solved and ``C^{-k} = conj(C^k)``; at k = -k the problem is
     taken real."""
+    return orbital_coefficients(cell, 0)[0]
+
+
+def orbital_coefficients(cell: Cell, nvir: int) -> tuple:
+    """(C_occ, C_vir): the n_occ lowest eigenvectors of H^k C = S^k C e, as
+    occupied_coefficients gives them, and the next ``nvir`` (virtual
+    orbitals, for orbital rotations), shapes (Nk, N, n_occ) and (Nk, N, nvir)."""
     import scipy.linalg as sla
 
     s = cell.quad_stride
@@ -423,7 +430,10 @@ def occupied_coefficients(cell: Cell) -> np.ndarray:
     G = grid_gvectors(qshape, cell.recip)
     wpot = well_potential(cell, pts)
     nk = kf.shape[0]
-    C = np.zeros((nk, cell.nbas, cell.nocc), dtype=np.complex128)
+    nall = cell.nocc + int(nvir)
+    if nall > cell.nbas:
+        raise ValueError("more orbitals than basis functions")
+    C = np.zeros((nk, cell.nbas, nall), dtype=np.complex128)
     done = np.zeros(nk, dtype=bool)
     terms = collocation_terms(cell, pts) if _ACCEL is None else None
     for k in range(nk):
@@ -440,15 +450,15 @@ def occupied_coefficients(cell: Cell) -> np.ndarray:
         H = 0.5 * (H + H.conj().T)
         S = 0.5 * (S + S.conj().T)
         if mk[k] == k:
-            e, v = sla.eigh(H.real, S.real, subset_by_index=[0, cell.nocc - 1])
+            e, v = sla.eigh(H.real, S.real, subset_by_index=[0, nall - 1])
             C[k] = v
         else:
-            e, v = sla.eigh(H, S, subset_by_index=[0, cell.nocc - 1])
+            e, v = sla.eigh(H, S, subset_by_index=[0, nall - 1])
             C[k] = v
             C[mk[k]] = v.conj()
             done[mk[k]] = True
         done[k] = True
-    return C
+    return np.ascontiguousarray(C[:, :, :cell.nocc]), np.ascontiguousarray(C[:, :, cell.nocc:])
 
 
 def grid_orbitals(cell: Cell, C: np.ndarray, stride: int = 1, as_tensor: bool = False):
