@@ -84,6 +84,9 @@ def parse():
                     help="skip timing the per-iteration kernel rebuild (C2 only)")
     ap.add_argument("--rebuild-fp64", action="store_true",
                     help="also time the all-FP64 kernel rebuild (about a minute at C2)")
+    ap.add_argument("--vo-gradient", action="store_true",
+                    help="also time the FP64 THC-oo-K orbital gradient with the kernel's response (all virtual "
+                         "orbitals) at --config; seconds at C1, minutes at C2")
     ap.add_argument("--mixed-only", action="store_true",
                     help="time the mixed build alone (no host-buffer, CUDA-core, FP64 or oracle arms): "
                          "the small process a profiler capture runs")
@@ -470,6 +473,55 @@ def time_rebuild(p, thc, args) -> dict:
     return out
 
 
+def qrep_pairs(mesh) -> int:
+    """Number of (q, representative) pairs of a mesh: a q on the zone
+    boundary of an even axis has two minimum-image representatives there."""
+    n = 1
+    for m in mesh:
+        n *= sum(2 if (2 * c == m) else 1 for c in range(m))
+    return n
+
+
+def time_vo_gradient(p, thc, fp64_rate: float) -> dict:
+    """The THC-oo-K orbital gradient with the kernel's response (Sec. 2.3)
+    over all virtual orbitals, FP64, at the bench's cell: device ms per step,
+    beside the kernel rebuild it follows in an iteration, and the (q, G)
+    contraction that dominates it against the measured FP64 rate."""
+    import torch
+    from paper_2304_05505_gb300 import cells
+    cell = p.cell
+    nvir = cell.nbas - cell.nocc
+    cells.set_accelerator("cuda")
+    try:
+        C, Cv = cells.orbital_coefficients(cell, nvir)
+        Ud = cells.grid_orbitals(cell, C, as_tensor=True)
+        Uvd = cells.grid_orbitals(cell, Cv, as_tensor=True)
+    finally:
+        cells.set_accelerator(None)
+    pts, _ = thc.thc_select_points(Ud, cell.nisdf)
+    V, reb = thc.thc_rebuild_kernel(Ud, cell.grid, cell.lattice, cell.mesh, pts, "mixed")
+    nk = int(np.prod(cell.mesh))
+    names = ["fixed_kernel_D_W_M_Y", "fit_B_R_S_chol_solve_fft", "contraction_qG", "adjoint_dft_solve_Sbar",
+             "orbital_T1_T2_G1_G2"]
+    thc.thc_vo_gradient(Ud, Uvd, nk, cell.grid, cell.lattice, cell.mesh, pts, V)   # warm-up
+    runs = [thc.thc_vo_gradient(Ud, Uvd, nk, cell.grid, cell.lattice, cell.mesh, pts, V)[3] for _ in range(2)]
+    mean = [sum(r[i] for r in runs) / len(runs) for i in range(5)]
+    h = [(g - 1) // 2 for g in cell.grid]
+    nG = (2 * h[0] + 1) * (2 * h[1] + 1) * (2 * h[2] + 1)
+    flops = 8.0 * qrep_pairs(cell.mesh) * cell.nisdf ** 2 * nG
+    achieved = flops / (mean[2] * 1e-3) / 1e12
+    out = {"unit": "ms per gradient (device time of its steps)", "ms": sum(mean), "steps_ms": dict(zip(names, mean)),
+           "n_vir": nvir, "n_occ": cell.nocc, "precision": "FP64 (CUDA cores)",
+           "kernel": "V from the tensor-core kernel rebuild at the FP64 full-grid pivoted-Cholesky points",
+           "rebuild_ms": sum(reb), "ratio_to_rebuild": sum(mean) / sum(reb),
+           "contraction_roofline": {"bound": "fp64", "achieved": achieved, "peak": fp64_rate, "unit": "TFLOP/s",
+                                    "frac": achieved / fp64_rate if fp64_rate else None,
+                                    "flops": flops, "peak_source": "measured FP64 FMA rate (thc_measure_fp64_rate)"}}
+    del Ud, Uvd, V
+    torch.cuda.empty_cache()
+    return out
+
+
 def time_aok(d, p, thc, dev, stream) -> dict:
     """The THC-AO-K form of the build (Algorithm 1's K step: the full AO
     exchange matrix K^k = conj(X^k) M^k X^{kT}) on the same inputs: mixed
@@ -653,6 +705,7 @@ def run_ours(args, world, rank, local):
     if args.config == "C2" and not args.no_rebuild:
         rebuild = time_rebuild(p, thc, args)
     aok = time_aok(d, p, thc, dev, stream) if args.config == "C2" else None
+    vo = time_vo_gradient(p, thc, fp64_rate) if args.vo_gradient else None
 
     if rank != 0:
         return
@@ -697,6 +750,8 @@ def run_ours(args, world, rank, local):
         line["kernel_rebuild"] = rebuild
     if aok is not None:
         line["thc_ao_k"] = aok
+    if vo is not None:
+        line["vo_gradient"] = vo
     if ext is not None:
         line["mixed_ext"] = {k: v for k, v in ext.items() if k not in ("KC", "Ex")}
     if ms_simt is not None:

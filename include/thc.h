@@ -291,6 +291,43 @@ thc_status thc_rebuild_kernel(const double* U, int nfunc, const int* grid_host, 
                               const int* mesh_host, const int* points_host, int npts, int precision, double* V_out,
                               float* step_ms_host, void* stream);
 
+/* The THC-oo-K orbital gradient: the vo block of the exchange matrix with the
+ * kernel's response to the orbitals (Sec. 2.3, the K_ai expression; Algorithm
+ * 2's dM/dtheta step), in FP64.  THC-oo-K fits the interpolation vectors to
+ * the occupied pair products (Eq. orbprodoo), so V moves with the orbitals.
+ * For the rotation C^k -> C^k + Cv^k theta^k (theta^k [n_vir][n_occ]) the
+ * call returns
+ *   g^k[a][i] = dE_x/dRe(theta^k[a][i]) + i dE_x/dIm(theta^k[a][i])   at theta = 0,
+ * the points fixed and the fit (xi = S^-1 R, as thc_fit_kernel computes it)
+ * and V redone along theta.  It is the sum of
+ *   g_explicit^k = -(4/N_k) Psi_v^kH M^k Psi^k   (the kernel held fixed: the
+ *     first term of K_ai; equal to -(4/N_k) Cv^kH (K C)^k with K C from thc_build),
+ * and the kernel's response (the two W^q terms of K_ai): the derivative of
+ *   E_x = -(1/N_k) sum_q sum_PQ W^q[P,Q] V^q[P,Q],  W^q = sum_k conj(D^k) o D^{k+q},
+ * through V^q, xh, xi = S^-1 R, R = |B|^2 and B to the orbitals.
+ * U: device, [N_k n_occ][N_g] complex128, the occupied orbitals' periodic
+ * parts u^k_i(r) on the grid, row k n_occ + i, as for thc_fit_kernel.  Uv:
+ * device, [N_k n_vir][N_g] complex128, the virtual orbitals' periodic parts,
+ * row k n_vir + a.  psi = e^{i k.r} u with k = (n1/N1, n2/N2, n3/N3) in
+ * reciprocal-lattice units (the mesh index order of thc_create).  grid_host,
+ * lattice_host, mesh_host, points_host, npts: as for thc_fit_kernel.  V:
+ * device, [N_k][npts][npts] complex128, the kernel fitted to U at these points
+ * (thc_fit_kernel's or thc_rebuild_kernel's output); the response terms use
+ * the fit recomputed here.  g_out: device, [N_k][n_vir][n_occ] complex128.
+ * g_explicit_out: the same shape, or NULL.  ex_host (host, may be NULL):
+ * E_x from W and V.  step_ms_host (host, 5 floats, may be NULL): the device
+ * ms of the fixed-kernel part, the fit, the (q, G) contraction, the adjoint
+ * DFT with the solve, and the orbital contractions.  Outputs must not overlap
+ * inputs.  Allocates its own scratch, at most about the largest of
+ * 48 N_k npts^2, 16 npts (N_k npts + 7 N_g) and 16 N_k n_occ N_g + 32 npts N_g
+ * bytes, and waits for `stream`.  THC_ERR_ARG for
+ * bad sizes, null or misaligned pointers, repeated or out-of-range points, or
+ * points whose metric S is numerically singular (as thc_fit_kernel). */
+thc_status thc_vo_gradient(const double* U, int nocc, const double* Uv, int nvir, const int* grid_host,
+                           const double* lattice_host, const int* mesh_host, const int* points_host, int npts,
+                           const double* V, double* g_out, double* g_explicit_out, double* ex_host,
+                           float* step_ms_host, void* stream);
+
 /* Learned interpolation-point proposal (setup, outside the timed build).  The
  * paper has no learned part (its points come from a QR decomposition with
  * column pivoting, Sec. 2.1, or from k-means on the density, Sec. 4); these

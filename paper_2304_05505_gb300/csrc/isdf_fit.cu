@@ -23,115 +23,13 @@
 // vector set Xq is rounded to FP32 and sliced inside the GEMM, three fp16
 // slices, 8 slice products, the leading products summed exactly in K chunks of
 // at most 1024 reals; chunks are combined in FP64.
-#include "thc_internal.cuh"
+#include "isdf_common.cuh"
 #include "tc_gemm.cuh"
-
-#include <math.h>
-
-#include <vector>
 
 namespace {
 
-constexpr int TB = 256;
-
-unsigned blocks(long n) { return (unsigned)((n + TB - 1) / TB); }
-
-// Ugc[P][f] = conj(U[f][pts[P]])
-__global__ void gather_conj(const double2* __restrict__ U, int nf, long ng, const int* __restrict__ pts, int np,
-                            double2* __restrict__ Ugc) {
-  const long i = (long)blockIdx.x * TB + threadIdx.x;
-  if (i >= (long)np * nf) return;
-  const int P = (int)(i / nf), f = (int)(i % nf);
-  const double2 u = U[(long)f * ng + pts[P]];
-  Ugc[i] = make_double2(u.x, -u.y);
-}
-
-// R[i] = |B[i]|^2
-__global__ void abs2_kernel(const double2* __restrict__ B, long n, double* __restrict__ R) {
-  const long i = (long)blockIdx.x * TB + threadIdx.x;
-  if (i >= n) return;
-  const double2 b = B[i];
-  R[i] = b.x * b.x + b.y * b.y;
-}
-
-// S[P][Q] = R[P][pts[Q]]
-__global__ void gather_cols(const double* __restrict__ R, long ng, const int* __restrict__ pts, int np,
-                            double* __restrict__ S) {
-  const long i = (long)blockIdx.x * TB + threadIdx.x;
-  if (i >= (long)np * np) return;
-  const int P = (int)(i / np), Q = (int)(i % np);
-  S[i] = R[(long)P * ng + pts[Q]];
-}
-
-// Column j of the Cholesky factor L (row-major, lower), left-looking: every
-// thread recomputes the pivot d_j = S_jj - sum_t L_jt^2 and forms its L_ij.
-// A pivot below 1e-12 S_jj marks the metric numerically singular.
-__global__ void chol_column(const double* __restrict__ S, double* __restrict__ L, int n, int j, int* bad) {
-  const int i = j + (int)((long)blockIdx.x * TB + threadIdx.x);
-  if (i >= n) return;
-  double d = S[(long)j * n + j];
-  const double sjj = d;
-  for (int t = 0; t < j; t++) d -= L[(long)j * n + t] * L[(long)j * n + t];
-  if (!(d > 1e-12 * sjj)) {
-    if (i == j) atomicOr(bad, 1);
-    return;
-  }
-  const double ljj = sqrt(d);
-  if (i == j) {
-    L[(long)j * n + j] = ljj;
-    return;
-  }
-  double a = S[(long)i * n + j];
-  for (int t = 0; t < j; t++) a -= L[(long)i * n + t] * L[(long)j * n + t];
-  L[(long)i * n + j] = a / ljj;
-}
-
-// X = L^-T L^-1 X for every column r of X[n][ng], in place.
-__global__ void chol_solve(const double* __restrict__ L, double* __restrict__ X, int n, long ng) {
-  const long r = (long)blockIdx.x * TB + threadIdx.x;
-  if (r >= ng) return;
-  for (int j = 0; j < n; j++) {
-    double a = X[(long)j * ng + r];
-    for (int t = 0; t < j; t++) a -= L[(long)j * n + t] * X[(long)t * ng + r];
-    X[(long)j * ng + r] = a / L[(long)j * n + j];
-  }
-  for (int j = n - 1; j >= 0; j--) {
-    double a = X[(long)j * ng + r];
-    for (int t = j + 1; t < n; t++) a -= L[(long)t * n + j] * X[(long)t * ng + r];
-    X[(long)j * ng + r] = a / L[(long)j * n + j];
-  }
-}
-
-// One axis of the forward DFT of [np][g1][g2][g3]: out = sum_j in(j) tw[(j m) mod g].
-// `real_in` reads a real array (the vectors themselves) for the first axis.
-__global__ void dft_axis_kernel(const void* __restrict__ in, bool real_in, double2* __restrict__ out, long total,
-                                int g, long st, const double2* __restrict__ tw) {
-  const long i = (long)blockIdx.x * TB + threadIdx.x;
-  if (i >= total) return;
-  const int m = (int)((i / st) % g);
-  const long base = i - (long)m * st;
-  double re = 0.0, im = 0.0;
-  for (int j = 0, jm = 0; j < g; j++, jm = (jm + m) % g) {
-    const double2 w = tw[jm];
-    if (real_in) {
-      const double x = ((const double*)in)[base + (long)j * st];
-      re += x * w.x;
-      im += x * w.y;
-    } else {
-      const double2 x = ((const double2*)in)[base + (long)j * st];
-      re += x.x * w.x - x.y * w.y;
-      im += x.x * w.y + x.y * w.x;
-    }
-  }
-  out[i] = make_double2(re, im);
-}
-
 // Xq[P][G] = F[P][flat[G]] * sqrt(w v(G + q)) * exp(-i q.r_P), with
 // K = (gm[G] + qf) B (Cartesian) and v(K) = 4 pi / |K|^2 (0 for K = 0).
-struct Recip {
-  double b[9];   // rows b1, b2, b3
-};
-
 __global__ void scale_xi(const double2* __restrict__ F, long ng, const int* __restrict__ flat,
                          const int* __restrict__ gm, int nG, const double* __restrict__ rP, int np, Recip B,
                          double q0, double q1, double q2, double w, double2* __restrict__ Xq) {
@@ -193,14 +91,6 @@ __global__ void add_herm_kernel(double2* __restrict__ V, const double2* __restri
   V[i] = make_double2(V[i].x + 0.5 * (a.x + b.x), V[i].y + 0.5 * (a.y - b.y));
 }
 
-// Minimum-image fractional representatives of q = qco / mesh along one axis.
-std::vector<double> axis_reps(int qc, int n) {
-  const double f = (double)(((qc % n) + n) % n) / n;
-  if (fabs(f - 0.5) < 1e-12) return {0.5, -0.5};
-  if (f > 0.5) return {f - 1.0};
-  return {f};
-}
-
 
 // G vectors per tensor-core product of step 4: at most 60,000 complex (120,000
 // real K, under the 127 exact K chunks of 1024 a product may take), even so
@@ -214,65 +104,19 @@ thc_status fit_impl(const double* U, int nfunc, const int* grid_host, const doub
   if (!U || !grid_host || !lattice_host || !mesh_host || !points_host || !V_out || nfunc < 1 || npts < 1)
     return THC_ERR_ARG;
   if (((uintptr_t)U & 15) || ((uintptr_t)V_out & 15) || ((uintptr_t)xi_out & 7)) return THC_ERR_ARG;
-  const int g1 = grid_host[0], g2 = grid_host[1], g3 = grid_host[2];
-  const int n1 = mesh_host[0], n2 = mesh_host[1], n3 = mesh_host[2];
-  if (g1 < 1 || g2 < 1 || g3 < 1 || n1 < 1 || n2 < 1 || n3 < 1 || n1 > 8 || n2 > 8 || n3 > 8) return THC_ERR_ARG;
-  const long ng = (long)g1 * g2 * g3;
-  if (npts > ng) return THC_ERR_ARG;
-  std::vector<char> seen(ng, 0);
-  for (int P = 0; P < npts; P++) {
-    const int p = points_host[P];
-    if (p < 0 || p >= ng || seen[p]) return THC_ERR_ARG;   // points must be distinct grid indices
-    seen[p] = 1;
-  }
-  const double* a = lattice_host;
-  const double vol = fabs(a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
-                          a[2] * (a[3] * a[7] - a[4] * a[6]));
-  if (!(vol > 0)) return THC_ERR_ARG;
-  // reciprocal rows b_i with a_i . b_j = 2 pi delta_ij
-  Recip B;
-  {
-    const double c = 2.0 * M_PI / (a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
-                                   a[2] * (a[3] * a[7] - a[4] * a[6]));
-    const double* a1 = a;
-    const double* a2 = a + 3;
-    const double* a3 = a + 6;
-    auto cross = [](const double* x, const double* y, double* o) {
-      o[0] = x[1] * y[2] - x[2] * y[1];
-      o[1] = x[2] * y[0] - x[0] * y[2];
-      o[2] = x[0] * y[1] - x[1] * y[0];
-    };
-    cross(a2, a3, B.b);
-    cross(a3, a1, B.b + 3);
-    cross(a1, a2, B.b + 6);
-    for (double& x : B.b) x *= c;
-  }
-  // G set without Nyquist planes, its flat grid index, point positions
-  const int h1 = (g1 - 1) / 2, h2 = (g2 - 1) / 2, h3 = (g3 - 1) / 2;
-  std::vector<int> gm, flat;
-  for (int i = -h1; i <= h1; i++)
-    for (int j = -h2; j <= h2; j++)
-      for (int l = -h3; l <= h3; l++) {
-        gm.push_back(i);
-        gm.push_back(j);
-        gm.push_back(l);
-        flat.push_back((((i % g1) + g1) % g1 * g2 + ((j % g2) + g2) % g2) * g3 + ((l % g3) + g3) % g3);
-      }
+  FitGeom geo;
+  if (!fit_geometry(grid_host, lattice_host, mesh_host, points_host, npts, geo)) return THC_ERR_ARG;
+  const int g1 = geo.g[0], g2 = geo.g[1], g3 = geo.g[2];
+  const int n1 = geo.n[0], n2 = geo.n[1], n3 = geo.n[2];
+  const long ng = geo.ng;
+  const double vol = geo.vol;
+  const Recip B = geo.B;
+  const std::vector<int>& gm = geo.gm;
+  const std::vector<int>& flat = geo.flat;
   const int nG = (int)flat.size();
-  std::vector<double> rP(3 * (size_t)npts);
-  for (int P = 0; P < npts; P++) {
-    const int p = points_host[P];
-    const double f0 = (double)(p / (g2 * g3)) / g1, f1 = (double)((p / g3) % g2) / g2, f2 = (double)(p % g3) / g3;
-    for (int x = 0; x < 3; x++) rP[3 * P + x] = f0 * a[x] + f1 * a[3 + x] + f2 * a[6 + x];
-  }
-  std::vector<double2> tw(g1 + g2 + g3);
-  int off[3] = {0, g1, g1 + g2};
-  const int gs[3] = {g1, g2, g3};
-  for (int ax = 0; ax < 3; ax++)
-    for (int t = 0; t < gs[ax]; t++) {
-      const double ang = -2.0 * M_PI * t / gs[ax];
-      tw[off[ax] + t] = make_double2(cos(ang), sin(ang));
-    }
+  const std::vector<double>& rP = geo.rP;
+  const std::vector<double2>& tw = geo.tw;
+  const int* off = geo.off;
 
   cudaStream_t s = (cudaStream_t)stream;
   const int nk = n1 * n2 * n3;

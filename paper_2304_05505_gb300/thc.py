@@ -33,7 +33,7 @@ EXPORTS = ["thc_create", "thc_memory_bytes", "thc_set_collocation", "thc_set_ker
            "thc_select_points", "thc_fit_kernel", "thc_profile_kernels", "thc_mlp_features", "thc_mlp_score",
            "thc_mlp_workspace_bytes", "thc_mlp_train_step", "thc_mlp_candidates", "thc_select_points_among",
            "thc_debug_set_wait_limit", "thc_debug_fail_alloc", "thc_rebuild_kernel", "thc_build_K",
-           "thc_measure_fp64_rate"]
+           "thc_measure_fp64_rate", "thc_vo_gradient"]
 
 MLP_NPARAM = 8641
 
@@ -89,6 +89,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_float), vp]
     lib.thc_fit_kernel.argtypes = [dp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, dp, dp, vp]
+    lib.thc_vo_gradient.argtypes = [dp, ip, dp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, dp, dp, dp,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), vp]
     fp = ctypes.POINTER(ctypes.c_float)
     lib.thc_mlp_features.argtypes = [dp, ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double), ip, dp, vp]
@@ -367,6 +370,41 @@ def thc_rebuild_kernel(U, grid, lattice, mesh, points, precision="mixed", stream
                                      ctypes.c_void_p(stream)),
            "thc_rebuild_kernel")
     return V, [float(x) for x in ms]
+
+
+def thc_vo_gradient(U, Uv, nk: int, grid, lattice, mesh, points, V, stream: int | None = None):
+    """The THC-oo-K orbital gradient with the kernel's response (see
+    include/thc.h): U [N_k n_occ][N_g] and Uv [N_k n_vir][N_g] complex128 CUDA
+    tensors, V [N_k][npts][npts] the kernel fitted to U at `points`.  Returns
+    (g, g_explicit, E_x, step_ms): g and g_explicit [N_k][n_vir][n_occ]
+    complex128 CUDA tensors (the full gradient and its fixed-kernel term), E_x
+    from sum_q W^q o V^q, and the device ms of the five steps."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    nk = int(nk)
+    nfo, ng = U.shape
+    nfv = Uv.shape[0]
+    if nfo % nk or nfv % nk:
+        raise ValueError("U and Uv rows must be N_k times the orbitals per k")
+    nocc, nvir = nfo // nk, nfv // nk
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    m = (ctypes.c_int * 3)(*[int(x) for x in mesh])
+    if int(np.prod([int(x) for x in mesh])) != nk:
+        raise ValueError("nk must be the number of k-mesh points")
+    lat = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(lattice, dtype=np.float64).ravel()])
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int32))
+    npts = int(pts.size)
+    gout = torch.empty((nk, nvir, nocc), dtype=torch.complex128, device=U.device)
+    gexp = torch.empty_like(gout)
+    ex = ctypes.c_double(0.0)
+    ms = (ctypes.c_float * 5)()
+    _check(load().thc_vo_gradient(_dev_ptr(U, (nfo, ng), name="U"), nocc, _dev_ptr(Uv, (nfv, ng), name="Uv"), nvir,
+                                  g, lat, m, pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), npts,
+                                  _dev_ptr(V, (nk, npts, npts), name="V"), gout.data_ptr(), gexp.data_ptr(),
+                                  ctypes.byref(ex), ms, ctypes.c_void_p(stream)),
+           "thc_vo_gradient")
+    return gout, gexp, float(ex.value), [float(x) for x in ms]
 
 
 def _f32_dev(t, n=None, name="tensor") -> int:

@@ -96,3 +96,13 @@ def test_s4a_split_rule():
     assert not bench.s4a_split(dict(C2, nisdf=512))
     assert bench.s4a_split(dict(C2, nisdf=513))
     assert not bench.s4a_split(dict(C2, nocc=61))      # odd n_occ: the combine kernel, S5 whole
+
+
+@pytest.mark.parametrize("mesh", [(4, 4, 4), (3, 3, 3), (2, 2, 1), (6, 1, 3)])
+def test_qrep_pairs_counts_the_representatives(mesh):
+    """The (q, representative) pairs the vo-gradient contraction runs over are
+    the setup oracle's minimum-image representatives of every q."""
+    from oracle import setup_oracle as S
+    from oracle import thc_oracle as O
+    n = sum(len(S.representatives(co, mesh)) for co in O.mesh_coords(mesh))
+    assert bench.qrep_pairs(mesh) == n

@@ -1,0 +1,99 @@
+"""GPU parity of the THC-oo-K orbital gradient (thc_vo_gradient) against the
+FP64 oracle (oracle/vo_oracle.py: autograd of the energy with the fit redone,
+pinned by finite differences in test_oracle_vo.py).
+
+Both sides are FP64.  The CUDA path solves the fit's metric by Cholesky and
+sums in another order than the oracle's LU solve and torch reductions; with
+cond(S) below 1e5 on these cells the two agree to about 1e-11 of max|g|, and
+the bound is 1e-9 of max|g| per element."""
+import numpy as np
+import pytest
+
+from oracle import setup_oracle as S
+from oracle import vo_oracle as VO
+from paper_2304_05505_gb300 import cells
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def thc(cuda_required):
+    import os
+
+    from paper_2304_05505_gb300 import build_lib, thc as mod
+    if not os.path.exists(mod.LIB_PATH):
+        build_lib.build()
+    mod.load()
+    return mod
+
+
+def _problem(mesh, grid, nvir, npts, seed=None):
+    c = cells.make_cell("C0", mesh=mesh, grid=grid, seed=seed)
+    kf = cells.kmesh_frac(c.mesh)
+    Xg = cells.bloch_collocation(c, cells.grid_points(c, 1), kf)
+    C, Cv = cells.orbital_coefficients(c, nvir)
+    p = dict(lattice=c.lattice, grid=c.grid, mesh=c.mesh, kfrac=kf, Xg=Xg, points=None)
+    U = VO.grid_orbitals(p, C)
+    p["points"] = S.pivoted_cholesky(U, npts)["points"]
+    V = S.fit_kernel(c.lattice, c.grid, c.mesh, U, p["points"])
+    return c, p, C, Cv, U, VO.grid_orbitals(p, Cv), V
+
+
+CASES = [
+    # (mesh, grid, nvir, npts): one GEMM tile; several tiles with ragged
+    # tails; odd grid axes, a zone-boundary q (two representatives)
+    ((3, 1, 2), (8, 8, 8), 4, 24),
+    ((2, 2, 2), (12, 12, 12), 6, 100),
+    ((2, 2, 1), (7, 6, 5), 3, 37),
+]
+
+
+@pytest.mark.parametrize("mesh,grid,nvir,npts", CASES)
+def test_vo_gradient_matches_oracle(thc, mesh, grid, nvir, npts):
+    c, p, C, Cv, U, Uv, V = _problem(mesh, grid, nvir, npts)
+    dev = torch.device("cuda:0")
+    g, ge, ex, ms = thc.thc_vo_gradient(torch.from_numpy(U).to(dev), torch.from_numpy(Uv).to(dev), C.shape[0],
+                                        c.grid, c.lattice, c.mesh, p["points"], torch.from_numpy(V).to(dev))
+    torch.cuda.synchronize()
+    g, ge = g.cpu().numpy(), ge.cpu().numpy()
+    ref = VO.vo_gradient(p, C, Cv)
+    ref_e = VO.explicit_gradient(p, C, Cv, V)
+    E = VO.energy(p, C, V)
+    scale = np.abs(ref).max()
+    assert np.abs(ge - ref_e).max() <= 1e-9 * scale
+    assert np.abs(g - ref).max() <= 1e-9 * scale
+    assert abs(ex - E) <= 1e-12 * abs(E)
+    # the kernel's response is a large part of the gradient on these cells
+    assert np.abs(g - ge).max() >= 0.05 * scale
+    assert len(ms) == 5 and all(m >= 0.0 for m in ms)
+
+
+def test_occupied_rotation_gradient_is_hermitian(thc):
+    """With the occupied orbitals in place of the virtual ones the gradient
+    is that of a rotation among them, which leaves E_x unchanged: Hermitian
+    for every k."""
+    c, p, C, Cv, U, Uv, V = _problem((3, 1, 2), (8, 8, 8), 4, 24)
+    dev = torch.device("cuda:0")
+    Ud = torch.from_numpy(U).to(dev)
+    g, _, _, _ = thc.thc_vo_gradient(Ud, Ud, C.shape[0], c.grid, c.lattice, c.mesh, p["points"],
+                                     torch.from_numpy(V).to(dev))
+    g = g.cpu().numpy()
+    assert np.abs(g - np.conj(np.transpose(g, (0, 2, 1)))).max() <= 1e-11 * np.abs(g).max()
+
+
+def test_vo_gradient_rejects_bad_points(thc):
+    c, p, C, Cv, U, Uv, V = _problem((3, 1, 2), (8, 8, 8), 4, 24)
+    dev = torch.device("cuda:0")
+    Ud, Uvd, Vd = (torch.from_numpy(x).to(dev) for x in (U, Uv, V))
+    pts = np.array(p["points"]).copy()
+    pts[1] = pts[0]
+    with pytest.raises(thc.ThcError) as e:
+        thc.thc_vo_gradient(Ud, Uvd, C.shape[0], c.grid, c.lattice, c.mesh, pts, Vd)
+    assert e.value.code == 1
+    pts = np.array(p["points"]).copy()
+    pts[0] = int(np.prod(c.grid))
+    with pytest.raises(thc.ThcError) as e:
+        thc.thc_vo_gradient(Ud, Uvd, C.shape[0], c.grid, c.lattice, c.mesh, pts, Vd)
+    assert e.value.code == 1
