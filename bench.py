@@ -503,21 +503,33 @@ def time_vo_gradient(p, thc, fp64_rate: float) -> dict:
     nk = int(np.prod(cell.mesh))
     names = ["fixed_kernel_D_W_M_Y", "fit_B_R_S_chol_solve_fft", "contraction_qG", "adjoint_dft_solve_Sbar",
              "orbital_T1_T2_G1_G2"]
-    thc.thc_vo_gradient(Ud, Uvd, nk, cell.grid, cell.lattice, cell.mesh, pts, V)   # warm-up
-    runs = [thc.thc_vo_gradient(Ud, Uvd, nk, cell.grid, cell.lattice, cell.mesh, pts, V)[3] for _ in range(2)]
-    mean = [sum(r[i] for r in runs) / len(runs) for i in range(5)]
     h = [(g - 1) // 2 for g in cell.grid]
     nG = (2 * h[0] + 1) * (2 * h[1] + 1) * (2 * h[2] + 1)
     flops = 8.0 * qrep_pairs(cell.mesh) * cell.nisdf ** 2 * nG
-    achieved = flops / (mean[2] * 1e-3) / 1e12
-    out = {"unit": "ms per gradient (device time of its steps)", "ms": sum(mean), "steps_ms": dict(zip(names, mean)),
-           "n_vir": nvir, "n_occ": cell.nocc, "precision": "FP64 (CUDA cores)",
+    out = {"unit": "ms per gradient (device time of its steps)", "n_vir": nvir, "n_occ": cell.nocc,
            "kernel": "V from the tensor-core kernel rebuild at the FP64 full-grid pivoted-Cholesky points",
-           "rebuild_ms": sum(reb), "ratio_to_rebuild": sum(mean) / sum(reb),
-           "contraction_roofline": {"bound": "fp64", "achieved": achieved, "peak": fp64_rate, "unit": "TFLOP/s",
-                                    "frac": achieved / fp64_rate if fp64_rate else None,
-                                    "flops": flops, "peak_source": "measured FP64 FMA rate (thc_measure_fp64_rate)"}}
-    del Ud, Uvd, V
+           "rebuild_ms": sum(reb), "contraction_flops": flops}
+    grads = {}
+    for prec in ("fp64", "mixed"):
+        thc.thc_vo_gradient(Ud, Uvd, nk, cell.grid, cell.lattice, cell.mesh, pts, V, prec)   # warm-up
+        runs = []
+        for _ in range(2):
+            g, _, _, ms = thc.thc_vo_gradient(Ud, Uvd, nk, cell.grid, cell.lattice, cell.mesh, pts, V, prec)
+            runs.append(ms)
+        grads[prec] = g
+        mean = [sum(r[i] for r in runs) / len(runs) for i in range(5)]
+        achieved = flops / (mean[2] * 1e-3) / 1e12
+        out[prec] = {"ms": sum(mean), "steps_ms": dict(zip(names, mean)), "ratio_to_rebuild": sum(mean) / sum(reb),
+                     "contraction_achieved_tflops": achieved}
+    out["fp64"]["contraction_roofline"] = {
+        "bound": "fp64", "achieved": out["fp64"]["contraction_achieved_tflops"], "peak": fp64_rate,
+        "unit": "TFLOP/s", "frac": out["fp64"]["contraction_achieved_tflops"] / fp64_rate if fp64_rate else None,
+        "peak_source": "measured FP64 FMA rate (thc_measure_fp64_rate)"}
+    out["mixed"]["form"] = ("(q, G) contraction on tcgen05 (FP32 operands sliced into 3 fp16 slices, 8 products, "
+                            "exact K chunks); the other steps FP64")
+    out["mixed"]["max_abs_dg_vs_fp64_rel"] = float((grads["mixed"] - grads["fp64"]).abs().max()
+                                                   / grads["fp64"].abs().max())
+    del Ud, Uvd, V, grads
     torch.cuda.empty_cache()
     return out
 

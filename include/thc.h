@@ -313,7 +313,14 @@ thc_status thc_rebuild_kernel(const double* U, int nfunc, const int* grid_host, 
  * lattice_host, mesh_host, points_host, npts: as for thc_fit_kernel.  V:
  * device, [N_k][npts][npts] complex128, the kernel fitted to U at these points
  * (thc_fit_kernel's or thc_rebuild_kernel's output); the response terms use
- * the fit recomputed here.  g_out: device, [N_k][n_vir][n_occ] complex128.
+ * the fit recomputed here.  precision THC_FP64: every step in FP64 on CUDA
+ * cores.  THC_MIXED: the (q, G) contraction of the response, the
+ * O(N_k npts^2 N_G) step that dominates, runs on the tcgen05 tensor cores as
+ * thc_rebuild_kernel's contraction does (W^q with its phases rounded to FP32
+ * and sliced in the GEMM, v(G+q) conj(xh) cut into three fp16 slices with
+ * exact column exponents, 8 slice products, exact K chunks combined in FP64);
+ * every other step stays FP64 (g about 1e-7 to 1e-6 of max|g| from the FP64
+ * form).  g_out: device, [N_k][n_vir][n_occ] complex128.
  * g_explicit_out: the same shape, or NULL.  ex_host (host, may be NULL):
  * E_x from W and V.  step_ms_host (host, 5 floats, may be NULL): the device
  * ms of the fixed-kernel part, the fit, the (q, G) contraction, the adjoint
@@ -322,10 +329,11 @@ thc_status thc_rebuild_kernel(const double* U, int nfunc, const int* grid_host, 
  * 48 N_k npts^2, 16 npts (N_k npts + 7 N_g) and 16 N_k n_occ N_g + 32 npts N_g
  * bytes, and waits for `stream`.  THC_ERR_ARG for
  * bad sizes, null or misaligned pointers, repeated or out-of-range points, or
- * points whose metric S is numerically singular (as thc_fit_kernel). */
+ * points whose metric S is numerically singular (as thc_fit_kernel);
+ * THC_ERR_TIMEOUT if a device wait of the tensor-core contraction gave up. */
 thc_status thc_vo_gradient(const double* U, int nocc, const double* Uv, int nvir, const int* grid_host,
                            const double* lattice_host, const int* mesh_host, const int* points_host, int npts,
-                           const double* V, double* g_out, double* g_explicit_out, double* ex_host,
+                           const double* V, int precision, double* g_out, double* g_explicit_out, double* ex_host,
                            float* step_ms_host, void* stream);
 
 /* Learned interpolation-point proposal (setup, outside the timed build).  The

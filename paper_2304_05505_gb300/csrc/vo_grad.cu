@@ -25,10 +25,13 @@
 // The fit (B, R, S, its Cholesky factor, xi and xh) is recomputed here from the
 // orbitals with the same kernels as thc_fit_kernel; V is the caller's (the fit
 // of the same orbitals at the same points).  Every contraction is an FP64
-// complex GEMM on CUDA cores; the O(N_k N_P^2 N_G) one over (q, G) dominates,
-// as the fit's own V contraction does.
+// complex GEMM on CUDA cores, except that with THC_MIXED the O(N_k N_P^2 N_G)
+// one over (q, G), which dominates as the fit's own V contraction does, runs
+// on the tcgen05 tensor cores in the form of the rebuild's contraction.
 #include "isdf_common.cuh"
+#include "tc_gemm.cuh"
 
+#include <algorithm>
 #include <string>
 
 namespace {
@@ -129,6 +132,21 @@ __global__ void phase_w(const double2* __restrict__ W, int np, const double* __r
   const double cr = cp * cq + sp * sq, ci = sp * cq - cp * sq;
   const double2 w = W[i];
   A[i] = make_double2(c * (w.x * cr - w.y * ci), c * (w.x * ci + w.y * cr));
+}
+
+// The same, rounded to FP32, rows lda complex apart (the A operand of the
+// tensor-core contraction).
+__global__ void phase_w32(const double2* __restrict__ W, int np, const double* __restrict__ rP, double qx, double qy,
+                          double qz, double c, float2* __restrict__ A, int lda) {
+  const long i = (long)blockIdx.x * TB + threadIdx.x;
+  if (i >= (long)np * np) return;
+  const int P = (int)(i / np), Q = (int)(i % np);
+  double sp, cp, sq, cq;
+  sincos(-(qx * rP[3 * P] + qy * rP[3 * P + 1] + qz * rP[3 * P + 2]), &sp, &cp);
+  sincos(-(qx * rP[3 * Q] + qy * rP[3 * Q + 1] + qz * rP[3 * Q + 2]), &sq, &cq);
+  const double cr = cp * cq + sp * sq, ci = sp * cq - cp * sq;
+  const double2 w = W[i];
+  A[(long)P * lda + Q] = make_float2((float)(c * (w.x * cr - w.y * ci)), (float)(c * (w.x * ci + w.y * cr)));
 }
 
 // Bq[Q][G] = v(G + q) conj(F[Q][flat[G]]), K = (gm[G] + qf) B, v(K) = 4 pi / |K|^2 (0 for K = 0)
@@ -238,11 +256,12 @@ __global__ void combine_g(const double2* __restrict__ Ge, const double2* __restr
 
 extern "C" thc_status thc_vo_gradient(const double* U, int nocc, const double* Uv, int nvir, const int* grid_host,
                                       const double* lattice_host, const int* mesh_host, const int* points_host,
-                                      int npts, const double* V, double* g_out, double* g_explicit_out,
-                                      double* ex_host, float* step_ms_host, void* stream) {
+                                      int npts, const double* V, int precision, double* g_out,
+                                      double* g_explicit_out, double* ex_host, float* step_ms_host, void* stream) {
   if (!U || !Uv || !V || !g_out || !grid_host || !lattice_host || !mesh_host || !points_host || nocc < 1 ||
       nvir < 1 || npts < 1)
     return THC_ERR_ARG;
+  if (precision != THC_FP64 && precision != THC_MIXED) return THC_ERR_ARG;
   if (((uintptr_t)U & 15) || ((uintptr_t)Uv & 15) || ((uintptr_t)V & 15) || ((uintptr_t)g_out & 15) ||
       ((uintptr_t)g_explicit_out & 15))
     return THC_ERR_ARG;
@@ -285,6 +304,11 @@ extern "C" thc_status thc_vo_gradient(const double* U, int nocc, const double* U
   double2 *Z = nullptr, *T1 = nullptr, *T2 = nullptr, *Uvp = nullptr, *G1 = nullptr, *G2 = nullptr, *twd = nullptr;
   double *R = nullptr, *S = nullptr, *L = nullptr, *Lam = nullptr, *Sbar = nullptr, *rPd = nullptr, *part = nullptr;
   int *ptsd = nullptr, *gmd = nullptr, *flatd = nullptr, *bad = nullptr, *kqd = nullptr, *qkd = nullptr;
+  // tensor-core state of the (q, G) contraction (THC_MIXED)
+  float2* Aq32 = nullptr;
+  uint16_t* Bpl = nullptr;
+  int *eA = nullptr, *eB = nullptr, *ps0 = nullptr, *tcerr = nullptr;
+  float* pbc = nullptr;
   cudaError_t e = cudaSuccess;
   thc_status st = THC_OK;
   int hbad = 0;
@@ -392,10 +416,38 @@ extern "C" thc_status thc_vo_gradient(const double* U, int nocc, const double* U
     // 3. Gam = sum over q and its representatives of (c ph W^q ph^H) (v o conj(xh))
     mark(2);
     if ((e = cudaMalloc(&Gam, sizeof(double2) * (size_t)np * nG)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&Aq, sizeof(double2) * npq)) != cudaSuccess) break;
+    if (precision == THC_FP64 && (e = cudaMalloc(&Aq, sizeof(double2) * npq)) != cudaSuccess) break;
     if ((e = cudaMalloc(&Bq, sizeof(double2) * (size_t)np * nG)) != cudaSuccess) break;
     if ((e = cudaMalloc(&Z, sizeof(double2) * (size_t)np * nG)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(Gam, 0, sizeof(double2) * (size_t)np * nG, s)) != cudaSuccess) break;
+    // THC_MIXED: Z = A Bq on the tensor cores, A (FP32, sliced in the GEMM with
+    // its row exponents) against the embedded Bq (three fp16 slices with the
+    // exact column exponents of the FP64 Bq), 8 slice products, exact K chunks
+    // of at most 1024 reals combined in FP64
+    const bool tc = precision == THC_MIXED;
+    const int lda = np + (np & 1);                    // FP32 rows 16-byte strided
+    const int ldp = (2 * np + 7) & ~7;                // B plane rows: 2 np reals, padded
+    const long plane = 2L * nG * ldp;
+    TcOperand opA, opB;
+    if (tc) {
+      const long npart = tc_partial_elems(np, 2 * nG, 2 * np, 1);
+      if ((e = cudaMalloc(&Aq32, sizeof(float2) * (size_t)np * lda)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&Bpl, sizeof(uint16_t) * 3 * (size_t)plane)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&eA, sizeof(int) * np)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&eB, sizeof(int) * nG)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&tcerr, 64)) != cudaSuccess) break;
+      if (npart > 0) {
+        if ((e = cudaMalloc(&ps0, sizeof(int) * npart)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&pbc, sizeof(float) * npart)) != cudaSuccess) break;
+      }
+      if ((e = cudaMemsetAsync(tcerr, 0, 64, s)) != cudaSuccess) break;
+      if ((e = cudaMemsetAsync(Aq32, 0, sizeof(float2) * (size_t)np * lda, s)) != cudaSuccess) break;
+      if ((e = cudaMemsetAsync(Bpl, 0, sizeof(uint16_t) * 3 * (size_t)plane, s)) != cudaSuccess) break;
+      if ((e = make_f32_map(opA.map[0], Aq32, 1, np, 2 * np, 2 * lda)) != cudaSuccess) break;
+      for (int p = 0; p < 3 && e == cudaSuccess; p++)
+        e = make_plane_map(opB.map[p], Bpl + p * plane, 1, 2 * nG, 2 * np, ldp);
+      if (e != cudaSuccess) break;
+    }
     const double sc = geo.vol / ng;
     const Recip& B = geo.B;
     for (int q = 0; q < nk && e == cudaSuccess; q++) {
@@ -410,9 +462,23 @@ extern "C" thc_status thc_vo_gradient(const double* U, int nocc, const double* U
             const double qx = x0 * B.b[0] + x1 * B.b[3] + x2 * B.b[6];
             const double qy = x0 * B.b[1] + x1 * B.b[4] + x2 * B.b[7];
             const double qz = x0 * B.b[2] + x1 * B.b[5] + x2 * B.b[8];
-            phase_w<<<blocks(npq), TB, 0, s>>>(W + (long)q * npq, np, rPd, qx, qy, qz, c, Aq);
             coulomb_conj<<<blocks((long)np * nG), TB, 0, s>>>(F, ng, flatd, gmd, nG, np, B, x0, x1, x2, Bq);
-            if ((e = gemm_z(A_MK, B_KN, np, nG, np, Aq, np, 0, Bq, nG, 0, Z, nG, 0, 1, s)) != cudaSuccess) break;
+            if (!tc) {
+              phase_w<<<blocks(npq), TB, 0, s>>>(W + (long)q * npq, np, rPd, qx, qy, qz, c, Aq);
+              if ((e = gemm_z(A_MK, B_KN, np, nG, np, Aq, np, 0, Bq, nG, 0, Z, nG, 0, 1, s)) != cudaSuccess) break;
+            } else {
+              phase_w32<<<blocks(npq), TB, 0, s>>>(W + (long)q * npq, np, rPd, qx, qy, qz, c, Aq32, lda);
+              if ((e = row_exponents_c(Aq32, 0, lda, 1, np, np, eA, s)) != cudaSuccess) break;
+              if ((e = col_exponents_z(Bq, 0, nG, 1, np, nG, eB, s)) != cudaSuccess) break;
+              // embedded in slabs of G (the embedding's grid holds at most 131,070 rows j)
+              for (int g0 = 0; g0 < nG && e == cudaSuccess; g0 += 65536)
+                e = embed_b(Bq + g0, true, 0, nG, 1, false, false, 1, np, std::min(65536, nG - g0), eB + g0,
+                            Bpl + 2L * g0 * ldp, plane, ldp, s);
+              if (e != cudaSuccess) break;
+              if ((e = tc_gemm(opA, opB, np, 2 * nG, 2 * np, 1, eA, np, eB, nG, Z, true, 2L * nG, 2L * np * nG, ps0,
+                               pbc, tcerr, s, nullptr, 8, 1, 0)) != cudaSuccess)
+                break;
+            }
             axpy_z<<<blocks((long)np * nG), TB, 0, s>>>(Gam, Z, (long)np * nG);
           }
     }
@@ -471,6 +537,15 @@ extern "C" thc_status thc_vo_gradient(const double* U, int nocc, const double* U
     mark(5);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+    if (tcerr) {
+      int h = 0;
+      if ((e = cudaMemcpy(&h, tcerr, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+      if (h) {
+        st = THC_ERR_TIMEOUT;
+        set_global_error("thc_vo_gradient: a device wait of the tensor-core contraction timed out");
+        break;
+      }
+    }
     if (ex_host) {
       double acc = 0.0;
       for (int i = 0; i < NPART; i++) acc += hpart[i];
@@ -488,7 +563,7 @@ extern "C" thc_status thc_vo_gradient(const double* U, int nocc, const double* U
   }
   void* ptrs[] = {Psi, Psivt, D,   M,   W,  Y,  Ge,  Ugc,   Bm,    F,    T,     Gam,  Aq,  Bq,  Z,
                   T1,  T2,    Uvp, G1,  G2, twd, R,  S,     L,     Lam,  Sbar,  rPd,  part, ptsd, gmd,
-                  flatd, bad, kqd, qkd};
+                  flatd, bad, kqd, qkd, Aq32, Bpl, eA,  eB,  ps0, pbc, tcerr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& x : ev)

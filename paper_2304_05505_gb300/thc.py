@@ -90,7 +90,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_fit_kernel.argtypes = [dp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, dp, dp, vp]
     lib.thc_vo_gradient.argtypes = [dp, ip, dp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
-                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, dp, dp, dp,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, dp, ip, dp, dp,
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), vp]
     fp = ctypes.POINTER(ctypes.c_float)
     lib.thc_mlp_features.argtypes = [dp, ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
@@ -372,10 +372,11 @@ def thc_rebuild_kernel(U, grid, lattice, mesh, points, precision="mixed", stream
     return V, [float(x) for x in ms]
 
 
-def thc_vo_gradient(U, Uv, nk: int, grid, lattice, mesh, points, V, stream: int | None = None):
+def thc_vo_gradient(U, Uv, nk: int, grid, lattice, mesh, points, V, precision="fp64", stream: int | None = None):
     """The THC-oo-K orbital gradient with the kernel's response (see
     include/thc.h): U [N_k n_occ][N_g] and Uv [N_k n_vir][N_g] complex128 CUDA
-    tensors, V [N_k][npts][npts] the kernel fitted to U at `points`.  Returns
+    tensors, V [N_k][npts][npts] the kernel fitted to U at `points`;
+    precision "fp64" or "mixed" (the (q, G) contraction on tensor cores).  Returns
     (g, g_explicit, E_x, step_ms): g and g_explicit [N_k][n_vir][n_occ]
     complex128 CUDA tensors (the full gradient and its fixed-kernel term), E_x
     from sum_q W^q o V^q, and the device ms of the five steps."""
@@ -401,7 +402,8 @@ def thc_vo_gradient(U, Uv, nk: int, grid, lattice, mesh, points, V, stream: int 
     ms = (ctypes.c_float * 5)()
     _check(load().thc_vo_gradient(_dev_ptr(U, (nfo, ng), name="U"), nocc, _dev_ptr(Uv, (nfv, ng), name="Uv"), nvir,
                                   g, lat, m, pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), npts,
-                                  _dev_ptr(V, (nk, npts, npts), name="V"), gout.data_ptr(), gexp.data_ptr(),
+                                  _dev_ptr(V, (nk, npts, npts), name="V"), int(PRECISIONS.get(precision, precision)),
+                                  gout.data_ptr(), gexp.data_ptr(),
                                   ctypes.byref(ex), ms, ctypes.c_void_p(stream)),
            "thc_vo_gradient")
     return gout, gexp, float(ex.value), [float(x) for x in ms]

@@ -2,10 +2,17 @@
 FP64 oracle (oracle/vo_oracle.py: autograd of the energy with the fit redone,
 pinned by finite differences in test_oracle_vo.py).
 
-Both sides are FP64.  The CUDA path solves the fit's metric by Cholesky and
-sums in another order than the oracle's LU solve and torch reductions; with
-cond(S) below 1e5 on these cells the two agree to about 1e-11 of max|g|, and
-the bound is 1e-9 of max|g| per element."""
+FP64 form: both sides are FP64.  The CUDA path solves the fit's metric by
+Cholesky and sums in another order than the oracle's LU solve and torch
+reductions; a Cholesky-based FP64 restatement of the same steps differs from
+the oracle by 2e-14 to 5e-12 of max|g| on these cells (cond(S) up to 1e6), and
+the bound is 1e-9 of max|g| per element.
+
+Mixed form: the (q, G) contraction takes its operands rounded to FP32 (then
+sliced exactly); the same steps with FP32-rounded operands and exact products
+differ from the oracle by 1e-7 to 5e-7 of max|g| on these cells, and the bound
+is 5e-6 of max|g|.  The fixed-kernel term and E_x do not go through that
+contraction and keep the FP64 bounds."""
 import numpy as np
 import pytest
 
@@ -50,12 +57,17 @@ CASES = [
 ]
 
 
+BOUND = {"fp64": 1e-9, "mixed": 5e-6}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("mesh,grid,nvir,npts", CASES)
-def test_vo_gradient_matches_oracle(thc, mesh, grid, nvir, npts):
+def test_vo_gradient_matches_oracle(thc, mesh, grid, nvir, npts, precision):
     c, p, C, Cv, U, Uv, V = _problem(mesh, grid, nvir, npts)
     dev = torch.device("cuda:0")
     g, ge, ex, ms = thc.thc_vo_gradient(torch.from_numpy(U).to(dev), torch.from_numpy(Uv).to(dev), C.shape[0],
-                                        c.grid, c.lattice, c.mesh, p["points"], torch.from_numpy(V).to(dev))
+                                        c.grid, c.lattice, c.mesh, p["points"], torch.from_numpy(V).to(dev),
+                                        precision)
     torch.cuda.synchronize()
     g, ge = g.cpu().numpy(), ge.cpu().numpy()
     ref = VO.vo_gradient(p, C, Cv)
@@ -63,7 +75,7 @@ def test_vo_gradient_matches_oracle(thc, mesh, grid, nvir, npts):
     E = VO.energy(p, C, V)
     scale = np.abs(ref).max()
     assert np.abs(ge - ref_e).max() <= 1e-9 * scale
-    assert np.abs(g - ref).max() <= 1e-9 * scale
+    assert np.abs(g - ref).max() <= BOUND[precision] * scale
     assert abs(ex - E) <= 1e-12 * abs(E)
     # the kernel's response is a large part of the gradient on these cells
     assert np.abs(g - ge).max() >= 0.05 * scale
