@@ -1,6 +1,7 @@
 // The THC-oo-K orbital gradient: the vo block of the exchange matrix with the
 // kernel's response to the orbitals (Sec. 2.3, the K_ai expression and
-// Algorithm 2's dM/dtheta step), FP64 throughout.
+// Algorithm 2's dM/dtheta step), in FP64, with the dominant contraction on
+// the tensor cores in the THC_MIXED form.
 //
 // With D^k = Psi^k Psi^kH at the points (Psi^k[P][i] = psi^k_i(r_P)) the
 // energy is a sum over q,
