@@ -318,9 +318,13 @@ thc_status thc_rebuild_kernel(const double* U, int nfunc, const int* grid_host, 
  * O(N_k npts^2 N_G) step that dominates, runs on the tcgen05 tensor cores as
  * thc_rebuild_kernel's contraction does (W^q with its phases rounded to FP32
  * and sliced in the GEMM, v(G+q) conj(xh) cut into three fp16 slices with
- * exact column exponents, 8 slice products, exact K chunks combined in FP64);
- * every other step stays FP64 (g about 1e-7 to 1e-6 of max|g| from the FP64
- * form).  g_out: device, [N_k][n_vir][n_occ] complex128.
+ * exact exponents, 8 slice products, exact K chunks combined in FP64), and so
+ * do the three grid contractions back to the orbitals (sum over r of the
+ * adjoint of |B|^2 with U, over the points with conj(U) at them, and over r
+ * of Uv with the result) when 2 N_G <= 126 * 1024; the fixed-kernel part, the
+ * fit and the adjoint DFT and solve stay FP64 (g about 1e-7 to 1e-5 of
+ * max|g| from the FP64 form, depending on the metric's conditioning).
+ * g_out: device, [N_k][n_vir][n_occ] complex128.
  * g_explicit_out: the same shape, or NULL.  ex_host (host, may be NULL):
  * E_x from W and V.  step_ms_host (host, 5 floats, may be NULL): the device
  * ms of the fixed-kernel part, the fit, the (q, G) contraction, the adjoint

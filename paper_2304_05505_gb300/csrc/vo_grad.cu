@@ -27,8 +27,9 @@
 // orbitals with the same kernels as thc_fit_kernel; V is the caller's (the fit
 // of the same orbitals at the same points).  Every contraction is an FP64
 // complex GEMM on CUDA cores, except that with THC_MIXED the O(N_k N_P^2 N_G)
-// one over (q, G), which dominates as the fit's own V contraction does, runs
-// on the tcgen05 tensor cores in the form of the rebuild's contraction.
+// one over (q, G), which dominates as the fit's own V contraction does, and
+// the grid contractions T1, T2 and the projection of T2 run on the tcgen05
+// tensor cores in the form of the rebuild's contraction.
 #include "isdf_common.cuh"
 #include "tc_gemm.cuh"
 
@@ -253,6 +254,74 @@ __global__ void combine_g(const double2* __restrict__ Ge, const double2* __restr
   if (gexp) gexp[i] = e;
 }
 
+// dst[r][c] = (float2) src[r][c] for r < rows, c < cols (rows lds / ldd apart)
+__global__ void to_f32_rows(const double2* __restrict__ src, long rows, int cols, long lds, float2* __restrict__ dst,
+                            int ldd) {
+  const long i = (long)blockIdx.x * TB + threadIdx.x;
+  if (i >= rows * cols) return;
+  const long r = i / cols;
+  const int c = (int)(i % cols);
+  const double2 v = src[r * lds + c];
+  dst[r * ldd + c] = make_float2((float)v.x, (float)v.y);
+}
+
+// A[f][P] = conj(U[f][pts[P]]) in FP32, rows lda apart
+__global__ void gather_conj_t32(const double2* __restrict__ U, int nf, long ng, const int* __restrict__ pts, int np,
+                                float2* __restrict__ A, int lda) {
+  const long i = (long)blockIdx.x * TB + threadIdx.x;
+  if (i >= (long)nf * np) return;
+  const int f = (int)(i / np), P = (int)(i % np);
+  const double2 u = U[(long)f * ng + pts[P]];
+  A[(long)f * lda + P] = make_float2((float)u.x, (float)-u.y);
+}
+
+// out[b][m][n] = sum_k A[b][m][k] B[b](k, n) on the tensor cores, in the form of
+// the kernel rebuild's contraction: A complex FP32 [batch][M][lda] (contiguous
+// batches) sliced in the GEMM with its row exponents eA[b M + m]; B(k, n) =
+// src[b sbs + k ldk + n ldj] complex128, embedded as three fp16 slices with
+// exponents eB[b N + n] (no smaller than the exponent of max_k |B(k, n)|); 8
+// slice products, exact K chunks of at most 1024 reals combined in FP64; out
+// complex128 with rows ldo and batches sbo complex apart.  Allocates its planes
+// and partial sums and frees them before returning.
+cudaError_t tc_product(const float2* A, int lda, const int* eA, const double2* src, long sbs, long ldk, long ldj,
+                       const int* eB, int batch, int M, int N, int K, double2* out, long ldo, long sbo, int* err,
+                       cudaStream_t s) {
+  if (batch > 1 && N > 65536) return cudaErrorInvalidValue;   // the embedding takes one slab of N per batch
+  const int ldp = (2 * K + 7) & ~7;
+  const long plane = (long)batch * 2 * N * ldp;
+  const long npart = tc_partial_elems(M, 2 * N, 2 * K, batch);
+  uint16_t* pl = nullptr;
+  int* ps0 = nullptr;
+  float* pbc = nullptr;
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((e = cudaMalloc(&pl, sizeof(uint16_t) * 3 * (size_t)plane)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(pl, 0, sizeof(uint16_t) * 3 * (size_t)plane, s)) != cudaSuccess) break;
+    if (npart > 0) {
+      if ((e = cudaMalloc(&ps0, sizeof(int) * npart)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&pbc, sizeof(float) * npart)) != cudaSuccess) break;
+    }
+    TcOperand opA, opB;
+    if ((e = make_f32_map(opA.map[0], A, batch, M, 2 * K, 2 * lda)) != cudaSuccess) break;
+    for (int p = 0; p < 3 && e == cudaSuccess; p++) e = make_plane_map(opB.map[p], pl + p * plane, batch, 2 * N, 2 * K, ldp);
+    if (e != cudaSuccess) break;
+    if (batch == 1) {
+      for (int n0 = 0; n0 < N && e == cudaSuccess; n0 += 65536)
+        e = embed_b(src + n0 * ldj, true, 0, ldk, ldj, false, false, 1, K, std::min(65536, N - n0), eB + n0,
+                    pl + 2L * n0 * ldp, plane, ldp, s);
+    } else {
+      e = embed_b(src, true, sbs, ldk, ldj, false, false, batch, K, N, eB, pl, plane, ldp, s);
+    }
+    if (e != cudaSuccess) break;
+    e = tc_gemm(opA, opB, M, 2 * N, 2 * K, batch, eA, M, eB, N, out, true, 2 * ldo, 2 * sbo, ps0, pbc, err, s,
+                nullptr, 8, 1, 0);
+  } while (0);
+  void* ptrs[] = {pl, ps0, pbc};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  return e;
+}
+
 }  // namespace
 
 extern "C" thc_status thc_vo_gradient(const double* U, int nocc, const double* Uv, int nvir, const int* grid_host,
@@ -310,6 +379,9 @@ extern "C" thc_status thc_vo_gradient(const double* U, int nocc, const double* U
   uint16_t* Bpl = nullptr;
   int *eA = nullptr, *eB = nullptr, *ps0 = nullptr, *tcerr = nullptr;
   float* pbc = nullptr;
+  // ... and of the orbital contractions
+  float2 *Y32 = nullptr, *A2 = nullptr, *Uv32 = nullptr;
+  int* eOrb = nullptr;
   cudaError_t e = cudaSuccess;
   thc_status st = THC_OK;
   int hbad = 0;
@@ -522,15 +594,56 @@ extern "C" thc_status thc_vo_gradient(const double* U, int nocc, const double* U
     if ((e = cudaMalloc(&Uvp, sizeof(double2) * (size_t)nk * nvir * np)) != cudaSuccess) break;
     if ((e = cudaMalloc(&G1, sizeof(double2) * ngo)) != cudaSuccess) break;
     if ((e = cudaMalloc(&G2, sizeof(double2) * ngo)) != cudaSuccess) break;
-    if ((e = gemm_z(A_MK, B_NK, np, nf, (int)ng, Bm, (int)ng, 0, U2, (int)ng, 0, T1, nf, 0, 1, s)) != cudaSuccess)
-      break;
-    if ((e = gemm_z(A_KM, B_KN, nf, (int)ng, np, Ugc, nf, 0, Bm, (int)ng, 0, T2, (int)ng, 0, 1, s)) != cudaSuccess)
-      break;
+    // THC_MIXED: T1, T2 and the projection of T2 on the tensor cores when the
+    // grid sum fits the exact K chunks of one product (2 N_G reals in at most
+    // 126 chunks of 1024); else, and in THC_FP64, FP64 GEMMs
+    const bool tc_orb = tc && 2L * ng <= 126L * 1024;
+    if (!tc_orb) {
+      if ((e = gemm_z(A_MK, B_NK, np, nf, (int)ng, Bm, (int)ng, 0, U2, (int)ng, 0, T1, nf, 0, 1, s)) != cudaSuccess)
+        break;
+      if ((e = gemm_z(A_KM, B_KN, nf, (int)ng, np, Ugc, nf, 0, Bm, (int)ng, 0, T2, (int)ng, 0, 1, s)) !=
+          cudaSuccess)
+        break;
+      if ((e = gemm_z(A_MK, B_NK, nvir, nocc, (int)ng, Uv2, (int)ng, (long)nvir * ng, T2, (int)ng, (long)nocc * ng,
+                      G1, nocc, (long)nvir * nocc, nk, s)) != cudaSuccess)
+        break;
+    } else {
+      const int ldy = (int)(ng + (ng & 1));           // FP32 grid rows 16-byte strided
+      const int lda2 = np + (np & 1);
+      const long nfv = (long)nk * nvir;
+      if ((e = cudaMalloc(&Y32, sizeof(float2) * (size_t)np * ldy)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&A2, sizeof(float2) * (size_t)nf * lda2)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&Uv32, sizeof(float2) * (size_t)nfv * ldy)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&eOrb, sizeof(int) * (size_t)(np + 3L * nf + ng + nfv))) != cudaSuccess) break;
+      int* eY = eOrb;
+      int* eU = eY + np;
+      int* eA2 = eU + nf;
+      int* eT2 = eA2 + nf;
+      int* eBm = eT2 + nf;
+      int* eUv = eBm + ng;
+      // T1[P][f] = sum_r Y2[P][r] U[f][r]
+      to_f32_rows<<<blocks((long)np * ng), TB, 0, s>>>(Bm, np, (int)ng, ng, Y32, ldy);
+      if ((e = row_exponents_c(Y32, 0, ldy, 1, np, (int)ng, eY, s)) != cudaSuccess) break;
+      if ((e = row_exponents_z(U2, 0, (int)ng, 1, nf, (int)ng, eU, s)) != cudaSuccess) break;
+      if ((e = tc_product(Y32, ldy, eY, U2, 0, 1, ng, eU, 1, np, nf, (int)ng, T1, nf, 0, tcerr, s)) != cudaSuccess)
+        break;
+      // T2[f][r] = sum_P conj(U[f][r_P]) Y2[P][r]
+      gather_conj_t32<<<blocks((long)nf * np), TB, 0, s>>>(U2, nf, ng, ptsd, np, A2, lda2);
+      if ((e = row_exponents_c(A2, 0, lda2, 1, nf, np, eA2, s)) != cudaSuccess) break;
+      if ((e = col_exponents_z(Bm, 0, (int)ng, 1, np, (int)ng, eBm, s)) != cudaSuccess) break;
+      if ((e = tc_product(A2, lda2, eA2, Bm, 0, ng, 1, eBm, 1, nf, (int)ng, np, T2, ng, 0, tcerr, s)) !=
+          cudaSuccess)
+        break;
+      // G1^k[a][i] = sum_r Uv[(k,a)][r] T2[(k,i)][r]
+      to_f32_rows<<<blocks(nfv * ng), TB, 0, s>>>(Uv2, nfv, (int)ng, ng, Uv32, ldy);
+      if ((e = row_exponents_c(Uv32, 0, ldy, 1, (int)nfv, (int)ng, eUv, s)) != cudaSuccess) break;
+      if ((e = row_exponents_z(T2, 0, (int)ng, 1, nf, (int)ng, eT2, s)) != cudaSuccess) break;
+      if ((e = tc_product(Uv32, ldy, eUv, T2, (long)nocc * ng, 1, ng, eT2, nk, nvir, nocc, (int)ng, G1, nocc,
+                          (long)nvir * nocc, tcerr, s)) != cudaSuccess)
+        break;
+    }
     point_values<<<blocks((long)nk * nvir * np), TB, 0, s>>>(Uv2, nk, nvir, ng, ptsd, np, g1, g2, g3, n1, n2, n3,
                                                              false, true, Uvp);
-    if ((e = gemm_z(A_MK, B_NK, nvir, nocc, (int)ng, Uv2, (int)ng, (long)nvir * ng, T2, (int)ng, (long)nocc * ng, G1,
-                    nocc, (long)nvir * nocc, nk, s)) != cudaSuccess)
-      break;
     if ((e = gemm_z(A_MK_CONJ, B_KN, nvir, nocc, np, Uvp, np, (long)nvir * np, T1, nf, nocc, G2, nocc,
                     (long)nvir * nocc, nk, s)) != cudaSuccess)
       break;
@@ -564,7 +677,7 @@ extern "C" thc_status thc_vo_gradient(const double* U, int nocc, const double* U
   }
   void* ptrs[] = {Psi, Psivt, D,   M,   W,  Y,  Ge,  Ugc,   Bm,    F,    T,     Gam,  Aq,  Bq,  Z,
                   T1,  T2,    Uvp, G1,  G2, twd, R,  S,     L,     Lam,  Sbar,  rPd,  part, ptsd, gmd,
-                  flatd, bad, kqd, qkd, Aq32, Bpl, eA,  eB,  ps0, pbc, tcerr};
+                  flatd, bad, kqd, qkd, Aq32, Bpl, eA,  eB,  ps0, pbc, tcerr, Y32, A2, Uv32, eOrb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& x : ev)

@@ -8,10 +8,11 @@ reductions; a Cholesky-based FP64 restatement of the same steps differs from
 the oracle by 2e-14 to 5e-12 of max|g| on these cells (cond(S) up to 1e6), and
 the bound is 1e-9 of max|g| per element.
 
-Mixed form: the (q, G) contraction takes its operands rounded to FP32 (then
-sliced exactly); the same steps with FP32-rounded operands and exact products
-differ from the oracle by 1e-7 to 5e-7 of max|g| on these cells, and the bound
-is 5e-6 of max|g|.  The fixed-kernel term and E_x do not go through that
+Mixed form: the (q, G) contraction and the grid contractions back to the
+orbitals take their operands rounded to FP32 (then sliced exactly); the same
+steps with FP32-rounded operands and exact products differ from the oracle by
+1e-7 to 5e-7 of max|g| on these cells for each of the two, and the bound is
+5e-6 of max|g|.  The fixed-kernel term and E_x do not go through that
 contraction and keep the FP64 bounds."""
 import numpy as np
 import pytest
