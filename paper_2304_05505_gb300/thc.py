@@ -375,37 +375,57 @@ def thc_rebuild_kernel(U, grid, lattice, mesh, points, precision="mixed", stream
 def thc_vo_gradient(U, Uv, nk: int, grid, lattice, mesh, points, V, precision="fp64", stream: int | None = None):
     """The THC-oo-K orbital gradient with the kernel's response (see
     include/thc.h): U [N_k n_occ][N_g] and Uv [N_k n_vir][N_g] complex128 CUDA
-    tensors, V [N_k][npts][npts] the kernel fitted to U at `points`;
-    precision "fp64" or "mixed" (the (q, G) contraction on tensor cores).  Returns
-    (g, g_explicit, E_x, step_ms): g and g_explicit [N_k][n_vir][n_occ]
-    complex128 CUDA tensors (the full gradient and its fixed-kernel term), E_x
-    from sum_q W^q o V^q, and the device ms of the five steps."""
+    tensors, V [N_k][npts][npts] the kernel fitted to U at `points`, all on one
+    device; precision "fp64" or "mixed" (the grid-sized contractions on the
+    tensor cores).  Sizes and devices are checked here, before anything is
+    allocated or queued; the call runs on that device (its current stream
+    unless `stream` is given).  Returns (g, g_explicit, E_x, step_ms): g and
+    g_explicit [N_k][n_vir][n_occ] complex128 CUDA tensors (the full gradient
+    and its fixed-kernel term), E_x from sum_q W^q o V^q, and the device ms of
+    the five steps."""
     import torch
-    if stream is None:
-        stream = torch.cuda.current_stream().cuda_stream
     nk = int(nk)
+    for t, nm in ((U, "U"), (Uv, "Uv"), (V, "V")):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{nm}: expected a CUDA tensor")
+    if U.dim() != 2 or Uv.dim() != 2 or Uv.shape[1] != U.shape[1]:
+        raise ValueError("U and Uv must be [rows][N_g] with the same N_g")
     nfo, ng = U.shape
     nfv = Uv.shape[0]
-    if nfo % nk or nfv % nk:
-        raise ValueError("U and Uv rows must be N_k times the orbitals per k")
-    nocc, nvir = nfo // nk, nfv // nk
-    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
-    m = (ctypes.c_int * 3)(*[int(x) for x in mesh])
     if int(np.prod([int(x) for x in mesh])) != nk:
         raise ValueError("nk must be the number of k-mesh points")
-    lat = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(lattice, dtype=np.float64).ravel()])
+    if int(np.prod([int(x) for x in grid])) != ng:
+        raise ValueError("the grid must have N_g points, the length of the rows of U")
+    if nfo % nk or nfv % nk or nfo == 0 or nfv == 0:
+        raise ValueError("U and Uv rows must be N_k times the orbitals per k")
+    nocc, nvir = nfo // nk, nfv // nk
     pts = np.ascontiguousarray(np.asarray(points, dtype=np.int32))
     npts = int(pts.size)
-    gout = torch.empty((nk, nvir, nocc), dtype=torch.complex128, device=U.device)
-    gexp = torch.empty_like(gout)
-    ex = ctypes.c_double(0.0)
-    ms = (ctypes.c_float * 5)()
-    _check(load().thc_vo_gradient(_dev_ptr(U, (nfo, ng), name="U"), nocc, _dev_ptr(Uv, (nfv, ng), name="Uv"), nvir,
-                                  g, lat, m, pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), npts,
-                                  _dev_ptr(V, (nk, npts, npts), name="V"), int(PRECISIONS.get(precision, precision)),
-                                  gout.data_ptr(), gexp.data_ptr(),
-                                  ctypes.byref(ex), ms, ctypes.c_void_p(stream)),
-           "thc_vo_gradient")
+    if tuple(V.shape) != (nk, npts, npts):
+        raise ValueError(f"V: shape {tuple(V.shape)} != {(nk, npts, npts)}")
+    if precision not in PRECISIONS and precision not in PRECISIONS.values():
+        raise ValueError(f"precision: {precision!r}")
+    for t, nm in ((U, "U"), (Uv, "Uv"), (V, "V")):
+        if not t.is_cuda:
+            raise TypeError(f"{nm}: expected a CUDA tensor")
+    if not (U.device == Uv.device == V.device):
+        raise ValueError("U, Uv and V must be on one device")
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    m = (ctypes.c_int * 3)(*[int(x) for x in mesh])
+    lat = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(lattice, dtype=np.float64).ravel()])
+    with torch.cuda.device(U.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(U.device).cuda_stream
+        gout = torch.empty((nk, nvir, nocc), dtype=torch.complex128, device=U.device)
+        gexp = torch.empty_like(gout)
+        ex = ctypes.c_double(0.0)
+        ms = (ctypes.c_float * 5)()
+        _check(load().thc_vo_gradient(_dev_ptr(U, (nfo, ng), name="U"), nocc, _dev_ptr(Uv, (nfv, ng), name="Uv"),
+                                      nvir, g, lat, m, pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), npts,
+                                      _dev_ptr(V, (nk, npts, npts), name="V"),
+                                      int(PRECISIONS.get(precision, precision)), gout.data_ptr(), gexp.data_ptr(),
+                                      ctypes.byref(ex), ms, ctypes.c_void_p(stream)),
+               "thc_vo_gradient")
     return gout, gexp, float(ex.value), [float(x) for x in ms]
 
 

@@ -122,3 +122,44 @@ def test_memory_bytes_extended_form():
     assert thc.thc_memory_bytes(d, thc.THC_MIXED_EXT) - thc.thc_memory_bytes(d, thc.THC_MIXED) == 4 * nk * P * P
     for other in (dict(d, n1=3, n2=3, n3=3), dict(d, n1=4, n2=4, n3=2), dict(d, nisdf=1202)):
         assert thc.thc_memory_bytes(other, thc.THC_MIXED_EXT) == thc.thc_memory_bytes(other, thc.THC_MIXED)
+
+
+def _vo_args(nk=2, nocc=3, nvir=2, grid=(4, 3, 2), npts=5, **over):
+    import torch
+    ng = grid[0] * grid[1] * grid[2]
+    a = dict(U=torch.zeros((nk * nocc, ng), dtype=torch.complex128),
+             Uv=torch.zeros((nk * nvir, ng), dtype=torch.complex128), nk=nk, grid=grid,
+             lattice=[[5.0, 0, 0], [0, 5.0, 0], [0, 0, 5.0]], mesh=(nk, 1, 1), points=list(range(npts)),
+             V=torch.zeros((nk, npts, npts), dtype=torch.complex128))
+    a.update(over)
+    return a
+
+
+@pytest.mark.parametrize("change,exc", [
+    (dict(nk=3), ValueError),                                    # mesh has 2 points
+    (dict(grid=(4, 3, 3)), ValueError),                          # N_g of U is 24
+    (dict(points=list(range(6))), ValueError),                   # V is [2][5][5]
+    (dict(precision="fp32"), ValueError),
+    ({}, TypeError),                                             # CPU tensors
+])
+def test_vo_gradient_wrapper_checks_before_launch(change, exc):
+    """The binding of thc_vo_gradient rejects inconsistent sizes, an unknown
+    precision and non-CUDA tensors on the host, before any allocation or
+    launch (so no call reaches the library here)."""
+    a = _vo_args()
+    change = dict(change)
+    prec = change.pop("precision", "fp64")
+    a.update(change)
+    with pytest.raises(exc):
+        thc.thc_vo_gradient(a["U"], a["Uv"], a["nk"], a["grid"], a["lattice"], a["mesh"], a["points"], a["V"], prec)
+
+
+def test_vo_gradient_wrapper_rejects_mismatched_rows():
+    import torch
+    a = _vo_args()
+    bad = torch.zeros((5, 24), dtype=torch.complex128)   # 5 rows is not a multiple of N_k = 2
+    with pytest.raises(ValueError):
+        thc.thc_vo_gradient(bad, a["Uv"], 2, a["grid"], a["lattice"], a["mesh"], a["points"], a["V"])
+    with pytest.raises(ValueError):
+        thc.thc_vo_gradient(a["U"], torch.zeros((4, 23), dtype=torch.complex128), 2, a["grid"], a["lattice"],
+                            a["mesh"], a["points"], a["V"])
