@@ -112,3 +112,23 @@ def test_full_grid_gradient_is_the_grid_exchange_gradient():
     fd = _directional_fd(
         lambda s: S.brute_force_exchange(c.lattice, c.grid, c.mesh, Xg, C + s * (Cv @ th))["Ex"])
     assert abs(fd - pred) <= 1e-8 * np.abs(g).sum() * np.abs(th).max()
+
+
+def test_refit_gradient_on_a_zone_boundary_mesh():
+    """The same finite-difference pin on a 2x2x1 mesh, whose q = (1/2, ., .)
+    have two minimum-image representatives each (the kernel averages them),
+    and a 7x6x5 grid (odd axes keep every frequency, the even one drops its
+    Nyquist plane)."""
+    c = cells.make_cell("C0", mesh=(2, 2, 1), grid=(7, 6, 5))
+    kf = cells.kmesh_frac(c.mesh)
+    Xg = cells.bloch_collocation(c, cells.grid_points(c, 1), kf)
+    C, Cv = cells.orbital_coefficients(c, 3)
+    p = dict(lattice=c.lattice, grid=c.grid, mesh=c.mesh, kfrac=kf, Xg=Xg, points=None)
+    p["points"] = S.pivoted_cholesky(VO.grid_orbitals(p, C), 30)["points"]
+    g = VO.vo_gradient(p, C, Cv)
+    rng = np.random.default_rng(11)
+    for _ in range(2):
+        th = rng.normal(size=g.shape) + 1j * rng.normal(size=g.shape)
+        pred = float(np.real(np.sum(g.conj() * th)))
+        fd = _directional_fd(lambda s: VO.energy(p, C + s * (Cv @ th)))
+        assert abs(fd - pred) <= 1e-8 * np.abs(g).sum() * np.abs(th).max()
