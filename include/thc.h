@@ -321,7 +321,7 @@ thc_status thc_rebuild_kernel(const double* U, int nfunc, const int* grid_host, 
  * exact exponents, 8 slice products, exact K chunks combined in FP64), and so
  * do the three grid contractions back to the orbitals (sum over r of the
  * adjoint of |B|^2 with U, over the points with conj(U) at them, and over r
- * of Uv with the result) when 2 N_G <= 126 * 1024; the fixed-kernel part, the
+ * of Uv with the result) when 2 N_g <= 126 * 1024; the fixed-kernel part, the
  * fit and the adjoint DFT and solve stay FP64 (g about 1e-7 to 1e-5 of
  * max|g| from the FP64 form, depending on the metric's conditioning).
  * g_out: device, [N_k][n_vir][n_occ] complex128.

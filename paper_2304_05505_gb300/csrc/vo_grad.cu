@@ -595,7 +595,7 @@ extern "C" thc_status thc_vo_gradient(const double* U, int nocc, const double* U
     if ((e = cudaMalloc(&G1, sizeof(double2) * ngo)) != cudaSuccess) break;
     if ((e = cudaMalloc(&G2, sizeof(double2) * ngo)) != cudaSuccess) break;
     // THC_MIXED: T1, T2 and the projection of T2 on the tensor cores when the
-    // grid sum fits the exact K chunks of one product (2 N_G reals in at most
+    // grid sum fits the exact K chunks of one product (2 N_g reals in at most
     // 126 chunks of 1024); else, and in THC_FP64, FP64 GEMMs
     const bool tc_orb = tc && 2L * ng <= 126L * 1024;
     if (!tc_orb) {
