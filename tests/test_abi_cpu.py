@@ -163,3 +163,28 @@ def test_vo_gradient_wrapper_rejects_mismatched_rows():
     with pytest.raises(ValueError):
         thc.thc_vo_gradient(a["U"], torch.zeros((4, 23), dtype=torch.complex128), 2, a["grid"], a["lattice"],
                             a["mesh"], a["points"], a["V"])
+
+
+def _vo_call(lib, U=256, nocc=2, Uv=512, nvir=2, grid=(4, 3, 2), mesh=(2, 1, 1), points=(0, 1, 2), V=768,
+             precision=0, g=1024):
+    gr = (ctypes.c_int * 3)(*grid)
+    me = (ctypes.c_int * 3)(*mesh)
+    lat = (ctypes.c_double * 9)(5.0, 0, 0, 0, 5.0, 0, 0, 0, 5.0)
+    pts = (ctypes.c_int * len(points))(*points)
+    return lib.thc_vo_gradient(ctypes.c_void_p(U), nocc, ctypes.c_void_p(Uv), nvir, gr, lat, me, pts, len(points),
+                               ctypes.c_void_p(V), precision, ctypes.c_void_p(g), None, None, None, None)
+
+
+@pytest.mark.parametrize("change", [
+    dict(U=0), dict(Uv=0), dict(V=0), dict(g=0),            # null pointers
+    dict(U=264),                                             # not 16-byte aligned
+    dict(nocc=0), dict(nvir=0),
+    dict(precision=2),                                       # only THC_FP64 and THC_MIXED
+    dict(points=(0, 1, 1)),                                  # repeated point
+    dict(points=(0, 24)),                                    # out of the 24-point grid
+    dict(mesh=(9, 1, 1)),                                    # mesh axis above 8
+])
+def test_vo_gradient_c_entry_rejects_bad_arguments(lib, change):
+    """thc_vo_gradient returns THC_ERR_ARG for each bad argument on the host,
+    before any CUDA call (the device pointers here are never dereferenced)."""
+    assert _vo_call(lib, **change) == 1
