@@ -42,3 +42,26 @@ def test_orbitals_routes_agree():
     finally:
         cells.set_accelerator(None)
     assert np.abs(Ut.numpy() - Ug).max() <= 1e-12 * np.abs(Ug).max()
+
+
+def test_virtual_orbitals_complete_an_orthonormal_set():
+    """orbital_coefficients(cell, nvir): the occupied part spans what
+    occupied_coefficients gives, the occupied and virtual orbitals together
+    are orthonormal in the overlap metric of the generator's quadrature
+    (S^k = (Omega/N_q) sum_r conj(phi_mu(r)) phi_nu(r)), and the virtual ones
+    keep C^{-k} = conj(C^k).  These are the inputs of the orbital gradient."""
+    c = cells.make_cell("C0", mesh=(3, 1, 2))
+    C, Cv = cells.orbital_coefficients(c, 4)
+    C0 = cells.occupied_coefficients(c)
+    P = np.einsum("kmi,kni->kmn", C, C.conj())
+    P0 = np.einsum("kmi,kni->kmn", C0, C0.conj())
+    assert np.abs(P - P0).max() <= 1e-9 * np.abs(P0).max()
+    pts = cells.grid_points(c, c.quad_stride)
+    kf = cells.kmesh_frac(c.mesh)
+    phi = cells.bloch_collocation(c, pts, kf)                      # [k][mu][r]
+    Sk = (c.volume / pts.shape[0]) * np.einsum("kmr,knr->kmn", phi.conj(), phi)
+    Call = np.concatenate([C, Cv], axis=2)
+    G = np.einsum("kma,kmn,knb->kab", Call.conj(), Sk, Call)
+    assert np.abs(G - np.eye(Call.shape[2])[None]).max() <= 1e-9
+    mk = cells.minus_k_index(c.mesh)
+    assert np.abs(Cv[mk] - Cv.conj()).max() <= 1e-12 * np.abs(Cv).max()
